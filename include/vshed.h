@@ -1,0 +1,187 @@
+/*
+ * vshed.h -- C ABI of the GB300 (sm_103a) observer-siting library libvshed.so.
+ *
+ * The library implements the data-parallel hot path of the multiple
+ * transmitter siting process of Franklin, Magalhaes & Li, "Siting thousands of
+ * radio transmitter towers on terrains with billions of points"
+ * (arXiv 2006.16783), Sec. "The multiple transmitter siting process":
+ *   Vix      -> vs_vix          sampled visibility index of every post
+ *   Findmax  -> vs_findmax      per-block top-k candidate transmitters
+ *   Viewshed -> vs_viewshed     ray-sweep viewshed bitmap of every candidate
+ *   Site     -> vs_site         greedy union of viewsheds
+ * plus the learned-proposal and batched entry points that sit beside them.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Terrain: int16 elevations z[y*pitch + x], 0 <= x < W, 0 <= y < H, posts
+ *    one unit apart (Sec. "Terrain visibility": z_ij, i = x, j = y).  The
+ *    pitch is in elements and must be a multiple of 8 (16 bytes) and >= W;
+ *    the base pointer must be 16-byte aligned.  Columns W..pitch-1 are never
+ *    interpreted as terrain.
+ *  - Post index p = y*W + x (int64 in the API).  H*W must be < 2^32.
+ *  - Heights ht (transmitter) and hr (receiver) are integers in the same unit
+ *    as z (Sec. "Definitions"); |ht|, |hr| <= 100000.  The ROI R is a
+ *    horizontal radius in posts, 1 <= R <= 4096 (Sec. "Definitions": ROI).
+ *  - All pointers to arrays are DEVICE pointers unless stated otherwise; the
+ *    caller owns every buffer.  No entry point allocates device memory; calls
+ *    that need scratch take a caller-provided workspace whose size is given by
+ *    the matching *_workspace() query.
+ *  - Every call is asynchronous on the given stream (NULL = legacy default
+ *    stream) and performs no host-device synchronisation unless stated.
+ *  - Return value: VS_OK (0) or a negative VS_ERR_* code.  Argument errors are
+ *    detected on the host before anything is launched; nothing is written then.
+ *  - Bitmaps are uint32 words; bit b of a word that covers global columns
+ *    32*g .. 32*g+31 is column 32*g + b.
+ */
+#ifndef VSHED_H
+#define VSHED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *vs_stream_t; /* identical to cudaStream_t */
+
+enum {
+    VS_OK = 0,
+    VS_ERR_ARG = -1,     /* null pointer, negative size, bad alignment / pitch */
+    VS_ERR_RANGE = -2,   /* a parameter outside its documented range           */
+    VS_ERR_WS = -3,      /* workspace missing or smaller than *_workspace()     */
+    VS_ERR_CUDA = -4,    /* a CUDA runtime call or launch failed                */
+    VS_ERR_TIMEOUT = -5, /* a bounded device wait gave up (reported on device)  */
+    VS_ERR_DEVICE = -6   /* no usable sm_100-family device                      */
+};
+
+/* Read-only view of a device-resident terrain. */
+typedef struct {
+    int32_t H, W;       /* rows, columns (>= 1)                          */
+    int64_t pitch;      /* row pitch in elements, multiple of 8, >= W    */
+    const int16_t *z;   /* device pointer, 16-byte aligned               */
+} vs_grid;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *vs_strerror(int code);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int vs_version(void);
+
+/* ------------------------------------------------------------------------
+ * Vix (Sec. "The multiple transmitter siting process", Vix; LOS as in
+ * Sec. "Definitions" and "Terrain visibility").
+ *
+ * For every post p and sample s < S, the receiver offset is
+ *   u   = SplitMix64 output number p*S+s of a generator seeded with seed
+ *         (state seed + 0x9E3779B97F4A7C15*(p*S+s+1), then the SplitMix64 mix)
+ *   idx = ((u >> 32) * N_R) >> 32
+ *   off = OFF_R[idx], OFF_R = {(dx,dy): dx^2+dy^2 <= R^2} minus (0,0), ordered
+ *         by dy ascending then dx ascending, N_R = |OFF_R|.
+ * The sample counts when the target lies inside the grid and the line of
+ * sight from (x, y, z+ht) to (x+dx, y+dy, z'+hr) clears the terrain linearly
+ * interpolated between the two posts it passes between, with grazing lines
+ * visible.  vix_out[p] (uint8, H*W entries, row-major with pitch W) is the
+ * number of counted samples, 0..S.
+ *
+ * Errors: VS_ERR_ARG (null pointers, pitch), VS_ERR_RANGE (R, S outside
+ * 1..4096 / 0..255, heights), VS_ERR_CUDA.
+ * ---------------------------------------------------------------------- */
+int vs_vix(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
+           uint8_t *vix_out, vs_stream_t st);
+
+/* vs_vix plus work accounting: *los_steps (device uint64, accumulated, not
+ * cleared) grows by the number of LOS crossings evaluated -- j = 1..D-1 for a
+ * visible sample, j = 1..j_block for a blocked one (the test ends at the first
+ * crossing above the line).  Output identical to vs_vix. */
+int vs_vix_count(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
+                 uint8_t *vix_out, uint64_t *los_steps, vs_stream_t st);
+
+/* ------------------------------------------------------------------------
+ * Findmax (Sec. "The multiple transmitter siting process", Findmax).
+ *
+ * The grid is cut into blocks of block x block posts (edge blocks may be
+ * partial).  From every block the k posts with the largest value are kept,
+ * ties going to the lower post index.  cand_out receives the post indices
+ * ordered by block (row-major over blocks), then by rank; a block with fewer
+ * than k posts contributes all of them.
+ *
+ * vs_findmax_count() returns the number of candidates that a call produces
+ * (computed on the host), or a negative error code.  cap is the capacity of
+ * cand_out in entries and must be >= that count (else VS_ERR_RANGE).
+ *
+ * vs_findmax:     vix is uint8 H x W (pitch W), as written by vs_vix.
+ * vs_findmax_f32: score is float on a proposal lattice of the given stride:
+ *                 score[i*Ws + j] belongs to post (j*stride, i*stride),
+ *                 Ws = ceil(W/stride), Hs = ceil(H/stride).  Floats are
+ *                 ordered by their IEEE-754 total order.
+ * ---------------------------------------------------------------------- */
+int64_t vs_findmax_count(int32_t H, int32_t W, int32_t stride, int32_t block, int32_t k);
+int vs_findmax(const uint8_t *vix, int32_t H, int32_t W, int32_t block, int32_t k,
+               int64_t *cand_out, int64_t cap, vs_stream_t st);
+int vs_findmax_f32(const float *score, int32_t H, int32_t W, int32_t stride, int32_t block,
+                   int32_t k, int64_t *cand_out, int64_t cap, vs_stream_t st);
+
+/* ------------------------------------------------------------------------
+ * Viewshed (Sec. "The multiple transmitter siting process", Viewshed; the
+ * bitmap packing of the same paragraph, here in 32-bit words).
+ *
+ * For each candidate post, rays run from the observer (eye z+ht) to the 8R
+ * cells of the square ring max(|dx|,|dy|) = R.  A ray to ring cell (ex,ey)
+ * with major axis x when |ex| >= |ey| visits at step k = 1..R the cell
+ * (major k, minor round(k*dmin/R)), ties rounded away from zero, and stops
+ * when that cell leaves the grid or the disc k^2+minor^2 > R^2.  The cell is
+ * visible on the ray when no horizon exists yet or its elevation angle
+ * (z+hr-eye)/k is >= the horizon's; then the terrain where the ray crosses
+ * the line major = k (linear interpolation between the straddling posts) is
+ * offered as the new horizon, and the ray stops when one of those posts lies
+ * outside the grid.  A cell's bit is the OR over the rays that visit it; the
+ * observer's own cell is always set.  All comparisons are exact integer
+ * cross-products.
+ *
+ * Output layout, per candidate c: bm_out[c*vs_bitmap_words(R) + r*P_R + w],
+ * P_R = floor(2R/32)+2 words per row, rows r = 0..2R are global rows
+ * cy-R+r, word w covers global columns 32*(floor((cx-R)/32)+w) .. +31.  Bits
+ * outside the grid or the disc are 0.  area_out[c] = popcount of the bitmap;
+ * a candidate index outside [0, H*W) yields an all-zero bitmap and area -1.
+ *
+ * ws / ws_bytes: workspace of at least vs_viewshed_workspace(R, n) bytes
+ * (may be NULL when that is 0).
+ * ---------------------------------------------------------------------- */
+int64_t vs_bitmap_words(int32_t R); /* (2R+1) * (floor(2R/32)+2) */
+size_t vs_viewshed_workspace(int32_t R, int64_t n);
+int vs_viewshed(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand, int64_t n,
+                uint32_t *bm_out, int32_t *area_out, void *ws, size_t ws_bytes, vs_stream_t st);
+
+/* ------------------------------------------------------------------------
+ * Site (Sec. "The multiple transmitter siting process", Site).
+ *
+ * Greedy: starting from the cumulative viewshed held in cum (uint32
+ * H x ceil(W/32), same bit convention; all zero for a fresh run), each step
+ * picks the candidate with the largest gain popcount(V_c AND NOT cum), ties to
+ * the lowest post index, appends its post index to chosen[] and its gain to
+ * gains[], and ORs V_c into cum.  It stops after n_obs observers, when the
+ * best gain is 0, or -- when coverage_target > 0 -- as soon as
+ * popcount(cum) >= ceil(coverage_target * H * W) before a step.
+ * *n_chosen (device int32) receives the number chosen.  Calling again with the
+ * returned cum continues the same greedy sequence (checkpoint / resume).
+ *
+ * bm, cand, n, R describe the candidates exactly as vs_viewshed wrote them.
+ * chosen and gains have room for n_obs int64 entries.  Requires W, H <= 65535.
+ * ws / ws_bytes: workspace of at least vs_site_workspace(n, R) bytes.
+ * ---------------------------------------------------------------------- */
+size_t vs_site_workspace(int64_t n, int32_t R);
+int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W, int32_t R,
+            int32_t n_obs, double coverage_target, int64_t *chosen, int64_t *gains,
+            uint32_t *cum, int32_t *n_chosen, void *ws, size_t ws_bytes, vs_stream_t st);
+
+/* Dense gain pass (the first step of vs_site, exposed on its own): for every
+ * candidate c, gains_out[c] = popcount(V_c AND NOT cum).  One streaming pass
+ * over all n bitmaps. */
+int vs_site_gains(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W,
+                  int32_t R, const uint32_t *cum, uint32_t *gains_out, vs_stream_t st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VSHED_H */

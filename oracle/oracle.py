@@ -46,6 +46,7 @@ def _load():
         "or_splitmix64_nth": (u64, [u64, u64]),
         "or_los": (ctypes.c_int, [P, i32, i32, i64, i32, i32, i32, i32, i32, i32]),
         "or_vix": (ctypes.c_int, [P, i32, i32, i64, i32, i32, i32, i32, u64, P, i32]),
+        "or_vix_posts": (ctypes.c_int, [P, i32, i32, i64, i32, i32, i32, i32, u64, P, i64, P]),
         "or_findmax": (i64, [P, i32, i32, i32, i32, P, i64]),
         "or_findmax_f32": (i64, [P, i32, i32, i32, i32, i32, P, i64]),
         "or_bitmap_words": (i64, [i32]),
@@ -123,6 +124,21 @@ def vix(z, R, ht, hr, S, seed, threads=1):
     rc = _load().or_vix(_p(z), H, W, pitch, R, ht, hr, S, seed & (2**64 - 1), _p(out), threads)
     if rc != 0:
         raise ValueError("or_vix: bad arguments")
+    return out
+
+
+def vix_posts(z, R, ht, hr, S, seed, posts, W=None):
+    """Vix counts of the listed posts only.  ``z`` may be pitched: pass the
+    logical width W when z has padding columns."""
+    z = np.ascontiguousarray(z, dtype=np.int16)
+    H, pitch = z.shape
+    W = pitch if W is None else W
+    posts = np.ascontiguousarray(posts, dtype=np.int64)
+    out = np.zeros(posts.shape[0], np.uint8)
+    rc = _load().or_vix_posts(_p(z), H, W, pitch, R, ht, hr, S, seed & (2**64 - 1), _p(posts),
+                              posts.shape[0], _p(out))
+    if rc != 0:
+        raise ValueError("or_vix_posts: bad arguments")
     return out
 
 

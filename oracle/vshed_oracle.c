@@ -206,6 +206,32 @@ int or_vix(const int16_t *z, int32_t H, int32_t W, int64_t pitch,
     return 0;
 }
 
+/* Vix counts of a list of posts only (same definition as or_vix; for
+ * spot checks of grids too large for the full oracle). */
+int or_vix_posts(const int16_t *z, int32_t H, int32_t W, int64_t pitch,
+                 int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
+                 const int64_t *posts, int64_t n, uint8_t *out)
+{
+    if (H < 0 || W < 0 || R < 1 || S < 0 || S > 255 || pitch < W) return -1;
+    int64_t NR = or_offsets(R, NULL, NULL);
+    int32_t *odx = (int32_t *)malloc(sizeof(int32_t) * (size_t)NR);
+    int32_t *ody = (int32_t *)malloc(sizeof(int32_t) * (size_t)NR);
+    or_offsets(R, odx, ody);
+    for (int64_t i = 0; i < n; i++) {
+        int64_t p = posts[i];
+        int32_t x = (int32_t)(p % W), y = (int32_t)(p / W);
+        int cnt = 0;
+        for (int32_t s = 0; s < S; s++) {
+            uint64_t u = or_splitmix64_nth(seed, (uint64_t)p * (uint64_t)S + (uint64_t)s);
+            uint64_t idx = ((u >> 32) * (uint64_t)NR) >> 32;
+            cnt += or_los(z, H, W, pitch, x, y, x + odx[idx], y + ody[idx], ht, hr);
+        }
+        out[i] = (uint8_t)cnt;
+    }
+    free(odx); free(ody);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Findmax stage (Sec. "The multiple transmitter siting process",      */
 /* Findmax): partition the terrain into b x b blocks (edge blocks may   */

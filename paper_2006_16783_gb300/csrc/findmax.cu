@@ -1,0 +1,136 @@
+// findmax.cu -- Findmax stage (Sec. "The multiple transmitter siting
+// process", Findmax): top-k posts of every block, ties to the lower index.
+//
+// One CTA per block.  Each post becomes a 64-bit key (value << 32 | ~p), so
+// "larger key" is exactly "larger value, then lower post index" and keys are
+// unique.  Round r takes the block-wide maximum over keys below the key
+// chosen in round r-1; the first round streams the block from HBM and later
+// rounds hit L2.  The CTA's output position is the sum of
+// min(k, block size) over the blocks before it, computed in parallel.
+#include <algorithm>
+
+#include "vs_common.cuh"
+
+namespace vs {
+
+constexpr int kFmThreads = 256;
+
+__device__ __forceinline__ uint32_t value_key(uint8_t v) { return v; }
+__device__ __forceinline__ uint32_t value_key(float v) {
+    const uint32_t u = __float_as_uint(v);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ long long llmin(long long a, long long b) { return a < b ? a : b; }
+
+__device__ __forceinline__ long long lattice_count(long long lo, long long hi, long long s) {
+    if (hi <= lo) return 0;
+    return (hi + s - 1) / s - (lo + s - 1) / s;
+}
+
+__device__ __forceinline__ uint64_t block_max_u64(uint64_t v, uint64_t *red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    v = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kFmThreads) k_findmax(const V *val, int H, int W, int stride,
+                                                        int Ws, int b, int k, int nbx,
+                                                        int64_t *out) {
+    __shared__ uint64_t red[32];
+    __shared__ long long s_off;
+    const int by = blockIdx.x / nbx, bx = blockIdx.x - (blockIdx.x / nbx) * nbx;
+    const long long i0 = ((long long)by * b + stride - 1) / stride;
+    const long long i1 = llmin(((long long)(by + 1) * b + stride - 1) / stride,
+                                             (H + stride - 1) / stride);
+    const long long j0 = ((long long)bx * b + stride - 1) / stride;
+    const long long j1 = llmin(((long long)(bx + 1) * b + stride - 1) / stride, Ws);
+    const long long m = (i1 - i0) * (j1 - j0);
+
+    // output offset: sum of min(k, size) over the blocks before this one
+    {
+        long long acc = 0;
+        for (int q = threadIdx.x; q < (int)blockIdx.x; q += blockDim.x) {
+            const int qy = q / nbx, qx = q - (q / nbx) * nbx;
+            const long long ny = lattice_count((long long)qy * b, llmin(H, (long long)(qy + 1) * b), stride);
+            const long long nx = lattice_count((long long)qx * b, llmin(W, (long long)(qx + 1) * b), stride);
+            acc += llmin(k, ny * nx);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (uint64_t)acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (long long)red[w];
+            s_off = t;
+        }
+        __syncthreads();
+    }
+    const long long off = s_off;
+
+    uint64_t bound = ~0ull;
+    const int rounds = (int)llmin(k, m);
+    for (int r = 0; r < rounds; ++r) {
+        uint64_t best = 0;
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (long long i = i0 + (threadIdx.x >> 5); i < i1; i += nw) {
+            const V *row = val + i * Ws;
+            const uint32_t prow = (uint32_t)(i * stride * (long long)W);
+            for (int j = (int)j0 + lane; j < (int)j1; j += 32) {
+                const uint32_t p = prow + (uint32_t)(j * stride);
+                const uint64_t key = ((uint64_t)value_key(row[j]) << 32) | (uint64_t)(0xFFFFFFFFu - p);
+                if (key < bound && key > best) best = key;
+            }
+        }
+        best = block_max_u64(best, red);
+        if (threadIdx.x == 0) out[off + r] = (int64_t)(0xFFFFFFFFu - (uint32_t)(best & 0xFFFFFFFFu));
+        bound = best;
+    }
+}
+
+}  // namespace vs
+
+using namespace vs;
+
+template <typename V>
+static int findmax_launch(const V *val, int32_t H, int32_t W, int32_t stride, int32_t block,
+                          int32_t k, int64_t *cand_out, int64_t cap, vs_stream_t st) {
+    if (!val || !cand_out) return VS_ERR_ARG;
+    if (H < 1 || W < 1 || stride < 1 || block < 1 || k < 1) return VS_ERR_RANGE;
+    if ((long long)H * W >= (1ll << 32) - 1) return VS_ERR_RANGE;
+    const int64_t need = vs_findmax_count(H, W, stride, block, k);
+    if (need < 0) return (int)need;
+    if (cap < need) return VS_ERR_RANGE;
+    const long long nby = (H + (long long)block - 1) / block, nbx = (W + (long long)block - 1) / block;
+    if (nby * nbx > 0x7fffffffll) return VS_ERR_RANGE;
+    int rc = check_device();
+    if (rc) return rc;
+    const int Ws = (W + stride - 1) / stride;
+    k_findmax<V><<<(unsigned)(nby * nbx), kFmThreads, 0, (cudaStream_t)st>>>(
+        val, H, W, stride, Ws, block, k, (int)nbx, cand_out);
+    VS_CUDA_TRY(cudaGetLastError());
+    return VS_OK;
+}
+
+extern "C" int vs_findmax(const uint8_t *vix, int32_t H, int32_t W, int32_t block, int32_t k,
+                          int64_t *cand_out, int64_t cap, vs_stream_t st) {
+    return findmax_launch<uint8_t>(vix, H, W, 1, block, k, cand_out, cap, st);
+}
+
+extern "C" int vs_findmax_f32(const float *score, int32_t H, int32_t W, int32_t stride,
+                              int32_t block, int32_t k, int64_t *cand_out, int64_t cap,
+                              vs_stream_t st) {
+    return findmax_launch<float>(score, H, W, stride, block, k, cand_out, cap, st);
+}

@@ -1,0 +1,113 @@
+// vs_api.cu -- host-side helpers of the C ABI: error strings, argument
+// checks, the TMA tensor-map builder and the size queries.
+#include <algorithm>
+#include <mutex>
+#include <string.h>
+
+#include "vs_common.cuh"
+
+namespace vs {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+int make_grid_map(GridMap *gm, const vs_grid &g, int wg, int rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return VS_ERR_CUDA;
+    if (wg < 1 || wg > 256 || rows < 1 || rows > 256) return VS_ERR_RANGE;
+    cuuint64_t dims[3] = {8, (cuuint64_t)(g.pitch / 8), (cuuint64_t)g.H};
+    cuuint64_t strides[2] = {16, (cuuint64_t)g.pitch * 2};
+    cuuint32_t box[3] = {8, (cuuint32_t)wg, (cuuint32_t)rows};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(&gm->map, CU_TENSOR_MAP_DATA_TYPE_UINT16 /* bit copy of int16 */, 3, (void *)g.z, dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? VS_OK : VS_ERR_CUDA;
+}
+
+int check_grid(const vs_grid &g) {
+    if (!g.z) return VS_ERR_ARG;
+    if (g.H < 1 || g.W < 1 || g.H > kMaxH || g.W > kMaxH) return VS_ERR_RANGE;
+    if ((long long)g.H * g.W >= (1ll << 32) - 1) return VS_ERR_RANGE;
+    if (g.pitch < g.W || (g.pitch % 8) != 0) return VS_ERR_ARG;
+    if (((uintptr_t)g.z & 15) != 0) return VS_ERR_ARG;
+    return VS_OK;
+}
+
+int check_device() {
+    static int ok_dev[64];  // 0 unknown, 1 ok, -1 bad
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return VS_ERR_DEVICE;
+    if (dev < 0 || dev >= 64) return VS_ERR_DEVICE;
+    if (ok_dev[dev] == 0) {
+        int major = 0, minor = 0;
+        if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+            return VS_ERR_DEVICE;
+        ok_dev[dev] = (major == 10 && minor == 3) ? 1 : -1;
+    }
+    return ok_dev[dev] == 1 ? VS_OK : VS_ERR_DEVICE;
+}
+
+}  // namespace vs
+
+extern "C" {
+
+const char *vs_strerror(int code) {
+    switch (code) {
+        case VS_OK: return "ok";
+        case VS_ERR_ARG: return "invalid argument (null pointer, size, alignment or pitch)";
+        case VS_ERR_RANGE: return "parameter outside its supported range";
+        case VS_ERR_WS: return "workspace missing or too small";
+        case VS_ERR_CUDA: return "CUDA runtime error";
+        case VS_ERR_TIMEOUT: return "bounded device wait timed out";
+        case VS_ERR_DEVICE: return "no usable sm_103 device";
+        default: return "unknown status";
+    }
+}
+
+int vs_version(void) { return 100; }
+
+int64_t vs_bitmap_words(int32_t R) {
+    if (R < 1 || R > vs::kMaxR) return VS_ERR_RANGE;
+    return (int64_t)(2 * R + 1) * vs::words_per_row(R);
+}
+
+// number of lattice points i >= 0 with lo <= i*stride < hi
+static inline int64_t lattice_count(int64_t lo, int64_t hi, int64_t stride) {
+    if (hi <= lo) return 0;
+    int64_t a = (lo + stride - 1) / stride, b = (hi + stride - 1) / stride;
+    return b - a;
+}
+
+int64_t vs_findmax_count(int32_t H, int32_t W, int32_t stride, int32_t block, int32_t k) {
+    if (H < 1 || W < 1 || stride < 1 || block < 1 || k < 1) return VS_ERR_RANGE;
+    int64_t nby = (H + (int64_t)block - 1) / block, nbx = (W + (int64_t)block - 1) / block;
+    int64_t total = 0;
+    for (int64_t by = 0; by < nby; ++by) {
+        int64_t ny = lattice_count(by * block, std::min<int64_t>(H, (by + 1) * block), stride);
+        for (int64_t bx = 0; bx < nbx; ++bx) {
+            int64_t nx = lattice_count(bx * block, std::min<int64_t>(W, (bx + 1) * block), stride);
+            total += std::min<int64_t>(k, ny * nx);
+        }
+    }
+    return total;
+}
+
+}  // extern "C"

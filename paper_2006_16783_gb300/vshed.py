@@ -1,0 +1,223 @@
+"""Python binding of libvshed.so (ctypes over the C ABI in include/vshed.h).
+
+Argument marshalling only: every step of the siting path runs in the CUDA
+kernels of the library.  Tensors must be CUDA tensors on the current device;
+the calls are enqueued on torch's current stream.  There is no CPU fallback:
+if the library is missing or a call fails, an exception is raised.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvshed.so")
+_lib = None
+
+VS_OK, VS_ERR_ARG, VS_ERR_RANGE, VS_ERR_WS, VS_ERR_CUDA, VS_ERR_TIMEOUT, VS_ERR_DEVICE = 0, -1, -2, -3, -4, -5, -6
+
+
+class VsError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__("%s failed: %s (%d)" % (fn, lib().vs_strerror(code).decode(), code))
+        self.code = code
+
+
+class vs_grid(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("pitch", ctypes.c_int64),
+                ("z", ctypes.c_void_p)]
+
+
+# name -> (restype, argtypes); the exported symbols of include/vshed.h
+P, i32, i64, u64, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                             ctypes.c_double, ctypes.c_size_t)
+SIGNATURES = {
+    "vs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "vs_version": (ctypes.c_int, []),
+    "vs_vix": (ctypes.c_int, [vs_grid, i32, i32, i32, i32, u64, P, P]),
+    "vs_vix_count": (ctypes.c_int, [vs_grid, i32, i32, i32, i32, u64, P, P, P]),
+    "vs_findmax_count": (i64, [i32, i32, i32, i32, i32]),
+    "vs_findmax": (ctypes.c_int, [P, i32, i32, i32, i32, P, i64, P]),
+    "vs_findmax_f32": (ctypes.c_int, [P, i32, i32, i32, i32, i32, P, i64, P]),
+    "vs_bitmap_words": (i64, [i32]),
+    "vs_viewshed_workspace": (sz, [i32, i64]),
+    "vs_viewshed": (ctypes.c_int, [vs_grid, i32, i32, i32, P, i64, P, P, P, sz, P]),
+    "vs_site_workspace": (sz, [i64, i32]),
+    "vs_site": (ctypes.c_int, [P, P, i64, i32, i32, i32, i32, f64, P, P, P, P, P, sz, P]),
+    "vs_site_gains": (ctypes.c_int, [P, P, i64, i32, i32, i32, P, P, P]),
+}
+
+
+def lib():
+    """Load libvshed.so (built by ``__graft_entry__.build()`` or
+    ``python -m paper_2006_16783_gb300._build``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libvshed.so not found at %s: build it first "
+                              "(python -c 'import __graft_entry__ as g; g.build()')" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(fn, rc):
+    if rc != VS_OK:
+        raise VsError(fn, rc)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("libvshed works on CUDA tensors only (got a %s tensor)" % t.device)
+
+
+# ------------------------------------------------------------------ terrain
+class Grid:
+    """A device-resident int16 terrain: ``storage`` is an (H, pitch) int16
+    CUDA tensor whose first W columns are the terrain (pitch % 8 == 0)."""
+
+    def __init__(self, storage, W=None):
+        _need_cuda(storage)
+        assert storage.dtype == torch.int16 and storage.dim() == 2 and storage.is_contiguous()
+        self.storage = storage
+        self.H = storage.shape[0]
+        self.pitch = storage.shape[1]
+        self.W = self.pitch if W is None else int(W)
+
+    @classmethod
+    def from_tensor(cls, z, device="cuda"):
+        """Copy an (H, W) int16 tensor into pitched device storage."""
+        H, W = z.shape
+        pitch = (W + 7) // 8 * 8
+        st = torch.zeros((H, pitch), dtype=torch.int16, device=device)
+        st[:, :W] = z.to(device)
+        return cls(st, W)
+
+    def c(self):
+        return vs_grid(self.H, self.W, self.pitch, self.storage.data_ptr())
+
+
+# ------------------------------------------------------------------ stages
+def vix(g, R, ht, hr, S, seed, out=None):
+    """Sampled visibility-index counts (uint8, H x W)."""
+    if out is None:
+        out = torch.empty((g.H, g.W), dtype=torch.uint8, device=g.storage.device)
+    _need_cuda(out)
+    _check("vs_vix", lib().vs_vix(g.c(), R, ht, hr, S, ctypes.c_uint64(seed & (2**64 - 1)), _ptr(out), _stream()))
+    return out
+
+
+def vix_count(g, R, ht, hr, S, seed, steps, out=None):
+    """vs_vix that also adds the number of LOS crossings it evaluated to the
+    device uint64 counter ``steps`` (an int64 CUDA tensor of one element)."""
+    if out is None:
+        out = torch.empty((g.H, g.W), dtype=torch.uint8, device=g.storage.device)
+    _need_cuda(out, steps)
+    _check("vs_vix_count", lib().vs_vix_count(g.c(), R, ht, hr, S, ctypes.c_uint64(seed & (2**64 - 1)),
+                                              _ptr(out), _ptr(steps), _stream()))
+    return out
+
+
+def findmax_count(H, W, stride, block, k):
+    n = lib().vs_findmax_count(H, W, stride, block, k)
+    if n < 0:
+        raise VsError("vs_findmax_count", n)
+    return n
+
+
+def findmax(v, block, k, out=None):
+    """Top-k posts per block of a uint8 H x W map -> int64 post indices."""
+    _need_cuda(v)
+    H, W = v.shape
+    n = findmax_count(H, W, 1, block, k)
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device=v.device)
+    _check("vs_findmax", lib().vs_findmax(_ptr(v), H, W, block, k, _ptr(out), out.numel(), _stream()))
+    return out[:n]
+
+
+def findmax_f32(score, H, W, stride, block, k, out=None):
+    """Top-k posts per block of a float score lattice of the given stride."""
+    _need_cuda(score)
+    assert score.dtype == torch.float32 and score.is_contiguous()
+    n = findmax_count(H, W, stride, block, k)
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device=score.device)
+    _check("vs_findmax_f32", lib().vs_findmax_f32(_ptr(score), H, W, stride, block, k, _ptr(out),
+                                                  out.numel(), _stream()))
+    return out[:n]
+
+
+def bitmap_words(R):
+    return lib().vs_bitmap_words(R)
+
+
+def words_per_row(R):
+    return (2 * R) // 32 + 2
+
+
+def viewshed(g, R, ht, hr, cand, bm=None, area=None):
+    """Viewshed bitmaps uint32 [n, 2R+1, P_R] and areas int32 [n]."""
+    _need_cuda(cand)
+    cand = cand.contiguous()
+    n = cand.numel()
+    if bm is None:
+        bm = torch.empty((n, 2 * R + 1, words_per_row(R)), dtype=torch.int32, device=cand.device)
+    if area is None:
+        area = torch.empty(n, dtype=torch.int32, device=cand.device)
+    wsb = lib().vs_viewshed_workspace(R, n)
+    ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=cand.device) if wsb else None
+    _check("vs_viewshed", lib().vs_viewshed(g.c(), R, ht, hr, _ptr(cand), n, _ptr(bm), _ptr(area),
+                                            _ptr(ws), wsb, _stream()))
+    return bm, area
+
+
+def site_workspace(n, R):
+    return lib().vs_site_workspace(n, R)
+
+
+def site(bm, cand, H, W, R, n_obs, target=0.0, cum=None, ws=None, sync=True):
+    """Greedy siting.  Returns (chosen int64, gains int64, cum int32 [H, ceil(W/32)],
+    n_chosen); with sync=True the lists are cut to n_chosen (a host sync)."""
+    _need_cuda(bm, cand)
+    dev = cand.device
+    n = cand.numel()
+    if cum is None:
+        cum = torch.zeros((H, (W + 31) // 32), dtype=torch.int32, device=dev)
+    chosen = torch.empty(max(n_obs, 1), dtype=torch.int64, device=dev)
+    gains = torch.empty(max(n_obs, 1), dtype=torch.int64, device=dev)
+    nch = torch.zeros(1, dtype=torch.int32, device=dev)
+    wsb = site_workspace(n, R)
+    if ws is None or ws.numel() < wsb:
+        ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
+    _check("vs_site", lib().vs_site(_ptr(bm), _ptr(cand.contiguous()), n, H, W, R, n_obs, float(target),
+                                    _ptr(chosen), _ptr(gains), _ptr(cum), _ptr(nch), _ptr(ws), wsb,
+                                    _stream()))
+    if sync:
+        t = int(nch.item())
+        return chosen[:t], gains[:t], cum, t
+    return chosen, gains, cum, nch
+
+
+def site_gains(bm, cand, H, W, R, cum, out=None):
+    """Dense gain pass: popcount(V_c AND NOT cum) for every candidate (uint32 as int32)."""
+    _need_cuda(bm, cand, cum)
+    n = cand.numel()
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=cand.device)
+    _check("vs_site_gains", lib().vs_site_gains(_ptr(bm), _ptr(cand), n, H, W, R, _ptr(cum), _ptr(out),
+                                                _stream()))
+    return out

@@ -1,0 +1,89 @@
+"""The five synthetic workloads, each shaped like a run of the paper
+(Sec. "Testing": DEM1000, US East, US West) with seeded fBm terrain standing in
+for the unavailable datasets.  Parameters only -- no siting arithmetic.
+
+    small   1000^2 spectral fBm (Hurst 0.8, 0..1000 m), R=50, h=10, S=10,
+            top-1 per 25x25 block (1600 candidates), 100 observers
+    scale   16384^2 spectral fBm (Hurst 0.75, 0..3000 m, lowest 10% flattened
+            to 0), R=200, h=10, S=20, top-2 per 256x256 block (8192
+            candidates), 2048 observers
+    batch   64 instances: side U{512..4096}, Hurst 0.8, 0..1000*U{1..3} m,
+            R in {50,100,150,250}, h in U{5..30}, n_obs in U{16..512}, S=10,
+            block ceil(R/2), k=1
+    learn   eight 4096^2 training terrains (seeds 3000..3007), a held-out
+            16384^2 terrain (seed 3100), labels = exact vix at R=100
+    full    46400^2 ridged multifractal (0..4000 m, lowest 5% flattened),
+            R=100, h=10, S=10, top-4 per 464x464 block (40000 candidates),
+            4096 observers
+"""
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import terrain
+
+
+@dataclass
+class Workload:
+    name: str
+    H: int
+    W: int
+    R: int
+    ht: int
+    hr: int
+    S: int
+    block: int
+    k: int
+    n_obs: int
+    seed: int
+    kind: str = "fbm"          # "fbm" or "ridged"
+    hurst: float = 0.8
+    zmax: int = 1000
+    lake_frac: float = 0.0
+    vix_seed: int = 0x5EED
+    extra: dict = field(default_factory=dict)
+
+    def make_terrain(self, device="cpu"):
+        """int16 (H, W) tensor on ``device``."""
+        if self.kind == "ridged":
+            return terrain.ridged_multifractal(self.H, self.W, self.seed, 0, self.zmax, self.lake_frac,
+                                               device=device, **self.extra)
+        return terrain.spectral_fbm(self.H, self.W, self.hurst, self.seed, 0, self.zmax,
+                                    self.lake_frac, device=device)
+
+    def n_candidates(self):
+        nby, nbx = math.ceil(self.H / self.block), math.ceil(self.W / self.block)
+        return nby * nbx * self.k  # exact when every block holds >= k posts
+
+
+SMALL = Workload("small_1000sq_R50", 1000, 1000, 50, 10, 10, 10, 25, 1, 100, seed=1000,
+                 hurst=0.8, zmax=1000)
+SCALE = Workload("scale_16384sq_R200", 16384, 16384, 200, 10, 10, 20, 256, 2, 2048, seed=1001,
+                 hurst=0.75, zmax=3000, lake_frac=0.10)
+FULL = Workload("full_46400sq_R100", 46400, 46400, 100, 10, 10, 10, 464, 4, 4096, seed=1004,
+                kind="ridged", zmax=4000, lake_frac=0.05, extra={"octaves": 12})
+
+
+def batch_instances(seed=1002, count=64, max_side=4096):
+    """The batched workload's 64 instances (parameters drawn from ``seed``)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        side = int(rng.integers(512, max_side + 1))
+        R = int(rng.choice([50, 100, 150, 250]))
+        h = int(rng.integers(5, 31))
+        out.append(Workload("batch_%02d" % i, side, side, R, h, h, 10, (R + 1) // 2, 1,
+                            int(rng.integers(16, 513)), seed=seed * 1000 + i, hurst=0.8,
+                            zmax=1000 * int(rng.integers(1, 4))))
+    return out
+
+
+def scaled(w, H, W, name=None, **kw):
+    """The same recipe at another size (used for parity cases the oracle can
+    finish in seconds)."""
+    d = dict(w.__dict__)
+    d.update(kw)
+    d["H"], d["W"] = H, W
+    d["name"] = name or ("%s_at_%dx%d" % (w.name, H, W))
+    return Workload(**d)

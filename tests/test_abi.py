@@ -1,0 +1,87 @@
+"""The C-ABI library: it loads without a GPU, exports every symbol that
+include/vshed.h declares, and its host-side argument checks and size queries
+answer without touching a device.  CPU only (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2006_16783_gb300 import _build
+    _build.build()
+    from paper_2006_16783_gb300 import vshed
+    return vshed.lib()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(vs_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_exported(L):
+    names = _declared()
+    assert {"vs_vix", "vs_findmax", "vs_viewshed", "vs_site"} <= names
+    for n in sorted(names):
+        assert hasattr(L, n), n
+
+
+def test_binding_covers_header():
+    from paper_2006_16783_gb300 import vshed
+    assert _declared() <= set(vshed.SIGNATURES)
+
+
+def test_size_queries(L):
+    from oracle import oracle as O
+    for R in (1, 2, 7, 50, 100, 200, 250, 1000):
+        assert L.vs_bitmap_words(R) == O.bitmap_words(R)
+    assert L.vs_bitmap_words(0) < 0
+    # Findmax counts: DEM1000's 100 x 100 blocks of 20 (Table t:1000) and the
+    # workloads' 1600 / 8192 / 40000 candidates
+    assert L.vs_findmax_count(1000, 1000, 1, 10, 20) == 200000
+    assert L.vs_findmax_count(1000, 1000, 1, 25, 1) == 1600
+    assert L.vs_findmax_count(16384, 16384, 1, 256, 2) == 8192
+    assert L.vs_findmax_count(46400, 46400, 1, 464, 4) == 40000
+    # a partial edge block with fewer posts than k contributes all of them
+    # 5 x 7 posts in 3 x 3 blocks hold 9, 9, 3 / 6, 6, 2 posts
+    assert L.vs_findmax_count(5, 7, 1, 3, 5) == 5 + 5 + 3 + 5 + 5 + 2
+    # stride-4 lattice {0,4,8}^2 in 8 x 8 blocks: 4, 2 / 2, 1 lattice posts
+    assert L.vs_findmax_count(10, 10, 4, 8, 2) == 2 + 2 + 2 + 1
+    assert L.vs_site_workspace(40000, 100) >= 40000 * 4
+
+
+def test_argument_errors_need_no_device(L):
+    from paper_2006_16783_gb300 import vshed
+    g = vshed.vs_grid(10, 10, 16, 0)       # null terrain
+    assert L.vs_vix(g, 5, 1, 1, 10, 1, None, None) == vshed.VS_ERR_ARG
+    g = vshed.vs_grid(10, 10, 12, 4096)    # pitch not a multiple of 8
+    assert L.vs_vix(g, 5, 1, 1, 10, 1, ctypes.c_void_p(4096), None) == vshed.VS_ERR_ARG
+    g = vshed.vs_grid(10, 10, 16, 4096)
+    assert L.vs_vix(g, 0, 1, 1, 10, 1, ctypes.c_void_p(4096), None) == vshed.VS_ERR_RANGE
+    assert L.vs_vix(g, 5, 1, 1, 256, 1, ctypes.c_void_p(4096), None) == vshed.VS_ERR_RANGE
+    assert L.vs_viewshed(g, 5, 1, 1, None, 3, None, None, None, 0, None) == vshed.VS_ERR_ARG
+    assert L.vs_findmax(None, 10, 10, 2, 1, None, 0, None) == vshed.VS_ERR_ARG
+    assert L.vs_site(None, ctypes.c_void_p(8), 1, 10, 10, 2, 1, 0.0, ctypes.c_void_p(8),
+                     ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8), None, 0,
+                     None) == vshed.VS_ERR_ARG
+    assert L.vs_site(ctypes.c_void_p(8), ctypes.c_void_p(8), 1, 10, 10, 2, 1, 0.0, ctypes.c_void_p(8),
+                     ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8), None, 0,
+                     None) == vshed.VS_ERR_WS
+    assert L.vs_strerror(-3) == b"workspace missing or too small"
+
+
+def test_binding_refuses_cpu_tensors():
+    import torch
+    import paper_2006_16783_gb300 as V
+    with pytest.raises(ValueError):
+        V.findmax(torch.zeros((4, 4), dtype=torch.uint8), 2, 1)
