@@ -321,7 +321,7 @@ extern "C" int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32
                        int64_t *gains, uint32_t *cum, int32_t *n_chosen, void *ws,
                        size_t ws_bytes, vs_stream_t st) {
     if (n < 0 || n_obs < 0) return VS_ERR_RANGE;
-    if (!cand || !cum || !n_chosen || (n > 0 && !bm) || (n_obs > 0 && (!chosen || !gains)))
+    if (!cum || !n_chosen || (n > 0 && (!bm || !cand)) || (n_obs > 0 && (!chosen || !gains)))
         return VS_ERR_ARG;
     if (H < 1 || W < 1 || H > 65535 || W > 65535 || R < 1 || R > kMaxR) return VS_ERR_RANGE;
     if (ws_bytes < vs_site_workspace(n, R) || !ws) return VS_ERR_WS;

@@ -64,17 +64,25 @@ def _rescale_to_int16(f, zmin, zmax):
     lo = f.min()
     hi = f.max()
     scale = (zmax - zmin) / torch.clamp(hi - lo, min=1e-30)
-    out = torch.round((f - lo) * scale + zmin)
-    return torch.clamp(out, zmin, zmax).to(torch.int16)
+    out = torch.empty(f.shape, dtype=torch.int16, device=f.device)
+    rows = max(1, (1 << 27) // max(1, f.shape[-1]))
+    for r0 in range(0, f.shape[0], rows):
+        v = torch.round((f[r0:r0 + rows] - lo) * scale + zmin)
+        out[r0:r0 + rows] = torch.clamp(v, zmin, zmax).to(torch.int16)
+    return out
 
 
 def _lakes(z, frac, zfloor):
     """Flatten every post at or below the frac-quantile of elevations to zfloor."""
     if frac <= 0:
         return z
-    zi = z.to(torch.int32) - int(zfloor)
-    nb = int(zi.max().item()) + 1
-    hist = torch.bincount(zi.reshape(-1), minlength=nb).to(torch.int64)
+    nb = int(z.max().item()) - int(zfloor) + 1
+    hist = torch.zeros(nb, dtype=torch.int64, device=z.device)
+    flat = z.reshape(-1)
+    step = 1 << 28
+    for i in range(0, flat.numel(), step):
+        zi = flat[i:i + step].to(torch.int32) - int(zfloor)
+        hist += torch.bincount(zi, minlength=nb).to(torch.int64)
     cum = torch.cumsum(hist, 0)
     need = math.ceil(frac * z.numel())
     vq = int(torch.nonzero(cum >= need)[0].item()) + int(zfloor)
@@ -106,46 +114,80 @@ def spectral_fbm(H, W, hurst, seed, zmin=0, zmax=1000, lake_frac=0.0, device="cp
     return _lakes(z, lake_frac, zmin)
 
 
-def _value_noise(H, W, wavelength, seed, octave, dev, ftype):
-    """Smooth value noise in [-1,1]: SplitMix64 values on a lattice of the
-    given wavelength, bicubically interpolated to H x W."""
+def _lattice(H, W, wavelength, seed, octave, dev, ftype):
     lh = int(math.ceil(H / wavelength)) + 3
     lw = int(math.ceil(W / wavelength)) + 3
     idx = torch.arange(lh * lw, device=dev, dtype=torch.int64).reshape(lh, lw)
-    lat = uniform01(seed * 1315423911 + octave * 2654435761 + 17, idx, ftype) * 2.0 - 1.0
-    up = torch.nn.functional.interpolate(lat[None, None], scale_factor=float(wavelength),
-                                         mode="bicubic", align_corners=False)[0, 0]
-    return up[wavelength:wavelength + H, wavelength:wavelength + W] if wavelength >= 1 else up[:H, :W]
+    return uniform01(seed * 1315423911 + octave * 2654435761 + 17, idx, ftype) * 2.0 - 1.0
+
+
+def _cubic_taps(n0, n1, wl, lmax, dev, ftype):
+    """Lattice indices and Catmull-Rom weights (4 each) for output samples
+    n0..n1-1 at lattice coordinate (n + 0.5)/wl - 0.5 + 1; the cell and the
+    fraction come from exact integer arithmetic, so a sample's value does
+    not depend on how the output is chunked."""
+    n = torch.arange(n0, n1, device=dev, dtype=torch.int64)
+    t = 2 * n + 1 + wl                       # 2*wl * (coordinate + 1)
+    cell = torch.div(t, 2 * wl, rounding_mode="floor")
+    fr = (t - cell * 2 * wl).to(ftype) / float(2 * wl)
+    f2, f3 = fr * fr, fr * fr * fr
+    w = torch.stack([-0.5 * f3 + f2 - 0.5 * fr,
+                     1.5 * f3 - 2.5 * f2 + 1.0,
+                     -1.5 * f3 + 2.0 * f2 + 0.5 * fr,
+                     0.5 * f3 - 0.5 * f2], dim=0)
+    idx = torch.stack([cell - 1 + k for k in range(4)], dim=0).clamp_(0, lmax - 1)
+    return idx, w
+
+
+def _value_noise_rows(lat, wavelength, r0, r1, W):
+    """Rows [r0, r1) (width W) of smooth value noise in [-1,1]: the lattice
+    interpolated with the Catmull-Rom cubic, separably (rows, then columns)."""
+    dev, ftype = lat.device, lat.dtype
+    iy, wy = _cubic_taps(r0, r1, wavelength, lat.shape[0], dev, ftype)
+    ix, wx = _cubic_taps(0, W, wavelength, lat.shape[1], dev, ftype)
+    T = sum(wy[k][:, None] * lat[iy[k]] for k in range(4))      # (rows, lw)
+    return sum(wx[k][None, :] * T[:, ix[k]] for k in range(4))  # (rows, W)
 
 
 def ridged_multifractal(H, W, seed, zmin=0, zmax=4000, lake_frac=0.0, octaves=10,
                         base_wavelength=None, lacunarity=2.0, hurst=0.8, gain=2.0,
-                        offset=1.0, device="cpu", chunk_rows=None):
-    """Ridged multifractal terrain from octave value noise, int16 (H, W)."""
+                        offset=1.0, device="cpu", chunk_rows=1024):
+    """Ridged multifractal terrain from octave value noise, int16 (H, W);
+    generated in row chunks so that any size fits the upsampling kernels."""
     dev = torch.device(device)
     ftype = torch.float32
     if base_wavelength is None:
         base_wavelength = max(8, min(H, W) // 6)
-    acc = None
-    weight = None
+    wls = []
     for i in range(octaves):
         wl = max(1, int(round(base_wavelength / (lacunarity ** i))))
         if wl < 2:
             break
-        n = _value_noise(H, W, wl, seed, i, dev, ftype)
-        sig = offset - n.abs_()
-        sig.mul_(sig)
-        if weight is not None:
-            sig.mul_(weight)
-        amp = lacunarity ** (-hurst * i)
-        if acc is None:
-            acc = sig * amp
-        else:
-            acc.add_(sig, alpha=amp)
-        weight = torch.clamp(sig * gain, 0.0, 1.0)
-        del n, sig
+        wls.append(wl)
+    lats = [_lattice(H, W, wl, seed, i, dev, ftype) for i, wl in enumerate(wls)]
+    acc = torch.empty((H, W), dtype=ftype, device=dev)
+    for r0 in range(0, H, chunk_rows):
+        r1 = min(H, r0 + chunk_rows)
+        a = None
+        weight = None
+        for i, wl in enumerate(wls):
+            n = _value_noise_rows(lats[i], wl, r0, r1, W)
+            sig = offset - n.abs()
+            sig.mul_(sig)
+            if weight is not None:
+                sig.mul_(weight)
+            amp = lacunarity ** (-hurst * i)
+            if a is None:
+                a = sig * amp
+            else:
+                a.add_(sig, alpha=amp)
+            weight = torch.clamp(sig * gain, 0.0, 1.0)
+            del n, sig
+        acc[r0:r1] = a
+        del a, weight
+    del lats
     z = _rescale_to_int16(acc, zmin, zmax)
-    del acc, weight
+    del acc
     return _lakes(z, lake_frac, zmin)
 
 
