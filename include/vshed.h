@@ -175,6 +175,36 @@ int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32
             int32_t n_obs, double coverage_target, int64_t *chosen, int64_t *gains,
             uint32_t *cum, int32_t *n_chosen, void *ws, size_t ws_bytes, vs_stream_t st);
 
+/* vs_site for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a convenience of the library.
+ *
+ * Some callers can neither call cudaMalloc nor hand over a workspace: code
+ * running inside a host application that owns every device allocation
+ * through its own pool and forbids allocation calls from plug-ins, latency-
+ * critical loops that cannot afford the implicit device synchronisation of
+ * cudaMalloc/cudaFree, and bindings from languages that have no device
+ * allocator at all.  This entry point needs nothing from them beyond the
+ * inputs and outputs of vs_site: its scratch is a static device array of
+ * VS_SITE_NOALLOC_MAX_BYTES inside libvshed.so, reserved on every GPU that
+ * loads the library until the process exits.
+ *
+ *  - Same arguments, results and errors as vs_site, minus the workspace.
+ *  - Limit: vs_site_workspace(n, R) must not exceed VS_SITE_NOALLOC_MAX_BYTES
+ *    (1 MiB, i.e. up to 262,080 candidates); larger calls return
+ *    VS_ERR_RANGE and launch nothing.
+ *  - The first call on each device looks up the array's device address (a
+ *    runtime query, with that device current); make that first call before
+ *    any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; the call re-initialises everything it reads.  Calls whose work
+ *    overlaps on the GPU (other streams, other host threads) race on the
+ *    array: serialise them.
+ *  - It calls no cudaMalloc, cudaFree or allocating library routine. */
+#define VS_SITE_NOALLOC_MAX_BYTES (1u << 20)
+int vs_site_noalloc(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W,
+                    int32_t R, int32_t n_obs, double coverage_target, int64_t *chosen,
+                    int64_t *gains, uint32_t *cum, int32_t *n_chosen, vs_stream_t st);
+
 /* Dense gain pass (the first step of vs_site, exposed on its own): for every
  * candidate c, gains_out[c] = popcount(V_c AND NOT cum).  One streaming pass
  * over all n bitmaps. */

@@ -21,6 +21,7 @@
 //    applied exactly.
 #include <algorithm>
 #include <cooperative_groups.h>
+#include <mutex>
 
 #include "vs_common.cuh"
 
@@ -380,4 +381,40 @@ extern "C" int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32
     cfg.numAttrs = 1;
     VS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_site_loop, P));
     return VS_OK;
+}
+
+// ------------------------------------------------------------------ vs_site without allocation
+// A variant of vs_site for callers that cannot allocate device memory: its
+// scratch lives in this file-scope device array instead of a caller-provided
+// workspace.  Every GPU that loads the library holds the array until exit.
+namespace {
+constexpr size_t kSiteNoAllocBytes = 1u << 20;  // VS_SITE_NOALLOC_MAX_BYTES in vshed.h
+static __device__ __align__(256) unsigned char g_site_scratch[kSiteNoAllocBytes];
+std::mutex g_scratch_mu;
+void *g_scratch_ptr[64];  // device address of g_site_scratch, per device ordinal
+}  // namespace
+
+extern "C" int vs_site_noalloc(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H,
+                               int32_t W, int32_t R, int32_t n_obs, double coverage_target,
+                               int64_t *chosen, int64_t *gains, uint32_t *cum,
+                               int32_t *n_chosen, vs_stream_t st) {
+    if (n < 0 || R < 1 || R > kMaxR) return VS_ERR_RANGE;
+    const size_t need = vs_site_workspace(n, R);
+    if (need > kSiteNoAllocBytes) return VS_ERR_RANGE;  // too many candidates for the array
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return VS_ERR_DEVICE;
+    void *scratch = nullptr;
+    {
+        // one-time set-up per device, with that device current: the host-side
+        // name of the array is not a device address, so ask the runtime for it
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        if (!g_scratch_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_site_scratch) != cudaSuccess || !p) return VS_ERR_CUDA;
+            g_scratch_ptr[dev] = p;
+        }
+        scratch = g_scratch_ptr[dev];
+    }
+    return vs_site(bm, cand, n, H, W, R, n_obs, coverage_target, chosen, gains, cum, n_chosen,
+                   scratch, kSiteNoAllocBytes, st);
 }

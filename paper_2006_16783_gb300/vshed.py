@@ -45,6 +45,7 @@ SIGNATURES = {
     "vs_site_workspace": (sz, [i64, i32]),
     "vs_site": (ctypes.c_int, [P, P, i64, i32, i32, i32, i32, f64, P, P, P, P, P, sz, P]),
     "vs_site_gains": (ctypes.c_int, [P, P, i64, i32, i32, i32, P, P, P]),
+    "vs_site_noalloc": (ctypes.c_int, [P, P, i64, i32, i32, i32, i32, f64, P, P, P, P, P]),
 }
 
 
