@@ -190,7 +190,7 @@ int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32
  *
  *  - Same arguments, results and errors as vs_site, minus the workspace.
  *  - Limit: vs_site_workspace(n, R) must not exceed VS_SITE_NOALLOC_MAX_BYTES
- *    (1 MiB, i.e. up to 262,080 candidates); larger calls return
+ *    (1 MiB, i.e. up to 52,416 candidates); larger calls return
  *    VS_ERR_RANGE and launch nothing.
  *  - The first call on each device looks up the array's device address (a
  *    runtime query, with that device current); make that first call before

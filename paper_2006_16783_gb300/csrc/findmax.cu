@@ -100,6 +100,78 @@ __global__ void __launch_bounds__(kFmThreads) k_findmax(const V *val, int H, int
     }
 }
 
+// Single pass for uint8 maps and k <= KM: every thread keeps its own KM
+// largest keys in registers while it streams its rows (4 posts per load);
+// the block's top k are then taken from the threads' lists, k rounds of a
+// block-wide maximum over the list heads.  Any key in the block's top k is
+// in its thread's top k, so the result equals the multi-round kernel's.
+template <int KM>
+__global__ void __launch_bounds__(kFmThreads) k_findmax_u8(const uint8_t *__restrict__ val, int H,
+                                                           int W, int b, int k, int nbx,
+                                                           const long long *__restrict__ unused,
+                                                           int64_t *out) {
+    (void)unused;
+    __shared__ uint64_t red[32];
+    __shared__ long long s_off;
+    const int by = blockIdx.x / nbx, bx = blockIdx.x - (blockIdx.x / nbx) * nbx;
+    const int y0 = by * b, y1 = min(H, (by + 1) * b);
+    const int x0 = bx * b, x1 = min(W, (bx + 1) * b);
+    {
+        // output offset: every block before this one gives min(k, its size)
+        long long acc = 0;
+        for (int q = threadIdx.x; q < (int)blockIdx.x; q += blockDim.x) {
+            const int qy = q / nbx, qx = q - (q / nbx) * nbx;
+            const long long ny = min(H, (qy + 1) * b) - qy * b, nx = min(W, (qx + 1) * b) - qx * b;
+            acc += llmin(k, ny * nx);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (uint64_t)acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (long long)red[w];
+            s_off = t;
+        }
+        __syncthreads();
+    }
+    uint64_t lst[KM];
+#pragma unroll
+    for (int i = 0; i < KM; ++i) lst[i] = 0;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int y = y0 + (threadIdx.x >> 5); y < y1; y += nw) {
+        const uint32_t prow = (uint32_t)y * (uint32_t)W;
+        const uint32_t a = prow + (uint32_t)x0, e = prow + (uint32_t)x1;  // byte range [a, e)
+        const uint32_t w0 = a >> 2, w1 = (e + 3) >> 2;
+        const uint32_t *words = (const uint32_t *)val;
+        for (uint32_t wi = w0 + lane; wi < w1; wi += 32) {
+            const uint32_t v4 = __ldg(words + wi);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t p = wi * 4 + j;
+                if (p < a || p >= e) continue;
+                const uint64_t key = ((uint64_t)((v4 >> (8 * j)) & 0xFFu) << 32) | (uint64_t)(0xFFFFFFFFu - p);
+                if (key > lst[KM - 1]) {
+                    lst[KM - 1] = key;
+#pragma unroll
+                    for (int i = KM - 1; i > 0; --i)
+                        if (lst[i] > lst[i - 1]) { const uint64_t t = lst[i]; lst[i] = lst[i - 1]; lst[i - 1] = t; }
+                }
+            }
+        }
+    }
+    const long long m = (long long)(y1 - y0) * (x1 - x0);
+    const int rounds = (int)llmin(k, m);
+    for (int r = 0; r < rounds; ++r) {
+        const uint64_t best = block_max_u64(lst[0], red);
+        if (lst[0] == best) {  // keys are unique: exactly one thread pops
+#pragma unroll
+            for (int i = 0; i < KM - 1; ++i) lst[i] = lst[i + 1];
+            lst[KM - 1] = 0;
+        }
+        if (threadIdx.x == 0) out[s_off + r] = (int64_t)(0xFFFFFFFFu - (uint32_t)(best & 0xFFFFFFFFu));
+    }
+}
+
 }  // namespace vs
 
 using namespace vs;
@@ -118,6 +190,19 @@ static int findmax_launch(const V *val, int32_t H, int32_t W, int32_t stride, in
     int rc = check_device();
     if (rc) return rc;
     const int Ws = (W + stride - 1) / stride;
+    // 4-post loads need a 4-byte aligned map whose size is a multiple of 4
+    // (the last word must not run past the caller's buffer)
+    if (sizeof(V) == 1 && stride == 1 && k <= 8 && (((uintptr_t)val) & 3) == 0 &&
+        ((long long)H * W) % 4 == 0) {
+        if (k <= 4)
+            k_findmax_u8<4><<<(unsigned)(nby * nbx), kFmThreads, 0, (cudaStream_t)st>>>(
+                (const uint8_t *)val, H, W, block, k, (int)nbx, nullptr, cand_out);
+        else
+            k_findmax_u8<8><<<(unsigned)(nby * nbx), kFmThreads, 0, (cudaStream_t)st>>>(
+                (const uint8_t *)val, H, W, block, k, (int)nbx, nullptr, cand_out);
+        VS_CUDA_TRY(cudaGetLastError());
+        return VS_OK;
+    }
     k_findmax<V><<<(unsigned)(nby * nbx), kFmThreads, 0, (cudaStream_t)st>>>(
         val, H, W, stride, Ws, block, k, (int)nbx, cand_out);
     VS_CUDA_TRY(cudaGetLastError());

@@ -263,6 +263,251 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_loop(const SiteParams 
     cl.sync();  // no CTA leaves while another may still address its shared memory
 }
 
+// ------------------------------------------------------------------ single-CTA greedy loop
+// For candidate counts whose gains fit in one CTA's shared memory.  Slots are
+// the candidates sorted by post index, so "largest gain, then lowest post
+// index" is "largest (gain, -slot)": the argmax needs no post indices.  Each
+// thread owns a contiguous run of slots and caches its best key; only runs
+// whose gains changed are rescanned.  Per greedy step there are three rounds
+// of memory latency: the winner's metadata, then its bitmap / C window / the
+// band of candidates within 2R rows, then the overlapping candidates' words.
+
+// slot of every candidate: rank by (post index, candidate index); invalid
+// posts sort last
+__global__ void k_site_rank(const int64_t *__restrict__ cand, int64_t n, int64_t HW,
+                            uint32_t *__restrict__ sp, uint32_t *__restrict__ sorig) {
+    __shared__ uint32_t tp[1024];
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t pc = 0xFFFFFFFFu;
+    if (c < n) {
+        const int64_t p = cand[c];
+        pc = (p >= 0 && p < HW) ? (uint32_t)p : 0xFFFFFFFFu;
+    }
+    int64_t rank = 0;
+    for (int64_t j0 = 0; j0 < n; j0 += 1024) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+            const int64_t j = j0 + i;
+            uint32_t v = 0xFFFFFFFFu;
+            if (j < n) {
+                const int64_t p = cand[j];
+                v = (p >= 0 && p < HW) ? (uint32_t)p : 0xFFFFFFFFu;
+            }
+            tp[i] = v;
+        }
+        __syncthreads();
+        if (c < n) {
+            const int m = (int)min((int64_t)1024, n - j0);
+            for (int i = 0; i < m; ++i) {
+                const uint32_t v = tp[i];
+                rank += (v < pc) || (v == pc && j0 + i < c);
+            }
+        }
+    }
+    if (c < n) {
+        sp[rank] = pc;
+        sorig[rank] = (uint32_t)c;
+    }
+}
+
+// for every slot, the slot range holding the candidates within 2R rows
+__global__ void k_site_bands(const uint32_t *__restrict__ sp, int64_t n, int W, int R,
+                             uint32_t *__restrict__ slo, uint32_t *__restrict__ shi) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t p = sp[i];
+    if (p == 0xFFFFFFFFu) { slo[i] = (uint32_t)i; shi[i] = (uint32_t)i; return; }
+    const int64_t y = p / (uint32_t)W;
+    const uint64_t a = (uint64_t)max((int64_t)0, y - 2 * R) * (uint64_t)W;
+    const uint64_t b = (uint64_t)(y + 2 * R + 1) * (uint64_t)W;
+    int64_t lo = 0, hi = n;  // first slot with sp >= a
+    while (lo < hi) { const int64_t m = (lo + hi) >> 1; if ((uint64_t)sp[m] < a) lo = m + 1; else hi = m; }
+    const int64_t L = lo;
+    lo = L; hi = n;          // first slot with sp >= b
+    while (lo < hi) { const int64_t m = (lo + hi) >> 1; if ((uint64_t)sp[m] < b) lo = m + 1; else hi = m; }
+    slo[i] = (uint32_t)L;
+    shi[i] = (uint32_t)lo;
+}
+
+struct Site1Params {
+    const uint32_t *bm;
+    int n;
+    int H, W, R, PR, words, WWc;
+    int n_obs;
+    long long need;
+    int64_t *chosen, *gains;
+    uint32_t *cum;
+    int32_t *n_chosen;
+    const uint32_t *gain0;   // candidate order
+    const uint32_t *sp, *sorig, *slo, *shi;  // slot order
+    const unsigned long long *covered0;
+};
+
+__device__ __forceinline__ uint64_t u64max(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+__global__ void __launch_bounds__(kSiteThreads, 1) k_site_loop1(const Site1Params P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *s_gain = (uint32_t *)smem;                  // n
+    uint32_t *s_delta = s_gain + ((P.n + 3) & ~3);        // words
+    int *s_list = (int *)(s_delta + ((P.words + 3) & ~3)); // kSiteThreads
+    __shared__ uint64_t s_red[32];
+    __shared__ int s_cnt[32];
+    __shared__ int s_dirty[kSiteThreads];
+    __shared__ int s_ovl[kSiteThreads];
+    __shared__ int s_pref[kSiteThreads + 1];
+    __shared__ unsigned s_sum[kSiteThreads];
+    __shared__ int4 s_geo[kSiteThreads];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int n = P.n, R = P.R, PR = P.PR, W = P.W, H = P.H, WWc = P.WWc;
+    const int cs = (n + kSiteThreads - 1) / kSiteThreads;
+    const int my0 = tid * cs, my1 = min(n, my0 + cs);
+
+    for (int i = tid; i < n; i += blockDim.x)
+        s_gain[i] = (P.sp[i] == 0xFFFFFFFFu) ? 0u : P.gain0[P.sorig[i]];
+    s_dirty[tid] = 0;
+    __syncthreads();
+    auto local_best = [&]() {
+        uint64_t b = 0;
+        for (int i = my0; i < my1; ++i) {
+            const uint32_t g = s_gain[i];
+            b = u64max(b, g ? (((uint64_t)g << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)i)) : 0ull);
+        }
+        return b;
+    };
+    uint64_t best = local_best();
+    long long covered = (P.need >= 0) ? (long long)*P.covered0 : 0;
+
+    int t = 0;
+    for (; t < P.n_obs; ++t) {
+        if (P.need >= 0 && covered >= P.need) break;
+        // ---- block argmax of the cached keys
+        uint64_t k = best;
+        for (int o = 16; o > 0; o >>= 1) k = u64max(k, __shfl_xor_sync(0xffffffffu, k, o));
+        if (lane == 0) s_red[wid] = k;
+        __syncthreads();
+        k = s_red[lane];
+        for (int o = 16; o > 0; o >>= 1) k = u64max(k, __shfl_xor_sync(0xffffffffu, k, o));
+        const uint32_t g = (uint32_t)(k >> 32);
+        if (g == 0) break;
+        const int s = (int)(0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFu));
+        // ---- round 1: the winner's metadata
+        const uint32_t wp = P.sp[s];
+        const uint32_t wc = P.sorig[s];
+        const int lo = (int)P.slo[s], hi = (int)P.shi[s];
+        if (tid == 0) {
+            P.chosen[t] = (int64_t)wp;
+            P.gains[t] = (int64_t)g;
+        }
+        covered += g;
+        const int wx = (int)(wp % (uint32_t)W), wy = (int)(wp / (uint32_t)W);
+        const int wgw0 = floordiv(wx - R, 32);
+        const uint32_t *Vw = P.bm + (int64_t)wc * P.words;
+        // ---- round 2: delta = V_win AND NOT C over the window, C |= V_win
+        // (both words are loaded up front so the two loads overlap)
+        for (int e = tid; e < P.words; e += blockDim.x) {
+            const int r = e / PR, w = e - r * PR;
+            const int y = wy - R + r, gw = wgw0 + w;
+            uint32_t d = 0;
+            if (y >= 0 && y < H && gw >= 0 && gw < WWc) {
+                uint32_t *cp = P.cum + (int64_t)y * WWc + gw;
+                const uint32_t v = __ldg(Vw + e);
+                const uint32_t old = *cp;
+                d = v & ~old;
+                if (d) *cp = old | v;
+            }
+            s_delta[e] = d;
+        }
+        // ---- band of slots within 2R rows: compact the ones within 2R columns
+        for (int b0 = lo; b0 < hi; b0 += blockDim.x) {
+            const int i = b0 + tid;
+            bool aff = false;
+            if (i < hi && s_gain[i] != 0) {
+                const int x = (int)(P.sp[i] % (uint32_t)W);
+                aff = abs(x - wx) <= 2 * R;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, aff);
+            if (lane == 0) s_cnt[wid] = __popc(bal);
+            __syncthreads();  // also publishes s_delta of the first chunk
+            int base = 0, tot = 0;
+            for (int q = 0; q < 32; ++q) { const int v = s_cnt[q]; base += (q < wid) ? v : 0; tot += v; }
+            if (aff) {
+                // overlap of the candidate's window with the winner's, in
+                // rows x words; its size goes to s_ovl for the prefix sum
+                const int li = base + __popc(bal & ((1u << lane) - 1u));
+                const uint32_t cpp = P.sp[i];
+                const int cx = (int)(cpp % (uint32_t)W), cy = (int)(cpp / (uint32_t)W);
+                const int cgw0 = floordiv(cx - R, 32);
+                const int ya = max(max(cy, wy) - R, 0), yb = min(min(cy, wy) + R, H - 1);
+                const int ga = max(max(cgw0, wgw0), 0), gb = min(min(cgw0, wgw0) + PR - 1, WWc - 1);
+                const int nrow = (ya <= yb && ga <= gb) ? yb - ya + 1 : 0;
+                const int nwd = (ya <= yb && ga <= gb) ? gb - ga + 1 : 0;
+                s_list[li] = i;
+                s_ovl[li] = nrow * nwd;
+                s_geo[li] = make_int4(ya, ga, nwd, (int)(((unsigned)cy << 16) | ((unsigned)cgw0 & 0xFFFFu)));
+                s_sum[li] = 0;
+            }
+            __syncthreads();
+            // exclusive prefix of the overlap sizes (warp 0)
+            if (wid == 0) {
+                const int per = (tot + 31) / 32;
+                const int a0 = lane * per, a1 = min(tot, a0 + per);
+                int loc = 0;
+                for (int q = a0; q < a1; ++q) loc += s_ovl[q];
+                int incl = loc;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                int run = incl - loc;
+                for (int q = a0; q < a1; ++q) { const int v = s_ovl[q]; s_pref[q] = run; run += v; }
+                if (lane == 31) s_pref[tot] = incl;
+            }
+            __syncthreads();
+            // ---- round 3: every thread takes an equal run of the overlap words
+            // of all listed candidates; the loads of a run are independent
+            const int TT = s_pref[tot];
+            const int per = (TT + blockDim.x - 1) / blockDim.x;
+            int e = tid * per;
+            const int e1 = min(TT, e + per);
+            if (e < e1) {
+                int l = 0, hi2 = tot - 1;  // last l with s_pref[l] <= e
+                while (l < hi2) { const int m = (l + hi2 + 1) >> 1; if (s_pref[m] <= e) l = m; else hi2 = m - 1; }
+                while (e < e1) {
+                    const int4 gq = s_geo[l];
+                    const int ya = gq.x, ga = gq.y, nwd = gq.z;
+                    const int cy = (int)((unsigned)gq.w >> 16), cgw0 = (int)(int16_t)(gq.w & 0xFFFF);
+                    const uint32_t *Vc = P.bm + (int64_t)P.sorig[s_list[l]] * P.words;
+                    const int lend = min(e1, s_pref[l + 1]);
+                    unsigned sum = 0;
+#pragma unroll 4
+                    for (; e < lend; ++e) {
+                        const int u = e - s_pref[l];
+                        const int dy = u / nwd, gw = ga + (u - dy * nwd), y = ya + dy;
+                        const uint32_t dl = s_delta[(y - wy + R) * PR + (gw - wgw0)];
+                        const uint32_t vc = __ldg(Vc + (y - cy + R) * PR + (gw - cgw0));
+                        sum += __popc(vc & dl);
+                    }
+                    if (sum) atomicAdd(&s_sum[l], sum);
+                    ++l;
+                }
+            }
+            __syncthreads();
+            for (int q = tid; q < tot; q += blockDim.x) {
+                const int ci = s_list[q];
+                s_gain[ci] -= s_sum[q];
+                s_dirty[ci / cs] = 1;
+            }
+            __syncthreads();
+        }
+        if (s_dirty[tid]) {
+            s_dirty[tid] = 0;
+            best = local_best();
+        }
+        __syncthreads();
+    }
+    if (tid == 0) *P.n_chosen = t;
+}
+
 static size_t site_smem_bytes(int slots, int words) {
     return (size_t)slots * 16 + (size_t)words * 4 + 16;
 }
@@ -298,7 +543,7 @@ static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 extern "C" size_t vs_site_workspace(int64_t n, int32_t R) {
     (void)R;
     if (n < 0) return 0;
-    return align256((size_t)n * 4) + 256;
+    return 5 * align256((size_t)n * 4) + 256;  // gains, sorted posts, order, band bounds
 }
 
 extern "C" int vs_site_gains(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H,
@@ -335,8 +580,13 @@ extern "C" int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32
     P.PR = words_per_row(R); P.words = (2 * R + 1) * P.PR; P.WWc = (W + 31) / 32;
     P.n_obs = n_obs;
     P.chosen = chosen; P.gains = gains; P.cum = cum; P.n_chosen = n_chosen;
+    const size_t a4 = align256((size_t)n * 4);
     uint32_t *g0 = (uint32_t *)ws;
-    unsigned long long *cov = (unsigned long long *)((char *)ws + align256((size_t)n * 4));
+    uint32_t *sp = (uint32_t *)((char *)ws + a4);
+    uint32_t *sorig = (uint32_t *)((char *)ws + 2 * a4);
+    uint32_t *slo = (uint32_t *)((char *)ws + 3 * a4);
+    uint32_t *shi = (uint32_t *)((char *)ws + 4 * a4);
+    unsigned long long *cov = (unsigned long long *)((char *)ws + 5 * a4);
     P.gain0 = g0;
     P.covered0 = cov;
     P.need = -1;
@@ -351,6 +601,26 @@ extern "C" int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32
         VS_CUDA_TRY(cudaGetLastError());
     }
     if (n > 0 && (rc = vs_site_gains(bm, cand, n, H, W, R, cum, g0, st))) return rc;
+
+    // one CTA when every gain fits in its shared memory
+    const size_t smem1 = (size_t)((n + 3) & ~3) * 4 + (size_t)((P.words + 3) & ~3) * 4 +
+                         (size_t)kSiteThreads * 4;
+    if (n > 0 && n < (1 << 30) && smem1 <= (size_t)kSmemLimit - 40 * 1024) {  // + ~33 KB static
+        k_site_rank<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cand, n, (int64_t)H * W, sp, sorig);
+        VS_CUDA_TRY(cudaGetLastError());
+        k_site_bands<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sp, n, W, R, slo, shi);
+        VS_CUDA_TRY(cudaGetLastError());
+        Site1Params Q1;
+        Q1.bm = bm; Q1.n = (int)n; Q1.H = H; Q1.W = W; Q1.R = R; Q1.PR = P.PR; Q1.words = P.words;
+        Q1.WWc = P.WWc; Q1.n_obs = n_obs; Q1.need = P.need; Q1.chosen = chosen; Q1.gains = gains;
+        Q1.cum = cum; Q1.n_chosen = n_chosen; Q1.gain0 = g0; Q1.sp = sp; Q1.sorig = sorig;
+        Q1.slo = slo; Q1.shi = shi; Q1.covered0 = cov;
+        VS_CUDA_TRY(cudaFuncSetAttribute(k_site_loop1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem1));
+        k_site_loop1<<<1, kSiteThreads, smem1, s>>>(Q1);
+        VS_CUDA_TRY(cudaGetLastError());
+        return VS_OK;
+    }
 
     // choose the cluster: largest Q whose slots fit in shared memory
     int Q = 0, slots = 0;

@@ -203,6 +203,272 @@ __global__ void __launch_bounds__(kVixThreads, 1) k_vix(const __grid_constant__ 
     }
 }
 
+// ------------------------------------------------------------------ length-sorted variant
+// The same computation with the lines of sight of a CTA ordered by length
+// before they are walked.  A warp walks 32 consecutive lines of the sorted
+// list, so its lanes have (nearly) the same number of crossings and little
+// time is lost waiting for the longest lane; the per-line set-up is paid
+// once per line instead of once per crossing.  Lines are described by a
+// packed 32-bit item (post in tile: 11 bits, dx+R and dy+R: 10 bits each),
+// so this variant serves R <= 511 and tiles of at most 2048 posts.
+constexpr int kVixSB = 10;  // samples per post in one sorted batch
+
+struct Vix2Params {
+    VixParams b;
+    int lgTX;          // log2(TX)
+    int sb;            // samples per batch
+};
+
+__device__ __forceinline__ void vix_offset(uint64_t state, unsigned NR, int R, const int *rowstart,
+                                           const int *hwtab, int &dx, int &dy) {
+    const uint64_t u = splitmix64_mix(state);
+    const unsigned idx = __umulhi((unsigned)(u >> 32), NR);
+    int lo = 0, hi = 2 * R;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((unsigned)rowstart[mid] <= idx) lo = mid; else hi = mid - 1;
+    }
+    dy = lo - R;
+    dx = -hwtab[lo] + (int)(idx - (unsigned)rowstart[lo]);
+    if (dy == 0 && dx >= 0) dx += 1;
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(kVixThreads, 1) k_vix2(const __grid_constant__ CUtensorMap tmap,
+                                                         const Vix2Params Q) {
+    const VixParams &P = Q.b;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    const int R = P.R, TX = P.TX, TY = P.TY, lgTX = Q.lgTX;
+    const int WW = P.WG * 8;
+    const int nposts = TX * TY;
+    int16_t *win = (int16_t *)smem;
+    const int win_elems = P.nbox * P.box_rows * WW;
+    uint32_t *items = (uint32_t *)(smem + ((win_elems * 2 + 127) & ~127));
+    int *cnt = (int *)(items + nposts * Q.sb);
+    int *hist = cnt + nposts;                      // R + 2 entries
+    int *rowstart = hist + ((R + 2 + 3) & ~3);      // 2R + 2 entries
+    int *hwtab = rowstart + (2 * R + 2);            // 2R + 1 entries
+    uint64_t *bar = (uint64_t *)(hwtab + ((2 * R + 1 + 1) & ~1));
+    __shared__ int warp_tot[32];
+    __shared__ int s_fail;
+
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        s_fail = 0;
+    }
+    for (int i = tid; i < nposts; i += blockDim.x) cnt[i] = 0;
+    // ---- row table of OFF_R (as in k_vix)
+    {
+        const int nrow = 2 * R + 1;
+        const int chunk = (nrow + kVixThreads - 1) / kVixThreads;
+        const int i0 = tid * chunk, i1 = min(nrow, i0 + chunk);
+        int local = 0;
+        for (int i = i0; i < i1; ++i) {
+            const int dy = i - R;
+            const int hw = isqrt_exact(R * R - dy * dy);
+            hwtab[i] = hw;
+            local += 2 * hw + 1 - (dy == 0 ? 1 : 0);
+        }
+        int incl = local;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int t = warp_tot[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += v;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        int run = incl - local + (wid > 0 ? warp_tot[wid - 1] : 0);
+        if (tid == 0) rowstart[0] = 0;
+        for (int i = i0; i < i1; ++i) {
+            run += 2 * hwtab[i] + 1 - (i == R ? 1 : 0);
+            rowstart[i + 1] = run;
+        }
+    }
+    __syncthreads();
+    const uint64_t GOLD = 0x9E3779B97F4A7C15ull;
+    const unsigned NR = (unsigned)P.NR;
+    unsigned long long nsteps = 0;
+
+    for (int sec = 0; sec < P.nsplit; ++sec) {
+        int col_lo = tx0 - R, row_lo = ty0 - R;
+        if (P.nsplit == 2) row_lo = (sec == 0) ? ty0 - R : ty0;
+        if (P.nsplit == 4) {
+            col_lo = (sec & 1) ? tx0 : tx0 - R;
+            row_lo = (sec & 2) ? ty0 : ty0 - R;
+        }
+        const int wx0 = floordiv(col_lo, 8) * 8;
+        const int wy0 = row_lo;
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, (uint32_t)(win_elems * 2));
+            for (int b = 0; b < P.nbox; ++b)
+                tma_load_3d(win + (size_t)b * P.box_rows * WW, &tmap, 0, wx0 / 8,
+                            wy0 + b * P.box_rows, bar);
+        }
+        if (!mbar_wait(bar, (uint32_t)(sec & 1))) s_fail = 1;
+        __syncthreads();
+        if (s_fail) {
+            mbar_wait(bar, (uint32_t)(sec & 1));
+            break;
+        }
+        for (int s0 = 0; s0 < P.S; s0 += Q.sb) {
+            const int nb = min(Q.sb, P.S - s0);
+            // ---- pass A: how many lines of each length
+            for (int i = tid; i < R + 2; i += blockDim.x) hist[i] = 0;
+            __syncthreads();
+            for (int pp = tid; pp < nposts; pp += blockDim.x) {
+                const int gx = tx0 + (pp & (TX - 1)), gy = ty0 + (pp >> lgTX);
+                const bool in = gx < P.W && gy < P.H;
+                const uint64_t p = (uint64_t)gy * (uint64_t)P.W + (uint64_t)gx;
+                uint64_t state = P.seed + GOLD * (p * (uint64_t)P.S + (uint64_t)s0 + 1ull);
+                for (int s = 0; s < nb; ++s, state += GOLD) {
+                    int dx, dy;
+                    vix_offset(state, NR, R, rowstart, hwtab, dx, dy);
+                    int s_of = 0;
+                    if (P.nsplit == 2) s_of = dy > 0;
+                    if (P.nsplit == 4) s_of = (dx > 0) + 2 * (dy > 0);
+                    const bool ok = in && s_of == sec && (unsigned)(gx + dx) < (unsigned)P.W &&
+                                    (unsigned)(gy + dy) < (unsigned)P.H;
+                    const int D = max(abs(dx), abs(dy));
+                    const unsigned m = __match_any_sync(__activemask(), ok ? D : -1);
+                    if (ok && lane == __ffs(m) - 1) atomicAdd(&hist[D], __popc(m));
+                }
+            }
+            __syncthreads();
+            // ---- exclusive scan of the histogram (warp 0); hist[R+1] = total
+            if (wid == 0) {
+                const int nbin = R + 2;
+                const int per = (nbin + 31) / 32;
+                const int b0 = lane * per, b1 = min(nbin, b0 + per);
+                int loc = 0;
+                for (int i = b0; i < b1; ++i) loc += hist[i];
+                int incl = loc;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                int run = incl - loc;
+                for (int i = b0; i < b1; ++i) {
+                    const int v = hist[i];
+                    hist[i] = run;
+                    run += v;
+                }
+            }
+            __syncthreads();
+            const int total = hist[R + 1];
+            __syncthreads();
+            // ---- pass B: the same lines again, scattered into length order
+            for (int pp = tid; pp < nposts; pp += blockDim.x) {
+                const int gx = tx0 + (pp & (TX - 1)), gy = ty0 + (pp >> lgTX);
+                const bool in = gx < P.W && gy < P.H;
+                const uint64_t p = (uint64_t)gy * (uint64_t)P.W + (uint64_t)gx;
+                uint64_t state = P.seed + GOLD * (p * (uint64_t)P.S + (uint64_t)s0 + 1ull);
+                for (int s = 0; s < nb; ++s, state += GOLD) {
+                    int dx, dy;
+                    vix_offset(state, NR, R, rowstart, hwtab, dx, dy);
+                    int s_of = 0;
+                    if (P.nsplit == 2) s_of = dy > 0;
+                    if (P.nsplit == 4) s_of = (dx > 0) + 2 * (dy > 0);
+                    const bool ok = in && s_of == sec && (unsigned)(gx + dx) < (unsigned)P.W &&
+                                    (unsigned)(gy + dy) < (unsigned)P.H;
+                    const int D = max(abs(dx), abs(dy));
+                    const unsigned m = __match_any_sync(__activemask(), ok ? D : -1);
+                    int base = 0;
+                    if (ok && lane == __ffs(m) - 1) base = atomicAdd(&hist[D], __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+                    if (ok)
+                        items[base + __popc(m & ((1u << lane) - 1u))] =
+                            (uint32_t)pp | ((uint32_t)(dx + R) << 11) | ((uint32_t)(dy + R) << 21);
+                }
+            }
+            __syncthreads();
+            // ---- pass C: walk the lines, 32 of (nearly) equal length per warp step
+            for (int i = wid * 32 + lane; i - lane < total; i += blockDim.x) {
+                if (i >= total) continue;
+                const uint32_t it = items[i];
+                const int pp = (int)(it & 2047u);
+                const int dx = (int)((it >> 11) & 1023u) - R, dy = (int)(it >> 21) - R;
+                const int gx = tx0 + (pp & (TX - 1)), gy = ty0 + (pp >> lgTX);
+                const int a0 = (gy - wy0) * WW + (gx - wx0);
+                const int E = (int)win[a0] + P.ht;
+                const int adx = abs(dx), ady = abs(dy);
+                const bool xmaj = adx >= ady;
+                const int D = xmaj ? adx : ady;
+                const int dmin = xmaj ? dy : dx;
+                const int ms = xmaj ? (dx > 0 ? 1 : -1) : (dy > 0 ? WW : -WW);
+                const int ns = xmaj ? WW : 1;
+                const int q = floordiv(dmin, D);
+                const int r = dmin - q * D;
+                const int step = ms + q * ns;
+                const int tsl = (int)win[a0 + dx + dy * WW] + P.hr - E;
+                const int16_t *w1 = win + ns;
+                // blocked at crossing j iff z0*(D-f) + z1*f > E*D + tsl*j
+                int a = a0, f = 0, thr = E * D;
+                bool vis = true;
+                int done = 0;
+                const int nstep = D - 1;
+                if (nstep & 1) {
+                    f += r; a += step; thr += tsl;
+                    if (f >= D) { f -= D; a += ns; }
+                    vis = (int)win[a] * (D - f) + (int)w1[a] * f <= thr;
+                    done = 1;
+                }
+                for (int k = nstep >> 1; vis && k > 0; --k) {
+                    f += r; a += step; thr += tsl;
+                    if (f >= D) { f -= D; a += ns; }
+                    const int v1 = (int)win[a] * (D - f) + (int)w1[a] * f;
+                    const int t1 = thr;
+                    f += r; a += step; thr += tsl;
+                    if (f >= D) { f -= D; a += ns; }
+                    const int v2 = (int)win[a] * (D - f) + (int)w1[a] * f;
+                    if (COUNT) done += (v1 > t1) ? 1 : 2;
+                    vis = (v1 <= t1) & (v2 <= thr);
+                }
+                if (COUNT) nsteps += done;
+                if (vis) atomicAdd(&cnt[pp], 1);
+            }
+            __syncthreads();
+        }
+    }
+
+    for (int pp = tid; pp < nposts; pp += blockDim.x) {
+        const int gx = tx0 + (pp & (TX - 1)), gy = ty0 + (pp >> lgTX);
+        if (gx >= P.W || gy >= P.H) continue;
+        P.out[(size_t)gy * P.W + gx] = s_fail ? (uint8_t)0xFF : (uint8_t)cnt[pp];
+    }
+    if (COUNT) {
+        for (int o = 16; o > 0; o >>= 1) nsteps += __shfl_xor_sync(0xffffffffu, nsteps, o);
+        if (lane == 0 && nsteps) atomicAdd(P.steps, nsteps);
+    }
+}
+
+static size_t vix2_smem_bytes(int R, int nsplit, int TX, int TY, int sb, int *WG, int *box_rows,
+                              int *nbox) {
+    // one spare row below and column to the right: the second straddling post
+    // of a crossing is read even when its weight is zero
+    const int rows = ((nsplit == 1) ? TY + 2 * R : TY + R) + 1;
+    const int cols = ((nsplit == 4) ? TX + R : TX + 2 * R) + 1;
+    const int wg = (cols + 7 + 7) / 8;
+    int nb = (rows + 255) / 256;
+    int br = ((rows + nb - 1) / nb + 7) / 8 * 8;
+    if (br > 256) { nb += 1; br = ((rows + nb - 1) / nb + 7) / 8 * 8; }
+    *WG = wg; *box_rows = br; *nbox = nb;
+    size_t win = ((size_t)nb * br * wg * 8 * 2 + 127) & ~(size_t)127;
+    return win + (size_t)TX * TY * sb * 4 + (size_t)TX * TY * 4 + (size_t)((R + 2 + 3) & ~3) * 4 +
+           (size_t)(2 * R + 2) * 4 + (size_t)(2 * R + 2) * 4 + 16 + 128;
+}
+
 static size_t vix_smem_bytes(int R, int nsplit, int TX, int TY, int *WG, int *box_rows,
                              int *nbox) {
     const int rows = (nsplit == 1) ? TY + 2 * R : TY + R;
@@ -239,6 +505,37 @@ static int vix_launch(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, u
         nr += 2 * s + 1;
     }
     P.NR = (int)(nr - 1);
+
+    // length-sorted variant when the packed line items can describe R
+    if (R <= 511) {
+        const int tiles2[2][2] = {{64, 32}, {32, 32}};
+        const int sb = std::min(S, kVixSB);
+        for (int ns : {1, 2, 4}) {
+            for (auto &t : tiles2) {
+                int WG, br, nb;
+                size_t b = vix2_smem_bytes(R, ns, t[0], t[1], std::max(sb, 1), &WG, &br, &nb);
+                if (WG > 256 || b > (size_t)225 * 1024) continue;
+                Vix2Params Q;
+                Q.b = P;
+                Q.b.nsplit = ns; Q.b.TX = t[0]; Q.b.TY = t[1]; Q.b.WG = WG; Q.b.box_rows = br;
+                Q.b.nbox = nb; Q.b.steps = steps;
+                Q.lgTX = (t[0] == 64) ? 6 : 5;
+                Q.sb = std::max(sb, 1);
+                GridMap gm;
+                if ((rc = make_grid_map(&gm, g, WG, br))) return rc;
+                dim3 grid((g.W + t[0] - 1) / t[0], (g.H + t[1] - 1) / t[1]);
+                if (steps) {
+                    VS_CUDA_TRY(cudaFuncSetAttribute(k_vix2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+                    k_vix2<true><<<grid, kVixThreads, b, (cudaStream_t)st>>>(gm.map, Q);
+                } else {
+                    VS_CUDA_TRY(cudaFuncSetAttribute(k_vix2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+                    k_vix2<false><<<grid, kVixThreads, b, (cudaStream_t)st>>>(gm.map, Q);
+                }
+                VS_CUDA_TRY(cudaGetLastError());
+                return VS_OK;
+            }
+        }
+    }
 
     // tile / split choice: the largest tile whose staged window fits, fewest
     // passes first (each pass re-draws the samples and re-stages a window)

@@ -154,6 +154,29 @@ def test_site_parity(V, O, seed, H, W, R, ncand, nobs):
     assert (_np(gC).view(np.uint32) == C).all()
 
 
+@pytest.mark.slow
+def test_site_parity_many_candidates(V, O):
+    """More candidates than one CTA's shared memory holds: the cluster path."""
+    H, W, R = 600, 620, 3
+    cand, bm = _site_case(O, 31, H, W, R, 70000)
+    ch, gn, C = O.site(bm, cand, H, W, R, 3000)
+    gch, ggn, gC, t = V.site(torch.as_tensor(bm.view(np.int32)).cuda(), torch.as_tensor(cand).cuda(),
+                             H, W, R, 3000)
+    assert _np(gch).tolist() == ch.tolist() and _np(ggn).tolist() == gn.tolist()
+    assert (_np(gC).view(np.uint32) == C).all()
+
+
+def test_site_duplicate_and_invalid_candidates(V, O):
+    H, W, R = 90, 110, 6
+    cand, bm = _site_case(O, 41, H, W, R, 80)
+    cand2 = np.concatenate([cand, cand[:10]])             # duplicated posts
+    bm2 = np.concatenate([bm, bm[:10]])
+    ch, gn, C = O.site(bm2, cand2, H, W, R, 50)
+    gch, ggn, gC, t = V.site(torch.as_tensor(bm2.view(np.int32)).cuda(), torch.as_tensor(cand2).cuda(),
+                             H, W, R, 50)
+    assert _np(gch).tolist() == ch.tolist() and (_np(gC).view(np.uint32) == C).all()
+
+
 def test_site_coverage_target_and_resume(V, O):
     H, W, R = 180, 200, 15
     cand, bm = _site_case(O, 9, H, W, R, 400)
