@@ -211,6 +211,58 @@ int vs_site_noalloc(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t 
 int vs_site_gains(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W,
                   int32_t R, const uint32_t *cum, uint32_t *gains_out, vs_stream_t st);
 
+/* ------------------------------------------------------------------------
+ * Learned candidate proposal (replaces the sampled ranking of the Vix stage,
+ * Sec. "The multiple transmitter siting process", Vix, whose only use is to
+ * rank posts; the network itself is this library's, the paper has none).
+ *
+ * Network: x0 = bf16((z - mean over the 65x65 patch) / 1000); four 3x3
+ * stride-2 convolutions and one 3x3 stride-1 convolution, 32 channels, bias +
+ * ReLU, activations rounded to bf16; global average pool; fc 32 -> 1;
+ * sigmoid.  Patches are centred on a post; rows/columns outside the grid are
+ * clamped to the nearest edge post.  Products are BF16 x BF16 on the tensor
+ * cores (tcgen05), accumulated in FP32.
+ *
+ * Parameters: vs_cnn_param_count() fp32 values ("master" weights, device):
+ *   w_l [32][cin][3][3] then b_l [32] for l = 0..4 (cin = 1 for l = 0, else
+ *   32), then fc weights [32] and fc bias [1].
+ * vs_cnn_pack converts them into the kernels' operand layout (a device
+ * buffer of vs_cnn_packed_bytes(), 16-byte aligned); repack after every
+ * weight update.
+ *
+ * vs_cnn_forward: n patches centred on posts centers[n] (int64 post indices);
+ * out[n] = predicted visibility index (fp32).  save (optional, device, n *
+ * vs_cnn_save_bytes() bytes, 16-byte aligned) receives every activation for
+ * vs_cnn_backward.  status (optional, device int32) is set to VS_ERR_TIMEOUT
+ * if a bounded tensor-core wait gave up.
+ * vs_cnn_score_lattice: one patch per lattice post (i*stride, j*stride),
+ * score_out [ceil(H/stride)][ceil(W/stride)], the input of vs_findmax_f32.
+ * ---------------------------------------------------------------------- */
+int vs_cnn_param_count(void);
+size_t vs_cnn_packed_bytes(void);
+size_t vs_cnn_save_bytes(void);
+int vs_cnn_pack(const float *master, void *packed, vs_stream_t st);
+int vs_cnn_forward(vs_grid g, const int64_t *centers, int64_t n, const void *packed, float *out,
+                   void *save, int32_t *status, vs_stream_t st);
+int vs_cnn_score_lattice(vs_grid g, int32_t stride, const void *packed, float *score_out,
+                         int32_t *status, vs_stream_t st);
+
+/* Training.  vs_cnn_backward: gradients of the mean L1 loss
+ * mean_b |y_b - labels[b]| over a batch of B patches whose forward pass
+ * (vs_cnn_forward with `save`) wrote `save`; master must be the weights that
+ * forward used.  grads (fp32, vs_cnn_param_count() values, same layout as
+ * master) is ACCUMULATED; *loss_sum (device fp32) grows by the sum of
+ * |y - label|.  Pre-activation gradients are rounded to bf16 before they meet
+ * weights or activations; products accumulate in FP32.  ws: at least
+ * vs_cnn_backward_workspace(B) bytes.
+ * vs_cnn_adam: one Adam step (Kingma & Ba 2015) on master with moments m, v
+ * (fp32, zero before step 1); step counts from 1; grads are cleared. */
+size_t vs_cnn_backward_workspace(int64_t B);
+int vs_cnn_backward(const void *save, const float *labels, int64_t B, const float *master,
+                    float *grads, float *loss_sum, void *ws, size_t ws_bytes, vs_stream_t st);
+int vs_cnn_adam(float *master, float *grads, float *m, float *v, int64_t step, float lr,
+                float beta1, float beta2, float eps, vs_stream_t st);
+
 #ifdef __cplusplus
 }
 #endif

@@ -153,3 +153,35 @@ def flops_per_patch():
         n = out_size(n, s)
         tot += 2 * n * n * co * ci * 9
     return tot + 2 * CH
+
+
+def extract_patch(z, cy, cx):
+    """65 x 65 elevations centred on post (cx, cy); rows and columns outside
+    the grid take the nearest edge post."""
+    H, W = z.shape
+    ys = np.clip(np.arange(cy - 32, cy + 33), 0, H - 1)
+    xs = np.clip(np.arange(cx - 32, cx + 33), 0, W - 1)
+    return np.asarray(z)[np.ix_(ys, xs)]
+
+
+def flatten_params(p):
+    """The library's flat fp32 parameter vector: w_l, b_l for l = 0..4, fc w, fc b."""
+    parts = []
+    for l in range(len(LAYERS)):
+        parts += [p["w%d" % l].ravel(), p["b%d" % l].ravel()]
+    parts += [p["fw"].ravel(), p["fb"].ravel()]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def unflatten_params(v):
+    v = np.asarray(v, dtype=np.float64)
+    p, o = {}, 0
+    for l, (ci, co, s) in enumerate(LAYERS):
+        n = co * ci * 9
+        p["w%d" % l] = v[o:o + n].reshape(co, ci, 3, 3)
+        o += n
+        p["b%d" % l] = v[o:o + co].copy()
+        o += co
+    p["fw"] = v[o:o + CH].copy()
+    p["fb"] = v[o + CH:o + CH + 1].copy()
+    return p

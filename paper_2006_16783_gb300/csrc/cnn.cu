@@ -1,0 +1,716 @@
+// cnn.cu -- learned candidate proposal: a 5-layer CNN that maps a 65x65
+// elevation patch to a predicted visibility index (the Vix stage's ranking
+// replaced by a learned one; the paper's Vix stage only ranks posts,
+// Sec. "The multiple transmitter siting process", Vix).
+//
+// Network (fixed by this library; the paper specifies none):
+//   x0 = bf16((z - mean(patch)) / 1000)                           65x65x1
+//   conv1 3x3 s2 p1 1->32, bias, ReLU, bf16                      33x33x32
+//   conv2 3x3 s2 p1 32->32                                       17x17x32
+//   conv3 3x3 s2 p1 32->32                                        9x 9x32
+//   conv4 3x3 s2 p1 32->32                                        5x 5x32
+//   conv5 3x3 s1 p1 32->32                                        5x 5x32
+//   global average pool -> fc 32->1 -> sigmoid
+//
+// Forward kernel: one persistent 128-thread CTA per SM works through patches
+// entirely in shared memory.  Every convolution is an implicit GEMM on the
+// 5th-generation tensor cores: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32),
+// M = 128 output pixels, N = 32 channels, K = 16 per instruction, the FP32
+// accumulator in tensor memory (32 columns), read back with tcgen05.ld by
+// the four warps (one TMEM lane quarter each) for the bias + ReLU + BF16
+// epilogue.  Operands are read straight from shared memory through matrix
+// descriptors (no swizzle, K-major 8x16-byte core matrices):
+//   * A stride-2 layer's input is stored as four parity planes (even/odd row
+//     x even/odd column) in blocks of 8 channels, each plane with a zero
+//     border row/column and a row pitch of (output width + 1) pixels.  For
+//     output pixel m = y*pitch + x, tap (ky,kx) reads plane
+//     (ky != 1, kx != 1) at m + (ky != 0)*pitch + (kx != 0): every tap of a
+//     128-pixel tile is one contiguous run of 16-byte rows, i.e. a plain
+//     descriptor (leading offset = next 8-channel block, stride offset =
+//     next 8 pixels).  The one junk column per row is discarded.
+//   * The stride-1 last layer uses one plane with a border on all sides.
+//   * The 1-channel first layer uses an explicit im2col tile (K = 9 taps
+//     padded to 16).
+#include <algorithm>
+
+#include <cuda_bf16.h>
+
+#include "vs_common.cuh"
+
+namespace vs {
+namespace cnn {
+
+constexpr int kThreads = 128;
+constexpr int kPatch = 65;
+
+// ---- master parameter layout (fp32): w_l [32][cin][3][3], b_l [32], fw [32], fb
+constexpr int kNParams = 288 + 32 + 4 * (9216 + 32) + 33;
+__host__ __device__ constexpr int off_w(int l) { return l == 0 ? 0 : 320 + (l - 1) * 9248; }
+__host__ __device__ constexpr int off_b(int l) { return l == 0 ? 288 : 320 + (l - 1) * 9248 + 9216; }
+constexpr int kOffFw = 320 + 4 * 9248;
+
+// ---- packed layout (bytes): B operands (bf16), biases (fp32), fc (fp32)
+constexpr int kB1Bytes = 1024;                 // 32 x 16
+constexpr int kBlBytes = 9 * 2 * 1024;         // per 32->32 layer: 9 taps x 2 K-steps
+constexpr int kPkB1 = 0;
+__host__ __device__ constexpr int pk_bl(int l) { return kB1Bytes + (l - 1) * kBlBytes; }  // l = 1..4
+constexpr int kPkBias = kB1Bytes + 4 * kBlBytes;  // 5 x 32 floats
+constexpr int kPkFc = kPkBias + 5 * 32 * 4;       // 32 + 1 floats (padded to 36)
+constexpr int kPackedBytes = kPkFc + 36 * 4;
+
+// ---- activations saved for the backward pass, per patch (bytes)
+constexpr int kA1 = 33 * 33 * 32 * 2, kA2 = 17 * 17 * 32 * 2, kA3 = 9 * 9 * 32 * 2,
+              kA4 = 5 * 5 * 32 * 2, kA5 = 5 * 5 * 32 * 2;
+constexpr int kSvA1 = 0, kSvA2 = kSvA1 + kA1, kSvA3 = kSvA2 + kA2, kSvA4 = kSvA3 + kA3,
+              kSvA5 = kSvA4 + kA4, kSvHead = kSvA5 + kA5;  // head: g[32], logit, y (fp32)
+constexpr int kSaveBytes = ((kSvHead + 34 * 4) + 127) & ~127;
+constexpr int kSvInput = kSaveBytes;                       // x0: 65x65 bf16
+constexpr int kSaveBytesTotal = kSaveBytes + ((kPatch * kPatch * 2 + 127) & ~127);
+
+// ---- shared-memory plan of the forward kernel (bytes, 128-aligned)
+constexpr int kPln2 = 18 * 18, kPln3 = 10 * 10, kPln4 = 6 * 6, kPln5 = 7 * 7;
+constexpr int kSmW = 0;
+constexpr int kSmP2 = ((kSmW + kPackedBytes) + 127) & ~127;
+constexpr int kP2Bytes = (16 * kPln2 + 96) * 16;
+constexpr int kSmU = ((kSmP2 + kP2Bytes) + 127) & ~127;  // A1 im2col, later P3/P4/P5
+constexpr int kA1Bytes = 1152 * 32;
+constexpr int kP3Off = 0, kP3Bytes = (16 * kPln3 + 40) * 16;
+constexpr int kP4Off = kP3Off + kP3Bytes, kP4Bytes = (16 * kPln4 + 104) * 16;
+constexpr int kP5Off = kP4Off + kP4Bytes, kP5Bytes = (4 * kPln5 + 100) * 16;
+constexpr int kUBytes = (kP5Off + kP5Bytes) > kA1Bytes ? (kP5Off + kP5Bytes) : kA1Bytes;
+constexpr int kSmPatch = ((kSmU + kUBytes) + 127) & ~127;   // 67x67 bf16, zero border
+constexpr int kPatchBytes = ((67 * 67 * 2) + 127) & ~127;
+constexpr int kSmGap = kSmPatch + kPatchBytes;              // 25 x 32 floats
+constexpr int kSmEnd = kSmGap + 25 * 32 * 4;
+constexpr int kSmemBytes = kSmEnd + 128;                    // + base alignment slack
+
+// instruction descriptor: kind::f16, A = B = BF16, D = F32, K-major A and B,
+// N = 32, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void umma(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__device__ __forceinline__ float bf16_round(float v) {
+    return __bfloat162float(__float2bfloat16_rn(v));
+}
+
+// ------------------------------------------------------------------ packing
+// fp32 master parameters -> bf16 B operands in the K-major core-matrix
+// layout ([n/8][k/8][n%8][k%8], 8x8 bf16 = 128 B per core matrix), fp32
+// biases and fc.
+__global__ void k_cnn_pack(const float *__restrict__ master, unsigned char *__restrict__ packed) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthr = gridDim.x * blockDim.x;
+    __nv_bfloat16 *B1 = (__nv_bfloat16 *)(packed + kPkB1);
+    for (int e = tid; e < 32 * 16; e += nthr) {
+        const int n = e / 16, k = e % 16;
+        const float w = (k < 9) ? master[off_w(0) + n * 9 + k] : 0.f;
+        B1[((n / 8) * 2 + k / 8) * 64 + (n % 8) * 8 + (k % 8)] = __float2bfloat16_rn(w);
+    }
+    for (int e = tid; e < 4 * 9 * 2 * 32 * 16; e += nthr) {
+        const int l = 1 + e / (9 * 2 * 512);
+        const int rem = e % (9 * 2 * 512);
+        const int t = rem / 1024, ks = (rem / 512) % 2, nk = rem % 512;
+        const int n = nk / 16, k = nk % 16;
+        const int cin = ks * 16 + k, ky = t / 3, kx = t % 3;
+        const float w = master[off_w(l) + ((n * 32 + cin) * 3 + ky) * 3 + kx];
+        __nv_bfloat16 *Bl = (__nv_bfloat16 *)(packed + pk_bl(l) + (t * 2 + ks) * 1024);
+        Bl[((n / 8) * 2 + k / 8) * 64 + (n % 8) * 8 + (k % 8)] = __float2bfloat16_rn(w);
+    }
+    float *bias = (float *)(packed + kPkBias);
+    for (int e = tid; e < 5 * 32; e += nthr) bias[e] = master[off_b(e / 32) + e % 32];
+    float *fc = (float *)(packed + kPkFc);
+    for (int e = tid; e < 33; e += nthr) fc[e] = master[kOffFw + e];
+}
+
+// ------------------------------------------------------------------ forward
+struct FwdParams {
+    const int16_t *z;
+    int H, W;
+    long long pitch;
+    const int64_t *centers;  // patch centres (post index) or null for the lattice
+    long long n;             // number of patches
+    int stride, Ws;          // lattice mode: patch i at post ((i / Ws)*stride, (i % Ws)*stride)
+    const unsigned char *packed;
+    float *out;              // n predicted visibility indices
+    unsigned char *save;     // optional: activations for the backward pass
+    int *status;             // optional: set to VS_ERR_TIMEOUT if an MMA wait gave up
+};
+
+// one implicit-GEMM tile: `nmma` MMAs accumulate into the TMEM accumulator,
+// then every thread reads its row (32 fp32).  Returns false on a timed-out wait.
+template <typename F>
+__device__ __forceinline__ bool gemm_tile(uint64_t *bar, uint32_t &phase, uint32_t tmem, int nmma,
+                                          F &&mma_desc, float *acc) {
+    // inputs written by every thread are visible to the tensor core
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc_fence_after();
+        for (int i = 0; i < nmma; ++i) {
+            uint64_t ad, bd;
+            mma_desc(i, ad, bd);
+            umma(tmem, ad, bd, i > 0 ? 1u : 0u);
+        }
+        umma_commit(bar);
+    }
+    const bool ok = mbar_wait(bar, phase);
+    phase ^= 1u;
+    tc_fence_after();
+    const int warp = threadIdx.x >> 5;
+    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), acc);
+    tc_fence_before();
+    return ok;
+}
+
+__device__ __forceinline__ void store_row(unsigned char *dst, long long stride16, const uint32_t *w16) {
+    // 32 bf16 channels = 4 x 16 bytes; block cb goes to dst + cb*stride16
+#pragma unroll
+    for (int cb = 0; cb < 4; ++cb)
+        *(uint4 *)(dst + cb * stride16) = make_uint4(w16[cb * 4], w16[cb * 4 + 1], w16[cb * 4 + 2],
+                                                     w16[cb * 4 + 3]);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const FwdParams P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *sm = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    __shared__ uint64_t bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_red[4];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    unsigned char *Wp = sm + kSmW;
+    unsigned char *P2 = sm + kSmP2;
+    unsigned char *U = sm + kSmU;
+    unsigned char *P3 = U + kP3Off, *P4 = U + kP4Off, *P5 = U + kP5Off;
+    __nv_bfloat16 *pb = (__nv_bfloat16 *)(sm + kSmPatch);
+    float *gap = (float *)(sm + kSmGap);
+
+    // ---- one-time set-up: weights, zeroed planes, barrier, tensor memory
+    for (int i = tid; i < kPackedBytes / 16; i += kThreads)
+        ((uint4 *)Wp)[i] = ((const uint4 *)P.packed)[i];
+    for (int i = tid; i < kP2Bytes / 16; i += kThreads) ((uint4 *)P2)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < kPatchBytes / 16; i += kThreads) ((uint4 *)pb)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) mbar_init(&bar, 1);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+                         smem_u32(&s_tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    uint32_t phase = 0;
+    bool ok = true;
+    const float *bias = (const float *)(Wp + kPkBias);
+    const float *fc = (const float *)(Wp + kPkFc);
+    const uint32_t sW = smem_u32(Wp), sP2 = smem_u32(P2), sU = smem_u32(U);
+    const uint32_t sP3 = sU + kP3Off, sP4 = sU + kP4Off, sP5 = sU + kP5Off;
+
+    for (long long pi = blockIdx.x; pi < P.n; pi += gridDim.x) {
+        // ---- patch: clamp to the grid, mean (exact integer sum), normalise
+        long long cpost;
+        if (P.centers) cpost = P.centers[pi];
+        else cpost = (pi / P.Ws) * (long long)P.stride * P.W + (pi % P.Ws) * (long long)P.stride;
+        const int cy = (int)(cpost / P.W), cx = (int)(cpost % P.W);
+        int sum = 0;
+        for (int e = tid; e < kPatch * kPatch; e += kThreads) {
+            const int r = min(max(cy - 32 + e / kPatch, 0), P.H - 1);
+            const int c = min(max(cx - 32 + e % kPatch, 0), P.W - 1);
+            sum += P.z[(long long)r * P.pitch + c];
+        }
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) s_red[warp] = sum;
+        __syncthreads();
+        const float mean = (float)(s_red[0] + s_red[1] + s_red[2] + s_red[3]) / (float)(kPatch * kPatch);
+        unsigned char *sv = P.save ? P.save + pi * (long long)kSaveBytesTotal : nullptr;
+        for (int e = tid; e < kPatch * kPatch; e += kThreads) {
+            const int rr = e / kPatch, cc = e % kPatch;
+            const int r = min(max(cy - 32 + rr, 0), P.H - 1);
+            const int c = min(max(cx - 32 + cc, 0), P.W - 1);
+            const __nv_bfloat16 x = __float2bfloat16_rn(((float)P.z[(long long)r * P.pitch + c] - mean) / 1000.0f);
+            pb[(rr + 1) * 67 + (cc + 1)] = x;
+            if (sv) ((__nv_bfloat16 *)(sv + kSvInput))[e] = x;
+        }
+        __syncthreads();
+
+        // ---- conv1: explicit im2col (1152 rows x 16 K), 9 M-tiles of one MMA each
+        for (int m = tid; m < 1152; m += kThreads) {
+            const int y = m / 34, x = m % 34;
+            uint32_t w[8];
+            if (y < 33 && x < 33) {
+                __nv_bfloat16 t[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) t[k] = __float2bfloat16_rn(0.f);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) t[k] = pb[(2 * y + k / 3) * 67 + (2 * x + k % 3)];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) w[k] = *(uint32_t *)&t[2 * k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) w[k] = 0;
+            }
+            unsigned char *row = U + (m / 8) * 256 + (m % 8) * 16;
+            *(uint4 *)row = make_uint4(w[0], w[1], w[2], w[3]);
+            *(uint4 *)(row + 128) = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+        float acc[32];
+        for (int mt = 0; mt < 9; ++mt) {
+            ok &= gemm_tile(&bar, phase, tmem, 1, [&](int, uint64_t &ad, uint64_t &bd) {
+                ad = sdesc(sU + mt * 4096, 128, 256);
+                bd = sdesc(sW + kPkB1, 128, 256);
+            }, acc);
+            const int m = mt * 128 + tid, y = m / 34, x = m % 34;
+            if (y < 33 && x < 33) {
+                uint32_t w16[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    w16[c] = pack_bf16x2(fmaxf(acc[2 * c] + bias[2 * c], 0.f),
+                                         fmaxf(acc[2 * c + 1] + bias[2 * c + 1], 0.f));
+                const int plane = ((y & 1) << 1) | (x & 1);
+                const int pix = ((y >> 1) + 1) * 18 + (x >> 1) + 1;
+                store_row(P2 + ((long long)plane * kPln2 + pix) * 16, 4LL * kPln2 * 16, w16);
+                if (sv) store_row(sv + kSvA1 + (y * 33 + x) * 64, 16, w16);
+            }
+        }
+        // A1 is dead: clear the region that now holds the next layers' planes
+        __syncthreads();
+        for (int i = tid; i < kUBytes / 16; i += kThreads) ((uint4 *)U)[i] = make_uint4(0, 0, 0, 0);
+
+        // ---- conv2..conv5: 9 taps x 2 K-steps per tile, descriptors into planes
+        // conv2: 3 tiles, input P2 (pitch 18, plane 324), output P3 (pitch 10)
+        for (int mt = 0; mt < 3; ++mt) {
+            ok &= gemm_tile(&bar, phase, tmem, 18, [&](int i, uint64_t &ad, uint64_t &bd) {
+                const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
+                const int plane = ((ky != 1) << 1) | (kx != 1);
+                const int shift = (ky != 0 ? 18 : 0) + (kx != 0 ? 1 : 0);
+                ad = sdesc(sP2 + ((2 * ks * 4 + plane) * kPln2 + mt * 128 + shift) * 16, 4 * kPln2 * 16, 128);
+                bd = sdesc(sW + pk_bl(1) + (t * 2 + ks) * 1024, 128, 256);
+            }, acc);
+            const int m = mt * 128 + tid, y = m / 18, x = m % 18;
+            if (y < 17 && x < 17) {
+                uint32_t w16[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    w16[c] = pack_bf16x2(fmaxf(acc[2 * c] + bias[32 + 2 * c], 0.f),
+                                         fmaxf(acc[2 * c + 1] + bias[32 + 2 * c + 1], 0.f));
+                const int plane = ((y & 1) << 1) | (x & 1);
+                const int pix = ((y >> 1) + 1) * 10 + (x >> 1) + 1;
+                store_row(P3 + ((long long)plane * kPln3 + pix) * 16, 4LL * kPln3 * 16, w16);
+                if (sv) store_row(sv + kSvA2 + (y * 17 + x) * 64, 16, w16);
+            }
+        }
+        // conv3: 1 tile, input P3 (pitch 10, plane 100), output P4 (pitch 6)
+        {
+            ok &= gemm_tile(&bar, phase, tmem, 18, [&](int i, uint64_t &ad, uint64_t &bd) {
+                const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
+                const int plane = ((ky != 1) << 1) | (kx != 1);
+                const int shift = (ky != 0 ? 10 : 0) + (kx != 0 ? 1 : 0);
+                ad = sdesc(sP3 + ((2 * ks * 4 + plane) * kPln3 + shift) * 16, 4 * kPln3 * 16, 128);
+                bd = sdesc(sW + pk_bl(2) + (t * 2 + ks) * 1024, 128, 256);
+            }, acc);
+            const int m = tid, y = m / 10, x = m % 10;
+            if (y < 9 && x < 9) {
+                uint32_t w16[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    w16[c] = pack_bf16x2(fmaxf(acc[2 * c] + bias[64 + 2 * c], 0.f),
+                                         fmaxf(acc[2 * c + 1] + bias[64 + 2 * c + 1], 0.f));
+                const int plane = ((y & 1) << 1) | (x & 1);
+                const int pix = ((y >> 1) + 1) * 6 + (x >> 1) + 1;
+                store_row(P4 + ((long long)plane * kPln4 + pix) * 16, 4LL * kPln4 * 16, w16);
+                if (sv) store_row(sv + kSvA3 + (y * 9 + x) * 64, 16, w16);
+            }
+        }
+        // conv4: 1 tile, input P4 (pitch 6, plane 36), output P5 (stride-1 plane, pitch 7)
+        {
+            ok &= gemm_tile(&bar, phase, tmem, 18, [&](int i, uint64_t &ad, uint64_t &bd) {
+                const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
+                const int plane = ((ky != 1) << 1) | (kx != 1);
+                const int shift = (ky != 0 ? 6 : 0) + (kx != 0 ? 1 : 0);
+                ad = sdesc(sP4 + ((2 * ks * 4 + plane) * kPln4 + shift) * 16, 4 * kPln4 * 16, 128);
+                bd = sdesc(sW + pk_bl(3) + (t * 2 + ks) * 1024, 128, 256);
+            }, acc);
+            const int m = tid, y = m / 6, x = m % 6;
+            if (y < 5 && x < 5) {
+                uint32_t w16[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    w16[c] = pack_bf16x2(fmaxf(acc[2 * c] + bias[96 + 2 * c], 0.f),
+                                         fmaxf(acc[2 * c + 1] + bias[96 + 2 * c + 1], 0.f));
+                const int pix = (y + 1) * 7 + (x + 1);
+                store_row(P5 + (long long)pix * 16, (long long)kPln5 * 16, w16);
+                if (sv) store_row(sv + kSvA4 + (y * 5 + x) * 64, 16, w16);
+            }
+        }
+        // conv5 (stride 1): 1 tile, input P5 (pitch 7, plane 49), output -> pooling buffer
+        {
+            ok &= gemm_tile(&bar, phase, tmem, 18, [&](int i, uint64_t &ad, uint64_t &bd) {
+                const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
+                ad = sdesc(sP5 + ((2 * ks) * kPln5 + ky * 7 + kx) * 16, kPln5 * 16, 128);
+                bd = sdesc(sW + pk_bl(4) + (t * 2 + ks) * 1024, 128, 256);
+            }, acc);
+            const int m = tid, y = m / 7, x = m % 7;
+            if (y < 5 && x < 5) {
+                uint32_t w16[16];
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    gap[(y * 5 + x) * 32 + c] = bf16_round(fmaxf(acc[c] + bias[128 + c], 0.f));
+                if (sv) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) w16[c] = pack_bf16x2(gap[(y * 5 + x) * 32 + 2 * c],
+                                                                      gap[(y * 5 + x) * 32 + 2 * c + 1]);
+                    store_row(sv + kSvA5 + (y * 5 + x) * 64, 16, w16);
+                }
+            }
+        }
+        __syncthreads();
+        // ---- global average pool, fc, sigmoid (fixed summation order)
+        if (tid < 32) {
+            float g = 0.f;
+            for (int r = 0; r < 25; ++r) g += gap[r * 32 + tid];
+            g *= (1.0f / 25.0f);
+            float t = g * fc[tid];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (tid == 0) {
+                const float logit = t + fc[32];
+                const float yv = 1.0f / (1.0f + expf(-logit));
+                P.out[pi] = yv;
+                if (sv) {
+                    float *hd = (float *)(sv + kSvHead);
+                    hd[32] = logit;
+                    hd[33] = yv;
+                }
+            }
+            if (sv) ((float *)(sv + kSvHead))[tid] = g;
+        }
+        // a timed-out tensor-core wait stops the CTA (uniformly) after this patch
+        if (!__syncthreads_and(ok)) break;
+    }
+    if (!ok && P.status && threadIdx.x == 0) atomicExch(P.status, VS_ERR_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+}
+
+// ------------------------------------------------------------------ training
+// Backward pass, layer by layer over a batch (the forward kernel saved every
+// activation).  Each CTA keeps its partial weight gradient in shared memory
+// over the patches it owns and adds it to the global gradient once, so the
+// global atomics do not scale with the batch.  Products take bf16-valued
+// operands (saved activations, bf16-rounded weights, bf16-rounded
+// pre-activation gradients) and accumulate in FP32 on the CUDA cores.
+constexpr int kBwdThreads = 256;
+
+struct LayerGeo {
+    int Hin, Win, Cin, Hout, Wout, stride;
+    int sv_in, sv_out;  // byte offsets of the layer's input / output in a save record
+};
+
+__host__ __device__ inline LayerGeo layer_geo(int l) {
+    const int hin[5] = {65, 33, 17, 9, 5}, hout[5] = {33, 17, 9, 5, 5};
+    const int svin[5] = {kSvInput, kSvA1, kSvA2, kSvA3, kSvA4};
+    const int svout[5] = {kSvA1, kSvA2, kSvA3, kSvA4, kSvA5};
+    LayerGeo g;
+    g.Hin = g.Win = hin[l];
+    g.Cin = l == 0 ? 1 : 32;
+    g.Hout = g.Wout = hout[l];
+    g.stride = l == 4 ? 1 : 2;
+    g.sv_in = svin[l];
+    g.sv_out = svout[l];
+    return g;
+}
+
+// dL/dlogit = sign(y - label) * y (1 - y) / B (L1 loss through the sigmoid);
+// fc gradients; dL/da5 = dL/dg / 25 on every pooled pixel.  One warp per patch.
+__global__ void k_cnn_head_bwd(const unsigned char *__restrict__ save, const float *__restrict__ labels,
+                               long long B, float inv_batch, const float *__restrict__ master,
+                               float *__restrict__ grads, float *__restrict__ da5,
+                               float *__restrict__ loss_sum) {
+    const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int c = threadIdx.x & 31;
+    if (b >= B) return;
+    const float *hd = (const float *)(save + b * (long long)kSaveBytesTotal + kSvHead);
+    const float y = hd[33], lab = labels[b];
+    const float sgn = (y > lab) ? 1.f : ((y < lab) ? -1.f : 0.f);
+    const float dlogit = sgn * y * (1.f - y) * inv_batch;
+    atomicAdd(&grads[kOffFw + c], dlogit * hd[c]);
+    if (c == 0) {
+        atomicAdd(&grads[kOffFw + 32], dlogit);
+        atomicAdd(loss_sum, fabsf(y - lab));
+    }
+    const float d = dlogit * master[kOffFw + c] * (1.0f / 25.0f);
+    for (int pix = 0; pix < 25; ++pix) da5[(b * 25 + pix) * 32 + c] = d;
+}
+
+__global__ void __launch_bounds__(kBwdThreads) k_cnn_conv_bwd(const unsigned char *__restrict__ save,
+                                                              long long B, int l,
+                                                              const float *__restrict__ da_out,
+                                                              const float *__restrict__ master,
+                                                              float *__restrict__ grads,
+                                                              float *__restrict__ da_in) {
+    extern __shared__ __align__(16) unsigned char smb[];
+    const LayerGeo G = layer_geo(l);
+    const int nW = 32 * G.Cin * 9;
+    const int nin = G.Hin * G.Win * G.Cin, nout = G.Hout * G.Wout * 32;
+    float *Wr = (float *)smb;                         // nW, bf16-rounded weights
+    float *dW = Wr + nW;                              // nW partial gradient
+    float *db = dW + nW;                              // 32
+    __nv_bfloat16 *ain = (__nv_bfloat16 *)(db + 32);  // nin
+    __nv_bfloat16 *dz = ain + ((nin + 7) & ~7);       // nout
+    const int tid = threadIdx.x;
+    for (int i = tid; i < nW; i += blockDim.x) {
+        Wr[i] = bf16_round(master[off_w(l) + i]);
+        dW[i] = 0.f;
+    }
+    if (tid < 32) db[tid] = 0.f;
+    __syncthreads();
+    const int s = G.stride;
+    for (long long b = blockIdx.x; b < B; b += gridDim.x) {
+        const unsigned char *rec = save + b * (long long)kSaveBytesTotal;
+        const __nv_bfloat16 *gin = (const __nv_bfloat16 *)(rec + G.sv_in);
+        const __nv_bfloat16 *gout = (const __nv_bfloat16 *)(rec + G.sv_out);
+        for (int i = tid; i < nin; i += blockDim.x) ain[i] = gin[i];
+        for (int i = tid; i < nout; i += blockDim.x) {
+            const float a = __bfloat162float(gout[i]);
+            dz[i] = __float2bfloat16_rn(a > 0.f ? da_out[b * nout + i] : 0.f);
+        }
+        __syncthreads();
+        if (tid < 32) {
+            float t = 0.f;
+            for (int p = 0; p < G.Hout * G.Wout; ++p) t += __bfloat162float(dz[p * 32 + tid]);
+            db[tid] += t;
+        }
+        // weight gradient: dW[cout][cin][ky][kx] += sum over output pixels
+        for (int o = tid; o < nW; o += blockDim.x) {
+            const int cout = o / (G.Cin * 9), rem = o - cout * (G.Cin * 9);
+            const int cin = rem / 9, tap = rem - cin * 9, ky = tap / 3, kx = tap - ky * 3;
+            float acc = 0.f;
+            for (int y = 0; y < G.Hout; ++y) {
+                const int iy = s * y + ky - 1;
+                if (iy < 0 || iy >= G.Hin) continue;
+                for (int x = 0; x < G.Wout; ++x) {
+                    const int ix = s * x + kx - 1;
+                    if (ix < 0 || ix >= G.Win) continue;
+                    acc += __bfloat162float(dz[(y * G.Wout + x) * 32 + cout]) *
+                           __bfloat162float(ain[(iy * G.Win + ix) * G.Cin + cin]);
+                }
+            }
+            dW[o] += acc;
+        }
+        // input gradient (not needed below the first layer)
+        if (da_in) {
+            for (int e = tid; e < nin; e += blockDim.x) {
+                const int ipix = e / G.Cin, cin = e - ipix * G.Cin;
+                const int iy = ipix / G.Win, ix = ipix - iy * G.Win;
+                float acc = 0.f;
+                for (int ky = 0; ky < 3; ++ky) {
+                    const int ty = iy + 1 - ky;
+                    if (ty < 0 || ty % s) continue;
+                    const int y = ty / s;
+                    if (y >= G.Hout) continue;
+                    for (int kx = 0; kx < 3; ++kx) {
+                        const int tx = ix + 1 - kx;
+                        if (tx < 0 || tx % s) continue;
+                        const int x = tx / s;
+                        if (x >= G.Wout) continue;
+                        const __nv_bfloat16 *dzp = dz + (y * G.Wout + x) * 32;
+                        const float *wp = Wr + cin * 9 + ky * 3 + kx;
+#pragma unroll 8
+                        for (int co = 0; co < 32; ++co) acc += __bfloat162float(dzp[co]) * wp[co * G.Cin * 9];
+                    }
+                }
+                da_in[b * nin + e] = acc;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < nW; i += blockDim.x) atomicAdd(&grads[off_w(l) + i], dW[i]);
+    if (tid < 32) atomicAdd(&grads[off_b(l) + tid], db[tid]);
+}
+
+__host__ __device__ inline size_t conv_bwd_smem(int l) {
+    const LayerGeo G = layer_geo(l);
+    const int nW = 32 * G.Cin * 9, nin = G.Hin * G.Win * G.Cin, nout = G.Hout * G.Wout * 32;
+    return (size_t)(2 * nW + 32) * 4 + (size_t)((nin + 7) & ~7) * 2 + (size_t)nout * 2 + 16;
+}
+
+// Adam (Kingma & Ba 2015) on the fp32 master weights; clears the gradients.
+__global__ void k_cnn_adam(float *__restrict__ w, float *__restrict__ g, float *__restrict__ m,
+                           float *__restrict__ v, int n, float lr, float b1, float b2, float eps,
+                           float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    g[i] = 0.f;
+}
+
+}  // namespace cnn
+}  // namespace vs
+
+using namespace vs;
+
+extern "C" int vs_cnn_param_count(void) { return cnn::kNParams; }
+extern "C" size_t vs_cnn_packed_bytes(void) { return (size_t)cnn::kPackedBytes; }
+extern "C" size_t vs_cnn_save_bytes(void) { return (size_t)cnn::kSaveBytesTotal; }
+
+extern "C" int vs_cnn_pack(const float *master, void *packed, vs_stream_t st) {
+    if (!master || !packed || ((uintptr_t)packed & 15)) return VS_ERR_ARG;
+    int rc = check_device();
+    if (rc) return rc;
+    cnn::k_cnn_pack<<<64, 256, 0, (cudaStream_t)st>>>(master, (unsigned char *)packed);
+    VS_CUDA_TRY(cudaGetLastError());
+    return VS_OK;
+}
+
+static int cnn_forward_launch(vs_grid g, const int64_t *centers, int64_t n, int32_t stride,
+                              const void *packed, float *out, void *save, int32_t *status,
+                              vs_stream_t st) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!packed || !out || ((uintptr_t)packed & 15) || (save && ((uintptr_t)save & 15)))
+        return VS_ERR_ARG;
+    if (n < 0) return VS_ERR_RANGE;
+    if (n == 0) return VS_OK;
+    if ((rc = check_device())) return rc;
+    cnn::FwdParams P;
+    P.z = g.z; P.H = g.H; P.W = g.W; P.pitch = g.pitch;
+    P.centers = centers; P.n = n; P.stride = stride;
+    P.Ws = stride > 0 ? (g.W + stride - 1) / stride : 1;
+    P.packed = (const unsigned char *)packed; P.out = out;
+    P.save = (unsigned char *)save; P.status = status;
+    int dev = 0, sms = 0;
+    VS_CUDA_TRY(cudaGetDevice(&dev));
+    VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    VS_CUDA_TRY(cudaFuncSetAttribute(cnn::k_cnn_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     cnn::kSmemBytes));
+    const long long grid = std::min<long long>(n, (long long)sms);
+    cnn::k_cnn_forward<<<(unsigned)grid, cnn::kThreads, cnn::kSmemBytes, (cudaStream_t)st>>>(P);
+    VS_CUDA_TRY(cudaGetLastError());
+    return VS_OK;
+}
+
+extern "C" int vs_cnn_forward(vs_grid g, const int64_t *centers, int64_t n, const void *packed,
+                              float *out, void *save, int32_t *status, vs_stream_t st) {
+    if (!centers && n > 0) return VS_ERR_ARG;
+    return cnn_forward_launch(g, centers, n, 0, packed, out, save, status, st);
+}
+
+extern "C" int vs_cnn_score_lattice(vs_grid g, int32_t stride, const void *packed, float *score_out,
+                                    int32_t *status, vs_stream_t st) {
+    if (stride < 1) return VS_ERR_RANGE;
+    if (g.H < 1 || g.W < 1) return VS_ERR_RANGE;
+    const int64_t Hs = (g.H + stride - 1) / stride, Ws = (g.W + stride - 1) / stride;
+    return cnn_forward_launch(g, nullptr, Hs * Ws, stride, packed, score_out, nullptr, status, st);
+}
+
+// per patch: dL/da of layers 5, 4, 3, 2, 1 (fp32)
+static size_t cnn_da_floats(int l) {  // gradient w.r.t. the output of layer l
+    const int h[5] = {33, 17, 9, 5, 5};
+    return (size_t)h[l] * h[l] * 32;
+}
+
+extern "C" size_t vs_cnn_backward_workspace(int64_t B) {
+    if (B < 0) return 0;
+    size_t per = 0;
+    for (int l = 0; l < 5; ++l) per += cnn_da_floats(l);
+    return (size_t)B * per * 4 + 256;
+}
+
+extern "C" int vs_cnn_backward(const void *save, const float *labels, int64_t B, const float *master,
+                               float *grads, float *loss_sum, void *ws, size_t ws_bytes,
+                               vs_stream_t st) {
+    if (!save || !labels || !master || !grads || !loss_sum || ((uintptr_t)save & 15)) return VS_ERR_ARG;
+    if (B < 1) return VS_ERR_RANGE;
+    if (!ws || ws_bytes < vs_cnn_backward_workspace(B)) return VS_ERR_WS;
+    int rc = check_device();
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)st;
+    float *da[5];
+    float *p = (float *)ws;
+    for (int l = 0; l < 5; ++l) { da[l] = p; p += (size_t)B * cnn_da_floats(l); }
+    const unsigned char *sv = (const unsigned char *)save;
+    cnn::k_cnn_head_bwd<<<(unsigned)((B * 32 + 255) / 256), 256, 0, s>>>(sv, labels, B, 1.0f / (float)B,
+                                                                          master, grads, da[4], loss_sum);
+    VS_CUDA_TRY(cudaGetLastError());
+    int dev = 0, sms = 0;
+    VS_CUDA_TRY(cudaGetDevice(&dev));
+    VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    for (int l = 4; l >= 0; --l) {
+        const size_t smem = cnn::conv_bwd_smem(l);
+        VS_CUDA_TRY(cudaFuncSetAttribute(cnn::k_cnn_conv_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const unsigned grid = (unsigned)std::min<long long>(B, (long long)sms);
+        cnn::k_cnn_conv_bwd<<<grid, cnn::kBwdThreads, smem, s>>>(sv, B, l, da[l], master, grads,
+                                                                  l > 0 ? da[l - 1] : nullptr);
+        VS_CUDA_TRY(cudaGetLastError());
+    }
+    return VS_OK;
+}
+
+extern "C" int vs_cnn_adam(float *master, float *grads, float *m, float *v, int64_t step, float lr,
+                           float beta1, float beta2, float eps, vs_stream_t st) {
+    if (!master || !grads || !m || !v) return VS_ERR_ARG;
+    if (step < 1 || !(lr > 0.f)) return VS_ERR_RANGE;
+    int rc = check_device();
+    if (rc) return rc;
+    const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
+    const int n = cnn::kNParams;
+    cnn::k_cnn_adam<<<(n + 255) / 256, 256, 0, (cudaStream_t)st>>>(master, grads, m, v, n, lr, beta1,
+                                                                   beta2, eps, c1, c2);
+    VS_CUDA_TRY(cudaGetLastError());
+    return VS_OK;
+}

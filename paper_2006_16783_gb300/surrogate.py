@@ -1,0 +1,152 @@
+"""Learned candidate proposal: labels, training loop and proposal on top of
+the C-ABI kernels (every step of the computation runs in libvshed).
+
+The label of a post is its exact visibility index at ROI R (Sec.
+"Definitions": the fraction of the receivers within the ROI that are
+visible), here the area of its ray-sweep viewshed (vs_viewshed) over the
+number of lattice points of the disc inside the grid.  The network is
+trained by Adam on the mean L1 error (vs_cnn_forward with saved activations,
+vs_cnn_backward, vs_cnn_adam, vs_cnn_pack).
+"""
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import vshed as V
+
+
+def disc_in_grid(posts, H, W, R):
+    """|{(dx,dy): dx^2+dy^2 <= R^2, post+(dx,dy) inside the grid}| per post."""
+    dev = posts.device
+    dy = torch.arange(-R, R + 1, device=dev)
+    hw = torch.sqrt((R * R - dy * dy).double()).floor().long()
+    # exact integer square root
+    hw = torch.where((hw + 1) * (hw + 1) <= R * R - dy * dy, hw + 1, hw)
+    hw = torch.where(hw * hw > R * R - dy * dy, hw - 1, hw)
+    out = torch.empty(posts.numel(), dtype=torch.int64, device=dev)
+    for i in range(0, posts.numel(), 1 << 18):
+        p = posts[i:i + (1 << 18)]
+        cy, cx = (p // W)[:, None], (p % W)[:, None]
+        y = cy + dy[None, :]
+        lo = torch.clamp(cx - hw[None, :], min=0)
+        hi = torch.clamp(cx + hw[None, :], max=W - 1)
+        n = torch.clamp(hi - lo + 1, min=0) * ((y >= 0) & (y < H))
+        out[i:i + (1 << 18)] = n.sum(1)
+    return out
+
+
+def exact_vix(g, posts, R, ht, hr, chunk=100000):
+    """Exact visibility index of every listed post (fp32 in [0, 1])."""
+    out = torch.empty(posts.numel(), dtype=torch.float32, device=posts.device)
+    bm = torch.empty((min(chunk, posts.numel()), 2 * R + 1, V.words_per_row(R)), dtype=torch.int32,
+                     device=posts.device)
+    area = torch.empty(min(chunk, posts.numel()), dtype=torch.int32, device=posts.device)
+    den = disc_in_grid(posts, g.H, g.W, R)
+    for i in range(0, posts.numel(), chunk):
+        p = posts[i:i + chunk].contiguous()
+        n = p.numel()
+        V.viewshed(g, R, ht, hr, p, bm=bm[:n], area=area[:n])
+        out[i:i + n] = area[:n].float() / den[i:i + n].float()
+    return out
+
+
+def sample_posts(H, W, n, margin, seed, device):
+    """n posts drawn uniformly at least ``margin`` from every edge."""
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    y = torch.randint(margin, H - margin, (n,), generator=gen)
+    x = torch.randint(margin, W - margin, (n,), generator=gen)
+    return (y * W + x).to(device)
+
+
+def init_master(seed=0, device="cuda"):
+    """He-normal conv weights, zero biases, small fc: the flat fp32 layout."""
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    parts = []
+    for l, cin in enumerate([1, 32, 32, 32, 32]):
+        parts.append(torch.randn(32 * cin * 9, generator=gen) * math.sqrt(2.0 / (9 * cin)))
+        parts.append(torch.zeros(32))
+    parts.append(torch.randn(32, generator=gen) * math.sqrt(1.0 / 32))
+    parts.append(torch.zeros(1))
+    w = torch.cat(parts).float().to(device)
+    assert w.numel() == V.cnn_param_count()
+    return w
+
+
+class Trainer:
+    """Mini-batch Adam on (grid, post, label) triples drawn from several grids."""
+
+    def __init__(self, master, batch=512, lr=2e-3):
+        self.master = master
+        self.batch = batch
+        self.lr = lr
+        dev = master.device
+        self.grads = torch.zeros_like(master)
+        self.m = torch.zeros_like(master)
+        self.v = torch.zeros_like(master)
+        self.packed = V.cnn_pack(master)
+        self.save = torch.empty(batch * V.cnn_save_bytes(), dtype=torch.uint8, device=dev)
+        self.out = torch.empty(batch, dtype=torch.float32, device=dev)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.ws = None
+        self.step = 0
+
+    def train_step(self, g, posts, labels):
+        B = posts.numel()
+        V.cnn_forward(g, posts, self.packed, out=self.out[:B], save=self.save[:B * V.cnn_save_bytes()])
+        self.ws = V.cnn_backward(self.save[:B * V.cnn_save_bytes()], labels, self.master, self.grads,
+                                 self.loss, ws=self.ws)
+        self.step += 1
+        lr = self.lr
+        V.cnn_adam(self.master, self.grads, self.m, self.v, self.step, lr=lr)
+        V.cnn_pack(self.master, self.packed)
+
+    def fit(self, data, epochs, seed=0, lr_decay=0.5, log=None):
+        """data: list of (grid, posts, labels).  Returns the mean training
+        loss of the last epoch."""
+        gen = torch.Generator(device="cpu").manual_seed(seed)
+        last = None
+        base_lr = self.lr
+        for ep in range(epochs):
+            self.lr = base_lr * (lr_decay ** ep)
+            self.loss.zero_()
+            seen = 0
+            t0 = time.time()
+            order = []
+            for gi, (g, posts, labels) in enumerate(data):
+                perm = torch.randperm(posts.numel(), generator=gen)
+                for i in range(0, posts.numel() - self.batch + 1, self.batch):
+                    order.append((gi, perm[i:i + self.batch]))
+            sel = torch.randperm(len(order), generator=gen).tolist()
+            for j in sel:
+                gi, idx = order[j]
+                g, posts, labels = data[gi]
+                idx = idx.to(posts.device)
+                self.train_step(g, posts[idx].contiguous(), labels[idx].contiguous())
+                seen += idx.numel()
+            last = float(self.loss.item()) / max(seen, 1)
+            if log:
+                log("epoch %d: mean |y - label| = %.4f (%.1f s)" % (ep, last, time.time() - t0))
+        self.lr = base_lr
+        return last
+
+    def predict(self, g, posts, chunk=1 << 20):
+        out = torch.empty(posts.numel(), dtype=torch.float32, device=posts.device)
+        for i in range(0, posts.numel(), chunk):
+            V.cnn_forward(g, posts[i:i + chunk].contiguous(), self.packed, out=out[i:i + chunk])
+        return out
+
+
+def sampled_vix_fraction(g, posts, R, ht, hr, S, seed):
+    """The plain method's estimate of the same quantity: vix count / S,
+    evaluated only at the listed posts (one vs_vix pass over the grid)."""
+    v = V.vix(g, R, ht, hr, S, seed)
+    return v.reshape(-1)[posts].float() / float(S)
+
+
+def propose(g, packed, stride, block, k, score=None):
+    """Candidate posts from the network's scores on a stride lattice:
+    top-k per block (vs_cnn_score_lattice then vs_findmax_f32)."""
+    score = V.cnn_score_lattice(g, stride, packed, out=score)
+    return V.findmax_f32(score, g.H, g.W, stride, block, k), score

@@ -46,6 +46,16 @@ SIGNATURES = {
     "vs_site": (ctypes.c_int, [P, P, i64, i32, i32, i32, i32, f64, P, P, P, P, P, sz, P]),
     "vs_site_gains": (ctypes.c_int, [P, P, i64, i32, i32, i32, P, P, P]),
     "vs_site_noalloc": (ctypes.c_int, [P, P, i64, i32, i32, i32, i32, f64, P, P, P, P, P]),
+    "vs_cnn_param_count": (ctypes.c_int, []),
+    "vs_cnn_packed_bytes": (sz, []),
+    "vs_cnn_save_bytes": (sz, []),
+    "vs_cnn_pack": (ctypes.c_int, [P, P, P]),
+    "vs_cnn_forward": (ctypes.c_int, [vs_grid, P, i64, P, P, P, P, P]),
+    "vs_cnn_score_lattice": (ctypes.c_int, [vs_grid, i32, P, P, P, P]),
+    "vs_cnn_backward_workspace": (sz, [i64]),
+    "vs_cnn_backward": (ctypes.c_int, [P, P, i64, P, P, P, P, sz, P]),
+    "vs_cnn_adam": (ctypes.c_int, [P, P, P, P, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, P]),
 }
 
 
@@ -222,3 +232,61 @@ def site_gains(bm, cand, H, W, R, cum, out=None):
     _check("vs_site_gains", lib().vs_site_gains(_ptr(bm), _ptr(cand), n, H, W, R, _ptr(cum), _ptr(out),
                                                 _stream()))
     return out
+
+
+# ------------------------------------------------------------------ learned proposal
+def cnn_param_count():
+    return lib().vs_cnn_param_count()
+
+
+def cnn_pack(master, packed=None):
+    """fp32 master parameters (CUDA, cnn_param_count() values) -> packed operands."""
+    _need_cuda(master)
+    assert master.dtype == torch.float32 and master.numel() == cnn_param_count()
+    if packed is None:
+        packed = torch.empty(lib().vs_cnn_packed_bytes(), dtype=torch.uint8, device=master.device)
+    _check("vs_cnn_pack", lib().vs_cnn_pack(_ptr(master), _ptr(packed), _stream()))
+    return packed
+
+
+def cnn_forward(g, centers, packed, out=None, save=None, status=None):
+    """Predicted visibility index of the patches centred on ``centers``."""
+    _need_cuda(centers, packed)
+    n = centers.numel()
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=centers.device)
+    _check("vs_cnn_forward", lib().vs_cnn_forward(g.c(), _ptr(centers), n, _ptr(packed), _ptr(out),
+                                                  _ptr(save), _ptr(status), _stream()))
+    return out
+
+
+def cnn_save_bytes():
+    return lib().vs_cnn_save_bytes()
+
+
+def cnn_score_lattice(g, stride, packed, out=None, status=None):
+    """Scores on the lattice of posts (i*stride, j*stride): [ceil(H/s), ceil(W/s)]."""
+    Hs, Ws = (g.H + stride - 1) // stride, (g.W + stride - 1) // stride
+    if out is None:
+        out = torch.empty((Hs, Ws), dtype=torch.float32, device=g.storage.device)
+    _check("vs_cnn_score_lattice", lib().vs_cnn_score_lattice(g.c(), stride, _ptr(packed), _ptr(out),
+                                                              _ptr(status), _stream()))
+    return out
+
+
+def cnn_backward(save, labels, master, grads, loss_sum, ws=None):
+    """Accumulate the batch's gradients (see vs_cnn_backward)."""
+    _need_cuda(save, labels, master, grads, loss_sum)
+    B = labels.numel()
+    wsb = lib().vs_cnn_backward_workspace(B)
+    if ws is None or ws.numel() < wsb:
+        ws = torch.empty(wsb, dtype=torch.uint8, device=labels.device)
+    _check("vs_cnn_backward", lib().vs_cnn_backward(_ptr(save), _ptr(labels), B, _ptr(master), _ptr(grads),
+                                                    _ptr(loss_sum), _ptr(ws), wsb, _stream()))
+    return ws
+
+
+def cnn_adam(master, grads, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    _need_cuda(master, grads, m, v)
+    _check("vs_cnn_adam", lib().vs_cnn_adam(_ptr(master), _ptr(grads), _ptr(m), _ptr(v), step, lr, beta1,
+                                            beta2, eps, _stream()))

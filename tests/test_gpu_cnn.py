@@ -1,0 +1,130 @@
+"""The learned proposal's tensor-core forward pass against the numpy oracle
+(fp64 products on the same bf16-rounded inputs and weights)."""
+import numpy as np
+import pytest
+import torch
+
+from synth import terrain as T
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_16783_gb300 import _build
+    _build.build()
+    import paper_2006_16783_gb300 as V
+    return V
+
+
+def _params(seed):
+    from oracle import cnn_oracle as C
+    p = C.init_params(seed)
+    rng = np.random.default_rng(seed + 100)
+    for l in range(5):
+        p["b%d" % l] = rng.normal(0, 0.05, 32)
+    p["fb"] = np.array([0.1])
+    return p
+
+
+def _bf16_close(got, want, ulps=3):
+    """|got - want| within a few bf16 ulps of the larger magnitude."""
+    scale = np.maximum(np.abs(want), np.abs(got))
+    return np.abs(got - want) <= ulps * scale * 2.0 ** -8 + 1e-6
+
+
+def test_cnn_forward_matches_oracle(V):
+    from oracle import cnn_oracle as C
+    H, W = 150, 170
+    z = T.spectral_fbm(H, W, 0.8, 77, 0, 1500).numpy()
+    g = V.Grid.from_tensor(torch.as_tensor(z), "cuda")
+    p = _params(3)
+    master = torch.as_tensor(C.flatten_params(p)).cuda()
+    packed = V.cnn_pack(master)
+    pts = [(75, 85), (0, 0), (H - 1, W - 1), (5, 160), (140, 3), (40, 100), (100, 40), (64, 64)]
+    cen = torch.tensor([y * W + x for y, x in pts], dtype=torch.int64, device="cuda")
+    save = torch.zeros(len(pts) * V.cnn_save_bytes(), dtype=torch.uint8, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    y = V.cnn_forward(g, cen, packed, save=save, status=status).cpu().numpy()
+    assert int(status.item()) == 0
+    x0 = np.stack([C.normalize_patch(C.extract_patch(z, cy, cx)) for cy, cx in pts])
+    want, (cache, a5, gg, logit) = C.forward(p, x0, keep=True)
+    assert np.all(np.abs(y - want) < 5e-3), (y, want)
+    # layer-by-layer: the saved activations (bf16, [y][x][c]) against the oracle's
+    sv = save.cpu().numpy().reshape(len(pts), -1)
+    offs = [0, 33 * 33 * 64, 33 * 33 * 64 + 17 * 17 * 64, 33 * 33 * 64 + 17 * 17 * 64 + 81 * 64,
+            33 * 33 * 64 + 17 * 17 * 64 + 81 * 64 + 25 * 64]
+    sizes = [33, 17, 9, 5, 5]
+    for l in range(5):
+        n = sizes[l]
+        raw = sv[:, offs[l]:offs[l] + n * n * 64].copy().view(np.uint16).astype(np.uint32) << 16
+        got = raw.view(np.float32).reshape(len(pts), n, n, 32)
+        nxt = cache[l + 1][0] if l < 4 else a5
+        want_a = nxt.transpose(0, 2, 3, 1)
+        close = _bf16_close(got, want_a)
+        assert close.mean() > 0.995, (l, close.mean())
+
+
+def test_cnn_lattice_matches_centres(V):
+    from oracle import cnn_oracle as C
+    H, W, s = 90, 130, 16
+    z = T.spectral_fbm(H, W, 0.8, 5, 0, 800).numpy()
+    g = V.Grid.from_tensor(torch.as_tensor(z), "cuda")
+    master = torch.as_tensor(C.flatten_params(_params(8))).cuda()
+    packed = V.cnn_pack(master)
+    lat = V.cnn_score_lattice(g, s, packed).cpu().numpy()
+    Hs, Ws = lat.shape
+    cen = torch.tensor([(i * s) * W + j * s for i in range(Hs) for j in range(Ws)], dtype=torch.int64,
+                       device="cuda")
+    y = V.cnn_forward(g, cen, packed).cpu().numpy().reshape(Hs, Ws)
+    assert np.array_equal(lat, y)
+
+
+def test_cnn_backward_matches_oracle(V):
+    """Gradients of the batch L1 loss, per parameter tensor, against the
+    oracle's fp64 backward on the same bf16-rounded operands."""
+    from oracle import cnn_oracle as C
+    H, W = 200, 210
+    z = T.spectral_fbm(H, W, 0.8, 91, 0, 1200).numpy()
+    g = V.Grid.from_tensor(torch.as_tensor(z), "cuda")
+    p = _params(11)
+    rng = np.random.default_rng(4)
+    pts = [(int(a), int(b)) for a, b in zip(rng.integers(0, H, 12), rng.integers(0, W, 12))]
+    labels = rng.random(len(pts)).astype(np.float32)
+    master = torch.as_tensor(C.flatten_params(p)).cuda()
+    packed = V.cnn_pack(master)
+    cen = torch.tensor([y * W + x for y, x in pts], dtype=torch.int64, device="cuda")
+    save = torch.zeros(len(pts) * V.cnn_save_bytes(), dtype=torch.uint8, device="cuda")
+    V.cnn_forward(g, cen, packed, save=save)
+    grads = torch.zeros_like(master)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    V.cnn_backward(save, torch.as_tensor(labels).cuda(), master, grads, loss)
+    gg = C.unflatten_params(grads.cpu().numpy())
+    x0 = np.stack([C.normalize_patch(C.extract_patch(z, cy, cx)) for cy, cx in pts])
+    want_loss, want = C.loss_and_grads(p, x0, labels.astype(np.float64))
+    assert abs(loss.item() / len(pts) - want_loss) < 5e-3
+    for k in want:
+        a, b = gg[k].ravel(), want[k].ravel()
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+        assert rel < 3e-2, (k, rel)
+
+
+def test_cnn_adam_step(V):
+    from oracle import cnn_oracle as C
+    n = V.cnn_param_count()
+    rng = np.random.default_rng(0)
+    w = rng.normal(size=n).astype(np.float32)
+    gr = rng.normal(size=n).astype(np.float32)
+    tw, tg = torch.as_tensor(w).cuda(), torch.as_tensor(gr).cuda()
+    m, v = torch.zeros_like(tw), torch.zeros_like(tw)
+    for step in (1, 2):
+        tg.copy_(torch.as_tensor(gr))
+        V.cnn_adam(tw, tg, m, v, step, lr=1e-2)
+    pw = {"a": w.astype(np.float64)}
+    st = {}
+    for step in (1, 2):
+        C.adam_step(pw, {"a": gr.astype(np.float64)}, st, lr=1e-2)
+    assert np.allclose(tw.cpu().numpy(), pw["a"], atol=1e-5)
+    assert float(tg.abs().max()) == 0.0
