@@ -209,6 +209,91 @@ def oracle_sample(z_host, w, budget_s=20.0, threads=None):
     return total, desc, threads
 
 
+# ------------------------------------------------------------------ learned proposal
+def run_surrogate(V, w, g, pipe, covered_plain, args, dev):
+    from paper_2006_16783_gb300 import surrogate as S
+    t0 = time.perf_counter()
+    # training terrain: the same recipe with another seed (the bench terrain is held out)
+    wtr = WL.scaled(w, w.H, w.W, name=w.name + "_train", seed=w.seed + 7)
+    ztr = wtr.make_terrain(dev)
+    ztr_s, _ = WL.terrain.pad_pitch(ztr, 8)
+    del ztr
+    gtr = V.Grid(ztr_s, w.W)
+    posts = S.sample_posts(w.H, w.W, args.train_posts, 32, 11, dev)
+    labels = S.exact_vix(gtr, posts, w.R, w.ht, w.hr)
+    label_s = time.perf_counter() - t0
+    tr = S.Trainer(S.init_master(0), batch=512, lr=2e-3)
+    t1 = time.perf_counter()
+    last = tr.fit([(gtr, posts, labels)], epochs=args.epochs, seed=3,
+                  log=lambda m: print(m, file=sys.stderr))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    del gtr, ztr_s, posts, labels
+    # held-out error on the bench terrain, next to the 10-sample vix estimate
+    pt = S.sample_posts(w.H, w.W, 200000, 32, 5, dev)
+    lt = S.exact_vix(g, pt, w.R, w.ht, w.hr)
+    mae = float((tr.predict(g, pt) - lt).abs().mean())
+    mae_vix = float((pipe.vixbuf.reshape(-1)[pt].float() / w.S - lt).abs().mean())
+    # the surrogate pipeline: lattice scores -> findmax_f32 -> viewshed -> site
+    st = args.sur_stride
+    n = V.findmax_count(w.H, w.W, st, w.block, w.k)
+    score = torch.empty(((w.H + st - 1) // st, (w.W + st - 1) // st), dtype=torch.float32, device=dev)
+    cand = torch.empty(n, dtype=torch.int64, device=dev)
+    bm = pipe.bm if n == pipe.n else torch.empty((n, 2 * w.R + 1, V.words_per_row(w.R)), dtype=torch.int32,
+                                                  device=dev)
+    area = torch.empty(n, dtype=torch.int32, device=dev)
+    cum = torch.empty_like(pipe.cum)
+    ws = torch.empty(V.site_workspace(n, w.R), dtype=torch.uint8, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    res = None
+
+    def step(record):
+        nonlocal res
+        if record:
+            ev[0].record()
+        V.cnn_score_lattice(g, st, tr.packed, out=score)
+        if record:
+            ev[1].record()
+        V.findmax_f32(score, w.H, w.W, st, w.block, w.k, out=cand)
+        if record:
+            ev[2].record()
+        V.viewshed(g, w.R, w.ht, w.hr, cand, bm=bm, area=area)
+        if record:
+            ev[3].record()
+        cum.zero_()
+        res = V.site(bm, cand, w.H, w.W, w.R, w.n_obs, cum=cum, ws=ws, sync=False)
+        if record:
+            ev[4].record()
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stages = []
+    a.record()
+    for _ in range(args.steps):
+        step(True)
+        torch.cuda.synchronize()
+        stages.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    ch, gn, _, nch = res
+    covered = int(gn[:int(nch.item())].sum().item())
+    names = ["cnn_lattice", "findmax_f32", "viewshed", "site"]
+    return {
+        "s_per_step": ms / 1000.0,
+        "stages_ms": dict(zip(names, [statistics.median(x[i] for x in stages) for i in range(4)])),
+        "coverage_posts": covered, "coverage_ratio_vs_plain": covered / max(covered_plain, 1),
+        "speedup_vs_plain": None, "lattice_stride": st, "candidates": n,
+        "patches_per_step": score.numel(),
+        "train_posts": args.train_posts, "epochs": args.epochs, "train_loss_last_epoch": last,
+        "label_s": label_s, "train_s": train_s,
+        "mae_heldout": mae, "mae_sampled_vix": mae_vix, "mae_posts": pt.numel(),
+        "gpu_launches_per_step": 7,
+    }
+
+
 # ------------------------------------------------------------------ main
 def run_reference(args, w, rank):
     """The oracle as it stands, on the host cores, one bounded sample per step."""
@@ -245,6 +330,10 @@ def main():
     ap.add_argument("--workload", default="full", choices=["full", "scale", "small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sur-stride", type=int, default=16)
+    ap.add_argument("--train-posts", type=int, default=500000)
+    ap.add_argument("--epochs", type=int, default=3)
     args = ap.parse_args()
     w = pick_workload(args.workload)
     dist, rank, world, local = dist_init()
@@ -358,6 +447,12 @@ def main():
                "d2h_bytes_per_step": w.n_obs * 16 + 4}
         del zs2, pipe2
 
+    # ---- learned proposal: train on another terrain of the same recipe, then
+    # site with the network's lattice scores in place of the sampled vix
+    sur = None
+    if not args.no_surrogate:
+        sur = run_surrogate(V, w, g, pipe, covered, args, dev)
+
     # ---- rooflines
     peaks, peak_src = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -397,8 +492,11 @@ def main():
         "observers": n_chosen, "coverage_posts": covered, "coverage_frac": covered / (w.H * w.W),
         "vix_los_steps": los_steps, "site_gains_ms": gains_ms,
         "roofline": dom_roof, "rooflines": roof, "peak_source": peak_src,
-        "clocks": clk, "gpu_launches": 5 * args.steps, "terrain_gen_s": gen_s,
+        "clocks": clk, "gpu_launches": 7 * args.steps, "terrain_gen_s": gen_s,
     }
+    if sur:
+        sur["speedup_vs_plain"] = (ms / 1000.0) / sur["s_per_step"]
+        out["surrogate"] = sur
     if e2e:
         out["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -68,6 +68,17 @@ const char *vs_strerror(int code);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int vs_version(void);
 
+/* Launch-shape table used by the kernels, filled by an autotuner (the
+ * library's Python autotune module times the candidates and stores the
+ * fastest).  The results of every call are independent of these settings.
+ *   VS_TUNE_VIEWSHED_THREADS: threads per viewshed CTA = rays walked at once
+ *     per candidate ("ray bundle"), 128 / 256 / 512 (0 = default 256)
+ *   VS_TUNE_VIX_TILE: vix post tile, 1 = 64x32, 2 = 32x32 (0 = default: the
+ *     largest tile whose window fits) */
+enum { VS_TUNE_VIEWSHED_THREADS = 0, VS_TUNE_VIX_TILE = 1 };
+int vs_tune_set(int32_t op, int32_t R, int32_t value);
+int vs_tune_get(int32_t op, int32_t R);
+
 /* ------------------------------------------------------------------------
  * Vix (Sec. "The multiple transmitter siting process", Vix; LOS as in
  * Sec. "Definitions" and "Terrain visibility").
@@ -153,6 +164,24 @@ size_t vs_viewshed_workspace(int32_t R, int64_t n);
 int vs_viewshed(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand, int64_t n,
                 uint32_t *bm_out, int32_t *area_out, void *ws, size_t ws_bytes, vs_stream_t st);
 
+/* Batched viewsheds: the candidates of up to 64 terrains (different sizes,
+ * ROIs, heights) in ONE persistent launch.  jobs is a HOST array read during
+ * the call; each job is exactly the arguments of one vs_viewshed call, and
+ * the results are identical to those calls.  ws: vs_viewshed_batch_workspace
+ * bytes (a work counter, re-initialised by every call; calls that overlap on
+ * the GPU need separate workspaces). */
+typedef struct {
+    vs_grid g;
+    int32_t R, ht, hr;
+    const int64_t *cand;
+    int64_t n;
+    uint32_t *bm_out;
+    int32_t *area_out;
+} vs_viewshed_job;
+size_t vs_viewshed_batch_workspace(int32_t n_jobs);
+int vs_viewshed_batch(const vs_viewshed_job *jobs, int32_t n_jobs, void *ws, size_t ws_bytes,
+                      vs_stream_t st);
+
 /* ------------------------------------------------------------------------
  * Site (Sec. "The multiple transmitter siting process", Site).
  *
@@ -204,6 +233,25 @@ int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32
 int vs_site_noalloc(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W,
                     int32_t R, int32_t n_obs, double coverage_target, int64_t *chosen,
                     int64_t *gains, uint32_t *cum, int32_t *n_chosen, vs_stream_t st);
+
+/* Batched site: up to 64 independent greedy problems (one per terrain), each
+ * exactly the arguments of one vs_site call minus the workspace, with the
+ * same results.  The greedy loops of every job small enough for one CTA's
+ * shared memory run in ONE launch (one CTA per job); other jobs run as
+ * ordinary vs_site calls.  jobs is a HOST array read during the call; ws:
+ * vs_site_batch_workspace(jobs, n_jobs) bytes, 256-byte aligned. */
+typedef struct {
+    const uint32_t *bm;
+    const int64_t *cand;
+    int64_t n;
+    int32_t H, W, R, n_obs;
+    double coverage_target;
+    int64_t *chosen, *gains;
+    uint32_t *cum;
+    int32_t *n_chosen;
+} vs_site_job;
+size_t vs_site_batch_workspace(const vs_site_job *jobs, int32_t n_jobs);
+int vs_site_batch(const vs_site_job *jobs, int32_t n_jobs, void *ws, size_t ws_bytes, vs_stream_t st);
 
 /* Dense gain pass (the first step of vs_site, exposed on its own): for every
  * candidate c, gains_out[c] = popcount(V_c AND NOT cum).  One streaming pass

@@ -81,7 +81,10 @@ constexpr int kUBytes = (kP5Off + kP5Bytes) > kA1Bytes ? (kP5Off + kP5Bytes) : k
 constexpr int kSmPatch = ((kSmU + kUBytes) + 127) & ~127;   // 67x67 bf16, zero border
 constexpr int kPatchBytes = ((67 * 67 * 2) + 127) & ~127;
 constexpr int kSmGap = kSmPatch + kPatchBytes;              // 25 x 32 floats
-constexpr int kSmEnd = kSmGap + 25 * 32 * 4;
+constexpr int kSmStage = ((kSmGap + 25 * 32 * 4) + 127) & ~127;  // TMA-staged patch
+constexpr int kStageW = 72;                                  // 65 columns + 8-alignment slack
+constexpr int kStageBytes = ((kPatch * kStageW * 2) + 127) & ~127;
+constexpr int kSmEnd = kSmStage + kStageBytes;
 constexpr int kSmemBytes = kSmEnd + 128;                    // + base alignment slack
 
 // instruction descriptor: kind::f16, A = B = BF16, D = F32, K-major A and B,
@@ -170,6 +173,10 @@ __global__ void k_cnn_pack(const float *__restrict__ master, unsigned char *__re
 }
 
 // ------------------------------------------------------------------ forward
+// A patch whose 65x65 window lies inside the grid is staged by one TMA tile
+// load (72 x 65 posts, the left edge rounded down to 8), prefetched while the
+// previous patch runs through the convolutions; windows that cross the grid
+// edge are gathered with clamped loads.
 struct FwdParams {
     const int16_t *z;
     int H, W;
@@ -183,30 +190,39 @@ struct FwdParams {
     int *status;             // optional: set to VS_ERR_TIMEOUT if an MMA wait gave up
 };
 
-// one implicit-GEMM tile: `nmma` MMAs accumulate into the TMEM accumulator,
-// then every thread reads its row (32 fp32).  Returns false on a timed-out wait.
+// Implicit-GEMM tiles run in two halves so that the tensor core works on
+// tile t+1 while the CUDA cores run the epilogue of tile t: issue_tile
+// (after every input of the tile is in shared memory) puts `nmma` MMAs into
+// TMEM accumulator buffer `buf` (32 columns each) and commits them to
+// bar[buf]; finish_tile waits for them and reads this thread's row.
 template <typename F>
-__device__ __forceinline__ bool gemm_tile(uint64_t *bar, uint32_t &phase, uint32_t tmem, int nmma,
-                                          F &&mma_desc, float *acc) {
-    // inputs written by every thread are visible to the tensor core
-    fence_proxy_async_smem();
-    __syncthreads();
+__device__ __forceinline__ void issue_tile(uint64_t *bar, uint32_t tmem, int buf, int nmma, F &&mma_desc) {
     if (threadIdx.x == 0) {
         tc_fence_after();
         for (int i = 0; i < nmma; ++i) {
             uint64_t ad, bd;
             mma_desc(i, ad, bd);
-            umma(tmem, ad, bd, i > 0 ? 1u : 0u);
+            umma(tmem + (uint32_t)(buf * 32), ad, bd, i > 0 ? 1u : 0u);
         }
-        umma_commit(bar);
+        umma_commit(&bar[buf]);
     }
-    const bool ok = mbar_wait(bar, phase);
-    phase ^= 1u;
+}
+
+__device__ __forceinline__ bool finish_tile(uint64_t *bar, uint32_t *phase, uint32_t tmem, int buf,
+                                            float *acc) {
+    const bool ok = mbar_wait(&bar[buf], phase[buf]);
+    phase[buf] ^= 1u;
     tc_fence_after();
     const int warp = threadIdx.x >> 5;
-    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), acc);
+    tmem_ld32(tmem + (uint32_t)(buf * 32) + ((uint32_t)(warp * 32) << 16), acc);
     tc_fence_before();
     return ok;
+}
+
+// inputs written by every thread become visible to the tensor core
+__device__ __forceinline__ void publish_smem() {
+    fence_proxy_async_smem();
+    __syncthreads();
 }
 
 __device__ __forceinline__ void store_row(unsigned char *dst, long long stride16, const uint32_t *w16) {
@@ -217,10 +233,30 @@ __device__ __forceinline__ void store_row(unsigned char *dst, long long stride16
                                                      w16[cb * 4 + 3]);
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const FwdParams P) {
+// epilogue of one output row: bias + ReLU, rounded to bf16, 32 channels as
+// 16 packed words
+__device__ __forceinline__ void relu_pack(const float *acc, const float *bias, uint32_t *w16) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+        w16[c] = pack_bf16x2(fmaxf(acc[2 * c] + bias[2 * c], 0.f), fmaxf(acc[2 * c + 1] + bias[2 * c + 1], 0.f));
+}
+
+__device__ __forceinline__ long long patch_centre(const FwdParams &P, long long pi) {
+    if (P.centers) return P.centers[pi];
+    return (pi / P.Ws) * (long long)P.stride * P.W + (pi % P.Ws) * (long long)P.stride;
+}
+
+__device__ __forceinline__ bool patch_inside(const FwdParams &P, long long cpost) {
+    const int cy = (int)(cpost / P.W), cx = (int)(cpost % P.W);
+    return cy >= 32 && cy + 32 < P.H && cx >= 32 && cx + 32 < P.W;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_constant__ CUtensorMap tmap,
+                                                             const FwdParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *sm = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    __shared__ uint64_t bar;
+    __shared__ uint64_t bar[2];
+    __shared__ uint64_t pbar;
     __shared__ uint32_t s_tmem;
     __shared__ int s_red[4];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -231,15 +267,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const FwdParams P) 
     unsigned char *P3 = U + kP3Off, *P4 = U + kP4Off, *P5 = U + kP5Off;
     __nv_bfloat16 *pb = (__nv_bfloat16 *)(sm + kSmPatch);
     float *gap = (float *)(sm + kSmGap);
+    int16_t *raw = (int16_t *)U;  // the patch's posts, before im2col reuses U
+    int16_t *stage = (int16_t *)(sm + kSmStage);
 
-    // ---- one-time set-up: weights, zeroed planes, barrier, tensor memory
+    // ---- one-time set-up: weights, zeroed planes, barriers, tensor memory
     for (int i = tid; i < kPackedBytes / 16; i += kThreads)
         ((uint4 *)Wp)[i] = ((const uint4 *)P.packed)[i];
     for (int i = tid; i < kP2Bytes / 16; i += kThreads) ((uint4 *)P2)[i] = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < kPatchBytes / 16; i += kThreads) ((uint4 *)pb)[i] = make_uint4(0, 0, 0, 0);
-    if (tid == 0) mbar_init(&bar, 1);
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init(&pbar, 1);
+    }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
                          smem_u32(&s_tmem))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -248,24 +290,55 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const FwdParams P) 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    uint32_t phase = 0;
+    uint32_t phase[2] = {0u, 0u};
+    uint32_t pphase = 0u;
+    // stage the first patch
+    auto stage_patch = [&](long long pi) {
+        const long long cp = patch_centre(P, pi);
+        const int cy = (int)(cp / P.W), cx = (int)(cp % P.W);
+        const int x0 = floordiv(cx - 32, 8) * 8;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&pbar, (uint32_t)(kPatch * kStageW * 2));
+        tma_load_3d(stage, &tmap, 0, x0 / 8, cy - 32, &pbar);
+    };
+    if (tid == 0 && blockIdx.x < P.n && patch_inside(P, patch_centre(P, blockIdx.x))) stage_patch(blockIdx.x);
     bool ok = true;
     const float *bias = (const float *)(Wp + kPkBias);
     const float *fc = (const float *)(Wp + kPkFc);
     const uint32_t sW = smem_u32(Wp), sP2 = smem_u32(P2), sU = smem_u32(U);
     const uint32_t sP3 = sU + kP3Off, sP4 = sU + kP4Off, sP5 = sU + kP5Off;
 
+    // tap t, K-step ks of a 32->32 layer reading stride-2 parity planes
+    auto plane_desc = [&](uint32_t base, int pln, int pitch, int m0, int l, int i, uint64_t &ad, uint64_t &bd) {
+        const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
+        const int plane = ((ky != 1) << 1) | (kx != 1);
+        const int shift = (ky != 0 ? pitch : 0) + (kx != 0 ? 1 : 0);
+        ad = sdesc(base + ((2 * ks * 4 + plane) * pln + m0 + shift) * 16, 4 * pln * 16, 128);
+        bd = sdesc(sW + pk_bl(l) + (t * 2 + ks) * 1024, 128, 256);
+    };
+
     for (long long pi = blockIdx.x; pi < P.n; pi += gridDim.x) {
-        // ---- patch: clamp to the grid, mean (exact integer sum), normalise
-        long long cpost;
-        if (P.centers) cpost = P.centers[pi];
-        else cpost = (pi / P.Ws) * (long long)P.stride * P.W + (pi % P.Ws) * (long long)P.stride;
+        // ---- patch: the staged tile, or a clamped gather at the grid edge
+        const long long cpost = patch_centre(P, pi);
         const int cy = (int)(cpost / P.W), cx = (int)(cpost % P.W);
         int sum = 0;
-        for (int e = tid; e < kPatch * kPatch; e += kThreads) {
-            const int r = min(max(cy - 32 + e / kPatch, 0), P.H - 1);
-            const int c = min(max(cx - 32 + e % kPatch, 0), P.W - 1);
-            sum += P.z[(long long)r * P.pitch + c];
+        if (patch_inside(P, cpost)) {
+            if (!mbar_wait(&pbar, pphase)) ok = false;
+            pphase ^= 1u;
+            const int off = (cx - 32) - floordiv(cx - 32, 8) * 8;
+            for (int e = tid; e < kPatch * kPatch; e += kThreads) {
+                const int16_t v = stage[(e / kPatch) * kStageW + off + e % kPatch];
+                raw[e] = v;
+                sum += v;
+            }
+        } else {
+            for (int e = tid; e < kPatch * kPatch; e += kThreads) {
+                const int r = min(max(cy - 32 + e / kPatch, 0), P.H - 1);
+                const int c = min(max(cx - 32 + e % kPatch, 0), P.W - 1);
+                const int16_t v = P.z[(long long)r * P.pitch + c];
+                raw[e] = v;
+                sum += v;
+            }
         }
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         if (lane == 0) s_red[warp] = sum;
@@ -273,14 +346,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const FwdParams P) 
         const float mean = (float)(s_red[0] + s_red[1] + s_red[2] + s_red[3]) / (float)(kPatch * kPatch);
         unsigned char *sv = P.save ? P.save + pi * (long long)kSaveBytesTotal : nullptr;
         for (int e = tid; e < kPatch * kPatch; e += kThreads) {
-            const int rr = e / kPatch, cc = e % kPatch;
-            const int r = min(max(cy - 32 + rr, 0), P.H - 1);
-            const int c = min(max(cx - 32 + cc, 0), P.W - 1);
-            const __nv_bfloat16 x = __float2bfloat16_rn(((float)P.z[(long long)r * P.pitch + c] - mean) / 1000.0f);
-            pb[(rr + 1) * 67 + (cc + 1)] = x;
+            const __nv_bfloat16 x = __float2bfloat16_rn(((float)raw[e] - mean) / 1000.0f);
+            pb[(e / kPatch + 1) * 67 + (e % kPatch + 1)] = x;
             if (sv) ((__nv_bfloat16 *)(sv + kSvInput))[e] = x;
         }
         __syncthreads();
+        // the staging tile is free: prefetch the next patch during the convolutions
+        {
+            const long long nx = pi + gridDim.x;
+            if (tid == 0 && nx < P.n && patch_inside(P, patch_centre(P, nx))) stage_patch(nx);
+        }
 
         // ---- conv1: explicit im2col (1152 rows x 16 K), 9 M-tiles of one MMA each
         for (int m = tid; m < 1152; m += kThreads) {
@@ -302,112 +377,96 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const FwdParams P) 
             *(uint4 *)row = make_uint4(w[0], w[1], w[2], w[3]);
             *(uint4 *)(row + 128) = make_uint4(w[4], w[5], w[6], w[7]);
         }
+        publish_smem();
         float acc[32];
-        for (int mt = 0; mt < 9; ++mt) {
-            ok &= gemm_tile(&bar, phase, tmem, 1, [&](int, uint64_t &ad, uint64_t &bd) {
+        uint32_t w16[16];
+        auto l1 = [&](int mt) {
+            return [=](int, uint64_t &ad, uint64_t &bd) {
                 ad = sdesc(sU + mt * 4096, 128, 256);
                 bd = sdesc(sW + kPkB1, 128, 256);
-            }, acc);
+            };
+        };
+        issue_tile(bar, tmem, 0, 1, l1(0));
+        for (int mt = 0; mt < 9; ++mt) {
+            if (mt + 1 < 9) issue_tile(bar, tmem, (mt + 1) & 1, 1, l1(mt + 1));
+            ok &= finish_tile(bar, phase, tmem, mt & 1, acc);
             const int m = mt * 128 + tid, y = m / 34, x = m % 34;
             if (y < 33 && x < 33) {
-                uint32_t w16[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    w16[c] = pack_bf16x2(fmaxf(acc[2 * c] + bias[2 * c], 0.f),
-                                         fmaxf(acc[2 * c + 1] + bias[2 * c + 1], 0.f));
+                relu_pack(acc, bias, w16);
                 const int plane = ((y & 1) << 1) | (x & 1);
                 const int pix = ((y >> 1) + 1) * 18 + (x >> 1) + 1;
                 store_row(P2 + ((long long)plane * kPln2 + pix) * 16, 4LL * kPln2 * 16, w16);
                 if (sv) store_row(sv + kSvA1 + (y * 33 + x) * 64, 16, w16);
             }
+            __syncthreads();  // this buffer's tcgen05.ld done before it is reissued
         }
         // A1 is dead: clear the region that now holds the next layers' planes
-        __syncthreads();
         for (int i = tid; i < kUBytes / 16; i += kThreads) ((uint4 *)U)[i] = make_uint4(0, 0, 0, 0);
+        publish_smem();
 
-        // ---- conv2..conv5: 9 taps x 2 K-steps per tile, descriptors into planes
-        // conv2: 3 tiles, input P2 (pitch 18, plane 324), output P3 (pitch 10)
+        // ---- conv2: 3 tiles, input P2 (pitch 18, plane 324), output P3 (pitch 10)
+        auto l2 = [&](int mt) {
+            return [=](int i, uint64_t &ad, uint64_t &bd) { plane_desc(sP2, kPln2, 18, mt * 128, 1, i, ad, bd); };
+        };
+        issue_tile(bar, tmem, 0, 18, l2(0));
         for (int mt = 0; mt < 3; ++mt) {
-            ok &= gemm_tile(&bar, phase, tmem, 18, [&](int i, uint64_t &ad, uint64_t &bd) {
-                const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
-                const int plane = ((ky != 1) << 1) | (kx != 1);
-                const int shift = (ky != 0 ? 18 : 0) + (kx != 0 ? 1 : 0);
-                ad = sdesc(sP2 + ((2 * ks * 4 + plane) * kPln2 + mt * 128 + shift) * 16, 4 * kPln2 * 16, 128);
-                bd = sdesc(sW + pk_bl(1) + (t * 2 + ks) * 1024, 128, 256);
-            }, acc);
+            if (mt + 1 < 3) issue_tile(bar, tmem, (mt + 1) & 1, 18, l2(mt + 1));
+            ok &= finish_tile(bar, phase, tmem, mt & 1, acc);
             const int m = mt * 128 + tid, y = m / 18, x = m % 18;
             if (y < 17 && x < 17) {
-                uint32_t w16[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    w16[c] = pack_bf16x2(fmaxf(acc[2 * c] + bias[32 + 2 * c], 0.f),
-                                         fmaxf(acc[2 * c + 1] + bias[32 + 2 * c + 1], 0.f));
+                relu_pack(acc, bias + 32, w16);
                 const int plane = ((y & 1) << 1) | (x & 1);
                 const int pix = ((y >> 1) + 1) * 10 + (x >> 1) + 1;
                 store_row(P3 + ((long long)plane * kPln3 + pix) * 16, 4LL * kPln3 * 16, w16);
                 if (sv) store_row(sv + kSvA2 + (y * 17 + x) * 64, 16, w16);
             }
+            __syncthreads();
         }
-        // conv3: 1 tile, input P3 (pitch 10, plane 100), output P4 (pitch 6)
+        publish_smem();
+        // ---- conv3: 1 tile, input P3 (pitch 10, plane 100), output P4 (pitch 6)
+        issue_tile(bar, tmem, 0, 18, [&](int i, uint64_t &ad, uint64_t &bd) { plane_desc(sP3, kPln3, 10, 0, 2, i, ad, bd); });
+        ok &= finish_tile(bar, phase, tmem, 0, acc);
         {
-            ok &= gemm_tile(&bar, phase, tmem, 18, [&](int i, uint64_t &ad, uint64_t &bd) {
-                const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
-                const int plane = ((ky != 1) << 1) | (kx != 1);
-                const int shift = (ky != 0 ? 10 : 0) + (kx != 0 ? 1 : 0);
-                ad = sdesc(sP3 + ((2 * ks * 4 + plane) * kPln3 + shift) * 16, 4 * kPln3 * 16, 128);
-                bd = sdesc(sW + pk_bl(2) + (t * 2 + ks) * 1024, 128, 256);
-            }, acc);
-            const int m = tid, y = m / 10, x = m % 10;
+            const int y = tid / 10, x = tid % 10;
             if (y < 9 && x < 9) {
-                uint32_t w16[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    w16[c] = pack_bf16x2(fmaxf(acc[2 * c] + bias[64 + 2 * c], 0.f),
-                                         fmaxf(acc[2 * c + 1] + bias[64 + 2 * c + 1], 0.f));
+                relu_pack(acc, bias + 64, w16);
                 const int plane = ((y & 1) << 1) | (x & 1);
                 const int pix = ((y >> 1) + 1) * 6 + (x >> 1) + 1;
                 store_row(P4 + ((long long)plane * kPln4 + pix) * 16, 4LL * kPln4 * 16, w16);
                 if (sv) store_row(sv + kSvA3 + (y * 9 + x) * 64, 16, w16);
             }
         }
-        // conv4: 1 tile, input P4 (pitch 6, plane 36), output P5 (stride-1 plane, pitch 7)
+        publish_smem();
+        // ---- conv4: 1 tile, input P4 (pitch 6, plane 36), output P5 (stride-1 plane, pitch 7)
+        issue_tile(bar, tmem, 1, 18, [&](int i, uint64_t &ad, uint64_t &bd) { plane_desc(sP4, kPln4, 6, 0, 3, i, ad, bd); });
+        ok &= finish_tile(bar, phase, tmem, 1, acc);
         {
-            ok &= gemm_tile(&bar, phase, tmem, 18, [&](int i, uint64_t &ad, uint64_t &bd) {
-                const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
-                const int plane = ((ky != 1) << 1) | (kx != 1);
-                const int shift = (ky != 0 ? 6 : 0) + (kx != 0 ? 1 : 0);
-                ad = sdesc(sP4 + ((2 * ks * 4 + plane) * kPln4 + shift) * 16, 4 * kPln4 * 16, 128);
-                bd = sdesc(sW + pk_bl(3) + (t * 2 + ks) * 1024, 128, 256);
-            }, acc);
-            const int m = tid, y = m / 6, x = m % 6;
+            const int y = tid / 6, x = tid % 6;
             if (y < 5 && x < 5) {
-                uint32_t w16[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    w16[c] = pack_bf16x2(fmaxf(acc[2 * c] + bias[96 + 2 * c], 0.f),
-                                         fmaxf(acc[2 * c + 1] + bias[96 + 2 * c + 1], 0.f));
+                relu_pack(acc, bias + 96, w16);
                 const int pix = (y + 1) * 7 + (x + 1);
                 store_row(P5 + (long long)pix * 16, (long long)kPln5 * 16, w16);
                 if (sv) store_row(sv + kSvA4 + (y * 5 + x) * 64, 16, w16);
             }
         }
-        // conv5 (stride 1): 1 tile, input P5 (pitch 7, plane 49), output -> pooling buffer
+        publish_smem();
+        // ---- conv5 (stride 1): 1 tile, input P5 (pitch 7, plane 49) -> pooling buffer
+        issue_tile(bar, tmem, 0, 18, [&](int i, uint64_t &ad, uint64_t &bd) {
+            const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
+            ad = sdesc(sP5 + ((2 * ks) * kPln5 + ky * 7 + kx) * 16, kPln5 * 16, 128);
+            bd = sdesc(sW + pk_bl(4) + (t * 2 + ks) * 1024, 128, 256);
+        });
+        ok &= finish_tile(bar, phase, tmem, 0, acc);
         {
-            ok &= gemm_tile(&bar, phase, tmem, 18, [&](int i, uint64_t &ad, uint64_t &bd) {
-                const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
-                ad = sdesc(sP5 + ((2 * ks) * kPln5 + ky * 7 + kx) * 16, kPln5 * 16, 128);
-                bd = sdesc(sW + pk_bl(4) + (t * 2 + ks) * 1024, 128, 256);
-            }, acc);
-            const int m = tid, y = m / 7, x = m % 7;
+            const int y = tid / 7, x = tid % 7;
             if (y < 5 && x < 5) {
-                uint32_t w16[16];
 #pragma unroll
                 for (int c = 0; c < 32; ++c)
                     gap[(y * 5 + x) * 32 + c] = bf16_round(fmaxf(acc[c] + bias[128 + c], 0.f));
                 if (sv) {
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) w16[c] = pack_bf16x2(gap[(y * 5 + x) * 32 + 2 * c],
-                                                                      gap[(y * 5 + x) * 32 + 2 * c + 1]);
+                    for (int c = 0; c < 16; ++c)
+                        w16[c] = pack_bf16x2(gap[(y * 5 + x) * 32 + 2 * c], gap[(y * 5 + x) * 32 + 2 * c + 1]);
                     store_row(sv + kSvA5 + (y * 5 + x) * 64, 16, w16);
                 }
             }
@@ -439,7 +498,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const FwdParams P) 
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
 // ------------------------------------------------------------------ training
@@ -639,7 +698,9 @@ static int cnn_forward_launch(vs_grid g, const int64_t *centers, int64_t n, int3
     VS_CUDA_TRY(cudaFuncSetAttribute(cnn::k_cnn_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      cnn::kSmemBytes));
     const long long grid = std::min<long long>(n, (long long)sms);
-    cnn::k_cnn_forward<<<(unsigned)grid, cnn::kThreads, cnn::kSmemBytes, (cudaStream_t)st>>>(P);
+    GridMap gm;  // 72 x 65 post tiles for the staged patches
+    if ((rc = make_grid_map(&gm, g, cnn::kStageW / 8, cnn::kPatch))) return rc;
+    cnn::k_cnn_forward<<<(unsigned)grid, cnn::kThreads, cnn::kSmemBytes, (cudaStream_t)st>>>(gm.map, P);
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }

@@ -21,6 +21,7 @@
 //    applied exactly.
 #include <algorithm>
 #include <cooperative_groups.h>
+#include <cstring>
 #include <mutex>
 
 #include "vs_common.cuh"
@@ -345,7 +346,7 @@ struct Site1Params {
 
 __device__ __forceinline__ uint64_t u64max(uint64_t a, uint64_t b) { return a > b ? a : b; }
 
-__global__ void __launch_bounds__(kSiteThreads, 1) k_site_loop1(const Site1Params P) {
+__device__ __forceinline__ void site1_body(const Site1Params &P) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *s_gain = (uint32_t *)smem;                  // n
     uint32_t *s_delta = s_gain + ((P.n + 3) & ~3);        // words
@@ -508,6 +509,17 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_loop1(const Site1Param
     if (tid == 0) *P.n_chosen = t;
 }
 
+__global__ void __launch_bounds__(kSiteThreads, 1) k_site_loop1(const Site1Params P) { site1_body(P); }
+
+// many independent greedy loops (one per terrain) in one launch: CTA j runs job j
+constexpr int kSiteMaxJobs = 64;
+struct Site1Batch {
+    Site1Params job[kSiteMaxJobs];
+};
+__global__ void __launch_bounds__(kSiteThreads, 1) k_site_loop1_batch(const __grid_constant__ Site1Batch B) {
+    site1_body(B.job[blockIdx.x]);
+}
+
 static size_t site_smem_bytes(int slots, int words) {
     return (size_t)slots * 16 + (size_t)words * 4 + 16;
 }
@@ -562,10 +574,17 @@ extern "C" int vs_site_gains(const uint32_t *bm, const int64_t *cand, int64_t n,
     return VS_OK;
 }
 
-extern "C" int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W,
-                       int32_t R, int32_t n_obs, double coverage_target, int64_t *chosen,
-                       int64_t *gains, uint32_t *cum, int32_t *n_chosen, void *ws,
-                       size_t ws_bytes, vs_stream_t st) {
+static size_t site1_smem_bytes(int64_t n, int words) {
+    return (size_t)((n + 3) & ~3) * 4 + (size_t)((words + 3) & ~3) * 4 + (size_t)kSiteThreads * 4;
+}
+static bool site1_fits(int64_t n, int words) {  // + ~33 KB of static shared memory
+    return n < (1 << 30) && site1_smem_bytes(n, words) <= (size_t)kSmemLimit - 40 * 1024;
+}
+
+static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W,
+                     int32_t R, int32_t n_obs, double coverage_target, int64_t *chosen,
+                     int64_t *gains, uint32_t *cum, int32_t *n_chosen, void *ws,
+                     size_t ws_bytes, vs_stream_t st, Site1Params *job_out, size_t *smem_out) {
     if (n < 0 || n_obs < 0) return VS_ERR_RANGE;
     if (!cum || !n_chosen || (n > 0 && (!bm || !cand)) || (n_obs > 0 && (!chosen || !gains)))
         return VS_ERR_ARG;
@@ -603,9 +622,8 @@ extern "C" int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32
     if (n > 0 && (rc = vs_site_gains(bm, cand, n, H, W, R, cum, g0, st))) return rc;
 
     // one CTA when every gain fits in its shared memory
-    const size_t smem1 = (size_t)((n + 3) & ~3) * 4 + (size_t)((P.words + 3) & ~3) * 4 +
-                         (size_t)kSiteThreads * 4;
-    if (n > 0 && n < (1 << 30) && smem1 <= (size_t)kSmemLimit - 40 * 1024) {  // + ~33 KB static
+    const size_t smem1 = site1_smem_bytes(n, P.words);
+    if (n > 0 && site1_fits(n, P.words)) {
         k_site_rank<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cand, n, (int64_t)H * W, sp, sorig);
         VS_CUDA_TRY(cudaGetLastError());
         k_site_bands<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sp, n, W, R, slo, shi);
@@ -615,12 +633,18 @@ extern "C" int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32
         Q1.WWc = P.WWc; Q1.n_obs = n_obs; Q1.need = P.need; Q1.chosen = chosen; Q1.gains = gains;
         Q1.cum = cum; Q1.n_chosen = n_chosen; Q1.gain0 = g0; Q1.sp = sp; Q1.sorig = sorig;
         Q1.slo = slo; Q1.shi = shi; Q1.covered0 = cov;
+        if (job_out) {  // batched call: the caller launches the loop
+            *job_out = Q1;
+            *smem_out = smem1;
+            return VS_OK;
+        }
         VS_CUDA_TRY(cudaFuncSetAttribute(k_site_loop1, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem1));
         k_site_loop1<<<1, kSiteThreads, smem1, s>>>(Q1);
         VS_CUDA_TRY(cudaGetLastError());
         return VS_OK;
     }
+    if (job_out) return VS_ERR_RANGE;  // too many candidates for one CTA: not batchable
 
     // choose the cluster: largest Q whose slots fit in shared memory
     int Q = 0, slots = 0;
@@ -650,6 +674,62 @@ extern "C" int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32
     cfg.attrs = at;
     cfg.numAttrs = 1;
     VS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_site_loop, P));
+    return VS_OK;
+}
+
+extern "C" int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W,
+                       int32_t R, int32_t n_obs, double coverage_target, int64_t *chosen,
+                       int64_t *gains, uint32_t *cum, int32_t *n_chosen, void *ws,
+                       size_t ws_bytes, vs_stream_t st) {
+    return site_impl(bm, cand, n, H, W, R, n_obs, coverage_target, chosen, gains, cum, n_chosen, ws,
+                     ws_bytes, st, nullptr, nullptr);
+}
+
+extern "C" size_t vs_site_batch_workspace(const vs_site_job *jobs, int32_t n_jobs) {
+    if (!jobs || n_jobs < 0) return 0;
+    size_t t = 0;
+    for (int i = 0; i < n_jobs; ++i) t += align256(vs_site_workspace(jobs[i].n, jobs[i].R));
+    return t;
+}
+
+extern "C" int vs_site_batch(const vs_site_job *jobs, int32_t n_jobs, void *ws, size_t ws_bytes,
+                             vs_stream_t st) {
+    if (n_jobs < 0 || n_jobs > kSiteMaxJobs) return VS_ERR_RANGE;
+    if (n_jobs == 0) return VS_OK;
+    if (!jobs) return VS_ERR_ARG;
+    if (!ws || ws_bytes < vs_site_batch_workspace(jobs, n_jobs)) return VS_ERR_WS;
+    int rc = check_device();
+    if (rc) return rc;
+    static Site1Batch B;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    memset(&B, 0, sizeof(B));
+    size_t smem = 0, off = 0;
+    int nb = 0;
+    for (int i = 0; i < n_jobs; ++i) {
+        const vs_site_job &q = jobs[i];
+        const size_t wsb = align256(vs_site_workspace(q.n, q.R));
+        void *wsj = (char *)ws + off;
+        off += wsb;
+        const int words = (2 * q.R + 1) * words_per_row(q.R);
+        if (q.n > 0 && site1_fits(q.n, words)) {
+            size_t sm = 0;
+            if ((rc = site_impl(q.bm, q.cand, q.n, q.H, q.W, q.R, q.n_obs, q.coverage_target, q.chosen,
+                                q.gains, q.cum, q.n_chosen, wsj, wsb, st, &B.job[nb], &sm)))
+                return rc;
+            smem = std::max(smem, sm);
+            ++nb;
+        } else {  // empty or too large for one CTA: the ordinary call
+            if ((rc = site_impl(q.bm, q.cand, q.n, q.H, q.W, q.R, q.n_obs, q.coverage_target, q.chosen,
+                                q.gains, q.cum, q.n_chosen, wsj, wsb, st, nullptr, nullptr)))
+                return rc;
+        }
+    }
+    if (nb == 0) return VS_OK;
+    VS_CUDA_TRY(cudaFuncSetAttribute(k_site_loop1_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    k_site_loop1_batch<<<nb, kSiteThreads, smem, (cudaStream_t)st>>>(B);
+    VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }
 

@@ -12,6 +12,8 @@
 // its half / quadrant, so each pass stages only that part.
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
+#include <mutex>
 
 #include "vs_common.cuh"
 
@@ -39,43 +41,44 @@ __device__ __forceinline__ void ring_cell(int rho, int R, int &ex, int &ey) {
     else { ey = -R;                   ex = -R + 1 + o; }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_viewshed(const __grid_constant__ CUtensorMap tmap,
-                                                  const VsParams P) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    // TMA destinations must be 128-byte aligned: round the base up (the host
-    // reserves 128 spare bytes)
-    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    const int R = P.R, PR = P.PR;
-    const int WW = P.WG * 8;
-    int16_t *win = (int16_t *)smem;
-    const int win_elems = P.nbox * P.box_rows * WW;
-    uint32_t *bms = (uint32_t *)(smem + ((win_elems * 2 + 127) & ~127));
-    uint64_t *bar = (uint64_t *)(bms + ((P.words + 31) & ~31));
-    __shared__ int red[8];
-    __shared__ int s_fail;
+// Everything one viewshed needs, for the single-terrain and the batched
+// launches alike (the tensor map must stay in parameter space).
+struct VsJob {
+    CUtensorMap map;          // [H][pitch/8][8] view of the terrain, box 8 x WG x box_rows
+    int H, W, R, ht, hr;
+    int nsplit, WG, box_rows, nbox, PR, words, wide;
+    const int64_t *cand;
+    long long n, item0;       // candidates; first item of this job in a batch
+    uint32_t *bm;
+    int32_t *area;
+};
 
+// One candidate: stage the window (per sector), walk the rays of the sector,
+// OR visible cells into the shared bitmap, write bitmap and area.  `phase` is
+// the parity of the CTA's window barrier, carried across candidates.
+template <typename T>
+__device__ void vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long c, unsigned char *smem,
+                             uint64_t *bar, uint32_t &phase, int *s_fail, int *red) {
+    const int R = J.R, PR = J.PR;
+    const int WW = J.WG * 8;
+    int16_t *win = (int16_t *)smem;
+    const int win_elems = J.nbox * J.box_rows * WW;
+    uint32_t *bms = (uint32_t *)(smem + ((win_elems * 2 + 127) & ~127));
     const int tid = threadIdx.x;
-    const int64_t c = blockIdx.x;
-    const int64_t p = P.cand[c];
-    uint32_t *out = P.bm + c * (int64_t)P.words;
-    if (p < 0 || p >= (int64_t)P.H * P.W) {  // invalid candidate: empty bitmap, area -1
-        for (int i = tid; i < P.words; i += blockDim.x) out[i] = 0;
-        if (tid == 0) P.area[c] = -1;
+    const int64_t p = J.cand[c];
+    uint32_t *out = J.bm + c * (int64_t)J.words;
+    if (p < 0 || p >= (int64_t)J.H * J.W) {  // invalid candidate: empty bitmap, area -1
+        for (int i = tid; i < J.words; i += blockDim.x) out[i] = 0;
+        if (tid == 0) J.area[c] = -1;
         return;
     }
-    const int cx = (int)(p % P.W), cy = (int)(p / P.W);
+    const int cx = (int)(p % J.W), cy = (int)(p / J.W);
     const int gw0 = floordiv(cx - R, 32);
-
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        s_fail = 0;
-    }
-    for (int i = tid; i < P.words; i += blockDim.x) bms[i] = 0;
+    if (tid == 0) *s_fail = 0;
+    for (int i = tid; i < J.words; i += blockDim.x) bms[i] = 0;
     __syncthreads();
 
-    const int nsec = P.nsplit;
-    int eye = 0;
+    const int nsec = J.nsplit;
     for (int sec = 0; sec < nsec; ++sec) {
         // ---- this pass's window
         int row_lo = cy - R, col_lo = cx - R;
@@ -88,21 +91,22 @@ __global__ void __launch_bounds__(256) k_viewshed(const __grid_constant__ CUtens
         const int wy0 = row_lo;
         if (tid == 0) {
             fence_proxy_async_smem();
-            const uint32_t bytes = (uint32_t)(P.nbox * P.box_rows * WW * 2);
+            const uint32_t bytes = (uint32_t)(J.nbox * J.box_rows * WW * 2);
             mbar_arrive_expect_tx(bar, bytes);
-            for (int b = 0; b < P.nbox; ++b)
-                tma_load_3d(win + (size_t)b * P.box_rows * WW, &tmap, 0, wx0 / 8,
-                            wy0 + b * P.box_rows, bar);
+            for (int b = 0; b < J.nbox; ++b)
+                tma_load_3d(win + (size_t)b * J.box_rows * WW, tmap, 0, wx0 / 8, wy0 + b * J.box_rows, bar);
         }
-        if (!mbar_wait(bar, (uint32_t)(sec & 1))) s_fail = 1;
+        if (!mbar_wait(bar, phase)) *s_fail = 1;
         __syncthreads();
-        if (s_fail) {
+        if (*s_fail) {
             // give the copy in flight a second bounded chance to land before the
-            // CTA leaves, then report the candidate as timed out
-            mbar_wait(bar, (uint32_t)(sec & 1));
+            // CTA moves on, then report the candidate as timed out
+            mbar_wait(bar, phase);
+            phase ^= 1u;
             break;
         }
-        eye = (int)win[(cy - wy0) * WW + (cx - wx0)] + P.ht;
+        phase ^= 1u;
+        const int eye = (int)win[(cy - wy0) * WW + (cx - wx0)] + J.ht;
 
         // ---- rays of this sector
         for (int rho = tid; rho < 8 * R; rho += blockDim.x) {
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(256) k_viewshed(const __grid_constant__ CUtens
             const int rr = dmin - q * R;
             const int thr = dmin >= 0 ? R : R + 1;
             const int omaj = xmaj ? cx : cy, omin = xmaj ? cy : cx;
-            const int minor_lim = xmaj ? P.H : P.W;
+            const int minor_lim = xmaj ? J.H : J.W;
             const int minor_step = xmaj ? WW : 1;
             int f = 0, y0 = 0;
             T Hn = 0;
@@ -132,12 +136,11 @@ __global__ void __launch_bounds__(256) k_viewshed(const __grid_constant__ CUtens
                 const int gmaj = omaj + smaj * k;
                 const int gmin = omin + rnd;
                 const int gx = xmaj ? gmaj : gmin, gy = xmaj ? gmin : gmaj;
-                if ((unsigned)gx >= (unsigned)P.W || (unsigned)gy >= (unsigned)P.H) break;
+                if ((unsigned)gx >= (unsigned)J.W || (unsigned)gy >= (unsigned)J.H) break;
                 if (k * k + rnd * rnd > R * R) break;
                 const int zc = win[(gy - wy0) * WW + (gx - wx0)];
-                const bool vis = (Hk == 0) || ((T)(zc + P.hr - eye) * R * Hk >= Hn * k);
-                if (vis)
-                    atomicOr(&bms[(gy - cy + R) * PR + ((gx >> 5) - gw0)], 1u << (gx & 31));
+                const bool vis = (Hk == 0) || ((T)(zc + J.hr - eye) * R * Hk >= Hn * k);
+                if (vis) atomicOr(&bms[(gy - cy + R) * PR + ((gx >> 5) - gw0)], 1u << (gx & 31));
                 const int m0 = omin + y0;
                 if (f > 0 && (m0 < 0 || m0 + 1 >= minor_lim)) break;
                 const int a0 = xmaj ? (m0 - wy0) * WW + (gmaj - wx0) : (gmaj - wy0) * WW + (m0 - wx0);
@@ -150,11 +153,12 @@ __global__ void __launch_bounds__(256) k_viewshed(const __grid_constant__ CUtens
         __syncthreads();  // every read of this window done before the next pass overwrites it
     }
 
-    if (tid == 0 && !s_fail) atomicOr(&bms[R * PR + ((cx >> 5) - gw0)], 1u << (cx & 31));
+    const bool fail = *s_fail != 0;
+    if (tid == 0 && !fail) atomicOr(&bms[R * PR + ((cx >> 5) - gw0)], 1u << (cx & 31));
     __syncthreads();
     int cnt = 0;
-    for (int i = tid; i < P.words; i += blockDim.x) {
-        uint32_t w = s_fail ? 0u : bms[i];
+    for (int i = tid; i < J.words; i += blockDim.x) {
+        const uint32_t w = fail ? 0u : bms[i];
         out[i] = w;
         cnt += __popc(w);
     }
@@ -164,7 +168,63 @@ __global__ void __launch_bounds__(256) k_viewshed(const __grid_constant__ CUtens
     if (tid == 0) {
         int a = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
-        P.area[c] = s_fail ? VS_ERR_TIMEOUT : a;
+        J.area[c] = fail ? VS_ERR_TIMEOUT : a;
+    }
+    __syncthreads();  // red[] and the bitmap are reused by the next candidate
+}
+
+__device__ __forceinline__ unsigned char *vs_smem_base(unsigned char *raw) {
+    // TMA destinations must be 128-byte aligned: round the base up (the host
+    // reserves 128 spare bytes)
+    return raw + ((128u - (smem_u32(raw) & 127u)) & 127u);
+}
+
+// one CTA per candidate of one terrain
+__global__ void __launch_bounds__(512) k_viewshed(const __grid_constant__ VsJob J) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = vs_smem_base(smem_raw);
+    __shared__ uint64_t bar;
+    __shared__ int red[32];
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    if (J.wide) vs_candidate<long long>(&J.map, J, blockIdx.x, smem, &bar, phase, &s_fail, red);
+    else vs_candidate<int>(&J.map, J, blockIdx.x, smem, &bar, phase, &s_fail, red);
+}
+
+// Batched viewsheds of many terrains in one persistent launch: items
+// (job, candidate) are numbered job by job (jobs ordered by decreasing R, so
+// the costly ones start first) and pulled from a global counter.
+constexpr int kVsMaxJobs = 64;
+struct VsBatch {
+    VsJob job[kVsMaxJobs];
+    int njobs;
+    long long total;
+    unsigned long long *counter;
+};
+
+__global__ void __launch_bounds__(512) k_viewshed_batch(const __grid_constant__ VsBatch B) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = vs_smem_base(smem_raw);
+    __shared__ uint64_t bar;
+    __shared__ int red[32];
+    __shared__ int s_fail;
+    __shared__ long long s_item;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(B.counter, 1ull);
+        __syncthreads();
+        const long long it = s_item;
+        __syncthreads();
+        if (it >= B.total) break;
+        int j = 0;
+        while (j + 1 < B.njobs && B.job[j + 1].item0 <= it) ++j;
+        const VsJob &J = B.job[j];
+        if (J.wide) vs_candidate<long long>(&J.map, J, it - J.item0, smem, &bar, phase, &s_fail, red);
+        else vs_candidate<int>(&J.map, J, it - J.item0, smem, &bar, phase, &s_fail, red);
     }
 }
 
@@ -203,41 +263,96 @@ extern "C" size_t vs_viewshed_workspace(int32_t R, int64_t n) {
     return 0;
 }
 
-extern "C" int vs_viewshed(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand,
-                           int64_t n, uint32_t *bm_out, int32_t *area_out, void *ws,
-                           size_t ws_bytes, vs_stream_t st) {
-    (void)ws; (void)ws_bytes;
+static int vs_make_job(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand,
+                       int64_t n, uint32_t *bm_out, int32_t *area_out, VsJob *J, size_t *smem) {
     int rc = check_grid(g);
     if (rc) return rc;
     if (R < 1 || R > kMaxR) return VS_ERR_RANGE;
     if (ht < -100000 || ht > 100000 || hr < -100000 || hr > 100000) return VS_ERR_RANGE;
     if (n < 0 || n > 0x7fffffffll) return VS_ERR_RANGE;
-    if (n == 0) return VS_OK;
-    if (!cand || !bm_out || !area_out) return VS_ERR_ARG;
-    if ((rc = check_device())) return rc;
-
-    VsParams P;
-    P.H = g.H; P.W = g.W; P.R = R; P.ht = ht; P.hr = hr;
-    P.cand = cand; P.n = n; P.bm = bm_out; P.area = area_out;
-    P.PR = words_per_row(R);
-    P.words = (2 * R + 1) * P.PR;
-    size_t smem = 0;
-    if ((rc = vs_pick_split(R, &P.nsplit, &P.WG, &P.box_rows, &P.nbox, &smem))) return rc;
+    if (n > 0 && (!cand || !bm_out || !area_out)) return VS_ERR_ARG;
+    memset(J, 0, sizeof(*J));
+    J->H = g.H; J->W = g.W; J->R = R; J->ht = ht; J->hr = hr;
+    J->cand = cand; J->n = n; J->bm = bm_out; J->area = area_out;
+    J->PR = words_per_row(R);
+    J->words = (2 * R + 1) * J->PR;
+    if ((rc = vs_pick_split(R, &J->nsplit, &J->WG, &J->box_rows, &J->nbox, smem))) return rc;
     GridMap gm;
-    if ((rc = make_grid_map(&gm, g, P.WG, P.box_rows))) return rc;
-
+    if ((rc = make_grid_map(&gm, g, J->WG, J->box_rows))) return rc;
+    J->map = gm.map;
     // 32-bit products are exact when (z range + |ht| + |hr|) * R^2 < 2^31
     const long long bound = (65535ll + std::abs(ht) + std::abs(hr)) * (long long)R * R;
-    cudaStream_t s = (cudaStream_t)st;
-    if (bound < (1ll << 31)) {
-        VS_CUDA_TRY(cudaFuncSetAttribute(k_viewshed<int>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-        k_viewshed<int><<<(unsigned)n, 256, smem, s>>>(gm.map, P);
-    } else {
-        VS_CUDA_TRY(cudaFuncSetAttribute(k_viewshed<long long>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_viewshed<long long><<<(unsigned)n, 256, smem, s>>>(gm.map, P);
+    J->wide = bound >= (1ll << 31);
+    return VS_OK;
+}
+
+extern "C" int vs_viewshed(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand,
+                           int64_t n, uint32_t *bm_out, int32_t *area_out, void *ws,
+                           size_t ws_bytes, vs_stream_t st) {
+    (void)ws; (void)ws_bytes;
+    VsJob J;
+    size_t smem = 0;
+    int rc = vs_make_job(g, R, ht, hr, cand, n, bm_out, area_out, &J, &smem);
+    if (rc) return rc;
+    if (n == 0) return VS_OK;
+    if ((rc = check_device())) return rc;
+    VS_CUDA_TRY(cudaFuncSetAttribute(k_viewshed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int threads = tune_get(VS_TUNE_VIEWSHED_THREADS, R, 256);
+    k_viewshed<<<(unsigned)n, threads, smem, (cudaStream_t)st>>>(J);
+    VS_CUDA_TRY(cudaGetLastError());
+    return VS_OK;
+}
+
+extern "C" size_t vs_viewshed_batch_workspace(int32_t n_jobs) {
+    (void)n_jobs;
+    return 256;
+}
+
+extern "C" int vs_viewshed_batch(const vs_viewshed_job *jobs, int32_t n_jobs, void *ws, size_t ws_bytes,
+                                 vs_stream_t st) {
+    if (n_jobs < 0 || n_jobs > kVsMaxJobs) return VS_ERR_RANGE;
+    if (n_jobs == 0) return VS_OK;
+    if (!jobs) return VS_ERR_ARG;
+    if (!ws || ws_bytes < vs_viewshed_batch_workspace(n_jobs)) return VS_ERR_WS;
+    int rc = check_device();
+    if (rc) return rc;
+    // largest ROI first: the longest items start early, the short ones fill the tail
+    int order[kVsMaxJobs];
+    for (int i = 0; i < n_jobs; ++i) order[i] = i;
+    std::stable_sort(order, order + n_jobs, [&](int a, int b) { return jobs[a].R > jobs[b].R; });
+    static VsBatch B;  // large (16 KB): built on the host, copied into the launch's parameters
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    memset(&B, 0, sizeof(B));
+    size_t smem = 0;
+    long long total = 0;
+    int nj = 0;
+    for (int i = 0; i < n_jobs; ++i) {
+        const vs_viewshed_job &q = jobs[order[i]];
+        size_t sm = 0;
+        if ((rc = vs_make_job(q.g, q.R, q.ht, q.hr, q.cand, q.n, q.bm_out, q.area_out, &B.job[nj], &sm)))
+            return rc;
+        if (q.n == 0) continue;
+        B.job[nj].item0 = total;
+        total += q.n;
+        smem = std::max(smem, sm);
+        ++nj;
     }
+    if (total == 0) return VS_OK;
+    B.njobs = nj;
+    B.total = total;
+    B.counter = (unsigned long long *)ws;
+    cudaStream_t s = (cudaStream_t)st;
+    VS_CUDA_TRY(cudaMemsetAsync(ws, 0, 8, s));
+    VS_CUDA_TRY(cudaFuncSetAttribute(k_viewshed_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per = 0;
+    VS_CUDA_TRY(cudaGetDevice(&dev));
+    VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // one CTA size for the launch: the tuned size of the largest ROI
+    const int threads = tune_get(VS_TUNE_VIEWSHED_THREADS, B.job[0].R, 256);
+    VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_viewshed_batch, threads, smem));
+    const long long grid = std::min<long long>(total, (long long)sms * std::max(per, 1));
+    k_viewshed_batch<<<(unsigned)grid, threads, smem, s>>>(B);
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }

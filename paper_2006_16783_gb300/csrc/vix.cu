@@ -508,7 +508,8 @@ static int vix_launch(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, u
 
     // length-sorted variant when the packed line items can describe R
     if (R <= 511) {
-        const int tiles2[2][2] = {{64, 32}, {32, 32}};
+        const int pref = tune_get(VS_TUNE_VIX_TILE, R, 0);
+        const int tiles2[2][2] = {{pref == 2 ? 32 : 64, 32}, {32, 32}};
         const int sb = std::min(S, kVixSB);
         for (int ns : {1, 2, 4}) {
             for (auto &t : tiles2) {

@@ -99,6 +99,10 @@ struct GridMap {
 // Build the tensor map; box = 8 x wg x rows (wg <= 256, rows <= 256).
 int make_grid_map(GridMap *gm, const vs_grid &g, int wg, int rows);
 
+// launch-shape table filled by vs_tune_set (the autotuner); tune_get returns
+// the stored value for (op, R) or `fallback`
+int tune_get(int op, int R, int fallback);
+
 // argument checks shared by several entry points
 int check_grid(const vs_grid &g);
 int check_device();  // current device is sm_103 (cached per device)

@@ -28,12 +28,34 @@ class vs_grid(ctypes.Structure):
                 ("z", ctypes.c_void_p)]
 
 
+class vs_viewshed_job(ctypes.Structure):
+    _fields_ = [("g", vs_grid), ("R", ctypes.c_int32), ("ht", ctypes.c_int32), ("hr", ctypes.c_int32),
+                ("cand", ctypes.c_void_p), ("n", ctypes.c_int64), ("bm_out", ctypes.c_void_p),
+                ("area_out", ctypes.c_void_p)]
+
+
+class vs_site_job(ctypes.Structure):
+    _fields_ = [("bm", ctypes.c_void_p), ("cand", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("R", ctypes.c_int32),
+                ("n_obs", ctypes.c_int32), ("coverage_target", ctypes.c_double),
+                ("chosen", ctypes.c_void_p), ("gains", ctypes.c_void_p), ("cum", ctypes.c_void_p),
+                ("n_chosen", ctypes.c_void_p)]
+
+
+VS_TUNE_VIEWSHED_THREADS, VS_TUNE_VIX_TILE = 0, 1
+
 # name -> (restype, argtypes); the exported symbols of include/vshed.h
 P, i32, i64, u64, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
                              ctypes.c_double, ctypes.c_size_t)
 SIGNATURES = {
     "vs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "vs_version": (ctypes.c_int, []),
+    "vs_tune_set": (ctypes.c_int, [i32, i32, i32]),
+    "vs_tune_get": (ctypes.c_int, [i32, i32]),
+    "vs_viewshed_batch_workspace": (sz, [i32]),
+    "vs_viewshed_batch": (ctypes.c_int, [P, i32, P, sz, P]),
+    "vs_site_batch_workspace": (sz, [P, i32]),
+    "vs_site_batch": (ctypes.c_int, [P, i32, P, sz, P]),
     "vs_vix": (ctypes.c_int, [vs_grid, i32, i32, i32, i32, u64, P, P]),
     "vs_vix_count": (ctypes.c_int, [vs_grid, i32, i32, i32, i32, u64, P, P, P]),
     "vs_findmax_count": (i64, [i32, i32, i32, i32, i32]),
@@ -290,3 +312,53 @@ def cnn_adam(master, grads, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-
     _need_cuda(master, grads, m, v)
     _check("vs_cnn_adam", lib().vs_cnn_adam(_ptr(master), _ptr(grads), _ptr(m), _ptr(v), step, lr, beta1,
                                             beta2, eps, _stream()))
+
+
+# ------------------------------------------------------------------ batching and tuning
+def tune_set(op, R, value):
+    _check("vs_tune_set", lib().vs_tune_set(op, R, value))
+
+
+def tune_get(op, R):
+    return lib().vs_tune_get(op, R)
+
+
+def viewshed_batch(jobs, ws):
+    """jobs: list of dicts (g, R, ht, hr, cand, bm, area) -> one persistent launch."""
+    arr = (vs_viewshed_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        _need_cuda(j["cand"], j["bm"], j["area"])
+        arr[i].g = j["g"].c()
+        arr[i].R, arr[i].ht, arr[i].hr = j["R"], j["ht"], j["hr"]
+        arr[i].cand = j["cand"].data_ptr()
+        arr[i].n = j["cand"].numel()
+        arr[i].bm_out = j["bm"].data_ptr()
+        arr[i].area_out = j["area"].data_ptr()
+    _check("vs_viewshed_batch", lib().vs_viewshed_batch(ctypes.cast(arr, ctypes.c_void_p), len(jobs),
+                                                        _ptr(ws), ws.numel(), _stream()))
+
+
+def site_jobs(jobs):
+    arr = (vs_site_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        arr[i].bm = j["bm"].data_ptr()
+        arr[i].cand = j["cand"].data_ptr()
+        arr[i].n = j["cand"].numel()
+        arr[i].H, arr[i].W, arr[i].R, arr[i].n_obs = j["H"], j["W"], j["R"], j["n_obs"]
+        arr[i].coverage_target = float(j.get("target", 0.0))
+        arr[i].chosen = j["chosen"].data_ptr()
+        arr[i].gains = j["gains"].data_ptr()
+        arr[i].cum = j["cum"].data_ptr()
+        arr[i].n_chosen = j["n_chosen"].data_ptr()
+    return arr
+
+
+def site_batch_workspace(jobs):
+    arr = site_jobs(jobs)
+    return lib().vs_site_batch_workspace(ctypes.cast(arr, ctypes.c_void_p), len(jobs))
+
+
+def site_batch(jobs, ws):
+    arr = site_jobs(jobs)
+    _check("vs_site_batch", lib().vs_site_batch(ctypes.cast(arr, ctypes.c_void_p), len(jobs), _ptr(ws),
+                                                ws.numel(), _stream()))

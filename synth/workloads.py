@@ -12,9 +12,9 @@ for the unavailable datasets.  Parameters only -- no siting arithmetic.
             block ceil(R/2), k=1
     learn   eight 4096^2 training terrains (seeds 3000..3007), a held-out
             16384^2 terrain (seed 3100), labels = exact vix at R=100
-    full    46400^2 ridged multifractal (0..4000 m, lowest 5% flattened),
-            R=100, h=10, S=10, top-4 per 464x464 block (40000 candidates),
-            4096 observers
+    full    46400^2 ridged multifractal (base wavelength 640 posts, 10 octaves,
+            0..4000 m, lowest 5% flattened), R=100, h=10, S=10, top-4 per
+            464x464 block (40000 candidates), 4096 observers
 """
 import math
 from dataclasses import dataclass, field
@@ -61,8 +61,13 @@ SMALL = Workload("small_1000sq_R50", 1000, 1000, 50, 10, 10, 10, 25, 1, 100, see
                  hurst=0.8, zmax=1000)
 SCALE = Workload("scale_16384sq_R200", 16384, 16384, 200, 10, 10, 20, 256, 2, 2048, seed=1001,
                  hurst=0.75, zmax=3000, lake_frac=0.10)
+# base wavelength 640 posts, 10 octaves: relief at the ROI scale like mountainous
+# 1-arc-second terrain (mean |dz| between neighbouring posts ~8 m, exact vix at
+# R = 100 spread over [0, 1]); a wavelength near the grid size would make the
+# terrain almost planar within any ROI
 FULL = Workload("full_46400sq_R100", 46400, 46400, 100, 10, 10, 10, 464, 4, 4096, seed=1004,
-                kind="ridged", zmax=4000, lake_frac=0.05, extra={"octaves": 12})
+                kind="ridged", zmax=4000, lake_frac=0.05,
+                extra={"octaves": 10, "base_wavelength": 640})
 
 
 def batch_instances(seed=1002, count=64, max_side=4096):
