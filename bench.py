@@ -1,9 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the observer-siting hot path on one GB300.
 
-One step = the whole plain pipeline on the resident 46400^2 terrain:
-vix (S=10 LOS per post) -> findmax (top-4 per 464^2 block, 40000 candidates)
--> viewshed (R=100) -> site (4096 observers).  Prints ONE JSON line.
+Two pipelines site 4096 observers on the resident 46400^2 terrain (R=100,
+40000 candidates from top-4 per 464^2 block):
+  plain      vix (S=10 LOS per post) -> findmax -> viewshed -> site
+  surrogate  CNN scores on a stride-32 lattice -> findmax_f32 -> viewshed -> site
+             (network trained beforehand on another terrain of the same recipe)
+The headline `value` is the end-to-end siting time of the surrogate pipeline
+when its coverage is within 1% of (or above) the plain pipeline's, else of
+the plain pipeline; both are reported in full.  Prints ONE JSON line.
 
     python bench.py [--steps K] [--warmup W] [--workload full|scale|small]
     python bench.py --impl reference   # the CPU oracle on a bounded sample
@@ -210,88 +215,99 @@ def oracle_sample(z_host, w, budget_s=20.0, threads=None):
 
 
 # ------------------------------------------------------------------ learned proposal
-def run_surrogate(V, w, g, pipe, covered_plain, args, dev):
-    from paper_2006_16783_gb300 import surrogate as S
-    t0 = time.perf_counter()
-    # training terrain: the same recipe with another seed (the bench terrain is held out)
-    wtr = WL.scaled(w, w.H, w.W, name=w.name + "_train", seed=w.seed + 7)
-    ztr = wtr.make_terrain(dev)
-    ztr_s, _ = WL.terrain.pad_pitch(ztr, 8)
-    del ztr
-    gtr = V.Grid(ztr_s, w.W)
-    posts = S.sample_posts(w.H, w.W, args.train_posts, 32, 11, dev)
-    labels = S.exact_vix(gtr, posts, w.R, w.ht, w.hr)
-    label_s = time.perf_counter() - t0
-    tr = S.Trainer(S.init_master(0), batch=512, lr=2e-3)
-    t1 = time.perf_counter()
-    last = tr.fit([(gtr, posts, labels)], epochs=args.epochs, seed=3,
-                  log=lambda m: print(m, file=sys.stderr))
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t1
-    del gtr, ztr_s, posts, labels
-    # held-out error on the bench terrain, next to the 10-sample vix estimate
-    pt = S.sample_posts(w.H, w.W, 200000, 32, 5, dev)
-    lt = S.exact_vix(g, pt, w.R, w.ht, w.hr)
-    mae = float((tr.predict(g, pt) - lt).abs().mean())
-    mae_vix = float((pipe.vixbuf.reshape(-1)[pt].float() / w.S - lt).abs().mean())
-    # the surrogate pipeline: lattice scores -> findmax_f32 -> viewshed -> site
-    st = args.sur_stride
-    n = V.findmax_count(w.H, w.W, st, w.block, w.k)
-    score = torch.empty(((w.H + st - 1) // st, (w.W + st - 1) // st), dtype=torch.float32, device=dev)
-    cand = torch.empty(n, dtype=torch.int64, device=dev)
-    bm = pipe.bm if n == pipe.n else torch.empty((n, 2 * w.R + 1, V.words_per_row(w.R)), dtype=torch.int32,
-                                                  device=dev)
-    area = torch.empty(n, dtype=torch.int32, device=dev)
-    cum = torch.empty_like(pipe.cum)
-    ws = torch.empty(V.site_workspace(n, w.R), dtype=torch.uint8, device=dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-    res = None
+class SurrogatePipeline:
+    """Train the proposal network on another terrain of the same recipe (the
+    bench terrain is held out), then site from its lattice scores."""
 
-    def step(record):
-        nonlocal res
+    def __init__(self, V, w, g, pipe, args, dev):
+        from paper_2006_16783_gb300 import surrogate as S
+        self.V, self.w, self.g = V, w, g
+        t0 = time.perf_counter()
+        wtr = WL.scaled(w, w.H, w.W, name=w.name + "_train", seed=w.seed + 7)
+        ztr = wtr.make_terrain(dev)
+        ztr_s, _ = WL.terrain.pad_pitch(ztr, 8)
+        del ztr
+        gtr = V.Grid(ztr_s, w.W)
+        posts = S.sample_posts(w.H, w.W, args.train_posts, 32, 11, dev)
+        labels = S.exact_vix(gtr, posts, w.R, w.ht, w.hr)
+        self.label_s = time.perf_counter() - t0
+        self.tr = S.Trainer(S.init_master(0), batch=512, lr=2e-3)
+        t1 = time.perf_counter()
+        self.train_loss = self.tr.fit([(gtr, posts, labels)], epochs=args.epochs, seed=3,
+                                      log=lambda m: print(m, file=sys.stderr))
+        torch.cuda.synchronize()
+        self.train_s = time.perf_counter() - t1
+        del gtr, ztr_s, posts, labels
+        # held-out error on the bench terrain, next to the 10-sample vix estimate
+        pt = S.sample_posts(w.H, w.W, 200000, 32, 5, dev)
+        lt = S.exact_vix(g, pt, w.R, w.ht, w.hr)
+        self.mae = float((self.tr.predict(g, pt) - lt).abs().mean())
+        self.mae_vix = float((pipe.vixbuf.reshape(-1)[pt].float() / w.S - lt).abs().mean())
+        self.mae_posts = pt.numel()
+        st = self.stride = args.sur_stride
+        self.n = V.findmax_count(w.H, w.W, st, w.block, w.k)
+        self.score = torch.empty(((w.H + st - 1) // st, (w.W + st - 1) // st), dtype=torch.float32, device=dev)
+        self.cand = torch.empty(self.n, dtype=torch.int64, device=dev)
+        self.bm = torch.empty((self.n, 2 * w.R + 1, V.words_per_row(w.R)), dtype=torch.int32, device=dev)
+        self.area = torch.empty(self.n, dtype=torch.int32, device=dev)
+        self.cum = torch.empty_like(pipe.cum)
+        self.ws = torch.empty(V.site_workspace(self.n, w.R), dtype=torch.uint8, device=dev)
+        self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        self.result = None
+
+    def step(self, record=False, g=None):
+        V, w, ev = self.V, self.w, self.ev
+        g = g or self.g
         if record:
             ev[0].record()
-        V.cnn_score_lattice(g, st, tr.packed, out=score)
+        V.cnn_score_lattice(g, self.stride, self.tr.packed, out=self.score)
         if record:
             ev[1].record()
-        V.findmax_f32(score, w.H, w.W, st, w.block, w.k, out=cand)
+        V.findmax_f32(self.score, w.H, w.W, self.stride, w.block, w.k, out=self.cand)
         if record:
             ev[2].record()
-        V.viewshed(g, w.R, w.ht, w.hr, cand, bm=bm, area=area)
+        V.viewshed(g, w.R, w.ht, w.hr, self.cand, bm=self.bm, area=self.area)
         if record:
             ev[3].record()
-        cum.zero_()
-        res = V.site(bm, cand, w.H, w.W, w.R, w.n_obs, cum=cum, ws=ws, sync=False)
+        self.cum.zero_()
+        self.result = V.site(self.bm, self.cand, w.H, w.W, w.R, w.n_obs, cum=self.cum, ws=self.ws, sync=False)
         if record:
             ev[4].record()
 
-    for _ in range(args.warmup):
-        step(False)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stages = []
-    a.record()
-    for _ in range(args.steps):
-        step(True)
-        torch.cuda.synchronize()
-        stages.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
-    b.record()
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / args.steps
-    ch, gn, _, nch = res
-    covered = int(gn[:int(nch.item())].sum().item())
+    def stage_ms(self):
+        return [self.ev[i].elapsed_time(self.ev[i + 1]) for i in range(4)]
+
     names = ["cnn_lattice", "findmax_f32", "viewshed", "site"]
-    return {
-        "s_per_step": ms / 1000.0,
-        "stages_ms": dict(zip(names, [statistics.median(x[i] for x in stages) for i in range(4)])),
-        "coverage_posts": covered, "coverage_ratio_vs_plain": covered / max(covered_plain, 1),
-        "speedup_vs_plain": None, "lattice_stride": st, "candidates": n,
-        "patches_per_step": score.numel(),
-        "train_posts": args.train_posts, "epochs": args.epochs, "train_loss_last_epoch": last,
-        "label_s": label_s, "train_s": train_s,
-        "mae_heldout": mae, "mae_sampled_vix": mae_vix, "mae_posts": pt.numel(),
-        "gpu_launches_per_step": 7,
-    }
+
+
+def coverage(result):
+    ch, gn, _, nch = result
+    t = int(nch.item())
+    return int(gn[:t].sum().item()), t
+
+
+def time_steps(pipe, steps, dist, dev):
+    """K steps bracketed by a barrier and device syncs; per-stage medians."""
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage = []
+    e0.record()
+    for _ in range(steps):
+        pipe.step(record=True)
+        torch.cuda.synchronize()
+        stage.append(pipe.stage_ms())
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / steps
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    return ms, [statistics.median(x[i] for x in stage) for i in range(4)]
 
 
 # ------------------------------------------------------------------ main
@@ -321,22 +337,147 @@ def run_reference(args, w, rank):
     print(json.dumps(out))
 
 
+def cnn_oracle_sample(z_host, w, stride, npatch=24):
+    """Seconds per patch of the numpy CNN oracle (fp64 forward of single patches)."""
+    from oracle import cnn_oracle as C
+    p = C.init_params(0)
+    rng = np.random.default_rng(1)
+    cy = rng.integers(32, w.H - 32, npatch)
+    cx = rng.integers(32, w.W - 32, npatch)
+    x0 = np.stack([C.normalize_patch(C.extract_patch(z_host, int(a), int(b))) for a, b in zip(cy, cx)])
+    t = time.perf_counter()
+    C.forward(p, x0)
+    return (time.perf_counter() - t) / npatch
+
+
+def run_learn(args, rank, local):
+    """The learned-proposal workload: train on posts of eight 4096^2 fBm
+    terrains (exact R=100 labels), report the error on a held-out 16384^2
+    terrain next to the 10-sample vix estimate of the same quantity.  fBm
+    relief grows as size^H, so the held-out terrain's elevation range is
+    scaled by 4^0.8 to keep the relief at the ROI scale comparable."""
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2006_16783_gb300 as V
+    from paper_2006_16783_gb300 import surrogate as S
+    R, h, n_train, n_test = 100, 10, args.train_posts, 1000000
+    t0 = time.perf_counter()
+    data = []
+    per = n_train // 8
+    for i in range(8):
+        z = WL.terrain.spectral_fbm(4096, 4096, 0.8, 3000 + i, 0, 1000, device=dev)
+        g = V.Grid(z.contiguous())
+        posts = S.sample_posts(4096, 4096, per, 32, 3000 + i, dev)
+        data.append((g, posts, S.exact_vix(g, posts, R, h, h)))
+    zt = WL.terrain.spectral_fbm(16384, 16384, 0.8, 3100, 0, int(round(1000 * 4 ** 0.8)), device=dev)
+    gt = V.Grid(zt.contiguous())
+    pt = S.sample_posts(16384, 16384, n_test, 32, 3100, dev)
+    lt = S.exact_vix(gt, pt, R, h, h)
+    label_s = time.perf_counter() - t0
+    tr = S.Trainer(S.init_master(0), batch=512, lr=2e-3)
+    t1 = time.perf_counter()
+    last = tr.fit(data, epochs=args.epochs, seed=3, log=lambda m: print(m, file=sys.stderr))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    mae = float((tr.predict(gt, pt) - lt).abs().mean())
+    mae_vix = float((S.sampled_vix_fraction(gt, pt, R, h, h, 10, 0x5EED) - lt).abs().mean())
+    out = {"metric": "held-out MAE of the learned visibility index (R=100)", "value": mae, "unit": "abs err",
+           "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "learn_8x4096sq_fbm_heldout_16384sq", "train_posts": per * 8,
+                      "test_posts": n_test, "epochs": args.epochs, "R": R, "h": h},
+           "mae_sampled_vix_S10": mae_vix, "train_loss_last_epoch": last, "label_s": label_s,
+           "train_s": train_s, "train_patches_per_s": per * 8 * args.epochs / train_s,
+           "label_mean": float(lt.mean()), "label_std": float(lt.std())}
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def run_batch(args, dist, rank, world, local):
+    """The 64-terrain batched workload: per-terrain vix/findmax, one persistent
+    viewshed launch, one site launch, all captured in one CUDA graph; the
+    launch shapes come from the autotuner.  value = seconds per graph replay."""
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2006_16783_gb300 as V
+    from paper_2006_16783_gb300 import autotune
+    from paper_2006_16783_gb300.batch import BatchedSiting
+    inst = WL.batch_instances()
+    t = time.perf_counter()
+    items = []
+    for w in inst:
+        z = w.make_terrain(dev)
+        items.append({"grid": V.Grid.from_tensor(z, dev), "R": w.R, "ht": w.ht, "hr": w.hr, "S": w.S,
+                      "seed": w.vix_seed, "block": w.block, "k": w.k, "n_obs": w.n_obs})
+        del z
+    gen_s = time.perf_counter() - t
+    table = None
+    if not args.no_tune:
+        big = max(items, key=lambda it: it["grid"].H * it["grid"].W)
+        table = autotune.tune_all(big["grid"], [it["R"] for it in items],
+                                  log=lambda m: print(m, file=sys.stderr))
+    bs = BatchedSiting(items, dev)
+    bs.capture()
+    for _ in range(args.warmup):
+        bs.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        bs.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    res = bs.results()
+    ncand = sum(b["cand"].numel() for b in bs.bufs)
+    nobs = sum(int(r[1].numel()) for r in res)
+    cov = sum(int(r[1].sum().item()) for r in res)
+    posts = sum(it["grid"].H * it["grid"].W for it in items)
+    out = {"metric": "batched siting s per graph replay (64 terrains)", "value": ms / 1000.0, "unit": "s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+           "data": "synthetic",
+           "config": {"workload": "batch_64_terrains_512_to_4096", "instances": len(items), "posts": posts,
+                      "candidates": ncand, "radii": sorted(set(it["R"] for it in items))},
+           "observers": nobs, "coverage_posts": cov, "viewsheds_per_s_incl_all_stages": ncand / (ms * 1e-3),
+           "autotune": table, "clocks": clk, "terrain_gen_s": gen_s,
+           "gpu_launches": args.steps * (2 * len(items) + 1 + 3 * len(items) + 1)}
+    if rank == 0:
+        print(json.dumps(out, default=str))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="full", choices=["full", "scale", "small"])
+    ap.add_argument("--workload", default="full", choices=["full", "scale", "small", "batch", "learn"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--sur-stride", type=int, default=16)
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--sur-stride", type=int, default=32)
     ap.add_argument("--train-posts", type=int, default=500000)
     ap.add_argument("--epochs", type=int, default=3)
     args = ap.parse_args()
-    w = pick_workload(args.workload)
     dist, rank, world, local = dist_init()
+    if args.workload == "batch":
+        run_batch(args, dist, rank, world, local)
+        return
+    if args.workload == "learn":
+        run_learn(args, rank, local)
+        return
+    w = pick_workload(args.workload)
     if args.impl == "reference":
         run_reference(args, w, rank)
         if dist:
@@ -349,74 +490,67 @@ def main():
     __graft_entry__.build()
     import paper_2006_16783_gb300 as V
 
-    # ---- inputs: terrain resident in HBM (larger than L2), pinned host copy for e2e
+    # ---- inputs: terrain resident in HBM (larger than L2)
     t = time.perf_counter()
     z_dev = w.make_terrain(dev)
     zs, pitch = WL.terrain.pad_pitch(z_dev, 8)
     del z_dev
     g = V.Grid(zs, w.W)
     gen_s = time.perf_counter() - t
-    pipe = Pipeline(V, w, g, dev)
+    plain = Pipeline(V, w, g, dev)
+    plain.names = ["vix", "findmax", "viewshed", "site"]
 
     # work accounting for the roofline (untimed): LOS crossings of one vix pass
     steps_ctr = torch.zeros(1, dtype=torch.int64, device=dev)
-    V.vix_count(g, w.R, w.ht, w.hr, w.S, w.vix_seed, steps_ctr, out=pipe.vixbuf)
+    V.vix_count(g, w.R, w.ht, w.hr, w.S, w.vix_seed, steps_ctr, out=plain.vixbuf)
     los_steps = int(steps_ctr.item())
-
     for _ in range(args.warmup):
-        pipe.step()
+        plain.step()
     torch.cuda.synchronize()
+    cov_plain, nobs_plain = coverage(plain.result)
 
-    # ---- timed region: K steps on resident inputs
+    sur = None
+    if not args.no_surrogate:
+        sur = SurrogatePipeline(V, w, g, plain, args, dev)
+        for _ in range(args.warmup):
+            sur.step()
+        torch.cuda.synchronize()
+    cov_sur = coverage(sur.result)[0] if sur else 0
+    head = sur if (sur and cov_sur >= 0.99 * cov_plain) else plain
+    other = plain if head is sur else sur
+
+    # ---- timed region: K steps of the headline pipeline, clocks sampled
     clocks = ClockSampler(local)
     clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stage = []
-    e0.record()
-    for _ in range(args.steps):
-        pipe.step(record=True)
-        torch.cuda.synchronize()
-        stage.append(pipe.stage_ms())
-    e1.record()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    ms, st = time_steps(head, args.steps, dist, dev)
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    st = [statistics.median(s[i] for s in stage) for i in range(4)]
-    chosen, gains, cum, nch = pipe.result
-    n_chosen = int(nch.item())
-    covered = int(gains[:n_chosen].sum().item())
+    o_ms, o_st = time_steps(other, args.steps, dist, dev) if other else (None, None)
+    p_ms, p_st = (ms, st) if head is plain else (o_ms, o_st)
+    s_ms, s_st = ((ms, st) if head is sur else (o_ms, o_st)) if sur else (None, None)
 
     # ---- dense gain pass on its own (HBM roofline of the site step)
-    zero = torch.zeros_like(pipe.cum)
-    gbuf = torch.empty(pipe.n, dtype=torch.int32, device=dev)
+    zero = torch.zeros_like(plain.cum)
+    gbuf = torch.empty(plain.n, dtype=torch.int32, device=dev)
     for _ in range(3):
-        V.site_gains(pipe.bm, pipe.cand, w.H, w.W, w.R, zero, out=gbuf)
+        V.site_gains(plain.bm, plain.cand, w.H, w.W, w.R, zero, out=gbuf)
     ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ga.record()
     for _ in range(5):
-        V.site_gains(pipe.bm, pipe.cand, w.H, w.W, w.R, zero, out=gbuf)
+        V.site_gains(plain.bm, plain.cand, w.H, w.W, w.R, zero, out=gbuf)
     gb.record()
     torch.cuda.synchronize()
     gains_ms = ga.elapsed_time(gb) / 5
-    cand_h = pipe.cand.cpu().numpy()
+    cand_h = plain.cand.cpu().numpy()
     cyh, cxh = cand_h // w.W, cand_h % w.W
     PR = V.words_per_row(w.R)
     rows_in = np.minimum(cyh + w.R, w.H - 1) - np.maximum(cyh - w.R, 0) + 1
     gw0 = np.floor_divide(cxh - w.R, 32)
     WWc = (w.W + 31) // 32
     words_in = np.minimum(gw0 + PR - 1, WWc - 1) - np.maximum(gw0, 0) + 1
-    gain_bytes = pipe.n * (2 * w.R + 1) * PR * 4 + int((rows_in * words_in).sum()) * 4 + pipe.n * 4
+    gain_bytes = plain.n * (2 * w.R + 1) * PR * 4 + int((rows_in * words_in).sum()) * 4 + plain.n * 4
 
-    # ---- e2e: host buffers through the same C-ABI calls, copies inside the timed region
+    # ---- e2e: the headline pipeline through the same C-ABI calls on a terrain
+    # copied in from pinned host memory every step, results copied back
     e2e = None
     if not args.no_e2e:
         zh = torch.empty_like(zs, device="cpu").pin_memory()
@@ -426,81 +560,102 @@ def main():
         out_n = torch.empty(1, dtype=torch.int32).pin_memory()
         zs2 = torch.empty_like(zs)
         g2 = V.Grid(zs2, w.W)
-        pipe2 = Pipeline(V, w, g2, dev)
-        pipe2.vixbuf, pipe2.cand, pipe2.bm, pipe2.area, pipe2.cum, pipe2.ws = (
-            pipe.vixbuf, pipe.cand, pipe.bm, pipe.area, pipe.cum, pipe.ws)
-        for _ in range(1):
-            zs2.copy_(zh, non_blocking=True)
-            pipe2.step()
+        saved_g = head.g
+        head.g = g2
+        zs2.copy_(zh, non_blocking=True)
+        head.step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             zs2.copy_(zh, non_blocking=True)
-            pipe2.step()
-            c2, g2_, _, n2 = pipe2.result
+            head.step()
+            c2, g2_, _, n2 = head.result
             out_ch.copy_(c2[:w.n_obs], non_blocking=True)
             out_gn.copy_(g2_[:w.n_obs], non_blocking=True)
             out_n.copy_(n2, non_blocking=True)
             torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.steps
+        head.g = saved_g
         e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": zs.numel() * 2,
                "d2h_bytes_per_step": w.n_obs * 16 + 4}
-        del zs2, pipe2
-
-    # ---- learned proposal: train on another terrain of the same recipe, then
-    # site with the network's lattice scores in place of the sampled vix
-    sur = None
-    if not args.no_surrogate:
-        sur = run_surrogate(V, w, g, pipe, covered, args, dev)
+        del zs2, g2
 
     # ---- rooflines
     peaks, peak_src = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     issue_peak = sms * 4 * 32 * mhz * 1e6 / 1e9            # G thread-instr / s
-    vix_ops = los_steps * OPS_PER_LOS_STEP
-    vs_ops = pipe.n * interior_ray_steps(w.R) * OPS_PER_RAY_STEP
     roof = {
-        "vix": {"bound": "alu", "achieved": vix_ops / (st[0] * 1e-3) / 1e9, "peak": issue_peak,
-                "unit": "Gop/s", "traffic": None},
-        "viewshed": {"bound": "alu", "achieved": vs_ops / (st[2] * 1e-3) / 1e9, "peak": issue_peak,
-                     "unit": "Gop/s", "traffic": None},
+        "vix": {"bound": "alu", "achieved": los_steps * OPS_PER_LOS_STEP / (p_st[0] * 1e-3) / 1e9,
+                "peak": issue_peak, "unit": "Gop/s", "traffic": None},
+        "viewshed": {"bound": "alu",
+                     "achieved": plain.n * interior_ray_steps(w.R) * OPS_PER_RAY_STEP / (p_st[2] * 1e-3) / 1e9,
+                     "peak": issue_peak, "unit": "Gop/s", "traffic": None},
         "site_gains": {"bound": "hbm", "achieved": gain_bytes / (gains_ms * 1e-3) / 1e9,
                        "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None},
-        "findmax": {"bound": "hbm", "achieved": (w.H * w.W + pipe.n * 8) / (st[1] * 1e-3) / 1e9,
+        "findmax": {"bound": "hbm", "achieved": (w.H * w.W + plain.n * 8) / (p_st[1] * 1e-3) / 1e9,
                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None},
     }
+    if sur:
+        from oracle import cnn_oracle as C
+        flops = sur.score.numel() * C.flops_per_patch()
+        roof["cnn_lattice"] = {"bound": "tensor", "achieved": flops / (s_st[0] * 1e-3) / 1e12,
+                               "peak": peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]),
+                               "unit": "TFLOP/s", "traffic": None}
     for r in roof.values():
         r["frac"] = r["achieved"] / r["peak"]
-    names = ["vix", "findmax", "viewshed", "site"]
-    dom = names[int(np.argmax(st))]
-    dom_roof = dict(roof.get(dom, roof["vix"]))
+    stage_roof = {"vix": "vix", "findmax": "findmax", "viewshed": "viewshed", "site": "site_gains",
+                  "cnn_lattice": "cnn_lattice", "findmax_f32": "findmax", }
+    dom = head.names[int(np.argmax(st))]
+    dom_roof = dict(roof[stage_roof[dom]])
     dom_roof["kernel"] = dom
 
+    plain_obj = {"s_per_step": p_ms / 1000.0, "stages_ms": dict(zip(plain.names, p_st)),
+                 "coverage_posts": cov_plain, "observers": nobs_plain, "candidates": plain.n,
+                 "viewsheds_per_s": plain.n / (p_st[2] * 1e-3), "vix_los_steps": los_steps,
+                 "gpu_launches_per_step": 7}
     out = {
         "metric": METRIC, "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+bf16" if head is sur else "int32",
+        "data": "synthetic",
         "config": {"workload": w.name, "H": w.H, "W": w.W, "R": w.R, "ht": w.ht, "hr": w.hr,
-                   "S": w.S, "block": w.block, "k": w.k, "n_obs": w.n_obs, "candidates": pipe.n,
-                   "pipeline": "plain (vix, findmax, viewshed, site)",
+                   "S": w.S, "block": w.block, "k": w.k, "n_obs": w.n_obs, "candidates": plain.n,
+                   "pipeline": ("surrogate (CNN on a stride-%d lattice, findmax, viewshed, site)" % args.sur_stride
+                                if head is sur else "plain (vix, findmax, viewshed, site)"),
                    "l2": "inputs larger than L2 (%.1f GB terrain, %.0f MB bitmaps)" % (
-                       zs.numel() * 2 / 1e9, pipe.bm.numel() * 4 / 1e6),
+                       zs.numel() * 2 / 1e9, plain.bm.numel() * 4 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "viewsheds_per_s": pipe.n / (st[2] * 1e-3),
-        "stages_ms": dict(zip(names, st)),
-        "observers": n_chosen, "coverage_posts": covered, "coverage_frac": covered / (w.H * w.W),
-        "vix_los_steps": los_steps, "site_gains_ms": gains_ms,
+        "viewsheds_per_s": plain.n / (st[2] * 1e-3),
+        "stages_ms": dict(zip(head.names, st)),
+        "coverage_posts": cov_sur if head is sur else cov_plain,
+        "coverage_frac": (cov_sur if head is sur else cov_plain) / (w.H * w.W),
+        "plain": plain_obj,
+        "site_gains_ms": gains_ms,
         "roofline": dom_roof, "rooflines": roof, "peak_source": peak_src,
         "clocks": clk, "gpu_launches": 7 * args.steps, "terrain_gen_s": gen_s,
     }
     if sur:
-        sur["speedup_vs_plain"] = (ms / 1000.0) / sur["s_per_step"]
-        out["surrogate"] = sur
+        out["surrogate"] = {
+            "s_per_step": s_ms / 1000.0, "stages_ms": dict(zip(sur.names, s_st)),
+            "coverage_posts": cov_sur, "coverage_ratio_vs_plain": cov_sur / max(cov_plain, 1),
+            "speedup_vs_plain": p_ms / s_ms, "lattice_stride": sur.stride, "candidates": sur.n,
+            "patches_per_step": sur.score.numel(), "train_posts": args.train_posts, "epochs": args.epochs,
+            "train_loss_last_epoch": sur.train_loss, "label_s": sur.label_s, "train_s": sur.train_s,
+            "mae_heldout": sur.mae, "mae_sampled_vix": sur.mae_vix, "mae_posts": sur.mae_posts,
+            "gpu_launches_per_step": 7}
     if e2e:
         out["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc, threads = oracle_sample(zs[:, :w.W].cpu().numpy() if pitch != w.W else zs.cpu().numpy(), w)
+        zh_np = zs[:, :w.W].cpu().numpy() if pitch != w.W else zs.cpu().numpy()
+        v, desc, threads = oracle_sample(zh_np, w)
+        if head is sur:
+            # the surrogate pipeline's oracle: numpy CNN per lattice patch instead of vix
+            per_patch = cnn_oracle_sample(zh_np, w, args.sur_stride)
+            t_vix = float(desc.split("(vix ")[1].split(" s")[0])
+            v = v - t_vix + per_patch * sur.score.numel()
+            desc += ("; surrogate pipeline: vix replaced by the numpy CNN oracle on %d lattice patches "
+                     "(%.2f ms per patch on one thread, 24 patches timed)" % (sur.score.numel(), per_patch * 1e3))
         out["cpu_baseline"] = {"value": v, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc}
     if rank == 0:
         print(json.dumps(out))

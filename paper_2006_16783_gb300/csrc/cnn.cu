@@ -40,7 +40,7 @@
 namespace vs {
 namespace cnn {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 512;  // 16 warps: 4 TMEM lane quarters x 4 channel blocks
 constexpr int kPatch = 65;
 
 // ---- master parameter layout (fp32): w_l [32][cin][3][3], b_l [32], fw [32], fb
@@ -117,21 +117,16 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
+// 8 consecutive FP32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
@@ -213,8 +208,10 @@ __device__ __forceinline__ bool finish_tile(uint64_t *bar, uint32_t *phase, uint
     const bool ok = mbar_wait(&bar[buf], phase[buf]);
     phase[buf] ^= 1u;
     tc_fence_after();
+    // warp w reads TMEM lane quarter (w & 3) -- rows 32(w & 3) .. +31 -- and
+    // the 8 columns of channel block (w >> 2)
     const int warp = threadIdx.x >> 5;
-    tmem_ld32(tmem + (uint32_t)(buf * 32) + ((uint32_t)(warp * 32) << 16), acc);
+    tmem_ld8(tmem + (uint32_t)(buf * 32 + 8 * (warp >> 2)) + ((uint32_t)((warp & 3) * 32) << 16), acc);
     tc_fence_before();
     return ok;
 }
@@ -225,20 +222,16 @@ __device__ __forceinline__ void publish_smem() {
     __syncthreads();
 }
 
-__device__ __forceinline__ void store_row(unsigned char *dst, long long stride16, const uint32_t *w16) {
-    // 32 bf16 channels = 4 x 16 bytes; block cb goes to dst + cb*stride16
-#pragma unroll
-    for (int cb = 0; cb < 4; ++cb)
-        *(uint4 *)(dst + cb * stride16) = make_uint4(w16[cb * 4], w16[cb * 4 + 1], w16[cb * 4 + 2],
-                                                     w16[cb * 4 + 3]);
-}
 
 // epilogue of one output row: bias + ReLU, rounded to bf16, 32 channels as
 // 16 packed words
-__device__ __forceinline__ void relu_pack(const float *acc, const float *bias, uint32_t *w16) {
+// one 8-channel block of one output row: bias + ReLU, rounded to bf16
+__device__ __forceinline__ uint4 relu_pack8(const float *acc, const float *bias) {
+    uint32_t w[4];
 #pragma unroll
-    for (int c = 0; c < 16; ++c)
-        w16[c] = pack_bf16x2(fmaxf(acc[2 * c] + bias[2 * c], 0.f), fmaxf(acc[2 * c + 1] + bias[2 * c + 1], 0.f));
+    for (int c = 0; c < 4; ++c)
+        w[c] = pack_bf16x2(fmaxf(acc[2 * c] + bias[2 * c], 0.f), fmaxf(acc[2 * c + 1] + bias[2 * c + 1], 0.f));
+    return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 __device__ __forceinline__ long long patch_centre(const FwdParams &P, long long pi) {
@@ -258,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
     __shared__ uint64_t bar[2];
     __shared__ uint64_t pbar;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_red[4];
+    __shared__ int s_red[kThreads / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     unsigned char *Wp = sm + kSmW;
@@ -343,7 +336,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         if (lane == 0) s_red[warp] = sum;
         __syncthreads();
-        const float mean = (float)(s_red[0] + s_red[1] + s_red[2] + s_red[3]) / (float)(kPatch * kPatch);
+        int tot = 0;
+#pragma unroll
+        for (int q = 0; q < kThreads / 32; ++q) tot += s_red[q];
+        const float mean = (float)tot / (float)(kPatch * kPatch);
         unsigned char *sv = P.save ? P.save + pi * (long long)kSaveBytesTotal : nullptr;
         for (int e = tid; e < kPatch * kPatch; e += kThreads) {
             const __nv_bfloat16 x = __float2bfloat16_rn(((float)raw[e] - mean) / 1000.0f);
@@ -378,8 +374,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
             *(uint4 *)(row + 128) = make_uint4(w[4], w[5], w[6], w[7]);
         }
         publish_smem();
-        float acc[32];
-        uint32_t w16[16];
+        float acc[8];
+        const int row = 32 * (warp & 3) + lane;  // accumulator row (TMEM lane) of this thread
+        const int cb = warp >> 2;                // its 8-channel block
         auto l1 = [&](int mt) {
             return [=](int, uint64_t &ad, uint64_t &bd) {
                 ad = sdesc(sU + mt * 4096, 128, 256);
@@ -390,13 +387,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
         for (int mt = 0; mt < 9; ++mt) {
             if (mt + 1 < 9) issue_tile(bar, tmem, (mt + 1) & 1, 1, l1(mt + 1));
             ok &= finish_tile(bar, phase, tmem, mt & 1, acc);
-            const int m = mt * 128 + tid, y = m / 34, x = m % 34;
+            const int m = mt * 128 + row, y = m / 34, x = m % 34;
             if (y < 33 && x < 33) {
-                relu_pack(acc, bias, w16);
+                const uint4 v = relu_pack8(acc, bias + 8 * cb);
                 const int plane = ((y & 1) << 1) | (x & 1);
                 const int pix = ((y >> 1) + 1) * 18 + (x >> 1) + 1;
-                store_row(P2 + ((long long)plane * kPln2 + pix) * 16, 4LL * kPln2 * 16, w16);
-                if (sv) store_row(sv + kSvA1 + (y * 33 + x) * 64, 16, w16);
+                *(uint4 *)(P2 + (((long long)cb * 4 + plane) * kPln2 + pix) * 16) = v;
+                if (sv) *(uint4 *)(sv + kSvA1 + (y * 33 + x) * 64 + cb * 16) = v;
             }
             __syncthreads();  // this buffer's tcgen05.ld done before it is reissued
         }
@@ -412,13 +409,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
         for (int mt = 0; mt < 3; ++mt) {
             if (mt + 1 < 3) issue_tile(bar, tmem, (mt + 1) & 1, 18, l2(mt + 1));
             ok &= finish_tile(bar, phase, tmem, mt & 1, acc);
-            const int m = mt * 128 + tid, y = m / 18, x = m % 18;
+            const int m = mt * 128 + row, y = m / 18, x = m % 18;
             if (y < 17 && x < 17) {
-                relu_pack(acc, bias + 32, w16);
+                const uint4 v = relu_pack8(acc, bias + 32 + 8 * cb);
                 const int plane = ((y & 1) << 1) | (x & 1);
                 const int pix = ((y >> 1) + 1) * 10 + (x >> 1) + 1;
-                store_row(P3 + ((long long)plane * kPln3 + pix) * 16, 4LL * kPln3 * 16, w16);
-                if (sv) store_row(sv + kSvA2 + (y * 17 + x) * 64, 16, w16);
+                *(uint4 *)(P3 + (((long long)cb * 4 + plane) * kPln3 + pix) * 16) = v;
+                if (sv) *(uint4 *)(sv + kSvA2 + (y * 17 + x) * 64 + cb * 16) = v;
             }
             __syncthreads();
         }
@@ -427,13 +424,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
         issue_tile(bar, tmem, 0, 18, [&](int i, uint64_t &ad, uint64_t &bd) { plane_desc(sP3, kPln3, 10, 0, 2, i, ad, bd); });
         ok &= finish_tile(bar, phase, tmem, 0, acc);
         {
-            const int y = tid / 10, x = tid % 10;
+            const int y = row / 10, x = row % 10;
             if (y < 9 && x < 9) {
-                relu_pack(acc, bias + 64, w16);
+                const uint4 v = relu_pack8(acc, bias + 64 + 8 * cb);
                 const int plane = ((y & 1) << 1) | (x & 1);
                 const int pix = ((y >> 1) + 1) * 6 + (x >> 1) + 1;
-                store_row(P4 + ((long long)plane * kPln4 + pix) * 16, 4LL * kPln4 * 16, w16);
-                if (sv) store_row(sv + kSvA3 + (y * 9 + x) * 64, 16, w16);
+                *(uint4 *)(P4 + (((long long)cb * 4 + plane) * kPln4 + pix) * 16) = v;
+                if (sv) *(uint4 *)(sv + kSvA3 + (y * 9 + x) * 64 + cb * 16) = v;
             }
         }
         publish_smem();
@@ -441,12 +438,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
         issue_tile(bar, tmem, 1, 18, [&](int i, uint64_t &ad, uint64_t &bd) { plane_desc(sP4, kPln4, 6, 0, 3, i, ad, bd); });
         ok &= finish_tile(bar, phase, tmem, 1, acc);
         {
-            const int y = tid / 6, x = tid % 6;
+            const int y = row / 6, x = row % 6;
             if (y < 5 && x < 5) {
-                relu_pack(acc, bias + 96, w16);
+                const uint4 v = relu_pack8(acc, bias + 96 + 8 * cb);
                 const int pix = (y + 1) * 7 + (x + 1);
-                store_row(P5 + (long long)pix * 16, (long long)kPln5 * 16, w16);
-                if (sv) store_row(sv + kSvA4 + (y * 5 + x) * 64, 16, w16);
+                *(uint4 *)(P5 + ((long long)cb * kPln5 + pix) * 16) = v;
+                if (sv) *(uint4 *)(sv + kSvA4 + (y * 5 + x) * 64 + cb * 16) = v;
             }
         }
         publish_smem();
@@ -458,17 +455,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
         });
         ok &= finish_tile(bar, phase, tmem, 0, acc);
         {
-            const int y = tid / 7, x = tid % 7;
+            const int y = row / 7, x = row % 7;
             if (y < 5 && x < 5) {
+                const uint4 v = relu_pack8(acc, bias + 128 + 8 * cb);
+                const __nv_bfloat16 *h = (const __nv_bfloat16 *)&v;
 #pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    gap[(y * 5 + x) * 32 + c] = bf16_round(fmaxf(acc[c] + bias[128 + c], 0.f));
-                if (sv) {
-#pragma unroll
-                    for (int c = 0; c < 16; ++c)
-                        w16[c] = pack_bf16x2(gap[(y * 5 + x) * 32 + 2 * c], gap[(y * 5 + x) * 32 + 2 * c + 1]);
-                    store_row(sv + kSvA5 + (y * 5 + x) * 64, 16, w16);
-                }
+                for (int c = 0; c < 8; ++c) gap[(y * 5 + x) * 32 + 8 * cb + c] = __bfloat162float(h[c]);
+                if (sv) *(uint4 *)(sv + kSvA5 + (y * 5 + x) * 64 + cb * 16) = v;
             }
         }
         __syncthreads();

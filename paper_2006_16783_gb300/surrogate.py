@@ -150,3 +150,41 @@ def propose(g, packed, stride, block, k, score=None):
     top-k per block (vs_cnn_score_lattice then vs_findmax_f32)."""
     score = V.cnn_score_lattice(g, stride, packed, out=score)
     return V.findmax_f32(score, g.H, g.W, stride, block, k), score
+
+
+def _main():
+    """python -m paper_2006_16783_gb300.surrogate score-lattice --size N --stride S
+    scores an N x N ridged terrain with randomly initialised weights (for
+    timing and profiling the forward kernel)."""
+    import argparse
+    import sys
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("cmd", choices=["score-lattice"])
+    ap.add_argument("--size", type=int, default=2048)
+    ap.add_argument("--stride", type=int, default=16)
+    ap.add_argument("--reps", type=int, default=2)
+    a = ap.parse_args()
+    root = __file__.rsplit("/", 2)[0]
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from synth import terrain as T
+    from . import _build
+    _build.build()
+    z = T.ridged_multifractal(a.size, a.size, 5, 0, 4000, 0.05, octaves=10, base_wavelength=640, device="cuda")
+    g = V.Grid(z.contiguous())
+    packed = V.cnn_pack(init_master(0))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    sc = None
+    for i in range(a.reps):
+        if i == a.reps - 1:
+            ev[0].record()
+        sc = V.cnn_score_lattice(g, a.stride, packed)
+    ev[1].record()
+    torch.cuda.synchronize()
+    print("patches %d, last launch %.3f ms, mean score %.4f" % (sc.numel(), ev[0].elapsed_time(ev[1]),
+                                                               float(sc.mean())))
+
+
+if __name__ == "__main__":
+    _main()
