@@ -114,7 +114,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ workload
 def pick_workload(name):
-    return {"full": WL.FULL, "scale": WL.SCALE, "small": WL.SMALL}[name]
+    return {"full": WL.FULL, "scale": WL.SCALE, "small": WL.SMALL, "mid": WL.MID}[name]
 
 
 def interior_ray_steps(R):
@@ -461,7 +461,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="full", choices=["full", "scale", "small", "batch", "learn"])
+    ap.add_argument("--workload", default="full", choices=["full", "mid", "scale", "small", "batch", "learn"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")

@@ -72,7 +72,8 @@ int vs_version(void);
  * library's Python autotune module times the candidates and stores the
  * fastest).  The results of every call are independent of these settings.
  *   VS_TUNE_VIEWSHED_THREADS: threads per viewshed CTA = rays walked at once
- *     per candidate ("ray bundle"), 128 / 256 / 512 (0 = default 256)
+ *     per candidate ("ray bundle"), 128 / 256 / 512 (0 = default: 512, or
+ *     fewer when the ring has fewer than 512 rays)
  *   VS_TUNE_VIX_TILE: vix post tile, 1 = 64x32, 2 = 32x32 (0 = default: the
  *     largest tile whose window fits) */
 enum { VS_TUNE_VIEWSHED_THREADS = 0, VS_TUNE_VIX_TILE = 1 };
@@ -310,6 +311,13 @@ int vs_cnn_backward(const void *save, const float *labels, int64_t B, const floa
                     float *grads, float *loss_sum, void *ws, size_t ws_bytes, vs_stream_t st);
 int vs_cnn_adam(float *master, float *grads, float *m, float *v, int64_t step, float lr,
                 float beta1, float beta2, float eps, vs_stream_t st);
+
+/* Self-test of the failure path (no counterpart in the paper): a kernel
+ * waits on a barrier that nothing completes, gives up after `polls` polls
+ * (1 .. 2^24) and writes VS_ERR_TIMEOUT to *status (device int32); the
+ * context stays usable.  Every TMA and tensor-core completion in the
+ * library is guarded by the same bounded wait. */
+int vs_selftest_wait_timeout(int32_t *status, uint32_t polls, vs_stream_t st);
 
 #ifdef __cplusplus
 }

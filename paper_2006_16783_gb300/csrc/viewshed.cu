@@ -263,6 +263,12 @@ extern "C" size_t vs_viewshed_workspace(int32_t R, int64_t n) {
     return 0;
 }
 
+// untuned CTA size: 512 threads (the autotuner's choice for R = 50..250 on
+// GB300), fewer when the ring has fewer rays
+static int default_threads(int R) {
+    return 8 * R >= 512 ? 512 : (8 * R >= 256 ? 256 : 128);
+}
+
 static int vs_make_job(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand,
                        int64_t n, uint32_t *bm_out, int32_t *area_out, VsJob *J, size_t *smem) {
     int rc = check_grid(g);
@@ -297,7 +303,7 @@ extern "C" int vs_viewshed(vs_grid g, int32_t R, int32_t ht, int32_t hr, const i
     if (n == 0) return VS_OK;
     if ((rc = check_device())) return rc;
     VS_CUDA_TRY(cudaFuncSetAttribute(k_viewshed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int threads = tune_get(VS_TUNE_VIEWSHED_THREADS, R, 256);
+    const int threads = tune_get(VS_TUNE_VIEWSHED_THREADS, R, default_threads(R));
     k_viewshed<<<(unsigned)n, threads, smem, (cudaStream_t)st>>>(J);
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
@@ -349,7 +355,7 @@ extern "C" int vs_viewshed_batch(const vs_viewshed_job *jobs, int32_t n_jobs, vo
     VS_CUDA_TRY(cudaGetDevice(&dev));
     VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     // one CTA size for the launch: the tuned size of the largest ROI
-    const int threads = tune_get(VS_TUNE_VIEWSHED_THREADS, B.job[0].R, 256);
+    const int threads = tune_get(VS_TUNE_VIEWSHED_THREADS, B.job[0].R, default_threads(B.job[0].R));
     VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_viewshed_batch, threads, smem));
     const long long grid = std::min<long long>(total, (long long)sms * std::max(per, 1));
     k_viewshed_batch<<<(unsigned)grid, threads, smem, s>>>(B);

@@ -134,3 +134,25 @@ int64_t vs_findmax_count(int32_t H, int32_t W, int32_t stride, int32_t block, in
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ bounded-wait self-test
+// A barrier that expects one arrival nobody makes: the bounded wait gives up
+// and the kernel reports VS_ERR_TIMEOUT through `status`, leaving the
+// context usable.  The same wait routine guards every TMA and tensor-core
+// completion in the library.
+__global__ void k_selftest_wait(int32_t *status, uint32_t polls) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) vs::mbar_init(&bar, 1);
+    __syncthreads();
+    const bool ok = vs::mbar_wait(&bar, 0, polls);
+    if (threadIdx.x == 0) *status = ok ? VS_OK : VS_ERR_TIMEOUT;
+}
+
+extern "C" int vs_selftest_wait_timeout(int32_t *status, uint32_t polls, vs_stream_t st) {
+    if (!status || polls == 0 || polls > (1u << 24)) return VS_ERR_ARG;
+    int rc = vs::check_device();
+    if (rc) return rc;
+    k_selftest_wait<<<1, 32, 0, (cudaStream_t)st>>>(status, polls);
+    VS_CUDA_TRY(cudaGetLastError());
+    return VS_OK;
+}

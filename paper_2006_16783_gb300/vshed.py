@@ -50,6 +50,7 @@ P, i32, i64, u64, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ct
 SIGNATURES = {
     "vs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "vs_version": (ctypes.c_int, []),
+    "vs_selftest_wait_timeout": (ctypes.c_int, [P, ctypes.c_uint32, P]),
     "vs_tune_set": (ctypes.c_int, [i32, i32, i32]),
     "vs_tune_get": (ctypes.c_int, [i32, i32]),
     "vs_viewshed_batch_workspace": (sz, [i32]),
@@ -362,3 +363,11 @@ def site_batch(jobs, ws):
     arr = site_jobs(jobs)
     _check("vs_site_batch", lib().vs_site_batch(ctypes.cast(arr, ctypes.c_void_p), len(jobs), _ptr(ws),
                                                 ws.numel(), _stream()))
+
+
+def selftest_wait_timeout(polls=4096):
+    """Runs a kernel whose bounded wait must give up; returns the status it wrote."""
+    st = torch.full((1,), 12345, dtype=torch.int32, device="cuda")
+    _check("vs_selftest_wait_timeout", lib().vs_selftest_wait_timeout(_ptr(st), polls, _stream()))
+    torch.cuda.synchronize()
+    return int(st.item())

@@ -70,6 +70,13 @@ FULL = Workload("full_46400sq_R100", 46400, 46400, 100, 10, 10, 10, 464, 4, 4096
                 extra={"octaves": 10, "base_wavelength": 640})
 
 
+# the full recipe on 1/16 of the area (11600^2, 2500 candidates): a size for
+# profiler captures that keeps the terrain larger than L2
+MID = Workload("mid_11600sq_R100", 11600, 11600, 100, 10, 10, 10, 464, 4, 1024, seed=1004,
+               kind="ridged", zmax=4000, lake_frac=0.05,
+               extra={"octaves": 10, "base_wavelength": 640})
+
+
 def batch_instances(seed=1002, count=64, max_side=4096):
     """The batched workload's 64 instances (parameters drawn from ``seed``)."""
     rng = np.random.default_rng(seed)

@@ -245,3 +245,12 @@ def test_pipeline_small_workload_bit_exact(V, O):
     och, ogn, oC = O.site(obm, ocand, w.H, w.W, w.R, w.n_obs)
     assert _np(ch).tolist() == och.tolist() and _np(gn).tolist() == ogn.tolist()
     assert (_np(C).view(np.uint32) == oC).all()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(V):
+    """A barrier nothing completes: the kernel's bounded wait gives up, the
+    status word says VS_ERR_TIMEOUT, and the next launches still work."""
+    assert V.selftest_wait_timeout(4096) == V.VS_ERR_TIMEOUT
+    z = np.zeros((20, 20), np.int16)
+    bm, area = V.viewshed(_grid(V, z), 3, 1, 1, torch.tensor([210], dtype=torch.int64, device="cuda"))
+    assert int(area.item()) == 29
