@@ -231,7 +231,7 @@ class SurrogatePipeline:
         posts = S.sample_posts(w.H, w.W, args.train_posts, 32, 11, dev)
         labels = S.exact_vix(gtr, posts, w.R, w.ht, w.hr)
         self.label_s = time.perf_counter() - t0
-        self.tr = S.Trainer(S.init_master(0), batch=512, lr=2e-3)
+        self.tr = S.Trainer(S.init_master(0), batch=512, lr=2e-3, patch_step=args.patch_step)
         t1 = time.perf_counter()
         self.train_loss = self.tr.fit([(gtr, posts, labels)], epochs=args.epochs, seed=3,
                                       log=lambda m: print(m, file=sys.stderr))
@@ -260,7 +260,7 @@ class SurrogatePipeline:
         g = g or self.g
         if record:
             ev[0].record()
-        V.cnn_score_lattice(g, self.stride, self.tr.packed, out=self.score)
+        V.cnn_score_lattice(g, self.stride, self.tr.packed, out=self.score, patch_step=self.tr.patch_step)
         if record:
             ev[1].record()
         V.findmax_f32(self.score, w.H, w.W, self.stride, w.block, w.k, out=self.cand)
@@ -337,14 +337,14 @@ def run_reference(args, w, rank):
     print(json.dumps(out))
 
 
-def cnn_oracle_sample(z_host, w, stride, npatch=24):
+def cnn_oracle_sample(z_host, w, stride, step, npatch=24):
     """Seconds per patch of the numpy CNN oracle (fp64 forward of single patches)."""
     from oracle import cnn_oracle as C
     p = C.init_params(0)
     rng = np.random.default_rng(1)
     cy = rng.integers(32, w.H - 32, npatch)
     cx = rng.integers(32, w.W - 32, npatch)
-    x0 = np.stack([C.normalize_patch(C.extract_patch(z_host, int(a), int(b))) for a, b in zip(cy, cx)])
+    x0 = np.stack([C.normalize_patch(C.extract_patch(z_host, int(a), int(b), step)) for a, b in zip(cy, cx)])
     t = time.perf_counter()
     C.forward(p, x0)
     return (time.perf_counter() - t) / npatch
@@ -376,7 +376,7 @@ def run_learn(args, rank, local):
     pt = S.sample_posts(16384, 16384, n_test, 32, 3100, dev)
     lt = S.exact_vix(gt, pt, R, h, h)
     label_s = time.perf_counter() - t0
-    tr = S.Trainer(S.init_master(0), batch=512, lr=2e-3)
+    tr = S.Trainer(S.init_master(0), batch=512, lr=2e-3, patch_step=args.patch_step)
     t1 = time.perf_counter()
     last = tr.fit(data, epochs=args.epochs, seed=3, log=lambda m: print(m, file=sys.stderr))
     torch.cuda.synchronize()
@@ -386,7 +386,8 @@ def run_learn(args, rank, local):
     out = {"metric": "held-out MAE of the learned visibility index (R=100)", "value": mae, "unit": "abs err",
            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
            "config": {"workload": "learn_8x4096sq_fbm_heldout_16384sq", "train_posts": per * 8,
-                      "test_posts": n_test, "epochs": args.epochs, "R": R, "h": h},
+                      "test_posts": n_test, "epochs": args.epochs, "R": R, "h": h,
+                      "patch_step": args.patch_step},
            "mae_sampled_vix_S10": mae_vix, "train_loss_last_epoch": last, "label_s": label_s,
            "train_s": train_s, "train_patches_per_s": per * 8 * args.epochs / train_s,
            "label_mean": float(lt.mean()), "label_std": float(lt.std())}
@@ -467,6 +468,8 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--sur-stride", type=int, default=32)
+    ap.add_argument("--patch-step", type=int, default=1,
+                    help="post spacing inside the CNN's 65x65 input patch")
     ap.add_argument("--train-posts", type=int, default=500000)
     ap.add_argument("--epochs", type=int, default=3)
     args = ap.parse_args()
@@ -640,6 +643,7 @@ def main():
             "s_per_step": s_ms / 1000.0, "stages_ms": dict(zip(sur.names, s_st)),
             "coverage_posts": cov_sur, "coverage_ratio_vs_plain": cov_sur / max(cov_plain, 1),
             "speedup_vs_plain": p_ms / s_ms, "lattice_stride": sur.stride, "candidates": sur.n,
+            "patch_step": sur.tr.patch_step,
             "patches_per_step": sur.score.numel(), "train_posts": args.train_posts, "epochs": args.epochs,
             "train_loss_last_epoch": sur.train_loss, "label_s": sur.label_s, "train_s": sur.train_s,
             "mae_heldout": sur.mae, "mae_sampled_vix": sur.mae_vix, "mae_posts": sur.mae_posts,
@@ -651,7 +655,7 @@ def main():
         v, desc, threads = oracle_sample(zh_np, w)
         if head is sur:
             # the surrogate pipeline's oracle: numpy CNN per lattice patch instead of vix
-            per_patch = cnn_oracle_sample(zh_np, w, args.sur_stride)
+            per_patch = cnn_oracle_sample(zh_np, w, args.sur_stride, args.patch_step)
             t_vix = float(desc.split("(vix ")[1].split(" s")[0])
             v = v - t_vix + per_patch * sur.score.numel()
             desc += ("; surrogate pipeline: vix replaced by the numpy CNN oracle on %d lattice patches "

@@ -268,8 +268,10 @@ int vs_site_gains(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H,
  * Network: x0 = bf16((z - mean over the 65x65 patch) / 1000); four 3x3
  * stride-2 convolutions and one 3x3 stride-1 convolution, 32 channels, bias +
  * ReLU, activations rounded to bf16; global average pool; fc 32 -> 1;
- * sigmoid.  Patches are centred on a post; rows/columns outside the grid are
- * clamped to the nearest edge post.  Products are BF16 x BF16 on the tensor
+ * sigmoid.  Patches are centred on a post; element (r, c), r, c = 0..64, is
+ * the post (cy + (r-32)*patch_step, cx + (c-32)*patch_step) (patch_step 1..64:
+ * step 3 lets the 65x65 input span an R = 100 ROI); rows/columns outside
+ * the grid are clamped to the nearest edge post.  Products are BF16 x BF16 on the tensor
  * cores (tcgen05), accumulated in FP32.
  *
  * Parameters: vs_cnn_param_count() fp32 values ("master" weights, device):
@@ -291,10 +293,10 @@ int vs_cnn_param_count(void);
 size_t vs_cnn_packed_bytes(void);
 size_t vs_cnn_save_bytes(void);
 int vs_cnn_pack(const float *master, void *packed, vs_stream_t st);
-int vs_cnn_forward(vs_grid g, const int64_t *centers, int64_t n, const void *packed, float *out,
-                   void *save, int32_t *status, vs_stream_t st);
-int vs_cnn_score_lattice(vs_grid g, int32_t stride, const void *packed, float *score_out,
-                         int32_t *status, vs_stream_t st);
+int vs_cnn_forward(vs_grid g, const int64_t *centers, int64_t n, int32_t patch_step,
+                   const void *packed, float *out, void *save, int32_t *status, vs_stream_t st);
+int vs_cnn_score_lattice(vs_grid g, int32_t stride, int32_t patch_step, const void *packed,
+                         float *score_out, int32_t *status, vs_stream_t st);
 
 /* Training.  vs_cnn_backward: gradients of the mean L1 loss
  * mean_b |y_b - labels[b]| over a batch of B patches whose forward pass

@@ -155,12 +155,12 @@ def flops_per_patch():
     return tot + 2 * CH
 
 
-def extract_patch(z, cy, cx):
-    """65 x 65 elevations centred on post (cx, cy); rows and columns outside
-    the grid take the nearest edge post."""
+def extract_patch(z, cy, cx, step=1):
+    """65 x 65 elevations centred on post (cx, cy), every ``step``-th post;
+    rows and columns outside the grid take the nearest edge post."""
     H, W = z.shape
-    ys = np.clip(np.arange(cy - 32, cy + 33), 0, H - 1)
-    xs = np.clip(np.arange(cx - 32, cx + 33), 0, W - 1)
+    ys = np.clip(cy + step * np.arange(-32, 33), 0, H - 1)
+    xs = np.clip(cx + step * np.arange(-32, 33), 0, W - 1)
     return np.asarray(z)[np.ix_(ys, xs)]
 
 

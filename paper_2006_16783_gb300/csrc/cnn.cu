@@ -179,6 +179,7 @@ struct FwdParams {
     const int64_t *centers;  // patch centres (post index) or null for the lattice
     long long n;             // number of patches
     int stride, Ws;          // lattice mode: patch i at post ((i / Ws)*stride, (i % Ws)*stride)
+    int step;                // patch element (r, c) is post (cy + (r-32)*step, cx + (c-32)*step)
     const unsigned char *packed;
     float *out;              // n predicted visibility indices
     unsigned char *save;     // optional: activations for the backward pass
@@ -239,9 +240,10 @@ __device__ __forceinline__ long long patch_centre(const FwdParams &P, long long 
     return (pi / P.Ws) * (long long)P.stride * P.W + (pi % P.Ws) * (long long)P.stride;
 }
 
+// staged by TMA: contiguous patches (step 1) whose window lies inside the grid
 __device__ __forceinline__ bool patch_inside(const FwdParams &P, long long cpost) {
     const int cy = (int)(cpost / P.W), cx = (int)(cpost % P.W);
-    return cy >= 32 && cy + 32 < P.H && cx >= 32 && cx + 32 < P.W;
+    return P.step == 1 && cy >= 32 && cy + 32 < P.H && cx >= 32 && cx + 32 < P.W;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_constant__ CUtensorMap tmap,
@@ -326,8 +328,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
             }
         } else {
             for (int e = tid; e < kPatch * kPatch; e += kThreads) {
-                const int r = min(max(cy - 32 + e / kPatch, 0), P.H - 1);
-                const int c = min(max(cx - 32 + e % kPatch, 0), P.W - 1);
+                const int r = min(max(cy + (e / kPatch - 32) * P.step, 0), P.H - 1);
+                const int c = min(max(cx + (e % kPatch - 32) * P.step, 0), P.W - 1);
                 const int16_t v = P.z[(long long)r * P.pitch + c];
                 raw[e] = v;
                 sum += v;
@@ -670,8 +672,9 @@ extern "C" int vs_cnn_pack(const float *master, void *packed, vs_stream_t st) {
 }
 
 static int cnn_forward_launch(vs_grid g, const int64_t *centers, int64_t n, int32_t stride,
-                              const void *packed, float *out, void *save, int32_t *status,
-                              vs_stream_t st) {
+                              int32_t patch_step, const void *packed, float *out, void *save,
+                              int32_t *status, vs_stream_t st) {
+    if (patch_step < 1 || patch_step > 64) return VS_ERR_RANGE;
     int rc = check_grid(g);
     if (rc) return rc;
     if (!packed || !out || ((uintptr_t)packed & 15) || (save && ((uintptr_t)save & 15)))
@@ -681,7 +684,7 @@ static int cnn_forward_launch(vs_grid g, const int64_t *centers, int64_t n, int3
     if ((rc = check_device())) return rc;
     cnn::FwdParams P;
     P.z = g.z; P.H = g.H; P.W = g.W; P.pitch = g.pitch;
-    P.centers = centers; P.n = n; P.stride = stride;
+    P.centers = centers; P.n = n; P.stride = stride; P.step = patch_step;
     P.Ws = stride > 0 ? (g.W + stride - 1) / stride : 1;
     P.packed = (const unsigned char *)packed; P.out = out;
     P.save = (unsigned char *)save; P.status = status;
@@ -698,18 +701,20 @@ static int cnn_forward_launch(vs_grid g, const int64_t *centers, int64_t n, int3
     return VS_OK;
 }
 
-extern "C" int vs_cnn_forward(vs_grid g, const int64_t *centers, int64_t n, const void *packed,
-                              float *out, void *save, int32_t *status, vs_stream_t st) {
+extern "C" int vs_cnn_forward(vs_grid g, const int64_t *centers, int64_t n, int32_t patch_step,
+                              const void *packed, float *out, void *save, int32_t *status,
+                              vs_stream_t st) {
     if (!centers && n > 0) return VS_ERR_ARG;
-    return cnn_forward_launch(g, centers, n, 0, packed, out, save, status, st);
+    return cnn_forward_launch(g, centers, n, 0, patch_step, packed, out, save, status, st);
 }
 
-extern "C" int vs_cnn_score_lattice(vs_grid g, int32_t stride, const void *packed, float *score_out,
-                                    int32_t *status, vs_stream_t st) {
+extern "C" int vs_cnn_score_lattice(vs_grid g, int32_t stride, int32_t patch_step, const void *packed,
+                                    float *score_out, int32_t *status, vs_stream_t st) {
     if (stride < 1) return VS_ERR_RANGE;
     if (g.H < 1 || g.W < 1) return VS_ERR_RANGE;
     const int64_t Hs = (g.H + stride - 1) / stride, Ws = (g.W + stride - 1) / stride;
-    return cnn_forward_launch(g, nullptr, Hs * Ws, stride, packed, score_out, nullptr, status, st);
+    return cnn_forward_launch(g, nullptr, Hs * Ws, stride, patch_step, packed, score_out, nullptr,
+                              status, st);
 }
 
 // per patch: dL/da of layers 5, 4, 3, 2, 1 (fp32)

@@ -77,8 +77,9 @@ def init_master(seed=0, device="cuda"):
 class Trainer:
     """Mini-batch Adam on (grid, post, label) triples drawn from several grids."""
 
-    def __init__(self, master, batch=512, lr=2e-3):
+    def __init__(self, master, batch=512, lr=2e-3, patch_step=1):
         self.master = master
+        self.patch_step = patch_step
         self.batch = batch
         self.lr = lr
         dev = master.device
@@ -94,7 +95,8 @@ class Trainer:
 
     def train_step(self, g, posts, labels):
         B = posts.numel()
-        V.cnn_forward(g, posts, self.packed, out=self.out[:B], save=self.save[:B * V.cnn_save_bytes()])
+        V.cnn_forward(g, posts, self.packed, out=self.out[:B], save=self.save[:B * V.cnn_save_bytes()],
+                      patch_step=self.patch_step)
         self.ws = V.cnn_backward(self.save[:B * V.cnn_save_bytes()], labels, self.master, self.grads,
                                  self.loss, ws=self.ws)
         self.step += 1
@@ -134,7 +136,8 @@ class Trainer:
     def predict(self, g, posts, chunk=1 << 20):
         out = torch.empty(posts.numel(), dtype=torch.float32, device=posts.device)
         for i in range(0, posts.numel(), chunk):
-            V.cnn_forward(g, posts[i:i + chunk].contiguous(), self.packed, out=out[i:i + chunk])
+            V.cnn_forward(g, posts[i:i + chunk].contiguous(), self.packed, out=out[i:i + chunk],
+                          patch_step=self.patch_step)
         return out
 
 
@@ -145,10 +148,10 @@ def sampled_vix_fraction(g, posts, R, ht, hr, S, seed):
     return v.reshape(-1)[posts].float() / float(S)
 
 
-def propose(g, packed, stride, block, k, score=None):
+def propose(g, packed, stride, block, k, score=None, patch_step=1):
     """Candidate posts from the network's scores on a stride lattice:
     top-k per block (vs_cnn_score_lattice then vs_findmax_f32)."""
-    score = V.cnn_score_lattice(g, stride, packed, out=score)
+    score = V.cnn_score_lattice(g, stride, packed, out=score, patch_step=patch_step)
     return V.findmax_f32(score, g.H, g.W, stride, block, k), score
 
 

@@ -73,8 +73,8 @@ SIGNATURES = {
     "vs_cnn_packed_bytes": (sz, []),
     "vs_cnn_save_bytes": (sz, []),
     "vs_cnn_pack": (ctypes.c_int, [P, P, P]),
-    "vs_cnn_forward": (ctypes.c_int, [vs_grid, P, i64, P, P, P, P, P]),
-    "vs_cnn_score_lattice": (ctypes.c_int, [vs_grid, i32, P, P, P, P]),
+    "vs_cnn_forward": (ctypes.c_int, [vs_grid, P, i64, i32, P, P, P, P, P]),
+    "vs_cnn_score_lattice": (ctypes.c_int, [vs_grid, i32, i32, P, P, P, P]),
     "vs_cnn_backward_workspace": (sz, [i64]),
     "vs_cnn_backward": (ctypes.c_int, [P, P, i64, P, P, P, P, sz, P]),
     "vs_cnn_adam": (ctypes.c_int, [P, P, P, P, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -272,14 +272,14 @@ def cnn_pack(master, packed=None):
     return packed
 
 
-def cnn_forward(g, centers, packed, out=None, save=None, status=None):
+def cnn_forward(g, centers, packed, out=None, save=None, status=None, patch_step=1):
     """Predicted visibility index of the patches centred on ``centers``."""
     _need_cuda(centers, packed)
     n = centers.numel()
     if out is None:
         out = torch.empty(n, dtype=torch.float32, device=centers.device)
-    _check("vs_cnn_forward", lib().vs_cnn_forward(g.c(), _ptr(centers), n, _ptr(packed), _ptr(out),
-                                                  _ptr(save), _ptr(status), _stream()))
+    _check("vs_cnn_forward", lib().vs_cnn_forward(g.c(), _ptr(centers), n, patch_step, _ptr(packed),
+                                                  _ptr(out), _ptr(save), _ptr(status), _stream()))
     return out
 
 
@@ -287,13 +287,13 @@ def cnn_save_bytes():
     return lib().vs_cnn_save_bytes()
 
 
-def cnn_score_lattice(g, stride, packed, out=None, status=None):
+def cnn_score_lattice(g, stride, packed, out=None, status=None, patch_step=1):
     """Scores on the lattice of posts (i*stride, j*stride): [ceil(H/s), ceil(W/s)]."""
     Hs, Ws = (g.H + stride - 1) // stride, (g.W + stride - 1) // stride
     if out is None:
         out = torch.empty((Hs, Ws), dtype=torch.float32, device=g.storage.device)
-    _check("vs_cnn_score_lattice", lib().vs_cnn_score_lattice(g.c(), stride, _ptr(packed), _ptr(out),
-                                                              _ptr(status), _stream()))
+    _check("vs_cnn_score_lattice", lib().vs_cnn_score_lattice(g.c(), stride, patch_step, _ptr(packed),
+                                                              _ptr(out), _ptr(status), _stream()))
     return out
 
 

@@ -83,3 +83,19 @@ def test_adam_moves_against_gradient():
     st = {}
     C.adam_step(p, {"a": np.array([0.5, -0.5])}, st, lr=0.1)
     assert np.allclose(p["a"], [0.9, -0.9])
+
+
+def test_extract_patch_slices_and_clamps():
+    """Inside the grid a patch is the plain (strided) slice; at the edges each
+    coordinate is clamped on its own (brute loop on a small grid)."""
+    rng = np.random.default_rng(3)
+    z = rng.integers(-500, 3000, (300, 280)).astype(np.int16)
+    assert np.array_equal(C.extract_patch(z, 150, 140), z[118:183, 108:173])
+    assert np.array_equal(C.extract_patch(z, 150, 140, step=3), z[54:247:3, 44:237:3])
+    for cy, cx, s in [(0, 0, 1), (299, 5, 2), (10, 279, 3), (150, 140, 5)]:
+        p = C.extract_patch(z, cy, cx, step=s)
+        for r in range(65):
+            for c in range(65):
+                y = min(max(cy + (r - 32) * s, 0), 299)
+                x = min(max(cx + (c - 32) * s, 0), 279)
+                assert p[r, c] == z[y, x]

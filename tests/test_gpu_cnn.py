@@ -82,6 +82,32 @@ def test_cnn_lattice_matches_centres(V):
     assert np.array_equal(lat, y)
 
 
+@pytest.mark.parametrize("step", [2, 3])
+def test_cnn_strided_patches(V, step):
+    """patch_step > 1 (every step-th post, clamped at the edges; these patches
+    skip the TMA staging): forward against the oracle, lattice against the
+    per-centre launch."""
+    from oracle import cnn_oracle as C
+    H, W, s = 260, 300, 16
+    z = T.spectral_fbm(H, W, 0.8, 21, 0, 1500).numpy()
+    g = V.Grid.from_tensor(torch.as_tensor(z), "cuda")
+    p = _params(5)
+    packed = V.cnn_pack(torch.as_tensor(C.flatten_params(p)).cuda())
+    pts = [(130, 150), (0, 0), (H - 1, W - 1), (97, 97), (5, 290), (200, 40)]
+    cen = torch.tensor([y * W + x for y, x in pts], dtype=torch.int64, device="cuda")
+    y = V.cnn_forward(g, cen, packed, patch_step=step).cpu().numpy()
+    x0 = np.stack([C.normalize_patch(C.extract_patch(z, cy, cx, step)) for cy, cx in pts])
+    want = C.forward(p, x0)
+    assert np.all(np.abs(y - want) < 5e-3), (y, want)
+    lat = V.cnn_score_lattice(g, s, packed, patch_step=step).cpu().numpy()
+    Hs, Ws = lat.shape
+    cen = torch.tensor([(i * s) * W + j * s for i in range(Hs) for j in range(Ws)], dtype=torch.int64,
+                       device="cuda")
+    assert np.array_equal(lat, V.cnn_forward(g, cen, packed, patch_step=step).cpu().numpy().reshape(Hs, Ws))
+    with pytest.raises(V.VsError):
+        V.cnn_forward(g, cen, packed, patch_step=0)
+
+
 def test_cnn_backward_matches_oracle(V):
     """Gradients of the batch L1 loss, per parameter tensor, against the
     oracle's fp64 backward on the same bf16-rounded operands."""
