@@ -302,12 +302,18 @@ def time_steps(pipe, steps, dist, dev):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1) / steps
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev)
     return ms, [statistics.median(x[i] for x in stage) for i in range(4)]
+
+
+def max_over_ranks(value, dist, dev):
+    """The slowest replica's figure (every rank gets it); identity without a
+    process group."""
+    if not dist:
+        return value
+    tt = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
 
 
 # ------------------------------------------------------------------ main
@@ -437,7 +443,9 @@ def run_batch(args, dist, rank, world, local):
     e1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        dist.barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
     res = bs.results()
     ncand = sum(b["cand"].numel() for b in bs.bufs)
     nobs = sum(int(r[1].numel()) for r in res)
