@@ -271,8 +271,8 @@ int vs_site_gains(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H,
  * sigmoid.  Patches are centred on a post; element (r, c), r, c = 0..64, is
  * the post (cy + (r-32)*patch_step, cx + (c-32)*patch_step) (patch_step 1..64:
  * step 3 lets the 65x65 input span an R = 100 ROI); rows/columns outside
- * the grid are clamped to the nearest edge post.  Products are BF16 x BF16 on the tensor
- * cores (tcgen05), accumulated in FP32.
+ * the grid are clamped to the nearest edge post.  Products are BF16 x BF16 on
+ * the tensor cores (tcgen05), accumulated in FP32.
  *
  * Parameters: vs_cnn_param_count() fp32 values ("master" weights, device):
  *   w_l [32][cin][3][3] then b_l [32] for l = 0..4 (cin = 1 for l = 0, else
@@ -281,8 +281,9 @@ int vs_site_gains(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H,
  * buffer of vs_cnn_packed_bytes(), 16-byte aligned); repack after every
  * weight update.
  *
- * vs_cnn_forward: n patches centred on posts centers[n] (int64 post indices);
- * out[n] = predicted visibility index (fp32).  save (optional, device, n *
+ * vs_cnn_forward: n patches centred on posts centers[n] (int64 post indices
+ * in [0, H*W)); out[n] = predicted visibility index (fp32).  Both entry
+ * points need H*W < 2^32 (else VS_ERR_RANGE).  save (optional, device, n *
  * vs_cnn_save_bytes() bytes, 16-byte aligned) receives every activation for
  * vs_cnn_backward.  status (optional, device int32) is set to VS_ERR_TIMEOUT
  * if a bounded tensor-core wait gave up.

@@ -5,6 +5,7 @@
 //
 // Network (fixed by this library; the paper specifies none):
 //   x0 = bf16((z - mean(patch)) / 1000)                           65x65x1
+//        (fp32: the integer sum / 4225, then a multiply by fp32(0.001))
 //   conv1 3x3 s2 p1 1->32, bias, ReLU, bf16                      33x33x32
 //   conv2 3x3 s2 p1 32->32                                       17x17x32
 //   conv3 3x3 s2 p1 32->32                                        9x 9x32
@@ -12,14 +13,16 @@
 //   conv5 3x3 s1 p1 32->32                                        5x 5x32
 //   global average pool -> fc 32->1 -> sigmoid
 //
-// Forward kernel: one persistent 128-thread CTA per SM works through patches
-// entirely in shared memory.  Every convolution is an implicit GEMM on the
-// 5th-generation tensor cores: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32),
-// M = 128 output pixels, N = 32 channels, K = 16 per instruction, the FP32
-// accumulator in tensor memory (32 columns), read back with tcgen05.ld by
-// the four warps (one TMEM lane quarter each) for the bias + ReLU + BF16
-// epilogue.  Operands are read straight from shared memory through matrix
-// descriptors (no swizzle, K-major 8x16-byte core matrices):
+// Forward kernel: one persistent 512-thread CTA per SM works through patches
+// entirely in shared memory, its warps split into roles (epilogue, front end,
+// MMA issue; see the role table below) that hand work to each other through
+// mbarriers.  Every convolution is an implicit GEMM on the 5th-generation
+// tensor cores: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32), M = 128 output
+// pixels, N = 32 channels, K = 16 per instruction, the FP32 accumulator in
+// tensor memory (32 columns per tile), read back with tcgen05.ld for the
+// bias + ReLU + BF16 epilogue.  Operands are read straight from shared
+// memory through matrix descriptors (no swizzle, K-major 8x16-byte core
+// matrices):
 //   * A stride-2 layer's input is stored as four parity planes (even/odd row
 //     x even/odd column) in blocks of 8 channels, each plane with a zero
 //     border row/column and a row pitch of (output width + 1) pixels.  For
@@ -31,6 +34,9 @@
 //   * The stride-1 last layer uses one plane with a border on all sides.
 //   * The 1-channel first layer uses an explicit im2col tile (K = 9 taps
 //     padded to 16).
+// At N = 32 an MMA costs a fixed ~46 cycles whatever N <= 64 (measured), so
+// the 117 MMAs of a patch bound the kernel at ~6K cycles per patch and SM;
+// the rest of a patch's chain is epilogue and hand-off latency.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -40,7 +46,7 @@
 namespace vs {
 namespace cnn {
 
-constexpr int kThreads = 512;  // 16 warps: 4 TMEM lane quarters x 4 channel blocks
+constexpr int kThreads = 512;  // 16 warps
 constexpr int kPatch = 65;
 
 // ---- master parameter layout (fp32): w_l [32][cin][3][3], b_l [32], fw [32], fb
@@ -72,12 +78,16 @@ constexpr int kPln2 = 18 * 18, kPln3 = 10 * 10, kPln4 = 6 * 6, kPln5 = 7 * 7;
 constexpr int kSmW = 0;
 constexpr int kSmP2 = ((kSmW + kPackedBytes) + 127) & ~127;
 constexpr int kP2Bytes = (16 * kPln2 + 96) * 16;
-constexpr int kSmU = ((kSmP2 + kP2Bytes) + 127) & ~127;  // A1 im2col, later P3/P4/P5
+constexpr int kSmU = ((kSmP2 + kP2Bytes) + 127) & ~127;  // conv1 im2col tile
 constexpr int kA1Bytes = 1152 * 32;
+constexpr int kUBytes = kA1Bytes;
+// conv3..5 inputs reuse the start of the conv2 input region (dead once every
+// conv2 MMA has completed)
 constexpr int kP3Off = 0, kP3Bytes = (16 * kPln3 + 40) * 16;
 constexpr int kP4Off = kP3Off + kP3Bytes, kP4Bytes = (16 * kPln4 + 104) * 16;
 constexpr int kP5Off = kP4Off + kP4Bytes, kP5Bytes = (4 * kPln5 + 100) * 16;
-constexpr int kUBytes = (kP5Off + kP5Bytes) > kA1Bytes ? (kP5Off + kP5Bytes) : kA1Bytes;
+constexpr int kP345Bytes = kP5Off + kP5Bytes;
+static_assert(kP345Bytes <= kP2Bytes, "conv3..5 planes must fit in the conv2 input region");
 constexpr int kSmPatch = ((kSmU + kUBytes) + 127) & ~127;   // 67x67 bf16, zero border
 constexpr int kPatchBytes = ((67 * 67 * 2) + 127) & ~127;
 constexpr int kSmGap = kSmPatch + kPatchBytes;              // 25 x 32 floats
@@ -97,13 +107,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-__device__ __forceinline__ void umma(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
-}
-
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
@@ -115,23 +118,6 @@ __device__ __forceinline__ void tc_fence_before() {
 }
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// 8 consecutive FP32 accumulator columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                   "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&h);
 }
 
 __device__ __forceinline__ float bf16_round(float v) {
@@ -186,314 +172,663 @@ struct FwdParams {
     int *status;             // optional: set to VS_ERR_TIMEOUT if an MMA wait gave up
 };
 
-// Implicit-GEMM tiles run in two halves so that the tensor core works on
-// tile t+1 while the CUDA cores run the epilogue of tile t: issue_tile
-// (after every input of the tile is in shared memory) puts `nmma` MMAs into
-// TMEM accumulator buffer `buf` (32 columns each) and commits them to
-// bar[buf]; finish_tile waits for them and reads this thread's row.
-template <typename F>
-__device__ __forceinline__ void issue_tile(uint64_t *bar, uint32_t tmem, int buf, int nmma, F &&mma_desc) {
-    if (threadIdx.x == 0) {
-        tc_fence_after();
-        for (int i = 0; i < nmma; ++i) {
-            uint64_t ad, bd;
-            mma_desc(i, ad, bd);
-            umma(tmem + (uint32_t)(buf * 32), ad, bd, i > 0 ? 1u : 0u);
-        }
-        umma_commit(&bar[buf]);
-    }
+// one 8-channel block of one accumulator row: bias + ReLU, rounded to bf16
+// (packed fp32 pair adds, then one relu-converting pack per channel pair)
+__device__ __forceinline__ void add_f32x2(float &a0, float &a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 x, y;\n\tmov.b64 x, {%0, %1};\n\tmov.b64 y, {%2, %3};\n\t"
+        "add.rn.f32x2 x, x, y;\n\tmov.b64 {%0, %1}, x;\n\t}"
+        : "+f"(a0), "+f"(a1)
+        : "f"(b0), "f"(b1));
 }
-
-__device__ __forceinline__ bool finish_tile(uint64_t *bar, uint32_t *phase, uint32_t tmem, int buf,
-                                            float *acc) {
-    const bool ok = mbar_wait(&bar[buf], phase[buf]);
-    phase[buf] ^= 1u;
-    tc_fence_after();
-    // warp w reads TMEM lane quarter (w & 3) -- rows 32(w & 3) .. +31 -- and
-    // the 8 columns of channel block (w >> 2)
-    const int warp = threadIdx.x >> 5;
-    tmem_ld8(tmem + (uint32_t)(buf * 32 + 8 * (warp >> 2)) + ((uint32_t)((warp & 3) * 32) << 16), acc);
-    tc_fence_before();
-    return ok;
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
 }
-
-// inputs written by every thread become visible to the tensor core
-__device__ __forceinline__ void publish_smem() {
-    fence_proxy_async_smem();
-    __syncthreads();
-}
-
-
-// epilogue of one output row: bias + ReLU, rounded to bf16, 32 channels as
-// 16 packed words
-// one 8-channel block of one output row: bias + ReLU, rounded to bf16
-__device__ __forceinline__ uint4 relu_pack8(const float *acc, const float *bias) {
+__device__ __forceinline__ uint4 relu_pack8(float *acc, const float *bias) {
     uint32_t w[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-        w[c] = pack_bf16x2(fmaxf(acc[2 * c] + bias[2 * c], 0.f), fmaxf(acc[2 * c + 1] + bias[2 * c + 1], 0.f));
+    for (int c = 0; c < 4; ++c) {
+        add_f32x2(acc[2 * c], acc[2 * c + 1], bias[2 * c], bias[2 * c + 1]);
+        w[c] = relu_bf16x2(acc[2 * c], acc[2 * c + 1]);
+    }
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-__device__ __forceinline__ long long patch_centre(const FwdParams &P, long long pi) {
-    if (P.centers) return P.centers[pi];
-    return (pi / P.Ws) * (long long)P.stride * P.W + (pi % P.Ws) * (long long)P.stride;
+// centre (row, column) of patch pi; posts and patch indices are below 2^32
+// (the host checks H*W), so 32-bit unsigned arithmetic suffices
+__device__ __forceinline__ void patch_rc(const FwdParams &P, long long pi, int &cy, int &cx) {
+    if (P.centers) {
+        const uint32_t c = (uint32_t)P.centers[pi];
+        const uint32_t y = c / (uint32_t)P.W;
+        cy = (int)y;
+        cx = (int)(c - y * (uint32_t)P.W);
+    } else {
+        const uint32_t iy = (uint32_t)pi / (uint32_t)P.Ws;
+        cy = (int)iy * P.stride;
+        cx = (int)((uint32_t)pi - iy * (uint32_t)P.Ws) * P.stride;
+    }
 }
 
 // staged by TMA: contiguous patches (step 1) whose window lies inside the grid
-__device__ __forceinline__ bool patch_inside(const FwdParams &P, long long cpost) {
-    const int cy = (int)(cpost / P.W), cx = (int)(cpost % P.W);
+__device__ __forceinline__ bool patch_inside(const FwdParams &P, int cy, int cx) {
     return P.step == 1 && cy >= 32 && cy + 32 < P.H && cx >= 32 && cx + 32 < P.W;
 }
+
+// ---- warp roles of the forward kernel (16 warps)
+//   warps 0..7   epilogue: TMEM -> bias + ReLU + bf16 -> the next layer's
+//                planes, and the pooling buffer (thread: one accumulator row,
+//                16 channels)
+//   warps 8..14  front: a later patch's posts, mean, normalisation and
+//                im2col, and the head (pool, fc, sigmoid) of an earlier one
+//   warp 15      MMA issue (one lane)
+// so the front end and the head run beside the chain conv1 epilogue -> conv2
+// -> epilogue -> conv3 -> ... -> conv5 epilogue, which alternates between the
+// tensor core and the epilogue warps.
+constexpr int kEpiWarps = 8, kFrontWarps = 7, kMmaWarp = kEpiWarps + kFrontWarps;
+constexpr int kEpiThreads = kEpiWarps * 32, kFrontThreads = kFrontWarps * 32;
+static_assert((kMmaWarp + 1) * 32 == kThreads, "role split must cover the CTA");
+constexpr int kPerFront = (kPatch * kPatch + kFrontThreads - 1) / kFrontThreads;  // posts per front thread
+constexpr int kRowsFront = (1152 + kFrontThreads - 1) / kFrontThreads;           // im2col rows per front thread
+
+// Tensor memory: every accumulator tile of a patch has its own 32 columns
+// (conv1 tiles 0..8, conv2 tiles 0..2, conv3, conv4, conv5: 15 x 32 = 480 of
+// the 512 columns).
+constexpr int kTmemCols = 512;
+constexpr int kColL2 = 9 * 32, kColL3 = 12 * 32, kColL4 = 13 * 32, kColL5 = 14 * 32;
+// mbarriers, each completing once per patch:
+//   tcgen05.commit   conv1 tiles in groups of three, conv2 tiles, conv3, conv4, conv5
+//   front -> MMA     im2col tile written (every front thread arrives)
+//   epilogue -> MMA  conv1 accumulators read; conv1 tiles 0..5 written (all
+//                    that conv2's first tile reads); every conv2 input plane
+//                    written; conv3, conv4, conv5 input planes written
+//   epilogue -> front  pooling buffer written (every epilogue thread arrives)
+//   front -> epilogue  pooling buffer read (one head warp arrives)
+enum {
+    kBarC1 = 0, kBarC2 = 3, kBarC3 = 6, kBarC4 = 7, kBarC5 = 8,
+    kBarURdy = 9, kBarC1Free = 10, kBarP2a = 11, kBarP2 = 12, kBarP3 = 13, kBarP4 = 14, kBarP5 = 15,
+    kBarGap = 16, kBarGapFree = 17,
+    kNBar = 18
+};
+__host__ __device__ constexpr uint32_t bar_count(int b) {
+    return b == kBarURdy ? kFrontThreads : b == kBarGapFree ? 32 : b >= kBarC1Free ? kEpiThreads : 1;
+}
+
+__device__ __forceinline__ void group_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// OR over a group of warps (named barrier with a predicate reduction): the
+// same answer in every thread of the group
+__device__ __forceinline__ bool group_any(int id, int n, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// non-suspending bounded wait (the MMA lane wakes as soon as the phase flips)
+__device__ __forceinline__ bool mbar_wait_spin(uint64_t *bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    for (uint32_t i = 0; i < kWaitPolls; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane, for one
+// or three tiles, with one wait
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld16x3(uint32_t t0, uint32_t t1, uint32_t t2, float (*v)[16]) {
+    uint32_t r[48];
+#define VS_R16(o) "=r"(r[o + 0]), "=r"(r[o + 1]), "=r"(r[o + 2]), "=r"(r[o + 3]), "=r"(r[o + 4]), \
+    "=r"(r[o + 5]), "=r"(r[o + 6]), "=r"(r[o + 7]), "=r"(r[o + 8]), "=r"(r[o + 9]), "=r"(r[o + 10]), \
+    "=r"(r[o + 11]), "=r"(r[o + 12]), "=r"(r[o + 13]), "=r"(r[o + 14]), "=r"(r[o + 15])
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%48];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%49];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%50];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : VS_R16(0), VS_R16(16), VS_R16(32)
+        : "r"(t0), "r"(t1), "r"(t2)
+        : "memory");
+#undef VS_R16
+#pragma unroll
+    for (int i = 0; i < 48; ++i) v[i / 16][i % 16] = __uint_as_float(r[i]);
+}
+// tensor-core MMA with a compile-time accumulate flag
+template <int ACC>
+__device__ __forceinline__ void umma_c(uint32_t dt, uint64_t ad, uint64_t bd) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
+        "l"(ad), "l"(bd), "r"(kIdesc), "n"(ACC));
+}
+
+// The conv3..5 input planes overwrite the start of the conv2 input planes
+// (kP345Bytes / 16 = 2616 sixteen-byte cells).  Cells no epilogue writes --
+// borders, the extra row/column of odd parity planes, tails -- must read as
+// zero, so each layer switch clears exactly those: p345_unwritten(u) for the
+// conv3..5 planes, p2_unwritten(u) for the conv2 planes.  They are disjoint
+// from the cells the epilogues write, so clearing needs no ordering against
+// the epilogue stores.
+__device__ __forceinline__ bool planes_written(int cell, int pitch, int rows_even, int pb) {
+    const int r = cell / pitch, c = cell - r * pitch;
+    const int py = (pb >> 1) & 1, px = pb & 1;  // parity plane of plane block pb
+    return r >= 1 && r <= rows_even - py && c >= 1 && c <= rows_even - px;
+}
+__device__ __forceinline__ bool p345_unwritten(int u) {
+    if (u < 16 * kPln3) return !planes_written(u % kPln3, 10, 9, u / kPln3);
+    u -= kP3Bytes / 16;
+    if (u < 0) return true;
+    if (u < 16 * kPln4) return !planes_written(u % kPln4, 6, 5, u / kPln4);
+    u -= kP4Bytes / 16;
+    if (u < 0) return true;
+    if (u < 4 * kPln5) {
+        const int c = u % kPln5, r = c / 7, x = c % 7;
+        return !(r >= 1 && r <= 5 && x >= 1 && x <= 5);
+    }
+    return true;
+}
+__device__ __forceinline__ bool p2_unwritten(int u) { return !planes_written(u % kPln2, 18, 17, u / kPln2); }
+constexpr int kP345Cells = kP345Bytes / 16;
 
 __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_constant__ CUtensorMap tmap,
                                                              const FwdParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *sm = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    __shared__ uint64_t bar[2];
+    __shared__ uint64_t bar[kNBar];
     __shared__ uint64_t pbar;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_red[kThreads / 32];
+    __shared__ int s_red[kFrontWarps];
+    __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     unsigned char *Wp = sm + kSmW;
-    unsigned char *P2 = sm + kSmP2;
+    unsigned char *X = sm + kSmP2;  // conv2 input planes, then conv3..5 input planes
     unsigned char *U = sm + kSmU;
-    unsigned char *P3 = U + kP3Off, *P4 = U + kP4Off, *P5 = U + kP5Off;
     __nv_bfloat16 *pb = (__nv_bfloat16 *)(sm + kSmPatch);
     float *gap = (float *)(sm + kSmGap);
-    int16_t *raw = (int16_t *)U;  // the patch's posts, before im2col reuses U
     int16_t *stage = (int16_t *)(sm + kSmStage);
 
     // ---- one-time set-up: weights, zeroed planes, barriers, tensor memory
     for (int i = tid; i < kPackedBytes / 16; i += kThreads)
         ((uint4 *)Wp)[i] = ((const uint4 *)P.packed)[i];
-    for (int i = tid; i < kP2Bytes / 16; i += kThreads) ((uint4 *)P2)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < kP2Bytes / 16; i += kThreads) ((uint4 *)X)[i] = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < kPatchBytes / 16; i += kThreads) ((uint4 *)pb)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int b = 0; b < kNBar; ++b) mbar_init(&bar[b], bar_count(b));
         mbar_init(&pbar, 1);
+        s_abort = 0;
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
-                         smem_u32(&s_tmem))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)), "n"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    uint32_t phase[2] = {0u, 0u};
-    uint32_t pphase = 0u;
-    // stage the first patch
-    auto stage_patch = [&](long long pi) {
-        const long long cp = patch_centre(P, pi);
-        const int cy = (int)(cp / P.W), cx = (int)(cp % P.W);
-        const int x0 = floordiv(cx - 32, 8) * 8;
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&pbar, (uint32_t)(kPatch * kStageW * 2));
-        tma_load_3d(stage, &tmap, 0, x0 / 8, cy - 32, &pbar);
-    };
-    if (tid == 0 && blockIdx.x < P.n && patch_inside(P, patch_centre(P, blockIdx.x))) stage_patch(blockIdx.x);
-    bool ok = true;
-    const float *bias = (const float *)(Wp + kPkBias);
-    const float *fc = (const float *)(Wp + kPkFc);
-    const uint32_t sW = smem_u32(Wp), sP2 = smem_u32(P2), sU = smem_u32(U);
-    const uint32_t sP3 = sU + kP3Off, sP4 = sU + kP4Off, sP5 = sU + kP5Off;
+    const long long nk = (P.n - blockIdx.x + gridDim.x - 1) / gridDim.x;  // patches of this CTA
+    volatile int *abort_flag = &s_abort;
 
-    // tap t, K-step ks of a 32->32 layer reading stride-2 parity planes
-    auto plane_desc = [&](uint32_t base, int pln, int pitch, int m0, int l, int i, uint64_t &ad, uint64_t &bd) {
-        const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
-        const int plane = ((ky != 1) << 1) | (kx != 1);
-        const int shift = (ky != 0 ? pitch : 0) + (kx != 0 ? 1 : 0);
-        ad = sdesc(base + ((2 * ks * 4 + plane) * pln + m0 + shift) * 16, 4 * pln * 16, 128);
-        bd = sdesc(sW + pk_bl(l) + (t * 2 + ks) * 1024, 128, 256);
-    };
-
-    for (long long pi = blockIdx.x; pi < P.n; pi += gridDim.x) {
-        // ---- patch: the staged tile, or a clamped gather at the grid edge
-        const long long cpost = patch_centre(P, pi);
-        const int cy = (int)(cpost / P.W), cx = (int)(cpost % P.W);
-        int sum = 0;
-        if (patch_inside(P, cpost)) {
-            if (!mbar_wait(&pbar, pphase)) ok = false;
-            pphase ^= 1u;
-            const int off = (cx - 32) - floordiv(cx - 32, 8) * 8;
-            for (int e = tid; e < kPatch * kPatch; e += kThreads) {
-                const int16_t v = stage[(e / kPatch) * kStageW + off + e % kPatch];
-                raw[e] = v;
-                sum += v;
-            }
-        } else {
-            for (int e = tid; e < kPatch * kPatch; e += kThreads) {
-                const int r = min(max(cy + (e / kPatch - 32) * P.step, 0), P.H - 1);
-                const int c = min(max(cx + (e % kPatch - 32) * P.step, 0), P.W - 1);
-                const int16_t v = P.z[(long long)r * P.pitch + c];
-                raw[e] = v;
-                sum += v;
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) s_red[warp] = sum;
-        __syncthreads();
-        int tot = 0;
+    if (warp < kEpiWarps) {
+        // ================================================================ epilogue
+        const int row = 32 * (warp & 3) + lane;  // accumulator row (TMEM lane)
+        const int half = warp >> 2;              // channels 16*half .. +15 (blocks 2h, 2h+1)
+        const uint32_t tq = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * half);
+        unsigned char *P3 = X + kP3Off, *P4 = X + kP4Off, *P5 = X + kP5Off;
+        const float *bias = (const float *)(Wp + kPkBias);
+        // destinations (16-byte units) of this thread's rows for channel block
+        // 2*half; block 2*half+1 is one plane set further; -1: junk row
+        int d1[9], d2[3], d3, d4, d5;
 #pragma unroll
-        for (int q = 0; q < kThreads / 32; ++q) tot += s_red[q];
-        const float mean = (float)tot / (float)(kPatch * kPatch);
-        unsigned char *sv = P.save ? P.save + pi * (long long)kSaveBytesTotal : nullptr;
-        for (int e = tid; e < kPatch * kPatch; e += kThreads) {
-            const __nv_bfloat16 x = __float2bfloat16_rn(((float)raw[e] - mean) / 1000.0f);
-            pb[(e / kPatch + 1) * 67 + (e % kPatch + 1)] = x;
-            if (sv) ((__nv_bfloat16 *)(sv + kSvInput))[e] = x;
-        }
-        __syncthreads();
-        // the staging tile is free: prefetch the next patch during the convolutions
-        {
-            const long long nx = pi + gridDim.x;
-            if (tid == 0 && nx < P.n && patch_inside(P, patch_centre(P, nx))) stage_patch(nx);
-        }
-
-        // ---- conv1: explicit im2col (1152 rows x 16 K), 9 M-tiles of one MMA each
-        for (int m = tid; m < 1152; m += kThreads) {
-            const int y = m / 34, x = m % 34;
-            uint32_t w[8];
-            if (y < 33 && x < 33) {
-                __nv_bfloat16 t[16];
-#pragma unroll
-                for (int k = 0; k < 16; ++k) t[k] = __float2bfloat16_rn(0.f);
-#pragma unroll
-                for (int k = 0; k < 9; ++k) t[k] = pb[(2 * y + k / 3) * 67 + (2 * x + k % 3)];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) w[k] = *(uint32_t *)&t[2 * k];
-            } else {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) w[k] = 0;
-            }
-            unsigned char *row = U + (m / 8) * 256 + (m % 8) * 16;
-            *(uint4 *)row = make_uint4(w[0], w[1], w[2], w[3]);
-            *(uint4 *)(row + 128) = make_uint4(w[4], w[5], w[6], w[7]);
-        }
-        publish_smem();
-        float acc[8];
-        const int row = 32 * (warp & 3) + lane;  // accumulator row (TMEM lane) of this thread
-        const int cb = warp >> 2;                // its 8-channel block
-        auto l1 = [&](int mt) {
-            return [=](int, uint64_t &ad, uint64_t &bd) {
-                ad = sdesc(sU + mt * 4096, 128, 256);
-                bd = sdesc(sW + kPkB1, 128, 256);
-            };
-        };
-        issue_tile(bar, tmem, 0, 1, l1(0));
         for (int mt = 0; mt < 9; ++mt) {
-            if (mt + 1 < 9) issue_tile(bar, tmem, (mt + 1) & 1, 1, l1(mt + 1));
-            ok &= finish_tile(bar, phase, tmem, mt & 1, acc);
             const int m = mt * 128 + row, y = m / 34, x = m % 34;
-            if (y < 33 && x < 33) {
-                const uint4 v = relu_pack8(acc, bias + 8 * cb);
-                const int plane = ((y & 1) << 1) | (x & 1);
-                const int pix = ((y >> 1) + 1) * 18 + (x >> 1) + 1;
-                *(uint4 *)(P2 + (((long long)cb * 4 + plane) * kPln2 + pix) * 16) = v;
-                if (sv) *(uint4 *)(sv + kSvA1 + (y * 33 + x) * 64 + cb * 16) = v;
-            }
-            __syncthreads();  // this buffer's tcgen05.ld done before it is reissued
+            d1[mt] = (y < 33 && x < 33)
+                         ? (2 * half * 4 + (((y & 1) << 1) | (x & 1))) * kPln2 + ((y >> 1) + 1) * 18 + (x >> 1) + 1
+                         : -1;
         }
-        // A1 is dead: clear the region that now holds the next layers' planes
-        for (int i = tid; i < kUBytes / 16; i += kThreads) ((uint4 *)U)[i] = make_uint4(0, 0, 0, 0);
-        publish_smem();
-
-        // ---- conv2: 3 tiles, input P2 (pitch 18, plane 324), output P3 (pitch 10)
-        auto l2 = [&](int mt) {
-            return [=](int i, uint64_t &ad, uint64_t &bd) { plane_desc(sP2, kPln2, 18, mt * 128, 1, i, ad, bd); };
-        };
-        issue_tile(bar, tmem, 0, 18, l2(0));
-        for (int mt = 0; mt < 3; ++mt) {
-            if (mt + 1 < 3) issue_tile(bar, tmem, (mt + 1) & 1, 18, l2(mt + 1));
-            ok &= finish_tile(bar, phase, tmem, mt & 1, acc);
-            const int m = mt * 128 + row, y = m / 18, x = m % 18;
-            if (y < 17 && x < 17) {
-                const uint4 v = relu_pack8(acc, bias + 32 + 8 * cb);
-                const int plane = ((y & 1) << 1) | (x & 1);
-                const int pix = ((y >> 1) + 1) * 10 + (x >> 1) + 1;
-                *(uint4 *)(P3 + (((long long)cb * 4 + plane) * kPln3 + pix) * 16) = v;
-                if (sv) *(uint4 *)(sv + kSvA2 + (y * 17 + x) * 64 + cb * 16) = v;
-            }
-            __syncthreads();
-        }
-        publish_smem();
-        // ---- conv3: 1 tile, input P3 (pitch 10, plane 100), output P4 (pitch 6)
-        issue_tile(bar, tmem, 0, 18, [&](int i, uint64_t &ad, uint64_t &bd) { plane_desc(sP3, kPln3, 10, 0, 2, i, ad, bd); });
-        ok &= finish_tile(bar, phase, tmem, 0, acc);
-        {
-            const int y = row / 10, x = row % 10;
-            if (y < 9 && x < 9) {
-                const uint4 v = relu_pack8(acc, bias + 64 + 8 * cb);
-                const int plane = ((y & 1) << 1) | (x & 1);
-                const int pix = ((y >> 1) + 1) * 6 + (x >> 1) + 1;
-                *(uint4 *)(P4 + (((long long)cb * 4 + plane) * kPln4 + pix) * 16) = v;
-                if (sv) *(uint4 *)(sv + kSvA3 + (y * 9 + x) * 64 + cb * 16) = v;
-            }
-        }
-        publish_smem();
-        // ---- conv4: 1 tile, input P4 (pitch 6, plane 36), output P5 (stride-1 plane, pitch 7)
-        issue_tile(bar, tmem, 1, 18, [&](int i, uint64_t &ad, uint64_t &bd) { plane_desc(sP4, kPln4, 6, 0, 3, i, ad, bd); });
-        ok &= finish_tile(bar, phase, tmem, 1, acc);
-        {
-            const int y = row / 6, x = row % 6;
-            if (y < 5 && x < 5) {
-                const uint4 v = relu_pack8(acc, bias + 96 + 8 * cb);
-                const int pix = (y + 1) * 7 + (x + 1);
-                *(uint4 *)(P5 + ((long long)cb * kPln5 + pix) * 16) = v;
-                if (sv) *(uint4 *)(sv + kSvA4 + (y * 5 + x) * 64 + cb * 16) = v;
-            }
-        }
-        publish_smem();
-        // ---- conv5 (stride 1): 1 tile, input P5 (pitch 7, plane 49) -> pooling buffer
-        issue_tile(bar, tmem, 0, 18, [&](int i, uint64_t &ad, uint64_t &bd) {
-            const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
-            ad = sdesc(sP5 + ((2 * ks) * kPln5 + ky * 7 + kx) * 16, kPln5 * 16, 128);
-            bd = sdesc(sW + pk_bl(4) + (t * 2 + ks) * 1024, 128, 256);
-        });
-        ok &= finish_tile(bar, phase, tmem, 0, acc);
-        {
-            const int y = row / 7, x = row % 7;
-            if (y < 5 && x < 5) {
-                const uint4 v = relu_pack8(acc, bias + 128 + 8 * cb);
-                const __nv_bfloat16 *h = (const __nv_bfloat16 *)&v;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) gap[(y * 5 + x) * 32 + 8 * cb + c] = __bfloat162float(h[c]);
-                if (sv) *(uint4 *)(sv + kSvA5 + (y * 5 + x) * 64 + cb * 16) = v;
+        for (int mt = 0; mt < 3; ++mt) {
+            const int m = mt * 128 + row, y = m / 18, x = m % 18;
+            d2[mt] = (y < 17 && x < 17)
+                         ? (2 * half * 4 + (((y & 1) << 1) | (x & 1))) * kPln3 + ((y >> 1) + 1) * 10 + (x >> 1) + 1
+                         : -1;
+        }
+        {
+            int y = row / 10, x = row % 10;
+            d3 = (y < 9 && x < 9)
+                     ? (2 * half * 4 + (((y & 1) << 1) | (x & 1))) * kPln4 + ((y >> 1) + 1) * 6 + (x >> 1) + 1
+                     : -1;
+            y = row / 6; x = row % 6;
+            d4 = (y < 5 && x < 5) ? 2 * half * kPln5 + (y + 1) * 7 + (x + 1) : -1;
+            y = row / 7; x = row % 7;
+            d5 = (y < 5 && x < 5) ? y * 5 + x : -1;
+        }
+        auto load_bias = [&](int l, float *b) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) b[c] = bias[32 * l + 16 * half + c];
+        };
+        auto put2 = [&](unsigned char *base, int d, int next, uint4 lo, uint4 hi) {
+            *(uint4 *)(base + (long long)d * 16) = lo;
+            *(uint4 *)(base + (long long)(d + next) * 16) = hi;
+        };
+        auto save2 = [&](unsigned char *sv, int off, int pix, uint4 lo, uint4 hi) {
+            unsigned char *o = sv + off + pix * 64 + half * 32;
+            *(uint4 *)o = lo;
+            *(uint4 *)(o + 16) = hi;
+        };
+        // this thread's cells u = tid + 256 i of the overlapped region that a
+        // layer switch clears (bit i)
+        constexpr int kCellIters = (kP345Cells + kEpiThreads - 1) / kEpiThreads;
+        uint32_t clr345 = 0u, clr2 = 0u;
+#pragma unroll
+        for (int i = 0; i < kCellIters; ++i) {
+            const int u = tid + i * kEpiThreads;
+            if (u < kP345Cells) {
+                clr345 |= (uint32_t)p345_unwritten(u) << i;
+                clr2 |= (uint32_t)p2_unwritten(u) << i;
             }
         }
-        __syncthreads();
-        // ---- global average pool, fc, sigmoid (fixed summation order)
-        if (tid < 32) {
-            float g = 0.f;
-            for (int r = 0; r < 25; ++r) g += gap[r * 32 + tid];
-            g *= (1.0f / 25.0f);
-            float t = g * fc[tid];
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (tid == 0) {
-                const float logit = t + fc[32];
-                const float yv = 1.0f / (1.0f + expf(-logit));
-                P.out[pi] = yv;
-                if (sv) {
-                    float *hd = (float *)(sv + kSvHead);
-                    hd[32] = logit;
-                    hd[33] = yv;
+        auto clear_cells = [&](uint32_t mask) {
+#pragma unroll
+            for (int i = 0; i < kCellIters; ++i)
+                if ((mask >> i) & 1u) ((uint4 *)X)[tid + i * kEpiThreads] = make_uint4(0, 0, 0, 0);
+        };
+        bool ok = true;
+        float bl[16], acc[16];
+        for (long long k = 0; k < nk; ++k) {
+            // a timed-out wait anywhere stops every epilogue thread here, together
+            if (group_any(1, kEpiThreads, !ok || *abort_flag)) {
+                ok = false;
+                break;
+            }
+            const uint32_t ph = (uint32_t)(k & 1);
+            const long long pi = blockIdx.x + k * gridDim.x;
+            unsigned char *sv = P.save ? P.save + pi * (long long)kSaveBytesTotal : nullptr;
+            // ---- conv1 epilogue -> conv2 input planes, three tiles per wait
+            load_bias(0, bl);
+#pragma unroll
+            for (int g = 0; g < 3; ++g) {
+                ok &= mbar_wait(&bar[kBarC1 + g], ph);
+                tc_fence_after();
+                float a3[3][16];
+                tmem_ld16x3(tq + (uint32_t)(96 * g), tq + (uint32_t)(96 * g + 32), tq + (uint32_t)(96 * g + 64), a3);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const int mt = 3 * g + i;
+                    if (d1[mt] >= 0) {
+                        const uint4 lo = relu_pack8(a3[i], bl), hi = relu_pack8(a3[i] + 8, bl + 8);
+                        put2(X, d1[mt], 4 * kPln2, lo, hi);
+                        if (sv) {
+                            const int m = mt * 128 + row;
+                            save2(sv, kSvA1, (m / 34) * 33 + m % 34, lo, hi);
+                        }
+                    }
+                }
+                if (g == 1) {
+                    // tiles 0..5 hold every input row that conv2's first tile reads
+                    fence_proxy_async_smem();
+                    mbar_arrive(&bar[kBarP2a]);
                 }
             }
-            if (sv) ((float *)(sv + kSvHead))[tid] = g;
+            tc_fence_before();
+            mbar_arrive(&bar[kBarC1Free]);
+            fence_proxy_async_smem();
+            mbar_arrive(&bar[kBarP2]);
+            // ---- conv2 epilogue: all three tiles read, then the region is
+            // refilled with the conv3 input planes
+            load_bias(1, bl);
+            uint4 o2[3][2];
+#pragma unroll
+            for (int mt = 0; mt < 3; ++mt) {
+                ok &= mbar_wait(&bar[kBarC2 + mt], ph);
+                tc_fence_after();
+                tmem_ld16(tq + (uint32_t)(kColL2 + 32 * mt), acc);
+                o2[mt][0] = relu_pack8(acc, bl);
+                o2[mt][1] = relu_pack8(acc + 8, bl + 8);
+            }
+            clear_cells(clr345);  // conv2 has completed: its input is dead
+#pragma unroll
+            for (int mt = 0; mt < 3; ++mt) {
+                if (d2[mt] >= 0) {
+                    put2(P3, d2[mt], 4 * kPln3, o2[mt][0], o2[mt][1]);
+                    if (sv) {
+                        const int m = mt * 128 + row;
+                        save2(sv, kSvA2, (m / 18) * 17 + m % 18, o2[mt][0], o2[mt][1]);
+                    }
+                }
+            }
+            tc_fence_before();
+            fence_proxy_async_smem();
+            mbar_arrive(&bar[kBarP3]);
+            // ---- conv3 epilogue -> conv4 input planes
+            load_bias(2, bl);
+            ok &= mbar_wait(&bar[kBarC3], ph);
+            tc_fence_after();
+            tmem_ld16(tq + (uint32_t)kColL3, acc);
+            if (d3 >= 0) {
+                const uint4 lo = relu_pack8(acc, bl), hi = relu_pack8(acc + 8, bl + 8);
+                put2(P4, d3, 4 * kPln4, lo, hi);
+                if (sv) save2(sv, kSvA3, (row / 10) * 9 + row % 10, lo, hi);
+            }
+            tc_fence_before();
+            fence_proxy_async_smem();
+            mbar_arrive(&bar[kBarP4]);
+            // ---- conv4 epilogue -> conv5 input plane (stride 1)
+            load_bias(3, bl);
+            ok &= mbar_wait(&bar[kBarC4], ph);
+            tc_fence_after();
+            tmem_ld16(tq + (uint32_t)kColL4, acc);
+            if (d4 >= 0) {
+                const uint4 lo = relu_pack8(acc, bl), hi = relu_pack8(acc + 8, bl + 8);
+                put2(P5, d4, kPln5, lo, hi);
+                if (sv) save2(sv, kSvA4, (row / 6) * 5 + row % 6, lo, hi);
+            }
+            tc_fence_before();
+            fence_proxy_async_smem();
+            mbar_arrive(&bar[kBarP5]);
+            // ---- conv5 epilogue -> pooling buffer (once the head has read
+            // the previous patch's)
+            load_bias(4, bl);
+            ok &= mbar_wait(&bar[kBarC5], ph);
+            tc_fence_after();
+            tmem_ld16(tq + (uint32_t)kColL5, acc);
+            tc_fence_before();
+            if (k > 0) ok &= mbar_wait(&bar[kBarGapFree], ph ^ 1u);
+            if (d5 >= 0) {
+                const uint4 lo = relu_pack8(acc, bl), hi = relu_pack8(acc + 8, bl + 8);
+                const __nv_bfloat16 *h0 = (const __nv_bfloat16 *)&lo, *h1 = (const __nv_bfloat16 *)&hi;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    gap[d5 * 32 + 16 * half + c] = __bfloat162float(h0[c]);
+                    gap[d5 * 32 + 16 * half + 8 + c] = __bfloat162float(h1[c]);
+                }
+                if (sv) save2(sv, kSvA5, d5, lo, hi);
+            }
+            mbar_arrive(&bar[kBarGap]);
+            clear_cells(clr2);  // conv5 has completed: the conv3..5 planes are dead
         }
-        // a timed-out tensor-core wait stops the CTA (uniformly) after this patch
-        if (!__syncthreads_and(ok)) break;
+        if (!ok) *abort_flag = 1;
+        if (!ok && P.status && tid == 0) atomicExch(P.status, VS_ERR_TIMEOUT);
+    } else if (warp < kMmaWarp) {
+        // ================================================================ front
+        const int ft = tid - kEpiThreads, fw = warp - kEpiWarps;
+        const float *fc = (const float *)(Wp + kPkFc);
+        auto stage_patch = [&](int cy, int cx) {
+            const int x0 = floordiv(cx - 32, 8) * 8;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&pbar, (uint32_t)(kPatch * kStageW * 2));
+            tma_load_3d(stage, &tmap, 0, x0 / 8, cy - 32, &pbar);
+        };
+        bool ok = true;
+        uint32_t pphase = 0u;
+        bool pending = false;  // a TMA load of a patch is in flight
+        if (ft == 0 && nk > 0) {
+            int y, x;
+            patch_rc(P, blockIdx.x, y, x);
+            if (patch_inside(P, y, x)) stage_patch(y, x);
+        }
+        // iteration k: front end of patch k (k < nk), head of patch k - 2
+        for (long long k = 0; k < nk + 2; ++k) {
+            if (group_any(2, kFrontThreads, !ok || *abort_flag)) {
+                ok = false;
+                break;
+            }
+            const long long pi = blockIdx.x + k * gridDim.x;
+            if (k < nk) {
+                int cy, cx;
+                patch_rc(P, pi, cy, cx);
+                int16_t pv[kPerFront];
+                if (patch_inside(P, cy, cx)) {
+                    ok &= mbar_wait(&pbar, pphase);
+                    pphase ^= 1u;
+                    const int off = (cx - 32) - floordiv(cx - 32, 8) * 8;
+#pragma unroll
+                    for (int j = 0; j < kPerFront; ++j) {
+                        const int e = ft + j * kFrontThreads, r = e / kPatch, c = e - r * kPatch;
+                        pv[j] = (e < kPatch * kPatch) ? stage[r * kStageW + off + c] : (int16_t)0;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kPerFront; ++j) {
+                        const int e = ft + j * kFrontThreads, r = e / kPatch, c = e - r * kPatch;
+                        const int gy = min(max(cy + (r - 32) * P.step, 0), P.H - 1);
+                        const int gx = min(max(cx + (c - 32) * P.step, 0), P.W - 1);
+                        pv[j] = (e < kPatch * kPatch) ? P.z[(long long)gy * P.pitch + gx] : (int16_t)0;
+                    }
+                }
+                int sum = 0;
+#pragma unroll
+                for (int j = 0; j < kPerFront; ++j) sum += pv[j];
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                if (lane == 0) s_red[fw] = sum;
+                group_sync(2, kFrontThreads);
+                // the staging tile has been read: prefetch the next patch
+                pending = false;
+                if (k + 1 < nk) {
+                    int y, x;
+                    patch_rc(P, pi + gridDim.x, y, x);
+                    if (patch_inside(P, y, x)) {
+                        pending = true;
+                        if (ft == 0) stage_patch(y, x);
+                    }
+                }
+                int tot = 0;
+#pragma unroll
+                for (int q = 0; q < kFrontWarps; ++q) tot += s_red[q];
+                const float mean = (float)tot / (float)(kPatch * kPatch);
+                unsigned char *sv = P.save ? P.save + pi * (long long)kSaveBytesTotal : nullptr;
+#pragma unroll
+                for (int j = 0; j < kPerFront; ++j) {
+                    const int e = ft + j * kFrontThreads, r = e / kPatch, c = e - r * kPatch;
+                    if (e < kPatch * kPatch) {
+                        const __nv_bfloat16 x = __float2bfloat16_rn(((float)pv[j] - mean) * 1.0e-3f);
+                        pb[(r + 1) * 67 + (c + 1)] = x;
+                        if (sv) ((__nv_bfloat16 *)(sv + kSvInput))[e] = x;
+                    }
+                }
+            }
+            // ---- head of patch k - 2: global average pool, fc, sigmoid
+            // (fixed summation order), by the first front warp
+            if (k >= 2 && fw == 0) {
+                const long long ph2 = k - 2;
+                bool w = mbar_wait(&bar[kBarGap], (uint32_t)(ph2 & 1));
+                float gv[25];
+#pragma unroll
+                for (int r = 0; r < 25; ++r) gv[r] = gap[r * 32 + lane];
+                __syncwarp();
+                mbar_arrive(&bar[kBarGapFree]);
+                float g = 0.f;
+#pragma unroll
+                for (int r = 0; r < 25; ++r) g += gv[r];
+                g *= (1.0f / 25.0f);
+                float t = g * fc[lane];
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                const long long p2 = blockIdx.x + ph2 * gridDim.x;
+                unsigned char *sv = P.save ? P.save + p2 * (long long)kSaveBytesTotal : nullptr;
+                if (lane == 0) {
+                    const float logit = t + fc[32];
+                    const float yv = 1.0f / (1.0f + expf(-logit));
+                    P.out[p2] = yv;
+                    if (sv) {
+                        float *hd = (float *)(sv + kSvHead);
+                        hd[32] = logit;
+                        hd[33] = yv;
+                    }
+                }
+                if (sv) ((float *)(sv + kSvHead))[lane] = g;
+                ok &= w;
+            }
+            if (k < nk) {
+                group_sync(2, kFrontThreads);
+                // im2col of this patch once the previous patch's conv1 has read U
+                if (k > 0) ok &= mbar_wait(&bar[kBarC1 + 2], (uint32_t)((k - 1) & 1));
+#pragma unroll
+                for (int j0 = 0; j0 < kRowsFront; j0 += 3) {
+                    uint32_t w[3][5];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const int m = ft + (j0 + j) * kFrontThreads, y = m / 34, x = m % 34;
+                        const unsigned short *src = (const unsigned short *)pb + (2 * y) * 67 + 2 * x;
+                        const bool live = m < 1152 && y < 33 && x < 33;
+                        uint32_t t[9];
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) t[q] = live ? (uint32_t)src[(q / 3) * 67 + (q % 3)] : 0u;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) w[j][q] = t[2 * q] | (t[2 * q + 1] << 16);
+                        w[j][4] = t[8];
+                    }
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const int m = ft + (j0 + j) * kFrontThreads;
+                        if (m < 1152) {
+                            unsigned char *dst = U + (m / 8) * 256 + (m % 8) * 16;
+                            *(uint4 *)dst = make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
+                            *(uint4 *)(dst + 128) = make_uint4(w[j][4], 0u, 0u, 0u);
+                        }
+                    }
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(&bar[kBarURdy]);
+            }
+        }
+        // leave no TMA load in flight
+        if (pending && ft == 0) mbar_wait(&pbar, pphase);
+        if (!ok) *abort_flag = 1;
+        if (!ok && P.status && ft == 0) atomicExch(P.status, VS_ERR_TIMEOUT);
+    } else {
+        // ================================================================ MMA issue
+        const uint32_t sW = smem_u32(Wp), sX = smem_u32(X), sU = smem_u32(U);
+        // descriptor bases; an operand at byte offset o from a base adds o >> 4
+        // to the address field (shared addresses stay below 2^18 bytes)
+        const uint64_t dB = sdesc(sW, 128, 256);
+        const uint64_t dA1 = sdesc(sU, 128, 256);
+        const uint64_t dA2 = sdesc(sX, 4 * kPln2 * 16, 128);
+        const uint64_t dA3 = sdesc(sX + kP3Off, 4 * kPln3 * 16, 128);
+        const uint64_t dA4 = sdesc(sX + kP4Off, 4 * kPln4 * 16, 128);
+        const uint64_t dA5 = sdesc(sX + kP5Off, kPln5 * 16, 128);
+        bool ok = true;
+        int last = -1;  // barrier of the last commit, for the exit wait
+        uint32_t last_ph = 0u;
+        auto wait_all = [&](int b, uint32_t ph) {
+            bool r = true;
+            if (lane == 0) r = mbar_wait_spin(&bar[b], ph);
+            r = __shfl_sync(0xffffffffu, (int)r, 0) != 0;
+            tc_fence_after();
+            return r;
+        };
+        // a 32->32 layer's tile: 9 taps x 2 K-steps reading stride-2 parity planes
+        auto conv_tile = [&](uint64_t dA, int pln, int pitch, int m0, int l, uint32_t col) {
+#pragma unroll
+            for (int i = 0; i < 18; ++i) {
+                const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
+                const int plane = ((ky != 1) << 1) | (kx != 1);
+                const int shift = (ky != 0 ? pitch : 0) + (kx != 0 ? 1 : 0);
+                const uint64_t ad = dA + (uint64_t)((2 * ks * 4 + plane) * pln + m0 + shift);
+                const uint64_t bd = dB + (uint64_t)((pk_bl(l) + (t * 2 + ks) * 1024) >> 4);
+                if (i == 0) umma_c<0>(tmem + col, ad, bd);
+                else umma_c<1>(tmem + col, ad, bd);
+            }
+        };
+        for (long long k = 0; k < nk; ++k) {
+            if (__any_sync(0xffffffffu, !ok || *abort_flag)) break;
+            const uint32_t ph = (uint32_t)(k & 1);
+            // ---- conv1: the im2col tile is written and the previous patch's
+            // conv1 accumulators have been read
+            ok &= wait_all(kBarURdy, ph);
+            if (k > 0) ok &= wait_all(kBarC1Free, ph ^ 1u);
+            if (lane == 0) {
+#pragma unroll
+                for (int mt = 0; mt < 9; ++mt) {
+                    umma_c<0>(tmem + (uint32_t)(32 * mt), dA1 + (uint64_t)(mt * 256), dB + (uint64_t)(kPkB1 >> 4));
+                    if (mt % 3 == 2) umma_commit(&bar[kBarC1 + mt / 3]);
+                }
+            }
+            __syncwarp();
+            // ---- conv2: 3 tiles, input pitch 18; the first needs conv1 tiles 0..5
+            ok &= wait_all(kBarP2a, ph);
+            if (lane == 0) {
+                conv_tile(dA2, kPln2, 18, 0, 1, (uint32_t)kColL2);
+                umma_commit(&bar[kBarC2]);
+            }
+            __syncwarp();
+            ok &= wait_all(kBarP2, ph);
+            if (lane == 0) {
+                for (int mt = 1; mt < 3; ++mt) {
+                    conv_tile(dA2, kPln2, 18, mt * 128, 1, (uint32_t)(kColL2 + 32 * mt));
+                    umma_commit(&bar[kBarC2 + mt]);
+                }
+            }
+            __syncwarp();
+            // ---- conv3: 1 tile, input pitch 10
+            ok &= wait_all(kBarP3, ph);
+            if (lane == 0) {
+                conv_tile(dA3, kPln3, 10, 0, 2, (uint32_t)kColL3);
+                umma_commit(&bar[kBarC3]);
+            }
+            __syncwarp();
+            // ---- conv4: 1 tile, input pitch 6
+            ok &= wait_all(kBarP4, ph);
+            if (lane == 0) {
+                conv_tile(dA4, kPln4, 6, 0, 3, (uint32_t)kColL4);
+                umma_commit(&bar[kBarC4]);
+            }
+            __syncwarp();
+            // ---- conv5 (stride 1): 1 tile, input pitch 7, one plane with a full border
+            ok &= wait_all(kBarP5, ph);
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < 18; ++i) {
+                    const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
+                    const uint64_t ad = dA5 + (uint64_t)((2 * ks) * kPln5 + ky * 7 + kx);
+                    const uint64_t bd = dB + (uint64_t)((pk_bl(4) + (t * 2 + ks) * 1024) >> 4);
+                    if (i == 0) umma_c<0>(tmem + (uint32_t)kColL5, ad, bd);
+                    else umma_c<1>(tmem + (uint32_t)kColL5, ad, bd);
+                }
+                umma_commit(&bar[kBarC5]);
+            }
+            __syncwarp();
+            last = kBarC5;
+            last_ph = ph;
+        }
+        // leave no MMA in flight
+        if (last >= 0) wait_all(last, last_ph);
+        if (!ok) *abort_flag = 1;
+        if (!ok && P.status && lane == 0) atomicExch(P.status, VS_ERR_TIMEOUT);
     }
-    if (!ok && P.status && threadIdx.x == 0) atomicExch(P.status, VS_ERR_TIMEOUT);
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTmemCols)
+                     : "memory");
 }
 
 // ------------------------------------------------------------------ training
@@ -677,6 +1012,7 @@ static int cnn_forward_launch(vs_grid g, const int64_t *centers, int64_t n, int3
     if (patch_step < 1 || patch_step > 64) return VS_ERR_RANGE;
     int rc = check_grid(g);
     if (rc) return rc;
+    if ((long long)g.H * g.W > 0xFFFFFFFFll) return VS_ERR_RANGE;  // posts are 32-bit in the kernel
     if (!packed || !out || ((uintptr_t)packed & 15) || (save && ((uintptr_t)save & 15)))
         return VS_ERR_ARG;
     if (n < 0) return VS_ERR_RANGE;

@@ -82,6 +82,33 @@ def test_cnn_lattice_matches_centres(V):
     assert np.array_equal(lat, y)
 
 
+def test_cnn_forward_many_patches_per_cta(V):
+    """1200 patches (several per CTA on any GB300, so every CTA reuses its
+    planes, tensor memory and barriers across patches), interior and edge
+    centres mixed, against the oracle on every patch."""
+    from oracle import cnn_oracle as C
+    H, W = 400, 420
+    z = T.spectral_fbm(H, W, 0.8, 33, 0, 2500).numpy()
+    g = V.Grid.from_tensor(torch.as_tensor(z), "cuda")
+    p = _params(9)
+    packed = V.cnn_pack(torch.as_tensor(C.flatten_params(p)).cuda())
+    rng = np.random.default_rng(12)
+    n = 1200
+    cy = rng.integers(0, H, n)
+    cx = rng.integers(0, W, n)
+    cy[::5] = rng.integers(32, H - 33, len(cy[::5]))  # plenty of staged (interior) patches
+    cen = torch.as_tensor(cy * W + cx).cuda()
+    y = V.cnn_forward(g, cen, packed).cpu().numpy()
+    x0 = np.stack([C.normalize_patch(C.extract_patch(z, int(a), int(b))) for a, b in zip(cy, cx)])
+    want = C.forward(p, x0)
+    err = np.abs(y - want)
+    assert err.max() < 5e-3, (err.max(), int(err.argmax()))
+    # the same patches in another order and launch size give the same scores
+    perm = rng.permutation(n)[:700]
+    y2 = V.cnn_forward(g, cen[torch.as_tensor(perm).cuda()].contiguous(), packed).cpu().numpy()
+    assert np.array_equal(y2, y[perm])
+
+
 @pytest.mark.parametrize("step", [2, 3])
 def test_cnn_strided_patches(V, step):
     """patch_step > 1 (every step-th post, clamped at the edges; these patches
