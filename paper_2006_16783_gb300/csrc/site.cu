@@ -346,18 +346,40 @@ struct Site1Params {
 
 __device__ __forceinline__ uint64_t u64max(uint64_t a, uint64_t b) { return a > b ? a : b; }
 
+// inclusive prefix sum over the lanes of a warp
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// One greedy step per iteration, the whole block on it.  Per step: the block
+// argmax of the cached gains; the winner's window, where the newly covered
+// bits (delta = V_win AND NOT C) are found and C is updated; the winner's
+// band (slots within 2R rows) compacted to the other candidates whose window
+// meets the winner's; their gains lowered by popc(V_c AND delta) over the
+// overlap, reading V_c only where delta is non-zero; the winner's gain set
+// to zero (all of it is now covered).
+// Global loads that do not depend on each other are issued together (the
+// window's V and C words with the band's slot posts; the refresh's words in
+// batches), and the compaction's counts and overlap prefixes come from warp
+// scans, so a step costs four block barriers.  One SM's scattered loads
+// (about 0.55 per cycle measured) bound the refresh.
 __device__ __forceinline__ void site1_body(const Site1Params &P) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *s_gain = (uint32_t *)smem;                  // n
     uint32_t *s_delta = s_gain + ((P.n + 3) & ~3);        // words
     int *s_list = (int *)(s_delta + ((P.words + 3) & ~3)); // kSiteThreads
     __shared__ uint64_t s_red[32];
-    __shared__ int s_cnt[32];
+    __shared__ int s_wcnt[32], s_wsum[32];
     __shared__ int s_dirty[kSiteThreads];
-    __shared__ int s_ovl[kSiteThreads];
     __shared__ int s_pref[kSiteThreads + 1];
     __shared__ unsigned s_sum[kSiteThreads];
     __shared__ int4 s_geo[kSiteThreads];
+    __shared__ uint32_t s_orig[kSiteThreads];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int n = P.n, R = P.R, PR = P.PR, W = P.W, H = P.H, WWc = P.WWc;
     const int cs = (n + kSiteThreads - 1) / kSiteThreads;
@@ -367,13 +389,22 @@ __device__ __forceinline__ void site1_body(const Site1Params &P) {
         s_gain[i] = (P.sp[i] == 0xFFFFFFFFu) ? 0u : P.gain0[P.sorig[i]];
     s_dirty[tid] = 0;
     __syncthreads();
+    // best cached key of this thread's slots (four independent max chains)
     auto local_best = [&]() {
-        uint64_t b = 0;
-        for (int i = my0; i < my1; ++i) {
-            const uint32_t g = s_gain[i];
-            b = u64max(b, g ? (((uint64_t)g << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)i)) : 0ull);
+        uint64_t b[4] = {0ull, 0ull, 0ull, 0ull};
+        int i = my0;
+        for (; i + 4 <= my1; i += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t g = s_gain[i + q];
+                b[q] = u64max(b[q], g ? (((uint64_t)g << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)(i + q))) : 0ull);
+            }
         }
-        return b;
+        for (; i < my1; ++i) {
+            const uint32_t g = s_gain[i];
+            b[0] = u64max(b[0], g ? (((uint64_t)g << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)i)) : 0ull);
+        }
+        return u64max(u64max(b[0], b[1]), u64max(b[2], b[3]));
     };
     uint64_t best = local_best();
     long long covered = (P.need >= 0) ? (long long)*P.covered0 : 0;
@@ -391,10 +422,10 @@ __device__ __forceinline__ void site1_body(const Site1Params &P) {
         const uint32_t g = (uint32_t)(k >> 32);
         if (g == 0) break;
         const int s = (int)(0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFu));
-        // ---- round 1: the winner's metadata
+        // ---- the winner's metadata
         const uint32_t wp = P.sp[s];
         const uint32_t wc = P.sorig[s];
-        const int lo = (int)P.slo[s], hi = (int)P.shi[s];
+        const int lo = (int)P.slo[s], hi = (int)P.shi[s];  // the winner's slot lies in [lo, hi)
         if (tid == 0) {
             P.chosen[t] = (int64_t)wp;
             P.gains[t] = (int64_t)g;
@@ -403,108 +434,159 @@ __device__ __forceinline__ void site1_body(const Site1Params &P) {
         const int wx = (int)(wp % (uint32_t)W), wy = (int)(wp / (uint32_t)W);
         const int wgw0 = floordiv(wx - R, 32);
         const uint32_t *Vw = P.bm + (int64_t)wc * P.words;
-        // ---- round 2: delta = V_win AND NOT C over the window, C |= V_win
-        // (both words are loaded up front so the two loads overlap)
-        for (int e = tid; e < P.words; e += blockDim.x) {
-            const int r = e / PR, w = e - r * PR;
-            const int y = wy - R + r, gw = wgw0 + w;
-            uint32_t d = 0;
-            if (y >= 0 && y < H && gw >= 0 && gw < WWc) {
-                uint32_t *cp = P.cum + (int64_t)y * WWc + gw;
-                const uint32_t v = __ldg(Vw + e);
-                const uint32_t old = *cp;
-                d = v & ~old;
-                if (d) *cp = old | v;
+        // the band's first slot posts and bitmap indices, loaded beside the
+        // window's words
+        uint32_t bsp = (lo + tid < hi) ? P.sp[lo + tid] : 0u;
+        uint32_t bso = (lo + tid < hi) ? P.sorig[lo + tid] : 0u;
+        // ---- delta = V_win AND NOT C over the window, C |= V_win (the
+        // loads of two passes are issued before either is used)
+        for (int e0 = 0; e0 < P.words; e0 += 2 * kSiteThreads) {
+            uint32_t v[2] = {0u, 0u}, old[2] = {0u, 0u};
+            uint32_t *cp[2] = {nullptr, nullptr};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e = e0 + h * kSiteThreads + tid;
+                if (e < P.words) {
+                    const int r = e / PR, w = e - r * PR;
+                    const int y = wy - R + r, gw = wgw0 + w;
+                    if (y >= 0 && y < H && gw >= 0 && gw < WWc) {
+                        cp[h] = P.cum + (int64_t)y * WWc + gw;
+                        v[h] = __ldg(Vw + e);
+                        old[h] = *cp[h];
+                    }
+                }
             }
-            s_delta[e] = d;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e = e0 + h * kSiteThreads + tid;
+                if (e < P.words) {
+                    const uint32_t d = cp[h] ? (v[h] & ~old[h]) : 0u;
+                    if (d) *cp[h] = old[h] | v[h];
+                    s_delta[e] = d;
+                }
+            }
         }
-        // ---- band of slots within 2R rows: compact the ones within 2R columns
-        for (int b0 = lo; b0 < hi; b0 += blockDim.x) {
+        // ---- band chunks: compact the other slots whose window meets the
+        // winner's, with their overlap (rows x words) and its exclusive prefix
+        for (int b0 = lo; b0 < hi; b0 += kSiteThreads) {
             const int i = b0 + tid;
+            if (b0 != lo) {
+                bsp = (i < hi) ? P.sp[i] : 0u;
+                bso = (i < hi) ? P.sorig[i] : 0u;
+            }
             bool aff = false;
-            if (i < hi && s_gain[i] != 0) {
-                const int x = (int)(P.sp[i] % (uint32_t)W);
-                aff = abs(x - wx) <= 2 * R;
+            int ovl = 0;
+            int4 geo = make_int4(0, 0, 0, 0);
+            if (i < hi && i != s && s_gain[i] != 0) {
+                const int cx = (int)(bsp % (uint32_t)W), cy = (int)(bsp / (uint32_t)W);
+                if (abs(cx - wx) <= 2 * R) {
+                    aff = true;
+                    const int cgw0 = floordiv(cx - R, 32);
+                    const int ya = max(max(cy, wy) - R, 0), yb = min(min(cy, wy) + R, H - 1);
+                    const int ga = max(max(cgw0, wgw0), 0), gb = min(min(cgw0, wgw0) + PR - 1, WWc - 1);
+                    const int nwd = (ya <= yb && ga <= gb) ? gb - ga + 1 : 0;
+                    ovl = (ya <= yb && ga <= gb) ? (yb - ya + 1) * nwd : 0;
+                    geo = make_int4(ya, ga, nwd, (int)(((unsigned)cy << 16) | ((unsigned)cgw0 & 0xFFFFu)));
+                }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, aff);
-            if (lane == 0) s_cnt[wid] = __popc(bal);
-            __syncthreads();  // also publishes s_delta of the first chunk
-            int base = 0, tot = 0;
-            for (int q = 0; q < 32; ++q) { const int v = s_cnt[q]; base += (q < wid) ? v : 0; tot += v; }
+            const int incl = warp_incl_scan(ovl, lane);
+            if (lane == 31) {
+                s_wcnt[wid] = __popc(bal);
+                s_wsum[wid] = incl;
+            }
+            __syncthreads();  // also publishes s_delta
+            // every warp scans the 32 warp totals
+            const int wcn = s_wcnt[lane], wsm = s_wsum[lane];
+            const int icn = warp_incl_scan(wcn, lane), ism = warp_incl_scan(wsm, lane);
+            const int cnt_base = __shfl_sync(0xffffffffu, icn - wcn, wid);
+            const int sum_base = __shfl_sync(0xffffffffu, ism - wsm, wid);
+            const int tot = __shfl_sync(0xffffffffu, icn, 31);
+            const int TT = __shfl_sync(0xffffffffu, ism, 31);
             if (aff) {
-                // overlap of the candidate's window with the winner's, in
-                // rows x words; its size goes to s_ovl for the prefix sum
-                const int li = base + __popc(bal & ((1u << lane) - 1u));
-                const uint32_t cpp = P.sp[i];
-                const int cx = (int)(cpp % (uint32_t)W), cy = (int)(cpp / (uint32_t)W);
-                const int cgw0 = floordiv(cx - R, 32);
-                const int ya = max(max(cy, wy) - R, 0), yb = min(min(cy, wy) + R, H - 1);
-                const int ga = max(max(cgw0, wgw0), 0), gb = min(min(cgw0, wgw0) + PR - 1, WWc - 1);
-                const int nrow = (ya <= yb && ga <= gb) ? yb - ya + 1 : 0;
-                const int nwd = (ya <= yb && ga <= gb) ? gb - ga + 1 : 0;
+                const int li = cnt_base + __popc(bal & ((1u << lane) - 1u));
                 s_list[li] = i;
-                s_ovl[li] = nrow * nwd;
-                s_geo[li] = make_int4(ya, ga, nwd, (int)(((unsigned)cy << 16) | ((unsigned)cgw0 & 0xFFFFu)));
+                s_orig[li] = bso;
+                s_pref[li] = sum_base + incl - ovl;
+                s_geo[li] = geo;
                 s_sum[li] = 0;
             }
+            if (tid == 0) s_pref[tot] = TT;
             __syncthreads();
-            // exclusive prefix of the overlap sizes (warp 0)
-            if (wid == 0) {
-                const int per = (tot + 31) / 32;
-                const int a0 = lane * per, a1 = min(tot, a0 + per);
-                int loc = 0;
-                for (int q = a0; q < a1; ++q) loc += s_ovl[q];
-                int incl = loc;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += v;
+            // ---- every thread takes an equal run of the overlap words of all
+            // listed candidates and loads them in batches of eight independent
+            // loads (a run may cross from one candidate to the next), reading
+            // V_c only where delta is non-zero
+            const int per = (TT + kSiteThreads - 1) / kSiteThreads;
+            const int e0 = tid * per, e1 = min(TT, e0 + per);
+            if (e0 < e1) {
+                int l = 0, hi2 = tot - 1;  // last l with s_pref[l] <= e0
+                while (l < hi2) {
+                    const int m = (l + hi2 + 1) >> 1;
+                    if (s_pref[m] <= e0) l = m; else hi2 = m - 1;
                 }
-                int run = incl - loc;
-                for (int q = a0; q < a1; ++q) { const int v = s_ovl[q]; s_pref[q] = run; run += v; }
-                if (lane == 31) s_pref[tot] = incl;
-            }
-            __syncthreads();
-            // ---- round 3: every thread takes an equal run of the overlap words
-            // of all listed candidates; the loads of a run are independent
-            const int TT = s_pref[tot];
-            const int per = (TT + blockDim.x - 1) / blockDim.x;
-            int e = tid * per;
-            const int e1 = min(TT, e + per);
-            if (e < e1) {
-                int l = 0, hi2 = tot - 1;  // last l with s_pref[l] <= e
-                while (l < hi2) { const int m = (l + hi2 + 1) >> 1; if (s_pref[m] <= e) l = m; else hi2 = m - 1; }
-                while (e < e1) {
-                    const int4 gq = s_geo[l];
-                    const int ya = gq.x, ga = gq.y, nwd = gq.z;
-                    const int cy = (int)((unsigned)gq.w >> 16), cgw0 = (int)(int16_t)(gq.w & 0xFFFF);
-                    const uint32_t *Vc = P.bm + (int64_t)P.sorig[s_list[l]] * P.words;
-                    const int lend = min(e1, s_pref[l + 1]);
-                    unsigned sum = 0;
-#pragma unroll 4
-                    for (; e < lend; ++e) {
-                        const int u = e - s_pref[l];
-                        const int dy = u / nwd, gw = ga + (u - dy * nwd), y = ya + dy;
-                        const uint32_t dl = s_delta[(y - wy + R) * PR + (gw - wgw0)];
-                        const uint32_t vc = __ldg(Vc + (y - cy + R) * PR + (gw - cgw0));
-                        sum += __popc(vc & dl);
+                int pl = s_pref[l], pn = s_pref[l + 1];
+                int4 gq = s_geo[l];
+                const uint32_t *Vc = P.bm + (int64_t)s_orig[l] * P.words;
+                int cur = l;
+                unsigned sum = 0;
+                for (int eb = e0; eb < e1; eb += 8) {
+                    uint32_t vc[8], dl[8];
+                    int lq[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int e = eb + q;
+                        lq[q] = -1;
+                        vc[q] = 0u;
+                        dl[q] = 0u;
+                        if (e < e1) {
+                            while (e >= pn) {  // the next listed candidate (empty overlaps skipped)
+                                ++l;
+                                pl = pn;
+                                pn = s_pref[l + 1];
+                                gq = s_geo[l];
+                                Vc = P.bm + (int64_t)s_orig[l] * P.words;
+                            }
+                            const int ya = gq.x, ga = gq.y, nwd = gq.z;
+                            const int cy = (int)((unsigned)gq.w >> 16), cgw0 = (int)(int16_t)(gq.w & 0xFFFF);
+                            const int u = e - pl;
+                            const int dy = u / nwd, gw = ga + (u - dy * nwd), y = ya + dy;
+                            dl[q] = s_delta[(y - wy + R) * PR + (gw - wgw0)];
+                            if (dl[q]) vc[q] = __ldg(Vc + (y - cy + R) * PR + (gw - cgw0));
+                            lq[q] = l;
+                        }
                     }
-                    if (sum) atomicAdd(&s_sum[l], sum);
-                    ++l;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (lq[q] < 0) continue;
+                        if (lq[q] != cur) {
+                            if (sum) atomicAdd(&s_sum[cur], sum);
+                            sum = 0;
+                            cur = lq[q];
+                        }
+                        sum += __popc(vc[q] & dl[q]);
+                    }
                 }
+                if (sum) atomicAdd(&s_sum[cur], sum);
             }
             __syncthreads();
-            for (int q = tid; q < tot; q += blockDim.x) {
+            for (int q = tid; q < tot; q += kSiteThreads) {
                 const int ci = s_list[q];
                 s_gain[ci] -= s_sum[q];
                 s_dirty[ci / cs] = 1;
             }
+            if (tid == 0 && b0 == lo) {  // the winner covers all of its own gain
+                s_gain[s] = 0;
+                s_dirty[s / cs] = 1;
+            }
             __syncthreads();
         }
+        // the band held at least the winner, so the chunk loop ran and its
+        // barriers order these gain reads after every update of this step
         if (s_dirty[tid]) {
             s_dirty[tid] = 0;
             best = local_best();
         }
-        __syncthreads();
     }
     if (tid == 0) *P.n_chosen = t;
 }
@@ -621,9 +703,11 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
     }
     if (n > 0 && (rc = vs_site_gains(bm, cand, n, H, W, R, cum, g0, st))) return rc;
 
-    // one CTA when every gain fits in its shared memory
+    // one CTA when every gain fits in its shared memory (unless the tuning
+    // table asks for a cluster of at most qmax CTAs)
+    const int qmax = job_out ? 0 : tune_get(VS_TUNE_SITE_CLUSTER, R, 0);
     const size_t smem1 = site1_smem_bytes(n, P.words);
-    if (n > 0 && site1_fits(n, P.words)) {
+    if (n > 0 && site1_fits(n, P.words) && qmax == 0) {
         k_site_rank<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cand, n, (int64_t)H * W, sp, sorig);
         VS_CUDA_TRY(cudaGetLastError());
         k_site_bands<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sp, n, W, R, slo, shi);
@@ -651,6 +735,7 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
     size_t smem = 0;
     VS_CUDA_TRY(cudaFuncSetAttribute(k_site_loop, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     for (int q : {16, 8, 4, 2, 1}) {
+        if (qmax != 0 && q > qmax) continue;
         const int sl = (int)std::max<int64_t>(1, (n + q - 1) / q);
         const size_t b = site_smem_bytes(sl, P.words);
         if (b > (size_t)kSmemLimit - 2048) continue;

@@ -42,7 +42,7 @@ class vs_site_job(ctypes.Structure):
                 ("n_chosen", ctypes.c_void_p)]
 
 
-VS_TUNE_VIEWSHED_THREADS, VS_TUNE_VIX_TILE = 0, 1
+VS_TUNE_VIEWSHED_THREADS, VS_TUNE_VIX_TILE, VS_TUNE_SITE_CLUSTER = 0, 1, 2
 
 # name -> (restype, argtypes); the exported symbols of include/vshed.h
 P, i32, i64, u64, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,

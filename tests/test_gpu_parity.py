@@ -166,6 +166,23 @@ def test_site_parity_many_candidates(V, O):
     assert (_np(gC).view(np.uint32) == C).all()
 
 
+@pytest.mark.parametrize("q", [2, 16])
+def test_site_cluster_path_by_tuning(V, O, q):
+    """The cluster loop chosen through the tuning table for a candidate set
+    one CTA would hold: the same result as the oracle."""
+    H, W, R = 257, 301, 50
+    cand, bm = _site_case(O, 3, H, W, R, 500)
+    ch, gn, C = O.site(bm, cand, H, W, R, 200)
+    V.tune_set(V.VS_TUNE_SITE_CLUSTER, R, q)
+    try:
+        gch, ggn, gC, t = V.site(torch.as_tensor(bm.view(np.int32)).cuda(), torch.as_tensor(cand).cuda(),
+                                 H, W, R, 200)
+    finally:
+        V.tune_set(V.VS_TUNE_SITE_CLUSTER, R, 0)
+    assert _np(gch).tolist() == ch.tolist() and _np(ggn).tolist() == gn.tolist()
+    assert (_np(gC).view(np.uint32) == C).all()
+
+
 def test_site_duplicate_and_invalid_candidates(V, O):
     H, W, R = 90, 110, 6
     cand, bm = _site_case(O, 41, H, W, R, 80)
