@@ -379,7 +379,6 @@ __device__ __forceinline__ void site1_body(const Site1Params &P) {
     __shared__ int s_pref[kSiteThreads + 1];
     __shared__ unsigned s_sum[kSiteThreads];
     __shared__ int4 s_geo[kSiteThreads];
-    __shared__ uint32_t s_orig[kSiteThreads];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int n = P.n, R = P.R, PR = P.PR, W = P.W, H = P.H, WWc = P.WWc;
     const int cs = (n + kSiteThreads - 1) / kSiteThreads;
@@ -486,7 +485,11 @@ __device__ __forceinline__ void site1_body(const Site1Params &P) {
                     const int ga = max(max(cgw0, wgw0), 0), gb = min(min(cgw0, wgw0) + PR - 1, WWc - 1);
                     const int nwd = (ya <= yb && ga <= gb) ? gb - ga + 1 : 0;
                     ovl = (ya <= yb && ga <= gb) ? (yb - ya + 1) * nwd : 0;
-                    geo = make_int4(ya, ga, nwd, (int)(((unsigned)cy << 16) | ((unsigned)cgw0 & 0xFFFFu)));
+                    // the overlap's first word in the delta window and in the
+                    // candidate's bitmap (n * words < 2^32 on this path)
+                    const int dbase = (ya - wy + R) * PR + (ga - wgw0);
+                    const uint32_t vbase = bso * (uint32_t)P.words + (uint32_t)((ya - cy + R) * PR + (ga - cgw0));
+                    geo = make_int4(dbase, (int)vbase, nwd, 0);
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, aff);
@@ -506,7 +509,6 @@ __device__ __forceinline__ void site1_body(const Site1Params &P) {
             if (aff) {
                 const int li = cnt_base + __popc(bal & ((1u << lane) - 1u));
                 s_list[li] = i;
-                s_orig[li] = bso;
                 s_pref[li] = sum_base + incl - ovl;
                 s_geo[li] = geo;
                 s_sum[li] = 0;
@@ -514,9 +516,9 @@ __device__ __forceinline__ void site1_body(const Site1Params &P) {
             if (tid == 0) s_pref[tot] = TT;
             __syncthreads();
             // ---- every thread takes an equal run of the overlap words of all
-            // listed candidates and loads them in batches of eight independent
-            // loads (a run may cross from one candidate to the next), reading
-            // V_c only where delta is non-zero
+            // listed candidates; within one candidate's overlap it walks rows
+            // and words with running indices, loading eight words at a time
+            // and reading V_c only where delta is non-zero
             const int per = (TT + kSiteThreads - 1) / kSiteThreads;
             const int e0 = tid * per, e1 = min(TT, e0 + per);
             if (e0 < e1) {
@@ -525,49 +527,46 @@ __device__ __forceinline__ void site1_body(const Site1Params &P) {
                     const int m = (l + hi2 + 1) >> 1;
                     if (s_pref[m] <= e0) l = m; else hi2 = m - 1;
                 }
-                int pl = s_pref[l], pn = s_pref[l + 1];
-                int4 gq = s_geo[l];
-                const uint32_t *Vc = P.bm + (int64_t)s_orig[l] * P.words;
-                int cur = l;
-                unsigned sum = 0;
-                for (int eb = e0; eb < e1; eb += 8) {
-                    uint32_t vc[8], dl[8];
-                    int lq[8];
+                int e = e0;
+                while (e < e1) {
+                    const int pl = s_pref[l], pn = s_pref[l + 1];
+                    if (e >= pn) {  // empty overlaps are skipped
+                        ++l;
+                        continue;
+                    }
+                    const int4 gq = s_geo[l];
+                    const int nwd = gq.z, skip = PR - nwd;
+                    const int u = e - pl, dy = u / nwd;
+                    int dw = u - dy * nwd;
+                    int di = gq.x + dy * PR + dw;
+                    const uint32_t *vp = P.bm + (uint32_t)gq.y + (uint32_t)(dy * PR + dw);
+                    const int send = min(e1, pn);
+                    unsigned sum = 0;
+                    for (; e < send; e += 8) {
+                        uint32_t v[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int e = eb + q;
-                        lq[q] = -1;
-                        vc[q] = 0u;
-                        dl[q] = 0u;
-                        if (e < e1) {
-                            while (e >= pn) {  // the next listed candidate (empty overlaps skipped)
-                                ++l;
-                                pl = pn;
-                                pn = s_pref[l + 1];
-                                gq = s_geo[l];
-                                Vc = P.bm + (int64_t)s_orig[l] * P.words;
+                        for (int q = 0; q < 8; ++q) {
+                            v[q] = 0u;
+                            if (e + q < send) {
+                                const uint32_t dl = s_delta[di];
+                                if (dl) v[q] = __ldg(vp) & dl;
+                                ++dw;
+                                ++di;
+                                ++vp;
+                                if (dw == nwd) {
+                                    dw = 0;
+                                    di += skip;
+                                    vp += skip;
+                                }
                             }
-                            const int ya = gq.x, ga = gq.y, nwd = gq.z;
-                            const int cy = (int)((unsigned)gq.w >> 16), cgw0 = (int)(int16_t)(gq.w & 0xFFFF);
-                            const int u = e - pl;
-                            const int dy = u / nwd, gw = ga + (u - dy * nwd), y = ya + dy;
-                            dl[q] = s_delta[(y - wy + R) * PR + (gw - wgw0)];
-                            if (dl[q]) vc[q] = __ldg(Vc + (y - cy + R) * PR + (gw - cgw0));
-                            lq[q] = l;
                         }
-                    }
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        if (lq[q] < 0) continue;
-                        if (lq[q] != cur) {
-                            if (sum) atomicAdd(&s_sum[cur], sum);
-                            sum = 0;
-                            cur = lq[q];
-                        }
-                        sum += __popc(vc[q] & dl[q]);
+                        for (int q = 0; q < 8; ++q) sum += __popc(v[q]);
                     }
+                    e = send;
+                    if (sum) atomicAdd(&s_sum[l], sum);
+                    ++l;
                 }
-                if (sum) atomicAdd(&s_sum[cur], sum);
             }
             __syncthreads();
             for (int q = tid; q < tot; q += kSiteThreads) {
