@@ -476,7 +476,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--sur-stride", type=int, default=32)
-    ap.add_argument("--patch-step", type=int, default=1,
+    ap.add_argument("--patch-step", type=int, default=3,
                     help="post spacing inside the CNN's 65x65 input patch")
     ap.add_argument("--train-posts", type=int, default=500000)
     ap.add_argument("--epochs", type=int, default=3)
