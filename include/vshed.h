@@ -303,6 +303,14 @@ int vs_cnn_forward(vs_grid g, const int64_t *centers, int64_t n, int32_t patch_s
                    const void *packed, float *out, void *save, int32_t *status, vs_stream_t st);
 int vs_cnn_score_lattice(vs_grid g, int32_t stride, int32_t patch_step, const void *packed,
                          float *score_out, int32_t *status, vs_stream_t st);
+/* Lattice rows row0 .. row0+nrows-1 only (0 <= row0, row0 + nrows <= ceil(H/stride)):
+ * score_out [nrows][ceil(W/stride)] receives exactly the rows vs_cnn_score_lattice
+ * writes there.  A patch of lattice row i reads terrain rows within 32*patch_step of
+ * i*stride, so a caller streaming the terrain in by row chunks can score the rows
+ * whose posts have arrived. */
+int vs_cnn_score_lattice_rows(vs_grid g, int32_t stride, int32_t patch_step, int32_t row0,
+                              int32_t nrows, const void *packed, float *score_out,
+                              int32_t *status, vs_stream_t st);
 
 /* Training.  vs_cnn_backward: gradients of the mean L1 loss
  * mean_b |y_b - labels[b]| over a batch of B patches whose forward pass

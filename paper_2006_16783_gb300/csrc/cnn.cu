@@ -164,7 +164,8 @@ struct FwdParams {
     long long pitch;
     const int64_t *centers;  // patch centres (post index) or null for the lattice
     long long n;             // number of patches
-    int stride, Ws;          // lattice mode: patch i at post ((i / Ws)*stride, (i % Ws)*stride)
+    int stride, Ws;          // lattice mode: patch i at post ((row0 + i / Ws)*stride, (i % Ws)*stride)
+    int row0;                // lattice mode: first lattice row of this launch
     int step;                // patch element (r, c) is post (cy + (r-32)*step, cx + (c-32)*step)
     const unsigned char *packed;
     float *out;              // n predicted visibility indices
@@ -205,7 +206,7 @@ __device__ __forceinline__ void patch_rc(const FwdParams &P, long long pi, int &
         cx = (int)(c - y * (uint32_t)P.W);
     } else {
         const uint32_t iy = (uint32_t)pi / (uint32_t)P.Ws;
-        cy = (int)iy * P.stride;
+        cy = ((int)iy + P.row0) * P.stride;
         cx = (int)((uint32_t)pi - iy * (uint32_t)P.Ws) * P.stride;
     }
 }
@@ -1007,8 +1008,8 @@ extern "C" int vs_cnn_pack(const float *master, void *packed, vs_stream_t st) {
 }
 
 static int cnn_forward_launch(vs_grid g, const int64_t *centers, int64_t n, int32_t stride,
-                              int32_t patch_step, const void *packed, float *out, void *save,
-                              int32_t *status, vs_stream_t st) {
+                              int32_t row0, int32_t patch_step, const void *packed, float *out,
+                              void *save, int32_t *status, vs_stream_t st) {
     if (patch_step < 1 || patch_step > 64) return VS_ERR_RANGE;
     int rc = check_grid(g);
     if (rc) return rc;
@@ -1020,7 +1021,7 @@ static int cnn_forward_launch(vs_grid g, const int64_t *centers, int64_t n, int3
     if ((rc = check_device())) return rc;
     cnn::FwdParams P;
     P.z = g.z; P.H = g.H; P.W = g.W; P.pitch = g.pitch;
-    P.centers = centers; P.n = n; P.stride = stride; P.step = patch_step;
+    P.centers = centers; P.n = n; P.stride = stride; P.step = patch_step; P.row0 = row0;
     P.Ws = stride > 0 ? (g.W + stride - 1) / stride : 1;
     P.packed = (const unsigned char *)packed; P.out = out;
     P.save = (unsigned char *)save; P.status = status;
@@ -1041,7 +1042,7 @@ extern "C" int vs_cnn_forward(vs_grid g, const int64_t *centers, int64_t n, int3
                               const void *packed, float *out, void *save, int32_t *status,
                               vs_stream_t st) {
     if (!centers && n > 0) return VS_ERR_ARG;
-    return cnn_forward_launch(g, centers, n, 0, patch_step, packed, out, save, status, st);
+    return cnn_forward_launch(g, centers, n, 0, 0, patch_step, packed, out, save, status, st);
 }
 
 extern "C" int vs_cnn_score_lattice(vs_grid g, int32_t stride, int32_t patch_step, const void *packed,
@@ -1049,8 +1050,19 @@ extern "C" int vs_cnn_score_lattice(vs_grid g, int32_t stride, int32_t patch_ste
     if (stride < 1) return VS_ERR_RANGE;
     if (g.H < 1 || g.W < 1) return VS_ERR_RANGE;
     const int64_t Hs = (g.H + stride - 1) / stride, Ws = (g.W + stride - 1) / stride;
-    return cnn_forward_launch(g, nullptr, Hs * Ws, stride, patch_step, packed, score_out, nullptr,
+    return cnn_forward_launch(g, nullptr, Hs * Ws, stride, 0, patch_step, packed, score_out, nullptr,
                               status, st);
+}
+
+extern "C" int vs_cnn_score_lattice_rows(vs_grid g, int32_t stride, int32_t patch_step, int32_t row0,
+                                         int32_t nrows, const void *packed, float *score_out,
+                                         int32_t *status, vs_stream_t st) {
+    if (stride < 1) return VS_ERR_RANGE;
+    if (g.H < 1 || g.W < 1) return VS_ERR_RANGE;
+    const int64_t Hs = (g.H + stride - 1) / stride, Ws = (g.W + stride - 1) / stride;
+    if (row0 < 0 || nrows < 0 || (int64_t)row0 + nrows > Hs) return VS_ERR_RANGE;
+    return cnn_forward_launch(g, nullptr, (int64_t)nrows * Ws, stride, row0, patch_step, packed, score_out,
+                              nullptr, status, st);
 }
 
 // per patch: dL/da of layers 5, 4, 3, 2, 1 (fp32)

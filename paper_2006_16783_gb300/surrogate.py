@@ -155,6 +155,46 @@ def propose(g, packed, stride, block, k, score=None, patch_step=1):
     return V.findmax_f32(score, g.H, g.W, stride, block, k), score
 
 
+def score_lattice_streamed(g, host, stride, packed, out, patch_step=1, chunks=8, copy_stream=None):
+    """Score the stride lattice of a terrain that is still in host memory.
+
+    ``host`` is a pinned CPU tensor laid out like ``g.storage`` ([H][pitch]
+    int16); it is copied into ``g.storage`` in ``chunks`` row bands on a side
+    stream, and every band of lattice rows is scored on the current stream as
+    soon as the terrain rows its patches read (within 32 * patch_step rows)
+    have arrived, so the copy overlaps the network.  On return the current
+    stream is ordered after the whole copy (later stages see the full
+    terrain); nothing is synchronised with the host."""
+    H, W = g.H, g.W
+    Hs, Ws = (H + stride - 1) // stride, (W + stride - 1) // stride
+    if tuple(host.shape) != tuple(g.storage.shape) or host.dtype != g.storage.dtype or not host.is_pinned():
+        raise ValueError("host must be a pinned tensor shaped like the grid's storage")
+    cur = torch.cuda.current_stream()
+    cs = copy_stream or torch.cuda.Stream()
+    cs.wait_stream(cur)  # earlier work on the device buffer is done
+    bounds = [(i * H) // chunks for i in range(chunks + 1)]
+    done = []
+    with torch.cuda.stream(cs):
+        for i in range(chunks):
+            a, b = bounds[i], bounds[i + 1]
+            if b > a:
+                g.storage[a:b].copy_(host[a:b], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(cs)
+            done.append((b, ev))
+    reach = 32 * patch_step
+    r = 0
+    for b, ev in done:
+        # lattice rows i whose patches read only rows below b
+        last = Hs if b >= H else max(0, min(Hs, (b - 1 - reach) // stride + 1))
+        if last > r:
+            cur.wait_event(ev)
+            V.cnn_score_lattice_rows(g, stride, packed, r, last - r, out[r:last], patch_step=patch_step)
+            r = last
+    cur.wait_stream(cs)
+    return out
+
+
 def _main():
     """python -m paper_2006_16783_gb300.surrogate score-lattice --size N --stride S
     scores an N x N ridged terrain with randomly initialised weights (for

@@ -75,6 +75,7 @@ SIGNATURES = {
     "vs_cnn_pack": (ctypes.c_int, [P, P, P]),
     "vs_cnn_forward": (ctypes.c_int, [vs_grid, P, i64, i32, P, P, P, P, P]),
     "vs_cnn_score_lattice": (ctypes.c_int, [vs_grid, i32, i32, P, P, P, P]),
+    "vs_cnn_score_lattice_rows": (ctypes.c_int, [vs_grid, i32, i32, i32, i32, P, P, P, P]),
     "vs_cnn_backward_workspace": (sz, [i64]),
     "vs_cnn_backward": (ctypes.c_int, [P, P, i64, P, P, P, P, sz, P]),
     "vs_cnn_adam": (ctypes.c_int, [P, P, P, P, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -285,6 +286,18 @@ def cnn_forward(g, centers, packed, out=None, save=None, status=None, patch_step
 
 def cnn_save_bytes():
     return lib().vs_cnn_save_bytes()
+
+
+def cnn_score_lattice_rows(g, stride, packed, row0, nrows, out, status=None, patch_step=1):
+    """Lattice rows row0 .. row0+nrows-1 into out[nrows][ceil(W/stride)] (a view
+    of the full score map is fine)."""
+    Ws = (g.W + stride - 1) // stride
+    if out.dtype != torch.float32 or not out.is_contiguous() or out.numel() < nrows * Ws:
+        raise ValueError("out must be contiguous float32 with nrows*ceil(W/stride) elements")
+    _check("vs_cnn_score_lattice_rows",
+           lib().vs_cnn_score_lattice_rows(g.c(), stride, patch_step, row0, nrows, _ptr(packed), _ptr(out),
+                                           _ptr(status), _stream()))
+    return out
 
 
 def cnn_score_lattice(g, stride, packed, out=None, status=None, patch_step=1):

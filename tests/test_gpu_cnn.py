@@ -109,6 +109,34 @@ def test_cnn_forward_many_patches_per_cta(V):
     assert np.array_equal(y2, y[perm])
 
 
+@pytest.mark.parametrize("step,chunks", [(1, 5), (3, 7)])
+def test_cnn_lattice_rows_and_streamed(V, step, chunks):
+    """Row bands of the lattice equal the full lattice's rows; scoring while
+    the terrain streams in from pinned host memory gives the same map and
+    leaves the whole terrain on the device."""
+    from oracle import cnn_oracle as C
+    from paper_2006_16783_gb300 import surrogate as S
+    H, W, s = 700, 650, 16
+    z = T.spectral_fbm(H, W, 0.8, 44, 0, 2000).numpy()
+    g = V.Grid.from_tensor(torch.as_tensor(z), "cuda")
+    packed = V.cnn_pack(torch.as_tensor(C.flatten_params(_params(4))).cuda())
+    full = V.cnn_score_lattice(g, s, packed, patch_step=step)
+    Hs = full.shape[0]
+    part = torch.full_like(full, -1.0)
+    for r0, r1 in [(0, 7), (7, 8), (8, Hs)]:
+        V.cnn_score_lattice_rows(g, s, packed, r0, r1 - r0, part[r0:r1], patch_step=step)
+    assert torch.equal(part, full)
+    host = g.storage.cpu().pin_memory()
+    g2 = V.Grid(torch.zeros_like(g.storage), W)
+    out = torch.full_like(full, -1.0)
+    S.score_lattice_streamed(g2, host, s, packed, out, patch_step=step, chunks=chunks)
+    torch.cuda.synchronize()
+    assert torch.equal(out, full)
+    assert torch.equal(g2.storage, g.storage)
+    with pytest.raises(V.VsError):
+        V.cnn_score_lattice_rows(g, s, packed, Hs - 1, 2, part, patch_step=step)
+
+
 @pytest.mark.parametrize("step", [2, 3])
 def test_cnn_strided_patches(V, step):
     """patch_step > 1 (every step-th post, clamped at the edges; these patches
