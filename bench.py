@@ -489,9 +489,15 @@ def main():
     ap.add_argument("--sur-stride", type=int, default=32)
     ap.add_argument("--patch-step", type=int, default=3,
                     help="post spacing inside the CNN's 65x65 input patch")
-    ap.add_argument("--train-posts", type=int, default=500000)
-    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--train-posts", type=int, default=None,
+                    help="training posts (default 500000; 4000000 for --workload learn)")
+    ap.add_argument("--epochs", type=int, default=None, help="default 3; 6 for --workload learn")
     args = ap.parse_args()
+    learn = args.workload == "learn"
+    if args.train_posts is None:
+        args.train_posts = 4000000 if learn else 500000
+    if args.epochs is None:
+        args.epochs = 6 if learn else 3
     dist, rank, world, local = dist_init()
     if args.workload == "batch":
         run_batch(args, dist, rank, world, local)
