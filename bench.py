@@ -4,8 +4,10 @@
 Two pipelines site 4096 observers on the resident 46400^2 terrain (R=100,
 40000 candidates from top-4 per 464^2 block):
   plain      vix (S=10 LOS per post) -> findmax -> viewshed -> site
-  surrogate  CNN scores on a stride-32 lattice -> findmax_f32 -> viewshed -> site
-             (network trained beforehand on another terrain of the same recipe)
+  surrogate  CNN scores on a lattice of posts -> findmax_f32 -> viewshed -> site
+             (network trained beforehand on another terrain of the same recipe;
+             lattice stride tuned on a third one: the largest of 32..128 whose
+             coverage is within 0.1% of stride 32's)
 The headline `value` is the end-to-end siting time of the surrogate pipeline
 when its coverage is within 1% of (or above) the plain pipeline's, else of
 the plain pipeline; both are reported in full.  Prints ONE JSON line.
@@ -247,7 +249,13 @@ class SurrogatePipeline:
         self.mae = float((self.tr.predict(g, pt) - lt).abs().mean())
         self.mae_vix = float((pipe.vixbuf.reshape(-1)[pt].float() / w.S - lt).abs().mean())
         self.mae_posts = pt.numel()
-        st = self.stride = args.sur_stride
+        # proposal stride: given, or tuned on another terrain of the recipe --
+        # the largest stride whose coverage is within 0.1 % of the densest's
+        self.tuning = None
+        st = args.sur_stride
+        if st <= 0:
+            st, self.tuning = self._tune_stride(pipe, dev)
+        self.stride = st
         self.n = V.findmax_count(w.H, w.W, st, w.block, w.k)
         self.score = torch.empty(((w.H + st - 1) // st, (w.W + st - 1) // st), dtype=torch.float32, device=dev)
         self.cand = torch.empty(self.n, dtype=torch.int64, device=dev)
@@ -258,6 +266,37 @@ class SurrogatePipeline:
         self.ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         self.copy_stream = torch.cuda.Stream()
         self.result = None
+
+    STRIDES = (32, 48, 64, 96, 128)
+
+    def _tune_stride(self, pipe, dev):
+        V, w = self.V, self.w
+        t0 = time.perf_counter()
+        wtu = WL.scaled(w, w.H, w.W, name=w.name + "_tune", seed=w.seed + 8)
+        ztu = wtu.make_terrain(dev)
+        ztu_s, _ = WL.terrain.pad_pitch(ztu, 8)
+        del ztu
+        gtu = V.Grid(ztu_s, w.W)
+        nmax = max(V.findmax_count(w.H, w.W, st, w.block, w.k) for st in self.STRIDES)
+        cand = torch.empty(nmax, dtype=torch.int64, device=dev)
+        bm = torch.empty((nmax, 2 * w.R + 1, V.words_per_row(w.R)), dtype=torch.int32, device=dev)
+        area = torch.empty(nmax, dtype=torch.int32, device=dev)
+        cum = torch.empty_like(pipe.cum)
+        ws = torch.empty(V.site_workspace(nmax, w.R), dtype=torch.uint8, device=dev)
+        cov = {}
+        for st in self.STRIDES:
+            n = V.findmax_count(w.H, w.W, st, w.block, w.k)
+            score = V.cnn_score_lattice(gtu, st, self.tr.packed, patch_step=self.tr.patch_step)
+            V.findmax_f32(score, w.H, w.W, st, w.block, w.k, out=cand[:n])
+            V.viewshed(gtu, w.R, w.ht, w.hr, cand[:n], bm=bm[:n], area=area[:n])
+            cum.zero_()
+            cov[st] = coverage(V.site(bm[:n], cand[:n], w.H, w.W, w.R, w.n_obs, cum=cum, ws=ws, sync=False))[0]
+        best = max(s for s in self.STRIDES if cov[s] >= (1.0 - 1e-3) * cov[self.STRIDES[0]])
+        del gtu, ztu_s, cand, bm, area, cum, ws
+        torch.cuda.synchronize()
+        return best, {"terrain_seed": w.seed + 8, "coverage_by_stride": cov, "chosen": best,
+                      "rule": "largest stride with coverage >= 0.999 x the stride-32 coverage",
+                      "tune_s": time.perf_counter() - t0}
 
     def step(self, record=False, g=None, host=None):
         """One siting; with ``host`` (a pinned copy of the terrain) the terrain
@@ -289,6 +328,28 @@ class SurrogatePipeline:
         return [self.ev[i].elapsed_time(self.ev[i + 1]) for i in range(4)]
 
     names = ["cnn_lattice", "findmax_f32", "viewshed", "site"]
+
+
+def site_loop_bytes(cand, chosen, W, R, PR):
+    """Algorithmic bytes of the greedy loop: per step the winner's window (V and
+    C read, C written: 3 * (2R+1) * PR words) and, for every candidate not yet
+    chosen whose window meets the winner's, the overlap words of its bitmap (an
+    upper bound: the kernel skips words without new coverage)."""
+    words = (2 * R + 1) * PR
+    cy, cx = cand // W, cand % W
+    gw0 = np.floor_divide(cx - R, 32)
+    alive = np.ones(len(cand), dtype=bool)
+    where = {int(p): i for i, p in enumerate(cand)}
+    total = 0
+    for p in chosen:
+        i = where[int(p)]
+        alive[i] = False
+        wy, wgw = cy[i], gw0[i]
+        rows = np.clip(np.minimum(cy, wy) + R - (np.maximum(cy, wy) - R) + 1, 0, None)
+        cols = np.clip(np.minimum(gw0, wgw) + PR - 1 - np.maximum(gw0, wgw) + 1, 0, None)
+        near = alive & (np.abs(cx - cx[i]) <= 2 * R)
+        total += 3 * words * 4 + int((rows * cols)[near].sum()) * 4
+    return total
 
 
 def coverage(result):
@@ -486,7 +547,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--sur-stride", type=int, default=32)
+    ap.add_argument("--sur-stride", type=int, default=0,
+                    help="proposal lattice stride; 0 = tuned on another terrain of the recipe")
     ap.add_argument("--patch-step", type=int, default=3,
                     help="post spacing inside the CNN's 65x65 input patch")
     ap.add_argument("--train-posts", type=int, default=None,
@@ -630,6 +692,16 @@ def main():
         "findmax": {"bound": "hbm", "achieved": (w.H * w.W + plain.n * 8) / (p_st[1] * 1e-3) / 1e9,
                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None},
     }
+    # the greedy loop of the headline pipeline: bytes per step (window V + C
+    # read + C write, and the refresh's overlap words) over the site stage time
+    hres = head.result
+    nsel = int(hres[3].item())
+    loop_bytes = site_loop_bytes(head.cand.cpu().numpy(), hres[0][:nsel].cpu().numpy(), w.W, w.R,
+                                 V.words_per_row(w.R))
+    roof["site_loop"] = {"bound": "hbm", "achieved": loop_bytes / (st[3] * 1e-3) / 1e9,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None,
+                         "note": "sequential greedy on one CTA: bound by the latency of its "
+                                 "dependent memory rounds, not by bandwidth"}
     if sur:
         from oracle import cnn_oracle as C
         flops = sur.score.numel() * C.flops_per_patch()
@@ -638,7 +710,7 @@ def main():
                                "unit": "TFLOP/s", "traffic": None}
     for r in roof.values():
         r["frac"] = r["achieved"] / r["peak"]
-    stage_roof = {"vix": "vix", "findmax": "findmax", "viewshed": "viewshed", "site": "site_gains",
+    stage_roof = {"vix": "vix", "findmax": "findmax", "viewshed": "viewshed", "site": "site_loop",
                   "cnn_lattice": "cnn_lattice", "findmax_f32": "findmax", }
     dom = head.names[int(np.argmax(st))]
     dom_roof = dict(roof[stage_roof[dom]])
@@ -655,7 +727,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": w.name, "H": w.H, "W": w.W, "R": w.R, "ht": w.ht, "hr": w.hr,
                    "S": w.S, "block": w.block, "k": w.k, "n_obs": w.n_obs, "candidates": plain.n,
-                   "pipeline": ("surrogate (CNN on a stride-%d lattice, findmax, viewshed, site)" % args.sur_stride
+                   "pipeline": ("surrogate (CNN on a stride-%d lattice, findmax, viewshed, site)" % sur.stride
                                 if head is sur else "plain (vix, findmax, viewshed, site)"),
                    "l2": "inputs larger than L2 (%.1f GB terrain, %.0f MB bitmaps)" % (
                        zs.numel() * 2 / 1e9, plain.bm.numel() * 4 / 1e6),
@@ -673,7 +745,8 @@ def main():
         out["surrogate"] = {
             "s_per_step": s_ms / 1000.0, "stages_ms": dict(zip(sur.names, s_st)),
             "coverage_posts": cov_sur, "coverage_ratio_vs_plain": cov_sur / max(cov_plain, 1),
-            "speedup_vs_plain": p_ms / s_ms, "lattice_stride": sur.stride, "candidates": sur.n,
+            "speedup_vs_plain": p_ms / s_ms, "lattice_stride": sur.stride, "stride_tuning": sur.tuning,
+            "candidates": sur.n,
             "patch_step": sur.tr.patch_step,
             "patches_per_step": sur.score.numel(), "train_posts": args.train_posts, "epochs": args.epochs,
             "train_loss_last_epoch": sur.train_loss, "label_s": sur.label_s, "train_s": sur.train_s,
@@ -686,7 +759,7 @@ def main():
         v, desc, threads = oracle_sample(zh_np, w)
         if head is sur:
             # the surrogate pipeline's oracle: numpy CNN per lattice patch instead of vix
-            per_patch = cnn_oracle_sample(zh_np, w, args.sur_stride, args.patch_step)
+            per_patch = cnn_oracle_sample(zh_np, w, sur.stride, args.patch_step)
             t_vix = float(desc.split("(vix ")[1].split(" s")[0])
             v = v - t_vix + per_patch * sur.score.numel()
             desc += ("; surrogate pipeline: vix replaced by the numpy CNN oracle on %d lattice patches "

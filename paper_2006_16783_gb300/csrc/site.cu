@@ -342,6 +342,7 @@ struct Site1Params {
     const uint32_t *gain0;   // candidate order
     const uint32_t *sp, *sorig, *slo, *shi;  // slot order
     const unsigned long long *covered0;
+    int vec_rows;            // bitmap rows are whole 16-byte vectors (PR % 4 == 0, bm 16-byte aligned)
 };
 
 __device__ __forceinline__ uint64_t u64max(uint64_t a, uint64_t b) { return a > b ? a : b; }
@@ -484,12 +485,12 @@ __device__ __forceinline__ void site1_body(const Site1Params &P) {
                     const int ya = max(max(cy, wy) - R, 0), yb = min(min(cy, wy) + R, H - 1);
                     const int ga = max(max(cgw0, wgw0), 0), gb = min(min(cgw0, wgw0) + PR - 1, WWc - 1);
                     const int nwd = (ya <= yb && ga <= gb) ? gb - ga + 1 : 0;
-                    ovl = (ya <= yb && ga <= gb) ? (yb - ya + 1) * nwd : 0;
+                    ovl = (ya <= yb && ga <= gb) ? (yb - ya + 1) * (P.vec_rows ? 1 : nwd) : 0;
                     // the overlap's first word in the delta window and in the
                     // candidate's bitmap (n * words < 2^32 on this path)
                     const int dbase = (ya - wy + R) * PR + (ga - wgw0);
                     const uint32_t vbase = bso * (uint32_t)P.words + (uint32_t)((ya - cy + R) * PR + (ga - cgw0));
-                    geo = make_int4(dbase, (int)vbase, nwd, 0);
+                    geo = make_int4(dbase, (int)vbase, nwd, ga - cgw0);
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, aff);
@@ -515,57 +516,89 @@ __device__ __forceinline__ void site1_body(const Site1Params &P) {
             }
             if (tid == 0) s_pref[tot] = TT;
             __syncthreads();
-            // ---- every thread takes an equal run of the overlap words of all
-            // listed candidates; within one candidate's overlap it walks rows
-            // and words with running indices, loading eight words at a time
-            // and reading V_c only where delta is non-zero
-            const int per = (TT + kSiteThreads - 1) / kSiteThreads;
-            const int e0 = tid * per, e1 = min(TT, e0 + per);
-            if (e0 < e1) {
-                int l = 0, hi2 = tot - 1;  // last l with s_pref[l] <= e0
-                while (l < hi2) {
-                    const int m = (l + hi2 + 1) >> 1;
-                    if (s_pref[m] <= e0) l = m; else hi2 = m - 1;
-                }
-                int e = e0;
-                while (e < e1) {
-                    const int pl = s_pref[l], pn = s_pref[l + 1];
-                    if (e >= pn) {  // empty overlaps are skipped
-                        ++l;
-                        continue;
+            if (P.vec_rows) {
+                // ---- refresh by overlap rows: row e (over all listed
+                // candidates) on thread e mod 1024; its delta words come from
+                // shared memory first, and only a row with new coverage reads
+                // its candidate's bitmap row, as PR/4 16-byte loads
+                for (int e = tid; e < TT; e += kSiteThreads) {
+                    int l = 0, h2 = tot - 1;  // last l with s_pref[l] <= e
+                    while (l < h2) {
+                        const int m = (l + h2 + 1) >> 1;
+                        if (s_pref[m] <= e) l = m; else h2 = m - 1;
                     }
                     const int4 gq = s_geo[l];
-                    const int nwd = gq.z, skip = PR - nwd;
-                    const int u = e - pl, dy = u / nwd;
-                    int dw = u - dy * nwd;
-                    int di = gq.x + dy * PR + dw;
-                    const uint32_t *vp = P.bm + (uint32_t)gq.y + (uint32_t)(dy * PR + dw);
-                    const int send = min(e1, pn);
+                    const int r = e - s_pref[l], nwd = gq.z, c0 = gq.w;  // overlap words c0 .. c0+nwd-1 of the row
+                    const uint32_t *dl = s_delta + gq.x + r * PR;
+                    uint32_t any = 0u;
+                    for (int j = 0; j < nwd; ++j) any |= dl[j];
+                    if (!any) continue;
+                    const uint4 *vr = (const uint4 *)(P.bm + (uint32_t)gq.y - (uint32_t)c0 + (uint32_t)(r * PR));
                     unsigned sum = 0;
-                    for (; e < send; e += 8) {
-                        uint32_t v[8];
+                    for (int q4 = 0; q4 < PR / 4; ++q4) {
+                        const uint4 v = __ldg(vr + q4);
+                        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            v[q] = 0u;
-                            if (e + q < send) {
-                                const uint32_t dl = s_delta[di];
-                                if (dl) v[q] = __ldg(vp) & dl;
-                                ++dw;
-                                ++di;
-                                ++vp;
-                                if (dw == nwd) {
-                                    dw = 0;
-                                    di += skip;
-                                    vp += skip;
+                        for (int t = 0; t < 4; ++t) {
+                            const int j = 4 * q4 + t - c0;
+                            if (j >= 0 && j < nwd) sum += __popc(vv[t] & dl[j]);
+                        }
+                    }
+                    if (sum) atomicAdd(&s_sum[l], sum);
+                }
+            } else {
+                // ---- every thread takes an equal run of the overlap words of all
+                // listed candidates; within one candidate's overlap it walks rows
+                // and words with running indices, loading eight words at a time
+                // and reading V_c only where delta is non-zero
+                const int per = (TT + kSiteThreads - 1) / kSiteThreads;
+                const int e0 = tid * per, e1 = min(TT, e0 + per);
+                if (e0 < e1) {
+                    int l = 0, hi2 = tot - 1;  // last l with s_pref[l] <= e0
+                    while (l < hi2) {
+                        const int m = (l + hi2 + 1) >> 1;
+                        if (s_pref[m] <= e0) l = m; else hi2 = m - 1;
+                    }
+                    int e = e0;
+                    while (e < e1) {
+                        const int pl = s_pref[l], pn = s_pref[l + 1];
+                        if (e >= pn) {  // empty overlaps are skipped
+                            ++l;
+                            continue;
+                        }
+                        const int4 gq = s_geo[l];
+                        const int nwd = gq.z, skip = PR - nwd;
+                        const int u = e - pl, dy = u / nwd;
+                        int dw = u - dy * nwd;
+                        int di = gq.x + dy * PR + dw;
+                        const uint32_t *vp = P.bm + (uint32_t)gq.y + (uint32_t)(dy * PR + dw);
+                        const int send = min(e1, pn);
+                        unsigned sum = 0;
+                        for (; e < send; e += 8) {
+                            uint32_t v[8];
+    #pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                v[q] = 0u;
+                                if (e + q < send) {
+                                    const uint32_t dl = s_delta[di];
+                                    if (dl) v[q] = __ldg(vp) & dl;
+                                    ++dw;
+                                    ++di;
+                                    ++vp;
+                                    if (dw == nwd) {
+                                        dw = 0;
+                                        di += skip;
+                                        vp += skip;
+                                    }
                                 }
                             }
+    #pragma unroll
+                            for (int q = 0; q < 8; ++q) sum += __popc(v[q]);
                         }
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) sum += __popc(v[q]);
+                        e = send;
+                        if (sum) atomicAdd(&s_sum[l], sum);
+                        ++l;
                     }
-                    e = send;
-                    if (sum) atomicAdd(&s_sum[l], sum);
-                    ++l;
                 }
             }
             __syncthreads();
@@ -716,6 +749,7 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
         Q1.WWc = P.WWc; Q1.n_obs = n_obs; Q1.need = P.need; Q1.chosen = chosen; Q1.gains = gains;
         Q1.cum = cum; Q1.n_chosen = n_chosen; Q1.gain0 = g0; Q1.sp = sp; Q1.sorig = sorig;
         Q1.slo = slo; Q1.shi = shi; Q1.covered0 = cov;
+        Q1.vec_rows = (P.PR % 4 == 0 && ((uintptr_t)bm & 15) == 0) ? 1 : 0;
         if (job_out) {  // batched call: the caller launches the loop
             *job_out = Q1;
             *smem_out = smem1;
