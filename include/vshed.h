@@ -76,11 +76,13 @@ int vs_version(void);
  *     fewer when the ring has fewer than 512 rays)
  *   VS_TUNE_VIX_TILE: vix post tile, 1 = 64x32, 2 = 32x32 (0 = default: the
  *     largest tile whose window fits)
- *   VS_TUNE_SITE_CLUSTER: the greedy site loop of vs_site; 0 = default (one
- *     CTA when every gain fits in its shared memory, else a cluster), 2 / 4 /
- *     8 / 16 = a cluster of at most that many CTAs (spreads the gain
- *     refresh's memory traffic over more SMs).  R is the call's R.  vs_site_batch
- *     always uses one CTA per job. */
+ *   VS_TUNE_SITE_CLUSTER: the greedy site loop of vs_site when every gain
+ *     fits in one CTA's shared memory: 0 = default (a leader cluster of 8
+ *     CTAs when bitmap rows are whole 16-byte vectors, i.e. (2R/32 + 2) % 4 == 0,
+ *     else one CTA), 1 = one CTA, 2 / 4 / 8 / 16 = a leader cluster of that
+ *     many CTAs (the leader keeps the gains and picks each winner, the window
+ *     and refresh loads are split over the cluster's SMs).  R is the call's R.
+ *     vs_site_batch always uses one CTA per job. */
 enum { VS_TUNE_VIEWSHED_THREADS = 0, VS_TUNE_VIX_TILE = 1, VS_TUNE_SITE_CLUSTER = 2 };
 int vs_tune_set(int32_t op, int32_t R, int32_t value);
 int vs_tune_get(int32_t op, int32_t R);

@@ -625,6 +625,317 @@ __device__ __forceinline__ void site1_body(const Site1Params &P) {
 
 __global__ void __launch_bounds__(kSiteThreads, 1) k_site_loop1(const Site1Params P) { site1_body(P); }
 
+// ------------------------------------------------------------------ leader cluster
+// The same greedy steps on a thread-block cluster of Q CTAs: the leader (rank
+// 0) keeps every gain in its shared memory and takes the sequential part of a
+// step (argmax, winner metadata, band compaction); the memory-heavy part --
+// the winner's window (V and C words, C updated) and the refresh of the
+// affected candidates' overlap rows -- is split by window row, row r on the
+// CTA of rank r mod Q, so Q SMs issue its loads.  A step is one or more
+// rounds (one per 1024-slot chunk of the winner's band):
+//   leader: [new step: stop test, argmax, metadata]; compaction of the chunk;
+//           header + list written into every CTA's shared memory
+//   cluster barrier A; every CTA reads the same stop flag
+//   all:    [new step: its window rows -> local delta rows, C updated];
+//           its refresh rows -> partial sums added into the leader's s_sum
+//   cluster barrier B
+//   leader: gains lowered; [last chunk: winner's gain 0, owners rescan]
+// Every CTA passes both barriers the same number of times.  Requires bitmap
+// rows that are whole 16-byte vectors (PR % 4 == 0).
+struct SiteQHeader {
+    int stop, first, last, tot;
+    int wx, wy, wgw0, pad;
+};
+
+__global__ void __launch_bounds__(kSiteThreads, 1) k_site_loopq(const Site1Params P) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), Q = (int)cl.num_blocks();
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *s_gain = (uint32_t *)smem;                 // n (leader)
+    uint32_t *s_dloc = s_gain + ((P.n + 3) & ~3);        // this CTA's delta rows
+    __shared__ SiteQHeader s_hdr;
+    __shared__ int4 s_geo[kSiteThreads];                 // per listed candidate (broadcast)
+    __shared__ unsigned s_sum[kSiteThreads];             // leader: summed partial refreshes
+    __shared__ unsigned s_part[kSiteThreads];            // this CTA's partial refreshes
+    __shared__ int s_cpref[kSiteThreads + 1];            // this CTA's row prefix over the list
+    __shared__ int s_list[kSiteThreads];                 // leader: slots of the list
+    __shared__ int s_dirty[kSiteThreads];                // leader
+    __shared__ uint64_t s_red[32];
+    __shared__ int s_wa[32], s_wb[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int n = P.n, R = P.R, PR = P.PR, W = P.W, H = P.H, WWc = P.WWc;
+    const int cs = (n + kSiteThreads - 1) / kSiteThreads;
+    const int my0 = tid * cs, my1 = min(n, my0 + cs);
+    const int nrow_loc = (2 * R + 1 - rank + Q - 1) / Q;  // window rows r = rank + Q*i of this CTA
+
+    if (rank == 0) {
+        for (int i = tid; i < n; i += kSiteThreads)
+            s_gain[i] = (P.sp[i] == 0xFFFFFFFFu) ? 0u : P.gain0[P.sorig[i]];
+        s_dirty[tid] = 0;
+    }
+    __syncthreads();
+    auto local_best = [&]() {
+        uint64_t b[4] = {0ull, 0ull, 0ull, 0ull};
+        int i = my0;
+        for (; i + 4 <= my1; i += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t g = s_gain[i + q];
+                b[q] = u64max(b[q], g ? (((uint64_t)g << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)(i + q))) : 0ull);
+            }
+        }
+        for (; i < my1; ++i) {
+            const uint32_t g = s_gain[i];
+            b[0] = u64max(b[0], g ? (((uint64_t)g << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)i)) : 0ull);
+        }
+        return u64max(u64max(b[0], b[1]), u64max(b[2], b[3]));
+    };
+    uint64_t best = (rank == 0) ? local_best() : 0ull;
+    long long covered = (rank == 0 && P.need >= 0) ? (long long)*P.covered0 : 0;
+    int t = 0;               // leader: steps done
+    int s = -1, lo = 0, hi = 0, b0 = 0;
+    uint32_t wc = 0u;
+    bool in_step = false;    // leader: a step's band is being processed
+    cl.sync();
+
+    for (;;) {
+        // ================================================ leader: the round's work list
+        if (rank == 0) {
+            bool stop = false, first = false;
+            if (!in_step) {
+                stop = t >= P.n_obs || (P.need >= 0 && covered >= P.need);
+                uint64_t k = 0ull;
+                if (!stop) {
+                    k = best;
+                    for (int o = 16; o > 0; o >>= 1) k = u64max(k, __shfl_xor_sync(0xffffffffu, k, o));
+                    if (lane == 0) s_red[wid] = k;
+                    __syncthreads();
+                    k = s_red[lane];
+                    for (int o = 16; o > 0; o >>= 1) k = u64max(k, __shfl_xor_sync(0xffffffffu, k, o));
+                    if ((uint32_t)(k >> 32) == 0u) stop = true;
+                }
+                if (!stop) {
+                    const uint32_t g = (uint32_t)(k >> 32);
+                    s = (int)(0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFu));
+                    const uint32_t wp = P.sp[s];
+                    wc = P.sorig[s];
+                    lo = (int)P.slo[s];
+                    hi = (int)P.shi[s];  // the winner's slot lies in [lo, hi)
+                    if (tid == 0) {
+                        P.chosen[t] = (int64_t)wp;
+                        P.gains[t] = (int64_t)g;
+                        s_hdr.wx = (int)(wp % (uint32_t)W);
+                        s_hdr.wy = (int)(wp / (uint32_t)W);
+                        s_hdr.wgw0 = floordiv((int)(wp % (uint32_t)W) - R, 32);
+                    }
+                    covered += g;
+                    b0 = lo;
+                    first = true;
+                    in_step = true;
+                }
+            }
+            int tot = 0;
+            bool last = true;
+            if (!stop) {
+                __syncthreads();  // s_hdr geometry of a new step
+                const int wx = s_hdr.wx, wy = s_hdr.wy, wgw0 = s_hdr.wgw0;
+                const int i = b0 + tid;
+                bool aff = false;
+                int4 geo = make_int4(0, 0, 0, 0);
+                if (i < hi && i != s && s_gain[i] != 0) {
+                    const uint32_t bsp = P.sp[i];
+                    const int cx = (int)(bsp % (uint32_t)W), cy = (int)(bsp / (uint32_t)W);
+                    if (abs(cx - wx) <= 2 * R) {
+                        const int cgw0 = floordiv(cx - R, 32);
+                        const int ya = max(max(cy, wy) - R, 0), yb = min(min(cy, wy) + R, H - 1);
+                        const int ga = max(max(cgw0, wgw0), 0), gb = min(min(cgw0, wgw0) + PR - 1, WWc - 1);
+                        if (ya <= yb && ga <= gb) {
+                            aff = true;
+                            const int ra = ya - (wy - R), rb = yb - (wy - R);
+                            const uint32_t vrow0 = P.sorig[i] * (uint32_t)P.words + (uint32_t)((ya - cy + R) * PR);
+                            geo = make_int4(ra | (rb << 16), (gb - ga + 1) | ((ga - cgw0) << 10) | ((ga - wgw0) << 20),
+                                            (int)vrow0, 0);
+                        }
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, aff);
+                if (lane == 0) s_wa[wid] = __popc(bal);
+                __syncthreads();
+                const int wcn = s_wa[lane];
+                int icn = wcn;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, icn, o);
+                    if (lane >= o) icn += u;
+                }
+                const int base = __shfl_sync(0xffffffffu, icn - wcn, wid);
+                tot = __shfl_sync(0xffffffffu, icn, 31);
+                last = b0 + kSiteThreads >= hi;
+                if (aff) {
+                    const int li = base + __popc(bal & ((1u << lane) - 1u));
+                    s_list[li] = i;
+                    s_sum[li] = 0u;
+                    for (int q = 0; q < Q; ++q) *cl.map_shared_rank(&s_geo[li], q) = geo;
+                }
+            }
+            if (tid < Q) {
+                SiteQHeader h;
+                h.stop = stop ? 1 : 0;
+                h.first = first ? 1 : 0;
+                h.last = last ? 1 : 0;
+                h.tot = tot;
+                h.wx = s_hdr.wx;
+                h.wy = s_hdr.wy;
+                h.wgw0 = s_hdr.wgw0;
+                h.pad = (int)wc;
+                *cl.map_shared_rank(&s_hdr, tid) = h;
+            }
+        }
+        cl.sync();  // A: the round's header and list are in every CTA
+        const SiteQHeader h = s_hdr;
+        if (h.stop) break;
+        const int wy = h.wy, wgw0 = h.wgw0, tot = h.tot;
+        // ================================================ all: this CTA's rows
+        // ---- its refresh rows: per listed candidate, the overlap rows r with
+        // r = rank (mod Q), as an exclusive prefix over the list
+        if (tid < tot) s_part[tid] = 0u;
+        int cnt = 0;
+        if (tid < tot) {
+            const int ra = s_geo[tid].x & 0xFFFF, rb = s_geo[tid].x >> 16;
+            const int r0 = ra + ((rank - ra) % Q + Q) % Q;
+            cnt = (r0 <= rb) ? (rb - r0) / Q + 1 : 0;
+        }
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) s_wb[wid] = inc;
+        __syncthreads();
+        {
+            const int wv = s_wb[lane];
+            int iw = wv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, iw, o);
+                if (lane >= o) iw += u;
+            }
+            const int wbase = __shfl_sync(0xffffffffu, iw - wv, wid);
+            const int rows_all = __shfl_sync(0xffffffffu, iw, 31);
+            if (tid < tot) s_cpref[tid] = wbase + inc - cnt;
+            if (tid == 0) s_cpref[tot] = rows_all;
+        }
+        __syncthreads();
+        const int TT = s_cpref[tot];
+        // row item e of this CTA: its candidate, window row and bitmap row
+        auto row_item = [&](int e, int &l, int &r, const uint4 *&vr) {
+            l = 0;
+            int h2 = tot - 1;  // last l with s_cpref[l] <= e
+            while (l < h2) {
+                const int m = (l + h2 + 1) >> 1;
+                if (s_cpref[m] <= e) l = m; else h2 = m - 1;
+            }
+            const int4 gq = s_geo[l];
+            const int ra = gq.x & 0xFFFF;
+            r = ra + ((rank - ra) % Q + Q) % Q + Q * (e - s_cpref[l]);
+            vr = (const uint4 *)(P.bm + (uint32_t)gq.z + (uint32_t)((r - ra) * PR));
+        };
+        // the first refresh row of this thread is loaded now, beside the
+        // window's words (the loads do not depend on the new coverage)
+        constexpr int kPreVec = 4;  // rows of up to 16 words
+        const bool pre = tid < TT && PR / 4 <= kPreVec;
+        uint4 pv[kPreVec];
+        int pl = 0, pr = 0;
+        if (pre) {
+            const uint4 *vr;
+            row_item(tid, pl, pr, vr);
+#pragma unroll
+            for (int q4 = 0; q4 < kPreVec; ++q4)
+                if (q4 < PR / 4) pv[q4] = __ldg(vr + q4);
+        }
+        // ---- its window rows (first round of a step): delta rows, C updated
+        if (h.first) {
+            const uint32_t *Vw = P.bm + (int64_t)(uint32_t)h.pad * P.words;
+            for (int e = tid; e < nrow_loc * PR; e += kSiteThreads) {
+                const int il = e / PR, w = e - il * PR;
+                const int r = rank + Q * il;
+                const int y = wy - R + r, gw = wgw0 + w;
+                uint32_t d = 0u;
+                if (y >= 0 && y < H && gw >= 0 && gw < WWc) {
+                    uint32_t *cp = P.cum + (int64_t)y * WWc + gw;
+                    const uint32_t v = __ldg(Vw + r * PR + w);
+                    const uint32_t old = *cp;
+                    d = v & ~old;
+                    if (d) *cp = old | v;
+                }
+                s_dloc[e] = d;
+            }
+        }
+        __syncthreads();  // publishes s_dloc and the zeroed s_part
+        // ---- refresh: popc(V_c AND delta) over each row's overlap words
+        auto popc_words = [&](const uint4 &v, int q4, const uint32_t *dl, int c0, int nwd) {
+            const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+            unsigned sum = 0;
+#pragma unroll
+            for (int t4 = 0; t4 < 4; ++t4) {
+                const int j = 4 * q4 + t4 - c0;
+                if (j >= 0 && j < nwd) sum += __popc(vv[t4] & dl[j]);
+            }
+            return sum;
+        };
+        if (pre) {
+            const int4 gq = s_geo[pl];
+            const int nwd = gq.y & 0x3FF, c0 = (gq.y >> 10) & 0x3FF, dw0 = gq.y >> 20;
+            const uint32_t *dl = s_dloc + ((pr - rank) / Q) * PR + dw0;
+            unsigned sum = 0;
+#pragma unroll
+            for (int q4 = 0; q4 < kPreVec; ++q4)
+                if (q4 < PR / 4) sum += popc_words(pv[q4], q4, dl, c0, nwd);
+            if (sum) atomicAdd(&s_part[pl], sum);
+        }
+        for (int e = tid + (pre ? kSiteThreads : 0); e < TT; e += kSiteThreads) {
+            int l, r;
+            const uint4 *vr;
+            row_item(e, l, r, vr);
+            const int4 gq = s_geo[l];
+            const int nwd = gq.y & 0x3FF, c0 = (gq.y >> 10) & 0x3FF, dw0 = gq.y >> 20;
+            const uint32_t *dl = s_dloc + ((r - rank) / Q) * PR + dw0;
+            unsigned sum = 0;
+            for (int q4 = 0; q4 < PR / 4; ++q4) sum += popc_words(__ldg(vr + q4), q4, dl, c0, nwd);
+            if (sum) atomicAdd(&s_part[l], sum);
+        }
+        __syncthreads();
+        if (tid < tot && s_part[tid]) atomicAdd(cl.map_shared_rank(&s_sum[tid], 0), s_part[tid]);
+        cl.sync();  // B: every partial refresh is in the leader's s_sum
+        // ================================================ leader: lower the gains
+        if (rank == 0) {
+            for (int q = tid; q < tot; q += kSiteThreads) {
+                const int ci = s_list[q];
+                s_gain[ci] -= s_sum[q];
+                s_dirty[ci / cs] = 1;
+            }
+            if (h.last) {
+                if (tid == 0) {
+                    s_gain[s] = 0u;
+                    s_dirty[s / cs] = 1;
+                }
+                in_step = false;
+                ++t;
+            } else {
+                b0 += kSiteThreads;
+            }
+            __syncthreads();
+            if (h.last && s_dirty[tid]) {
+                s_dirty[tid] = 0;
+                best = local_best();
+            }
+        }
+    }
+    if (rank == 0 && tid == 0) *P.n_chosen = t;
+    cl.sync();  // no CTA leaves while another may still address its shared memory
+}
+
 // many independent greedy loops (one per terrain) in one launch: CTA j runs job j
 constexpr int kSiteMaxJobs = 64;
 struct Site1Batch {
@@ -695,6 +1006,39 @@ static bool site1_fits(int64_t n, int words) {  // + ~33 KB of static shared mem
     return n < (1 << 30) && site1_smem_bytes(n, words) <= (size_t)kSmemLimit - 40 * 1024;
 }
 
+// leader cluster: the leader's gains plus a CTA's window rows of delta
+static size_t siteq_smem_bytes(int64_t n, int R, int PR, int q) {
+    const int rows = (2 * R + 1 + q - 1) / q;
+    return (size_t)((n + 3) & ~3) * 4 + (size_t)rows * PR * 4 + 16;
+}
+static bool siteq_fits(size_t smem) {  // + ~37 KB of static shared memory
+    return smem <= (size_t)kSmemLimit - 40 * 1024;
+}
+static bool siteq_launchable(size_t smem, int q) {
+    if (cudaFuncSetAttribute(k_site_loopq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_site_loopq, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(q);
+    cfg.blockDim = dim3(kSiteThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = q;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclus = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclus, k_site_loopq, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return nclus >= 1;
+}
+
 static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W,
                      int32_t R, int32_t n_obs, double coverage_target, int64_t *chosen,
                      int64_t *gains, uint32_t *cum, int32_t *n_chosen, void *ws,
@@ -735,11 +1079,11 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
     }
     if (n > 0 && (rc = vs_site_gains(bm, cand, n, H, W, R, cum, g0, st))) return rc;
 
-    // one CTA when every gain fits in its shared memory (unless the tuning
-    // table asks for a cluster of at most qmax CTAs)
-    const int qmax = job_out ? 0 : tune_get(VS_TUNE_SITE_CLUSTER, R, 0);
+    // one CTA, or a leader cluster, when every gain fits in one CTA's shared
+    // memory; the tuning table picks the cluster size (0 = 8 CTAs, 1 = one CTA)
+    const int qtune = job_out ? 1 : tune_get(VS_TUNE_SITE_CLUSTER, R, 0);
     const size_t smem1 = site1_smem_bytes(n, P.words);
-    if (n > 0 && site1_fits(n, P.words) && qmax == 0) {
+    if (n > 0 && site1_fits(n, P.words)) {
         k_site_rank<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cand, n, (int64_t)H * W, sp, sorig);
         VS_CUDA_TRY(cudaGetLastError());
         k_site_bands<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sp, n, W, R, slo, shi);
@@ -755,6 +1099,27 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
             *smem_out = smem1;
             return VS_OK;
         }
+        // leader cluster: bitmap rows must be whole 16-byte vectors
+        const int qc = (qtune == 0) ? 8 : qtune;
+        if (qc >= 2 && Q1.vec_rows && (uintptr_t)cum % 16 == 0) {
+            const size_t smemq = siteq_smem_bytes(n, R, P.PR, qc);
+            if (siteq_fits(smemq) && siteq_launchable(smemq, qc)) {
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(qc);
+                cfg.blockDim = dim3(kSiteThreads);
+                cfg.dynamicSmemBytes = smemq;
+                cfg.stream = s;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = qc;
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                VS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_site_loopq, Q1));
+                return VS_OK;
+            }
+        }
         VS_CUDA_TRY(cudaFuncSetAttribute(k_site_loop1, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem1));
         k_site_loop1<<<1, kSiteThreads, smem1, s>>>(Q1);
@@ -768,7 +1133,6 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
     size_t smem = 0;
     VS_CUDA_TRY(cudaFuncSetAttribute(k_site_loop, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     for (int q : {16, 8, 4, 2, 1}) {
-        if (qmax != 0 && q > qmax) continue;
         const int sl = (int)std::max<int64_t>(1, (n + q - 1) / q);
         const size_t b = site_smem_bytes(sl, P.words);
         if (b > (size_t)kSmemLimit - 2048) continue;

@@ -166,21 +166,47 @@ def test_site_parity_many_candidates(V, O):
     assert (_np(gC).view(np.uint32) == C).all()
 
 
-@pytest.mark.parametrize("q", [2, 16])
-def test_site_cluster_path_by_tuning(V, O, q):
-    """The cluster loop chosen through the tuning table for a candidate set
-    one CTA would hold: the same result as the oracle."""
-    H, W, R = 257, 301, 50
-    cand, bm = _site_case(O, 3, H, W, R, 500)
-    ch, gn, C = O.site(bm, cand, H, W, R, 200)
+@pytest.fixture(scope="module")
+def r100_case(O):
+    """R = 100 (bitmap rows of 8 words: the leader-cluster loop's vector
+    refresh), 2600 candidates on a 600 x 620 grid, so that a winner's band
+    (slots within 2R rows) spans more than 1024 slots and a step takes several
+    rounds."""
+    H, W, R = 600, 620, 100
+    cand, bm = _site_case(O, 41, H, W, R, 2600, zr=900)
+    return H, W, R, cand, bm
+
+
+@pytest.mark.parametrize("q", [0, 1, 2, 4, 16])
+def test_site_leader_cluster_by_tuning(V, O, r100_case, q):
+    """Every cluster size of the leader-cluster loop (0 = default, 1 = one
+    CTA) gives the oracle's observers, gains and cumulative viewshed."""
+    H, W, R, cand, bm = r100_case
+    ch, gn, C = O.site(bm, cand, H, W, R, 300)
     V.tune_set(V.VS_TUNE_SITE_CLUSTER, R, q)
     try:
         gch, ggn, gC, t = V.site(torch.as_tensor(bm.view(np.int32)).cuda(), torch.as_tensor(cand).cuda(),
-                                 H, W, R, 200)
+                                 H, W, R, 300)
     finally:
         V.tune_set(V.VS_TUNE_SITE_CLUSTER, R, 0)
+    assert t == len(ch)
     assert _np(gch).tolist() == ch.tolist() and _np(ggn).tolist() == gn.tolist()
     assert (_np(gC).view(np.uint32) == C).all()
+
+
+def test_site_leader_cluster_target_and_resume(V, O, r100_case):
+    H, W, R, cand, bm = r100_case
+    tb = torch.as_tensor(bm.view(np.int32)).cuda()
+    tc = torch.as_tensor(cand).cuda()
+    for target in (0.4, 0.9):
+        ch, gn, C = O.site(bm, cand, H, W, R, 2600, target=target)
+        gch, ggn, gC, t = V.site(tb, tc, H, W, R, 2600, target=target)
+        assert _np(gch).tolist() == ch.tolist() and (_np(gC).view(np.uint32) == C).all()
+    full = O.site(bm, cand, H, W, R, 90)
+    a = V.site(tb, tc, H, W, R, 40)
+    b = V.site(tb, tc, H, W, R, 50, cum=a[2].clone())
+    assert _np(a[0]).tolist() + _np(b[0]).tolist() == full[0].tolist()
+    assert (_np(b[2]).view(np.uint32) == full[2]).all()
 
 
 def test_site_duplicate_and_invalid_candidates(V, O):
