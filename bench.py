@@ -63,7 +63,7 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -76,7 +76,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -539,7 +539,7 @@ def run_batch(args, dist, rank, world, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="full", choices=["full", "mid", "scale", "small", "batch", "learn"])
@@ -700,8 +700,8 @@ def main():
                                  V.words_per_row(w.R))
     roof["site_loop"] = {"bound": "hbm", "achieved": loop_bytes / (st[3] * 1e-3) / 1e9,
                          "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None,
-                         "note": "sequential greedy on one CTA: bound by the latency of its "
-                                 "dependent memory rounds, not by bandwidth"}
+                         "note": "sequential greedy (one CTA or a leader cluster): bound by the "
+                                 "latency of its dependent memory rounds and barriers, not by bandwidth"}
     if sur:
         from oracle import cnn_oracle as C
         flops = sur.score.numel() * C.flops_per_patch()
