@@ -275,40 +275,77 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_loop(const SiteParams 
 
 // slot of every candidate: rank by (post index, candidate index); invalid
 // posts sort last
-__global__ void k_site_rank(const int64_t *__restrict__ cand, int64_t n, int64_t HW,
-                            uint32_t *__restrict__ sp, uint32_t *__restrict__ sorig) {
-    __shared__ uint32_t tp[1024];
+// ---- slot order: candidates sorted by (post, candidate index); an invalid
+// post sorts as 0xFFFFFFFF.  Keys (post << 32 | candidate) are sorted in
+// chunks of 1024 in shared memory (bitonic network); a key's rank is its
+// position in its chunk plus, for every other chunk, the number of smaller
+// keys there (binary search); candidates are then scattered to their ranks.
+constexpr int kRankChunk = 1024;
+
+__device__ __forceinline__ uint64_t slot_key(const int64_t *cand, int64_t c, int64_t HW) {
+    const int64_t p = cand[c];
+    const uint32_t pc = (p >= 0 && p < HW) ? (uint32_t)p : 0xFFFFFFFFu;
+    return ((uint64_t)pc << 32) | (uint64_t)(uint32_t)c;
+}
+
+// sorted chunks into keys[]; rank[c] = position of candidate c in its chunk
+__global__ void __launch_bounds__(kRankChunk) k_rank_chunks(const int64_t *__restrict__ cand, int64_t n, int64_t HW,
+                                                           uint64_t *__restrict__ keys, uint32_t *__restrict__ rank) {
+    __shared__ uint64_t sk[kRankChunk];
+    const int t = threadIdx.x;
+    const int64_t c = (int64_t)blockIdx.x * kRankChunk + t;
+    sk[t] = (c < n) ? slot_key(cand, c, HW) : ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= kRankChunk; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const int j = t ^ stride;
+            if (j > t) {
+                const uint64_t a = sk[t], b = sk[j];
+                const bool up = (t & size) == 0;
+                if ((a > b) == up) {
+                    sk[t] = b;
+                    sk[j] = a;
+                }
+            }
+            __syncthreads();
+        }
+    if (c < n) {
+        const uint64_t k = sk[t];  // padding (~0) sorts after every real key
+        keys[(int64_t)blockIdx.x * kRankChunk + t] = k;
+        rank[(uint32_t)k] = (uint32_t)t;
+    }
+}
+
+// rank[c] += number of keys of chunk blockIdx.y below candidate c's key, for
+// the keys of chunk blockIdx.x
+__global__ void __launch_bounds__(kRankChunk) k_rank_cross(const uint64_t *__restrict__ keys, int64_t n,
+                                                          uint32_t *__restrict__ rank) {
+    if (blockIdx.x == blockIdx.y) return;
+    __shared__ uint64_t sk[kRankChunk];
+    const int t = threadIdx.x;
+    const int64_t b0 = (int64_t)blockIdx.y * kRankChunk, a0 = (int64_t)blockIdx.x * kRankChunk;
+    const int mb = (int)min((int64_t)kRankChunk, n - b0);
+    if (t < mb) sk[t] = keys[b0 + t];
+    __syncthreads();
+    if (a0 + t >= n) return;
+    const uint64_t k = keys[a0 + t];
+    int lo = 0, hi = mb;  // first key of chunk y not below k
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (sk[m] < k) lo = m + 1; else hi = m;
+    }
+    if (lo) atomicAdd(&rank[(uint32_t)k], (uint32_t)lo);
+}
+
+__global__ void k_rank_scatter(const uint32_t *__restrict__ rank, int64_t n, uint32_t *__restrict__ sorig) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t pc = 0xFFFFFFFFu;
-    if (c < n) {
-        const int64_t p = cand[c];
-        pc = (p >= 0 && p < HW) ? (uint32_t)p : 0xFFFFFFFFu;
-    }
-    int64_t rank = 0;
-    for (int64_t j0 = 0; j0 < n; j0 += 1024) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
-            const int64_t j = j0 + i;
-            uint32_t v = 0xFFFFFFFFu;
-            if (j < n) {
-                const int64_t p = cand[j];
-                v = (p >= 0 && p < HW) ? (uint32_t)p : 0xFFFFFFFFu;
-            }
-            tp[i] = v;
-        }
-        __syncthreads();
-        if (c < n) {
-            const int m = (int)min((int64_t)1024, n - j0);
-            for (int i = 0; i < m; ++i) {
-                const uint32_t v = tp[i];
-                rank += (v < pc) || (v == pc && j0 + i < c);
-            }
-        }
-    }
-    if (c < n) {
-        sp[rank] = pc;
-        sorig[rank] = (uint32_t)c;
-    }
+    if (c < n) sorig[rank[c]] = (uint32_t)c;
+}
+
+__global__ void k_rank_posts(const int64_t *__restrict__ cand, const uint32_t *__restrict__ sorig, int64_t n,
+                             int64_t HW, uint32_t *__restrict__ sp) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) sp[i] = (uint32_t)(slot_key(cand, sorig[i], HW) >> 32);
 }
 
 // for every slot, the slot range holding the candidates within 2R rows
@@ -1084,8 +1121,20 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
     const int qtune = job_out ? 1 : tune_get(VS_TUNE_SITE_CLUSTER, R, 0);
     const size_t smem1 = site1_smem_bytes(n, P.words);
     if (n > 0 && site1_fits(n, P.words)) {
-        k_site_rank<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cand, n, (int64_t)H * W, sp, sorig);
-        VS_CUDA_TRY(cudaGetLastError());
+        {   // slot order (sp doubles as the rank array, slo..shi as the key buffer)
+            const unsigned nch = (unsigned)((n + kRankChunk - 1) / kRankChunk);
+            uint64_t *keys = (uint64_t *)slo;
+            k_rank_chunks<<<nch, kRankChunk, 0, s>>>(cand, n, (int64_t)H * W, keys, sp);
+            VS_CUDA_TRY(cudaGetLastError());
+            if (nch > 1) {
+                k_rank_cross<<<dim3(nch, nch), kRankChunk, 0, s>>>(keys, n, sp);
+                VS_CUDA_TRY(cudaGetLastError());
+            }
+            k_rank_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sp, n, sorig);
+            VS_CUDA_TRY(cudaGetLastError());
+            k_rank_posts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cand, sorig, n, (int64_t)H * W, sp);
+            VS_CUDA_TRY(cudaGetLastError());
+        }
         k_site_bands<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sp, n, W, R, slo, shi);
         VS_CUDA_TRY(cudaGetLastError());
         Site1Params Q1;
