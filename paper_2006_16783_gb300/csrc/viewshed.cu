@@ -6,7 +6,10 @@
 // then walk the 8R rays to the square ring max(|dx|,|dy|) = R, keeping each
 // ray's running horizon (the steepest interpolated crossing so far) as an
 // exact rational (numerator over step), and OR visible cells into a
-// shared-memory bitmap laid out exactly like the output.  When the window does
+// shared-memory bitmap (the output's layout with an odd row pitch, so that
+// rays on rows four apart do not share a bank).  A step reads two posts --
+// the two the line passes between, one of which is the cell tested -- at a
+// running window address.  When the window does
 // not fit in shared memory it is processed in halves (rays by the sign of the
 // ring cell's dy) or quadrants (signs of dx and dy); every ray stays inside
 // its half / quadrant, so each pass stages only that part.
@@ -60,6 +63,7 @@ template <typename T>
 __device__ void vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long c, unsigned char *smem,
                              uint64_t *bar, uint32_t &phase, int *s_fail, int *red) {
     const int R = J.R, PR = J.PR;
+    const int PRs = PR | 1;  // odd row pitch of the shared bitmap: rays on nearby rows hit other banks
     const int WW = J.WG * 8;
     int16_t *win = (int16_t *)smem;
     const int win_elems = J.nbox * J.box_rows * WW;
@@ -75,7 +79,7 @@ __device__ void vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long 
     const int cx = (int)(p % J.W), cy = (int)(p / J.W);
     const int gw0 = floordiv(cx - R, 32);
     if (tid == 0) *s_fail = 0;
-    for (int i = tid; i < J.words; i += blockDim.x) bms[i] = 0;
+    for (int i = tid; i < (2 * R + 1) * PRs; i += blockDim.x) bms[i] = 0;
     __syncthreads();
 
     const int nsec = J.nsplit;
@@ -124,29 +128,44 @@ __device__ void vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long 
             const int thr = dmin >= 0 ? R : R + 1;
             const int omaj = xmaj ? cx : cy, omin = xmaj ? cy : cx;
             const int minor_lim = xmaj ? J.H : J.W;
-            const int minor_step = xmaj ? WW : 1;
-            int f = 0, y0 = 0;
+            // a0: window address of the post (major omaj + smaj*k, minor omin + y0),
+            // the first of the two posts the line passes between at step k; the
+            // cell tested at step k is that post or the next one along the minor
+            // axis (amin further)
+            const int amin = xmaj ? WW : 1;
+            const int astep = (xmaj ? smaj : smaj * WW) + q * amin;
+            int a0 = xmaj ? (omin - wy0) * WW + (omaj - wx0) : (omaj - wy0) * WW + (omin - wx0);
+            const T eyeR = (T)eye * R;
+            const int hre = J.hr - eye;
+            int f = 0, y0 = 0, gmaj = omaj, k2 = 0;
             T Hn = 0;
             int Hk = 0;
             for (int k = 1; k <= R; ++k) {
                 f += rr;
                 y0 += q;
-                if (f >= R) { f -= R; y0 += 1; }
-                const int rnd = y0 + (2 * f >= thr ? 1 : 0);
-                const int gmaj = omaj + smaj * k;
+                a0 += astep;
+                if (f >= R) { f -= R; y0 += 1; a0 += amin; }
+                const int rb = (2 * f >= thr) ? 1 : 0;  // round half away from zero
+                const int rnd = y0 + rb;
+                gmaj += smaj;
+                k2 += 2 * k - 1;
                 const int gmin = omin + rnd;
                 const int gx = xmaj ? gmaj : gmin, gy = xmaj ? gmin : gmaj;
                 if ((unsigned)gx >= (unsigned)J.W || (unsigned)gy >= (unsigned)J.H) break;
-                if (k * k + rnd * rnd > R * R) break;
-                const int zc = win[(gy - wy0) * WW + (gx - wx0)];
-                const bool vis = (Hk == 0) || ((T)(zc + J.hr - eye) * R * Hk >= Hn * k);
-                if (vis) atomicOr(&bms[(gy - cy + R) * PR + ((gx >> 5) - gw0)], 1u << (gx & 31));
+                if (k2 + rnd * rnd > R * R) break;
+                const int zc = win[a0 + (rb ? amin : 0)];
+                const bool vis = (Hk == 0) || ((T)(zc + hre) * R * Hk >= Hn * k);
+                if (vis) atomicOr(&bms[(gy - cy + R) * PRs + ((gx >> 5) - gw0)], 1u << (gx & 31));
                 const int m0 = omin + y0;
                 if (f > 0 && (m0 < 0 || m0 + 1 >= minor_lim)) break;
-                const int a0 = xmaj ? (m0 - wy0) * WW + (gmaj - wx0) : (gmaj - wy0) * WW + (m0 - wx0);
-                const int z0 = win[a0];
-                const int z1 = win[a0 + (f > 0 ? minor_step : 0)];
-                const T num = (T)z0 * (R - f) + (T)z1 * f - (T)eye * R;
+                // the straddling posts: the tested cell and, off a post, the other one
+                int z0 = zc, z1 = zc;
+                if (f > 0) {
+                    const int zo = win[a0 + (rb ? 0 : amin)];
+                    z0 = rb ? zo : zc;
+                    z1 = rb ? zc : zo;
+                }
+                const T num = (T)z0 * (R - f) + (T)z1 * f - eyeR;
                 if (Hk == 0 || num * Hk > Hn * k) { Hn = num; Hk = k; }
             }
         }
@@ -154,11 +173,12 @@ __device__ void vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long 
     }
 
     const bool fail = *s_fail != 0;
-    if (tid == 0 && !fail) atomicOr(&bms[R * PR + ((cx >> 5) - gw0)], 1u << (cx & 31));
+    if (tid == 0 && !fail) atomicOr(&bms[R * PRs + ((cx >> 5) - gw0)], 1u << (cx & 31));
     __syncthreads();
     int cnt = 0;
     for (int i = tid; i < J.words; i += blockDim.x) {
-        const uint32_t w = fail ? 0u : bms[i];
+        const int r = i / PR;
+        const uint32_t w = fail ? 0u : bms[r * PRs + (i - r * PR)];
         out[i] = w;
         cnt += __popc(w);
     }
@@ -239,7 +259,7 @@ static size_t vs_smem_bytes(int R, int nsplit, int *WG, int *box_rows, int *nbox
     *WG = wg; *box_rows = br; *nbox = nb;
     size_t win = (size_t)nb * br * wg * 8 * 2;
     win = (win + 127) & ~(size_t)127;
-    size_t words = (size_t)(2 * R + 1) * words_per_row(R);
+    size_t words = (size_t)(2 * R + 1) * (words_per_row(R) | 1);  // odd row pitch in shared memory
     return win + ((words + 31) & ~(size_t)31) * 4 + 64 + 128;
 }
 
