@@ -75,15 +75,30 @@ int vs_version(void);
  *     per candidate ("ray bundle"), 128 / 256 / 512 (0 = default: 512, or
  *     fewer when the ring has fewer than 512 rays)
  *   VS_TUNE_VIX_TILE: vix post tile, 1 = 64x32, 2 = 32x32 (0 = default: the
- *     largest tile whose window fits)
+ *     largest tile whose window fits), 3 = the warp-per-line kernel that reads
+ *     the terrain in global memory (the path every R takes whose halo window
+ *     does not fit in shared memory, R above ~280)
  *   VS_TUNE_SITE_CLUSTER: the greedy site loop of vs_site when every gain
  *     fits in one CTA's shared memory: 0 = default (a leader cluster of 8
  *     CTAs when bitmap rows are whole 16-byte vectors, i.e. (2R/32 + 2) % 4 == 0,
  *     else one CTA), 1 = one CTA, 2 / 4 / 8 / 16 = a leader cluster of that
  *     many CTAs (the leader keeps the gains and picks each winner, the window
  *     and refresh loads are split over the cluster's SMs).  R is the call's R.
- *     vs_site_batch always uses one CTA per job. */
-enum { VS_TUNE_VIEWSHED_THREADS = 0, VS_TUNE_VIX_TILE = 1, VS_TUNE_SITE_CLUSTER = 2 };
+ *     vs_site_batch always uses one CTA per job.
+ *   VS_TUNE_VIEWSHED_WIDE: 1 = vs_viewshed walks the rays in bands of steps
+ *     against the terrain in global memory (the path every R takes whose
+ *     window does not fit in shared memory, R above ~280) even when the
+ *     window would fit; 0 = default.
+ *   VS_TUNE_SITE_LAZY: 1 = vs_site runs the lazy greedy (the path of calls
+ *     whose gains or windows do not fit in one cluster's shared memory) even
+ *     when another loop would fit; 0 = default. */
+enum {
+    VS_TUNE_VIEWSHED_THREADS = 0,
+    VS_TUNE_VIX_TILE = 1,
+    VS_TUNE_SITE_CLUSTER = 2,
+    VS_TUNE_VIEWSHED_WIDE = 3,
+    VS_TUNE_SITE_LAZY = 4
+};
 int vs_tune_set(int32_t op, int32_t R, int32_t value);
 int vs_tune_get(int32_t op, int32_t R);
 
@@ -108,6 +123,22 @@ int vs_tune_get(int32_t op, int32_t R);
  * ---------------------------------------------------------------------- */
 int vs_vix(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
            uint8_t *vix_out, vs_stream_t st);
+
+/* Large ROIs.  A tile's halo window fits in shared memory up to R ~ 280;
+ * beyond that (the paper's runs use R = 500..2000, Sec. "Experiments") a warp
+ * walks one line of sight at a time, 32 consecutive crossings per
+ * instruction, against the terrain in global memory.  Its y-major lines read
+ * a transposed copy of the terrain when the caller provides room for one:
+ * vs_vix_workspace(H, W, R, S) bytes (0 when the staged kernels cover R,
+ * else W x ceil8(H) int16 plus 256 bytes).  vs_vix_ws is vs_vix (los_steps
+ * NULL) or vs_vix_count (los_steps set) with that workspace; ws may be NULL
+ * or smaller, then y-major lines read the terrain with a row stride (same
+ * results, slower).  vs_vix and vs_vix_count are vs_vix_ws without a
+ * workspace.  Large R needs (2R + 64) * max(pitch, ceil8(H)) < 2^31 (else
+ * VS_ERR_RANGE). */
+size_t vs_vix_workspace(int32_t H, int32_t W, int32_t R, int32_t S);
+int vs_vix_ws(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
+              uint8_t *vix_out, uint64_t *los_steps, void *ws, size_t ws_bytes, vs_stream_t st);
 
 /* vs_vix plus work accounting: *los_steps (device uint64, accumulated, not
  * cleared) grows by the number of LOS crossings evaluated -- j = 1..D-1 for a
@@ -164,11 +195,21 @@ int vs_findmax_f32(const float *score, int32_t H, int32_t W, int32_t stride, int
  * outside the grid or the disc are 0.  area_out[c] = popcount of the bitmap;
  * a candidate index outside [0, H*W) yields an all-zero bitmap and area -1.
  *
- * ws / ws_bytes: workspace of at least vs_viewshed_workspace(R, n) bytes
- * (may be NULL when that is 0).
+ * Windows that fit in shared memory (R up to ~280 posts) are staged there by
+ * TMA.  Larger ROIs -- the paper's own runs use R = 500..2000 (Sec.
+ * "Experiments", Tables of the DEM1000 and US-West runs) -- walk the rays in
+ * bands of steps against the terrain in global memory; the x-major rays read
+ * a transposed copy of the terrain that the call writes into the workspace
+ * first.  Both paths give identical bitmaps.
+ *
+ * ws / ws_bytes: workspace of at least vs_viewshed_workspace(H, W, R, n)
+ * bytes: 0 when the window fits in shared memory (ws may then be NULL), else
+ * W x ceil8(H) int16 for the transposed terrain plus 256 bytes of alignment
+ * (4.3 GB at 46400^2).  Too small: VS_ERR_WS.  With a large R the row pitch
+ * must satisfy R * (max(pitch, ceil8(H)) + 1) < 2^31 (else VS_ERR_RANGE).
  * ---------------------------------------------------------------------- */
 int64_t vs_bitmap_words(int32_t R); /* (2R+1) * (floor(2R/32)+2) */
-size_t vs_viewshed_workspace(int32_t R, int64_t n);
+size_t vs_viewshed_workspace(int32_t H, int32_t W, int32_t R, int64_t n);
 int vs_viewshed(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand, int64_t n,
                 uint32_t *bm_out, int32_t *area_out, void *ws, size_t ws_bytes, vs_stream_t st);
 

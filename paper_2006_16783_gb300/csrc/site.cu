@@ -982,6 +982,285 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_loop1_batch(const __gr
     site1_body(B.job[blockIdx.x]);
 }
 
+// ------------------------------------------------------------------ lazy greedy
+// For calls whose gains or windows do not fit in one cluster's shared memory
+// (the paper's own regime: R = 1000, ~386,000 candidates, 512 KB bitmaps),
+// one CTA runs the paper's lazy evaluation (Sec. "The multiple transmitter
+// siting process", Site: a candidate cannot gain more later than it gains
+// now).  Gains live in global memory as upper bounds with a flag saying that
+// the bound is exact for the current C.  A table of per-block maxima of the
+// keys (bound, lowest post, lowest index) sits in shared memory.  Each round
+// takes the table's best candidate: when its bound is exact it is the true
+// argmax -- every other bound is at least its candidate's gain -- and is
+// accepted; otherwise its gain is evaluated over its window and the round
+// repeats.  Accepting ORs the winner's window into C and clears the flag of
+// every candidate whose window can meet the winner's (Chebyshev distance of
+// the posts <= 2R), found through a grid of cells of side >= 2R that buckets
+// the candidates, so a bound stays exact as long as nothing near it changes.
+struct LazyParams {
+    const uint32_t *bm;
+    const int64_t *cand;
+    int n, H, W, R, PR, words, WWc;
+    int n_obs;
+    long long need;
+    int64_t *chosen, *gains;
+    uint32_t *cum;
+    int32_t *n_chosen;
+    uint32_t *g;             // [n] gain bounds (initialised with the exact gains)
+    uint8_t *fresh;          // [n] 1 = bound exact for the current C
+    int bs, nb;              // candidates per block of the maxima table, blocks
+    const uint32_t *cstart;  // [ncell + 1] first item of each cell
+    const uint32_t *citems;  // candidate indices grouped by cell
+    int cs, ncx, ncy;        // cell side (>= 2R), cells per row / column
+    const unsigned long long *covered0;
+};
+
+__global__ void k_lazy_count(const int64_t *__restrict__ cand, int n, int H, int W, int cs, int ncx,
+                             uint32_t *__restrict__ counts) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int64_t p = cand[c];
+    if (p < 0 || p >= (int64_t)H * W) return;
+    const int x = (int)(p % W), y = (int)(p / W);
+    atomicAdd(&counts[(y / cs) * ncx + x / cs], 1u);
+}
+
+// exclusive scan of the cell counts (one CTA), copied to the scatter cursors
+// (counts and cursor may be the same array: each entry is read and written by one thread)
+__global__ void __launch_bounds__(1024) k_lazy_scan(const uint32_t *counts, int ncell, uint32_t *cstart,
+                                                    uint32_t *cursor) {
+    __shared__ uint32_t s_w[32];
+    __shared__ uint32_t s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < ncell; base += 1024) {
+        const int i = base + tid;
+        const uint32_t v = i < ncell ? counts[i] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        if (lane == 31) s_w[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t y = s_w[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += u;
+            }
+            s_w[lane] = y;
+        }
+        __syncthreads();
+        const uint32_t excl = s_carry + (wid ? s_w[wid - 1] : 0u) + x - v;
+        if (i < ncell) { cstart[i] = excl; cursor[i] = excl; }
+        __syncthreads();
+        if (tid == 1023) s_carry = excl + v;
+        __syncthreads();
+    }
+    if (tid == 0) cstart[ncell] = s_carry;
+}
+
+__global__ void k_lazy_scatter(const int64_t *__restrict__ cand, int n, int H, int W, int cs, int ncx,
+                               uint32_t *__restrict__ cursor, uint32_t *__restrict__ citems) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int64_t p = cand[c];
+    if (p < 0 || p >= (int64_t)H * W) return;
+    const int x = (int)(p % W), y = (int)(p / W);
+    citems[atomicAdd(&cursor[(y / cs) * ncx + x / cs], 1u)] = (uint32_t)c;
+}
+
+__device__ __forceinline__ uint64_t lazy_key(uint32_t g, int64_t p) {
+    return ((uint64_t)g << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)p);
+}
+
+// block-wide argmax of (key, index): larger key, then lower index
+__device__ __forceinline__ void lazy_block_best(uint64_t &k, int &c, uint64_t *s_k, int *s_c) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t k2 = __shfl_xor_sync(0xffffffffu, k, o);
+        const int c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        if (ki_better(k2, c2, k, c)) { k = k2; c = c2; }
+    }
+    if (lane == 0) { s_k[wid] = k; s_c[wid] = c; }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        k = lane < nw ? s_k[lane] : 0ull;
+        c = lane < nw ? s_c[lane] : 0x7fffffff;
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t k2 = __shfl_xor_sync(0xffffffffu, k, o);
+            const int c2 = __shfl_xor_sync(0xffffffffu, c, o);
+            if (ki_better(k2, c2, k, c)) { k = k2; c = c2; }
+        }
+        if (lane == 0) { s_k[32] = k; s_c[32] = c; }
+    }
+    __syncthreads();
+    k = s_k[32];
+    c = s_c[32];
+    __syncthreads();  // s_k / s_c reused by the next call
+}
+
+// this thread's share of popcount(V_c AND NOT C) over c's window clipped to
+// the grid; with commit, C |= V_c.  The clipped window is walked as one flat
+// range of (row, word) pairs, eight pairs per thread in flight.
+__device__ __forceinline__ unsigned lazy_window(const LazyParams &P, int c, int64_t p, bool commit) {
+    constexpr int U = 8;
+    const int R = P.R, PR = P.PR, WWc = P.WWc;
+    const int cx = (int)(p % P.W), cy = (int)(p / P.W);
+    const int gw0 = floordiv(cx - R, 32);
+    const int r_lo = max(0, R - cy), r_hi = min(2 * R, P.H - 1 - cy + R);
+    const int w_lo = max(0, -gw0), w_hi = min(PR - 1, WWc - 1 - gw0);
+    const int nr = r_hi - r_lo + 1, nw = w_hi - w_lo + 1;
+    const int total = nr * nw;
+    const uint32_t *V = P.bm + (long long)c * P.words + (long long)r_lo * PR + w_lo;
+    uint32_t *C = P.cum + (long long)(cy - R + r_lo) * WWc + (gw0 + w_lo);
+    const int nt = blockDim.x;
+    const int dr = nt / nw, dw = nt - dr * nw;
+    int r = threadIdx.x / nw, w = threadIdx.x - r * nw;
+    unsigned sum = 0;
+    for (int i = threadIdx.x; i < total; i += U * nt) {
+        uint32_t v[U], cw[U];
+        int off[U];
+        int rr = r, ww = w;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            off[u] = -1;
+            if (i + u * nt < total) {
+                off[u] = rr * WWc + ww;
+                v[u] = __ldg(V + rr * PR + ww);
+                cw[u] = C[off[u]];
+            }
+            ww += dw;
+            rr += dr;
+            if (ww >= nw) { ww -= nw; rr += 1; }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (off[u] < 0) continue;
+            const uint32_t d = v[u] & ~cw[u];
+            sum += __popc(d);
+            if (commit && d) C[off[u]] = cw[u] | v[u];
+        }
+        r = rr;
+        w = ww;
+    }
+    return sum;
+}
+
+__device__ __forceinline__ unsigned lazy_block_sum(unsigned s, unsigned *s_u) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) s_u[wid] = s;
+    __syncthreads();
+    unsigned t = 0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += s_u[j];
+    __syncthreads();
+    return t;
+}
+
+// recompute the table entry of block b from the gains in global memory
+__device__ __forceinline__ void lazy_refresh_block(const LazyParams &P, int b, uint64_t *bkey, int *bidx,
+                                                   uint64_t *s_k, int *s_c) {
+    uint64_t k = 0;
+    int c = 0x7fffffff;
+    const int e = min(P.n, (b + 1) * P.bs);
+    for (int i = b * P.bs + threadIdx.x; i < e; i += blockDim.x) {
+        const uint64_t ki = lazy_key(P.g[i], P.cand[i]);
+        if (ki_better(ki, i, k, c)) { k = ki; c = i; }
+    }
+    lazy_block_best(k, c, s_k, s_c);
+    if (threadIdx.x == 0) { bkey[b] = k; bidx[b] = c; }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSiteThreads, 1) k_site_lazy(const LazyParams P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *bkey = (uint64_t *)smem;
+    int *bidx = (int *)(bkey + P.nb);
+    __shared__ uint64_t s_k[33];
+    __shared__ int s_c[33];
+    __shared__ unsigned s_u[32];
+    __shared__ long long s_p;
+    __shared__ int s_fresh;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+    // the table: warp per block
+    for (int b = wid; b < P.nb; b += (int)(blockDim.x >> 5)) {
+        uint64_t k = 0;
+        int c = 0x7fffffff;
+        const int e = min(P.n, (b + 1) * P.bs);
+        for (int i = b * P.bs + lane; i < e; i += 32) {
+            const uint64_t ki = lazy_key(P.g[i], P.cand[i]);
+            if (ki_better(ki, i, k, c)) { k = ki; c = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t k2 = __shfl_xor_sync(0xffffffffu, k, o);
+            const int c2 = __shfl_xor_sync(0xffffffffu, c, o);
+            if (ki_better(k2, c2, k, c)) { k = k2; c = c2; }
+        }
+        if (lane == 0) { bkey[b] = k; bidx[b] = c; }
+    }
+    __syncthreads();
+
+    long long covered = P.need >= 0 ? (long long)*P.covered0 : 0;
+    int t = 0;
+    // between two acceptances each candidate is evaluated at most once, so the
+    // rounds are bounded; the guard only stops a loop that broke that rule
+    const long long max_rounds = (long long)P.n * ((long long)P.n_obs + 1) + 2ll * P.n_obs + 16;
+    long long rounds = 0;
+    while (t < P.n_obs && ++rounds <= max_rounds) {
+        if (P.need >= 0 && covered >= P.need) break;
+        uint64_t k = 0;
+        int c = 0x7fffffff;
+        for (int b = tid; b < P.nb; b += blockDim.x)
+            if (ki_better(bkey[b], bidx[b], k, c)) { k = bkey[b]; c = bidx[b]; }
+        lazy_block_best(k, c, s_k, s_c);
+        if ((k >> 32) == 0) break;  // best gain 0: nothing left to cover
+        if (tid == 0) { s_p = P.cand[c]; s_fresh = P.fresh[c]; }
+        __syncthreads();
+        const int64_t p = s_p;
+        const int fresh = s_fresh;
+        if (!fresh) {  // a stale bound: evaluate the gain and search again
+            const unsigned gnew = lazy_block_sum(lazy_window(P, c, p, false), s_u);
+            if (tid == 0) { P.g[c] = gnew; P.fresh[c] = 1; }
+            __syncthreads();
+            lazy_refresh_block(P, c / P.bs, bkey, bidx, s_k, s_c);
+            continue;
+        }
+        const uint32_t gw = (uint32_t)(k >> 32);
+        if (tid == 0) {
+            P.chosen[t] = p;
+            P.gains[t] = gw;
+            P.g[c] = 0;  // all of its viewshed is covered now
+        }
+        lazy_window(P, c, p, true);
+        covered += gw;
+        __syncthreads();
+        lazy_refresh_block(P, c / P.bs, bkey, bidx, s_k, s_c);
+        // bounds that may have changed: candidates within Chebyshev distance 2R
+        const int cx = (int)(p % P.W), cy = (int)(p / P.W), R2 = 2 * P.R;
+        const int x0 = max(0, cx - R2) / P.cs, x1 = min(P.W - 1, cx + R2) / P.cs;
+        const int y0 = max(0, cy - R2) / P.cs, y1 = min(P.H - 1, cy + R2) / P.cs;
+        for (int yc = y0; yc <= y1; ++yc)
+            for (int xc = x0; xc <= x1; ++xc) {
+                const int cell = yc * P.ncx + xc;
+                const uint32_t e = P.cstart[cell + 1];
+                for (uint32_t j = P.cstart[cell] + tid; j < e; j += blockDim.x) {
+                    const int c2 = (int)P.citems[j];
+                    const int64_t p2 = P.cand[c2];
+                    const int x2 = (int)(p2 % P.W), y2 = (int)(p2 / P.W);
+                    if (c2 != c && abs(x2 - cx) <= R2 && abs(y2 - cy) <= R2) P.fresh[c2] = 0;
+                }
+            }
+        __syncthreads();
+        ++t;
+    }
+    if (tid == 0) *P.n_chosen = t;
+}
+
 static size_t site_smem_bytes(int slots, int words) {
     return (size_t)slots * 16 + (size_t)words * 4 + 16;
 }
@@ -1014,10 +1293,59 @@ using namespace vs;
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// cells of the lazy greedy's bucket grid: at most max(64, min(n, 65536))
+static int64_t lazy_cell_cap(int64_t n) { return std::max<int64_t>(64, std::min<int64_t>(n, 65536)); }
+
 extern "C" size_t vs_site_workspace(int64_t n, int32_t R) {
     (void)R;
     if (n < 0) return 0;
-    return 5 * align256((size_t)n * 4) + 256;  // gains, sorted posts, order, band bounds
+    // gains, sorted posts, order, band bounds (the lazy greedy: bounds, flags,
+    // items by cell), plus the lazy greedy's cell starts and cursors
+    return 5 * align256((size_t)n * 4) + 2 * align256((size_t)(lazy_cell_cap(n) + 1) * 4) + 256;
+}
+
+// lazy greedy: bucket the candidates and launch the loop
+static int site_lazy(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W, int32_t R,
+                     int32_t n_obs, long long need, int64_t *chosen, int64_t *gains, uint32_t *cum,
+                     int32_t *n_chosen, uint32_t *g0, void *ws, const unsigned long long *cov, cudaStream_t s) {
+    if (n >= (1ll << 31) - 1) return VS_ERR_RANGE;
+    const size_t a4 = align256((size_t)n * 4);
+    uint8_t *fresh = (uint8_t *)((char *)ws + a4);
+    uint32_t *citems = (uint32_t *)((char *)ws + 2 * a4);
+    const int64_t cap = lazy_cell_cap(n);
+    // after the coverage counter (ws + 5 * a4, 8 of 256 bytes)
+    uint32_t *cstart = (uint32_t *)((char *)ws + 5 * a4 + 256);
+    uint32_t *cursor = (uint32_t *)((char *)cstart + align256((size_t)(cap + 1) * 4));
+    // cell side: 2R, doubled until the grid has at most cap cells
+    long long cs = 2ll * R;
+    while (((H + cs - 1) / cs) * ((W + cs - 1) / cs) > cap) cs *= 2;
+    const int ncx = (int)((W + cs - 1) / cs), ncy = (int)((H + cs - 1) / cs);
+    const int ncell = ncx * ncy;
+    // table blocks: at most 16384 entries (12 bytes each) in shared memory
+    int bs = 256;
+    while ((n + bs - 1) / bs > 16384) bs *= 2;
+    const int nb = (int)((n + bs - 1) / bs);
+    VS_CUDA_TRY(cudaMemsetAsync(fresh, 1, (size_t)n, s));
+    VS_CUDA_TRY(cudaMemsetAsync(cursor, 0, (size_t)ncell * 4, s));
+    const unsigned gb = (unsigned)((n + 255) / 256);
+    k_lazy_count<<<gb, 256, 0, s>>>(cand, (int)n, H, W, (int)cs, ncx, cursor);
+    VS_CUDA_TRY(cudaGetLastError());
+    // counts -> starts, and the cursors (in place) for the scatter
+    k_lazy_scan<<<1, 1024, 0, s>>>(cursor, ncell, cstart, cursor);
+    VS_CUDA_TRY(cudaGetLastError());
+    k_lazy_scatter<<<gb, 256, 0, s>>>(cand, (int)n, H, W, (int)cs, ncx, cursor, citems);
+    VS_CUDA_TRY(cudaGetLastError());
+    LazyParams L;
+    L.bm = bm; L.cand = cand; L.n = (int)n; L.H = H; L.W = W; L.R = R;
+    L.PR = words_per_row(R); L.words = (2 * R + 1) * L.PR; L.WWc = (W + 31) / 32;
+    L.n_obs = n_obs; L.need = need; L.chosen = chosen; L.gains = gains; L.cum = cum; L.n_chosen = n_chosen;
+    L.g = g0; L.fresh = fresh; L.bs = bs; L.nb = nb; L.cstart = cstart; L.citems = citems;
+    L.cs = (int)cs; L.ncx = ncx; L.ncy = ncy; L.covered0 = cov;
+    const size_t smem = (size_t)nb * 12 + 16;
+    VS_CUDA_TRY(cudaFuncSetAttribute(k_site_lazy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_site_lazy<<<1, kSiteThreads, smem, s>>>(L);
+    VS_CUDA_TRY(cudaGetLastError());
+    return VS_OK;
 }
 
 extern "C" int vs_site_gains(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H,
@@ -1115,6 +1443,8 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
         VS_CUDA_TRY(cudaGetLastError());
     }
     if (n > 0 && (rc = vs_site_gains(bm, cand, n, H, W, R, cum, g0, st))) return rc;
+    if (!job_out && n > 0 && tune_get(VS_TUNE_SITE_LAZY, R, 0) == 1)
+        return site_lazy(bm, cand, n, H, W, R, n_obs, P.need, chosen, gains, cum, n_chosen, g0, ws, cov, s);
 
     // one CTA, or a leader cluster, when every gain fits in one CTA's shared
     // memory; the tuning table picks the cluster size (0 = 8 CTAs, 1 = one CTA)
@@ -1189,7 +1519,8 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
         const int qq = pick_cluster(b);
         if (qq >= q) { Q = q; slots = sl; smem = b; break; }
     }
-    if (Q == 0) return VS_ERR_RANGE;
+    if (Q == 0)  // neither the gains nor the windows fit: the lazy greedy
+        return site_lazy(bm, cand, n, H, W, R, n_obs, P.need, chosen, gains, cum, n_chosen, g0, ws, cov, s);
     P.slots = slots;
 
     cudaLaunchConfig_t cfg = {};

@@ -12,7 +12,9 @@
 // running window address.  When the window does
 // not fit in shared memory it is processed in halves (rays by the sign of the
 // ring cell's dy) or quadrants (signs of dx and dy); every ray stays inside
-// its half / quadrant, so each pass stages only that part.
+// its half / quadrant, so each pass stages only that part.  When not even a
+// quadrant fits (R above ~280), k_viewshed_wide walks the rays in bands of
+// steps against the terrain in global memory (see there).
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -248,6 +250,204 @@ __global__ void __launch_bounds__(512) k_viewshed_batch(const __grid_constant__ 
     }
 }
 
+// ------------------------------------------------------------------ wide ROI
+// When the ROI window does not fit in shared memory (R above ~280 posts; the
+// paper's own runs use R = 500 .. 2000) one CTA per candidate walks the rays
+// of each side of the ring side by side, one ray per thread, in bands of
+// steps.  The terrain is read through the L1/L2 caches instead of a staged
+// window.  Rays of the east and west sides (x-major) read a transposed copy of
+// the terrain, so that neighbouring rays -- neighbouring threads -- read
+// neighbouring addresses, as the north and south sides (y-major) do in the
+// terrain itself.  Each band's visible cells collect in a shared-memory tile
+// (east / west: every window row x 4 words = 128 columns; north / south: 128
+// window rows x every word) that is then ORed into the candidate's bitmap in
+// global memory.  The arithmetic is that of vs_candidate: the same cells, the
+// same rounding and the same horizon test, so the bitmaps are identical.
+// Values stay in 32 bits with 64-bit products, exact for every accepted input:
+// |z*R + (hr - eye)*R| <= (65535 + 2*100000)*4096 < 2^31 and the interpolated
+// numerator |z0*(R-f) + z1*f - eye*R| < 2^31 for R <= 4096.
+constexpr int kWideThreads = 1024;
+constexpr int kWideTW = 4;    // east / west tile: words per window row
+constexpr int kWideTP = 5;    // its row pitch, odd: neighbouring rows in other banks
+constexpr int kWideBN = 128;  // north / south tile: window rows per band
+
+struct VsWide {
+    const int16_t *z;
+    long long pitch;
+    const int16_t *zt;  // zt[x * pitcht + y] = z[y * pitch + x]
+    long long pitcht;
+    int H, W, R, ht, hr, PR, words;
+    const int64_t *cand;
+    long long n;
+    uint32_t *bm;
+    int32_t *area;
+};
+
+// zt = transpose of z (32 x 32 tiles through shared memory)
+__global__ void __launch_bounds__(256) k_transpose_i16(const int16_t *__restrict__ z, long long pitch, int H,
+                                                       int W, int16_t *__restrict__ zt, long long pitcht) {
+    __shared__ int t[32][33];
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int j = ty; j < 32; j += 8) {
+        const int y = y0 + j, x = x0 + tx;
+        if (y < H && x < W) t[j][tx] = z[(long long)y * pitch + x];
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int x = x0 + j, y = y0 + tx;
+        if (x < W && y < H) zt[(long long)x * pitcht + y] = (int16_t)t[tx][j];
+    }
+}
+
+__global__ void __launch_bounds__(kWideThreads) k_viewshed_wide(const VsWide P) {
+    extern __shared__ __align__(16) uint32_t tile[];
+    __shared__ int red[32];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const long long c = blockIdx.x;
+    const int R = P.R, PR = P.PR, PRs = PR | 1;
+    const int64_t p = P.cand[c];
+    uint32_t *out = P.bm + c * (long long)P.words;
+    for (int i = tid; i < P.words; i += nt) out[i] = 0u;
+    if (p < 0 || p >= (int64_t)P.H * P.W) {  // invalid candidate: empty bitmap, area -1
+        if (tid == 0) P.area[c] = -1;
+        return;
+    }
+    const int cx = (int)(p % P.W), cy = (int)(p / P.W);
+    const int gw0 = floordiv(cx - R, 32);
+    const int eye = (int)P.z[(long long)cy * P.pitch + cx] + P.ht;
+    const int eyeR = eye * R;
+    const int hreR = (P.hr - eye) * R;
+
+    for (int side = 0; side < 4; ++side) {  // east, west, north, south
+        const bool xmaj = side < 2;
+        const int smaj = (side & 1) ? -1 : 1;
+        // ring cells (smaj*R, e) for x-major sides (corners included), (e, smaj*R)
+        // with |e| < R for y-major ones
+        const int elo = xmaj ? -R : -R + 1, ehi = -elo;
+        const int omaj = xmaj ? cx : cy, omin = xmaj ? cy : cx;
+        const int major_lim = xmaj ? P.W : P.H, minor_lim = xmaj ? P.H : P.W;
+        const int16_t *base = xmaj ? P.zt + (long long)cx * P.pitcht + cy : P.z + (long long)cy * P.pitch + cx;
+        const int pm = (int)(xmaj ? P.pitcht : P.pitch);
+        for (int ea = elo; ea <= ehi; ea += nt) {
+            const int eb = min(ehi, ea + nt - 1);
+            const int e = ea + tid;  // this thread's ray
+            bool alive = e <= eb;
+            const int q = floordiv(e, R);
+            const int rr = e - q * R;
+            const int thr = e >= 0 ? R : R + 1;
+            const int astep = smaj * pm + q;
+            // a0: offset from the observer's post of the post (major omaj +
+            // smaj*k, minor omin + y0); the cell tested is that post or the
+            // next one along the minor axis (offset 1 in both arrays)
+            int f = 0, y0 = 0, a0 = 0, Hn = 0, Hk = 0;
+            // window rows an east / west pass can touch
+            const int rlo = R + min(0, ea), rhi = R + max(0, eb);
+            for (int b = 0;; ++b) {
+                int klo, khi, bw0 = 0;
+                if (xmaj) {
+                    if (smaj > 0) {
+                        bw0 = ((cx + 1) >> 5) + kWideTW * b;
+                        klo = max(1, 32 * bw0 - cx);
+                        khi = min(R, 32 * (bw0 + kWideTW) - 1 - cx);
+                    } else {
+                        const int bhi = floordiv(cx - 1, 32) - kWideTW * b;
+                        bw0 = bhi - kWideTW + 1;
+                        klo = max(1, cx - (32 * bhi + 31));
+                        khi = min(R, cx - 32 * bw0);
+                    }
+                } else {
+                    klo = 1 + kWideBN * b;
+                    khi = min(R, kWideBN * (b + 1));
+                }
+                if (klo > R) break;
+                // also orders the previous band's merge before this clear
+                if (!__syncthreads_or(alive ? 1 : 0)) break;
+                const int nrow = khi - klo + 1;
+                if (xmaj) {
+                    for (int i = tid; i < (rhi - rlo + 1) * kWideTW; i += nt)
+                        tile[(rlo + i / kWideTW) * kWideTP + (i % kWideTW)] = 0u;
+                } else {
+                    for (int i = tid; i < nrow * PRs; i += nt) tile[i] = 0u;
+                }
+                __syncthreads();
+                if (alive) {
+                    for (int k = klo; k <= khi; ++k) {
+                        f += rr;
+                        y0 += q;
+                        a0 += astep;
+                        if (f >= R) { f -= R; y0 += 1; a0 += 1; }
+                        const int rb = (2 * f >= thr) ? 1 : 0;  // round half away from zero
+                        const int rnd = y0 + rb;
+                        const int gmaj = omaj + smaj * k, gmin = omin + rnd;
+                        if ((unsigned)gmaj >= (unsigned)major_lim || (unsigned)gmin >= (unsigned)minor_lim ||
+                            k * k + rnd * rnd > R * R) {
+                            alive = false;
+                            break;
+                        }
+                        const int zc = __ldg(base + a0 + rb);
+                        const bool vis = (Hk == 0) || ((long long)(zc * R + hreR) * Hk >= (long long)Hn * k);
+                        if (vis) {
+                            if (xmaj)
+                                atomicOr(&tile[(rnd + R) * kWideTP + ((gmaj >> 5) - bw0)], 1u << (gmaj & 31));
+                            else
+                                atomicOr(&tile[(k - klo) * PRs + ((gmin >> 5) - gw0)], 1u << (gmin & 31));
+                        }
+                        const int m0 = omin + y0;
+                        if (f > 0 && (m0 < 0 || m0 + 1 >= minor_lim)) {
+                            alive = false;
+                            break;
+                        }
+                        int z0 = zc, z1 = zc;
+                        if (f > 0) {
+                            const int zo = __ldg(base + a0 + (rb ? 0 : 1));
+                            z0 = rb ? zo : zc;
+                            z1 = rb ? zc : zo;
+                        }
+                        const int num = z0 * (R - f) + z1 * f - eyeR;
+                        if (Hk == 0 || (long long)num * Hk > (long long)Hn * k) { Hn = num; Hk = k; }
+                    }
+                }
+                __syncthreads();
+                // OR the band into the bitmap; one thread per word, read-modify-write
+                if (xmaj) {
+                    for (int i = tid; i < (rhi - rlo + 1) * kWideTW; i += nt) {
+                        const int r = rlo + i / kWideTW, j = i % kWideTW;
+                        const uint32_t t = tile[r * kWideTP + j];
+                        const int w = bw0 + j - gw0;
+                        if (t && w >= 0 && w < PR) out[(long long)r * PR + w] |= t;
+                    }
+                } else {
+                    for (int i = tid; i < nrow * PR; i += nt) {
+                        const int ri = i / PR, w = i - ri * PR;
+                        const uint32_t t = tile[ri * PRs + w];
+                        if (t) out[(long long)(R + smaj * (klo + ri)) * PR + w] |= t;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();  // every merge done before the observer's word is touched
+    if (tid == 0) out[(long long)R * PR + ((cx >> 5) - gw0)] |= 1u << (cx & 31);
+    __syncthreads();
+    int cnt = 0;
+    for (int i = tid; i < P.words; i += nt) cnt += __popc(out[i]);
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((tid & 31) == 0) red[tid >> 5] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+        int a = 0;
+        for (int w = 0; w < (nt >> 5); ++w) a += red[w];
+        P.area[c] = a;
+    }
+}
+
+static size_t wide_smem_bytes(int R) {
+    const size_t ew = (size_t)(2 * R + 1) * kWideTP;
+    const size_t ns = (size_t)kWideBN * (words_per_row(R) | 1);
+    return std::max(ew, ns) * 4;
+}
+
 // shared-memory bytes for a split choice
 static size_t vs_smem_bytes(int R, int nsplit, int *WG, int *box_rows, int *nbox) {
     int rows = (nsplit == 1) ? 2 * R + 1 : R + 1;
@@ -278,9 +478,52 @@ static int vs_pick_split(int R, int *nsplit, int *WG, int *box_rows, int *nbox, 
 
 using namespace vs;
 
-extern "C" size_t vs_viewshed_workspace(int32_t R, int64_t n) {
-    (void)R; (void)n;
-    return 0;
+// R whose window does not fit in shared memory (or forced by the tuning
+// table) takes the banded kernel, which needs the transposed terrain
+static bool vs_wide(int R) {
+    if (tune_get(VS_TUNE_VIEWSHED_WIDE, R, 0) == 1) return true;
+    int ns = 0, wg = 0, br = 0, nb = 0;
+    size_t sm = 0;
+    return vs_pick_split(R, &ns, &wg, &br, &nb, &sm) != VS_OK;
+}
+static long long vs_pitcht(int H) { return ((long long)H + 7) & ~7ll; }
+
+extern "C" size_t vs_viewshed_workspace(int32_t H, int32_t W, int32_t R, int64_t n) {
+    (void)n;
+    if (H < 1 || W < 1 || H > kMaxH || W > kMaxH || R < 1 || R > kMaxR || !vs_wide(R)) return 0;
+    return (size_t)W * (size_t)vs_pitcht(H) * 2 + 256;
+}
+
+static int vs_viewshed_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand,
+                            int64_t n, uint32_t *bm_out, int32_t *area_out, void *ws, size_t ws_bytes,
+                            cudaStream_t s) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (ht < -100000 || ht > 100000 || hr < -100000 || hr > 100000) return VS_ERR_RANGE;
+    if (n < 0 || n > 0x7fffffffll) return VS_ERR_RANGE;
+    if (n > 0 && (!cand || !bm_out || !area_out)) return VS_ERR_ARG;
+    const long long pitcht = vs_pitcht(g.H);
+    // window offsets of the ray walk are 32-bit
+    if ((long long)R * (std::max<long long>(g.pitch, pitcht) + 1) >= (1ll << 31)) return VS_ERR_RANGE;
+    const size_t need = vs_viewshed_workspace(g.H, g.W, R, n);
+    if (n == 0) return VS_OK;
+    if (!ws || ws_bytes < need) return VS_ERR_WS;
+    if ((rc = check_device())) return rc;
+    int16_t *zt = (int16_t *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    const dim3 tg((unsigned)((g.W + 31) / 32), (unsigned)((g.H + 31) / 32));
+    k_transpose_i16<<<tg, 256, 0, s>>>(g.z, g.pitch, g.H, g.W, zt, pitcht);
+    VS_CUDA_TRY(cudaGetLastError());
+    VsWide P;
+    P.z = g.z; P.pitch = g.pitch; P.zt = zt; P.pitcht = pitcht;
+    P.H = g.H; P.W = g.W; P.R = R; P.ht = ht; P.hr = hr;
+    P.PR = words_per_row(R);
+    P.words = (2 * R + 1) * P.PR;
+    P.cand = cand; P.n = n; P.bm = bm_out; P.area = area_out;
+    const size_t smem = wide_smem_bytes(R);
+    VS_CUDA_TRY(cudaFuncSetAttribute(k_viewshed_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_viewshed_wide<<<(unsigned)n, kWideThreads, smem, s>>>(P);
+    VS_CUDA_TRY(cudaGetLastError());
+    return VS_OK;
 }
 
 // untuned CTA size: 512 threads (the autotuner's choice for R = 50..250 on
@@ -315,7 +558,8 @@ static int vs_make_job(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, cons
 extern "C" int vs_viewshed(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand,
                            int64_t n, uint32_t *bm_out, int32_t *area_out, void *ws,
                            size_t ws_bytes, vs_stream_t st) {
-    (void)ws; (void)ws_bytes;
+    if (R < 1 || R > kMaxR) return VS_ERR_RANGE;
+    if (vs_wide(R)) return vs_viewshed_wide(g, R, ht, hr, cand, n, bm_out, area_out, ws, ws_bytes, (cudaStream_t)st);
     VsJob J;
     size_t smem = 0;
     int rc = vs_make_job(g, R, ht, hr, cand, n, bm_out, area_out, &J, &smem);

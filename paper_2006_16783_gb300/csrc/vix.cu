@@ -453,6 +453,169 @@ __global__ void __launch_bounds__(kVixThreads, 1) k_vix2(const __grid_constant__
     }
 }
 
+// zt = transpose of z (32 x 32 tiles through shared memory)
+__global__ void __launch_bounds__(256) k_transpose_i16_vix(const int16_t *__restrict__ z, long long pitch, int H,
+                                                           int W, int16_t *__restrict__ zt, long long pitcht) {
+    __shared__ int t[32][33];
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int j = ty; j < 32; j += 8) {
+        const int yy = y0 + j, xx = x0 + tx;
+        if (yy < H && xx < W) t[j][tx] = z[(long long)yy * pitch + xx];
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int xx = x0 + j, yy = y0 + tx;
+        if (xx < W && yy < H) zt[(long long)xx * pitcht + yy] = (int16_t)t[tx][j];
+    }
+}
+
+// ------------------------------------------------------------------ wide ROI
+// For ROIs whose halo window does not fit in shared memory (R above ~280; the
+// paper's own runs use R = 500 .. 2000), a warp walks one line of sight at a
+// time, 32 consecutive crossings per instruction (lane l takes crossing
+// j0 + l), against the terrain in global memory, and a warp vote ends the
+// line at its first blocked crossing.  x-major lines read terrain rows;
+// y-major lines read the transposed terrain when the caller gives one (else
+// the terrain with a row stride), so a warp's loads are contiguous.  Each lane
+// draws the samples of its own post (the same generator and offset table as
+// k_vix); the warp then walks its 32 posts' lines one after another.  The
+// test is k_vix's: visible iff j*(z_T + hr - E) >= (z0 - E)*D + (z1 - z0)*f
+// at every crossing j = 1 .. D-1, in 32-bit integers.
+struct VixWide {
+    const int16_t *z;
+    long long pitch;
+    const int16_t *zt;  // transposed terrain zt[x * pitcht + y], or null
+    long long pitcht;
+    int H, W, R, ht, hr, S, NR;
+    uint64_t seed;
+    uint8_t *out;
+    unsigned long long *steps;
+};
+
+// row table of OFF_R (rows dy = -R..R, dx ascending, origin removed):
+// hwtab[i] = half-width of row dy = i - R, rowstart[i] = entries before it
+__device__ void vix_tables(int R, int *rowstart, int *hwtab, int *warp_tot) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nt = blockDim.x;
+    const int nrow = 2 * R + 1;
+    const int chunk = (nrow + nt - 1) / nt;
+    const int i0 = tid * chunk, i1 = min(nrow, i0 + chunk);
+    int local = 0;
+    for (int i = i0; i < i1; ++i) {
+        const int dy = i - R;
+        const int hw = isqrt_exact(R * R - dy * dy);
+        hwtab[i] = hw;
+        local += 2 * hw + 1 - (dy == 0 ? 1 : 0);
+    }
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < (nt >> 5) ? warp_tot[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += v;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    int run = incl - local + (wid > 0 ? warp_tot[wid - 1] : 0);
+    if (tid == 0) rowstart[0] = 0;
+    for (int i = i0; i < i1; ++i) {
+        run += 2 * hwtab[i] + 1 - (i == R ? 1 : 0);
+        rowstart[i + 1] = run;
+    }
+    __syncthreads();
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(kVixThreads) k_vix_wide(const VixWide P) {
+    extern __shared__ int vix_tab[];
+    __shared__ int warp_tot[32];
+    const int R = P.R;
+    int *rowstart = vix_tab;            // 2R + 2 entries
+    int *hwtab = vix_tab + 2 * R + 2;   // 2R + 1 entries
+    vix_tables(R, rowstart, hwtab, warp_tot);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int x0 = blockIdx.x * 32, y = blockIdx.y * 32 + wid;
+    const int x = x0 + lane;
+    if (y >= P.H) return;  // whole warp: no block barrier follows
+    const bool mine = x < P.W;
+    const int16_t *zrow = P.z + (long long)y * P.pitch;
+    const int E = mine ? (int)zrow[x] + P.ht : 0;
+    const uint64_t GOLD = 0x9E3779B97F4A7C15ull;
+    const uint64_t p = (uint64_t)y * (uint64_t)P.W + (uint64_t)x;
+    uint64_t state = P.seed + GOLD * (p * (uint64_t)P.S + 1ull);
+    int cnt = 0;
+    unsigned long long nsteps = 0;
+    for (int s = 0; s < P.S; ++s, state += GOLD) {
+        int dx = 0, dy = 0, tsl = 0;
+        bool valid = false;
+        if (mine) {
+            vix_offset(state, (unsigned)P.NR, R, rowstart, hwtab, dx, dy);
+            valid = (unsigned)(x + dx) < (unsigned)P.W && (unsigned)(y + dy) < (unsigned)P.H;
+            if (valid) tsl = (int)__ldg(P.z + (long long)(y + dy) * P.pitch + (x + dx)) + P.hr - E;
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, valid);
+        unsigned visbits = 0;
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int ldx = __shfl_sync(0xffffffffu, dx, src), ldy = __shfl_sync(0xffffffffu, dy, src);
+            const int lE = __shfl_sync(0xffffffffu, E, src), lts = __shfl_sync(0xffffffffu, tsl, src);
+            const int lx = x0 + src;
+            const int adx = abs(ldx), ady = abs(ldy);
+            const bool xmaj = adx >= ady;
+            const int D = xmaj ? adx : ady;
+            const int dmin = xmaj ? ldy : ldx;
+            const int sg = xmaj ? (ldx > 0 ? 1 : -1) : (ldy > 0 ? 1 : -1);
+            // strides along the major (ms) and minor (ns) axes of the array read
+            const int16_t *bp;
+            int ms, ns;
+            if (xmaj) { bp = zrow + lx; ms = 1; ns = (int)P.pitch; }
+            else if (P.zt) { bp = P.zt + (long long)lx * P.pitcht + y; ms = 1; ns = (int)P.pitcht; }
+            else { bp = zrow + lx; ms = (int)P.pitch; ns = 1; }
+            // this lane's first crossing j = 1 + lane
+            int j = 1 + lane;
+            const int yq = floordiv(j * dmin, D);
+            int f = j * dmin - yq * D;
+            int off = j * sg * ms + yq * ns;
+            const int q32 = floordiv(32 * dmin, D), r32 = 32 * dmin - q32 * D;
+            const int step32 = 32 * sg * ms + q32 * ns;
+            int lhs = j * lts;
+            bool vis = true;
+            for (int j0 = 1; j0 < D; j0 += 32) {
+                bool blocked = false;
+                if (j < D) {
+                    const int z0 = __ldg(bp + off);
+                    const int z1 = f ? (int)__ldg(bp + off + ns) : z0;
+                    blocked = lhs < (z0 - lE) * D + (z1 - z0) * f;
+                }
+                const unsigned bb = __ballot_sync(0xffffffffu, blocked);
+                if (bb) {
+                    vis = false;
+                    if (COUNT) nsteps += (unsigned long long)(j0 + __ffs(bb) - 1);
+                    break;
+                }
+                j += 32;
+                lhs += 32 * lts;
+                off += step32;
+                f += r32;
+                if (f >= D) { f -= D; off += ns; }
+            }
+            if (COUNT && vis && D > 1) nsteps += (unsigned long long)(D - 1);
+            if (vis) visbits |= 1u << src;
+        }
+        cnt += (visbits >> lane) & 1u;
+    }
+    if (mine) P.out[(size_t)y * P.W + x] = (uint8_t)cnt;
+    if (COUNT && lane == 0 && nsteps) atomicAdd(P.steps, nsteps);  // every lane counted the same lines
+}
+
 static size_t vix2_smem_bytes(int R, int nsplit, int TX, int TY, int sb, int *WG, int *box_rows,
                               int *nbox) {
     // one spare row below and column to the right: the second straddling post
@@ -486,8 +649,62 @@ static size_t vix_smem_bytes(int R, int nsplit, int TX, int TY, int *WG, int *bo
 
 using namespace vs;
 
+// the staged kernels cover R when one of their windows fits in shared memory
+static bool vix_staged_fits(int R, int S) {
+    const int sb = std::max(std::min(S, kVixSB), 1);
+    int WG, br, nb;
+    for (int ns : {1, 2, 4})
+        for (int t : {64, 32}) {
+            if (R <= 511) {
+                const size_t b = vix2_smem_bytes(R, ns, t, 32, sb, &WG, &br, &nb);
+                if (WG <= 256 && b <= (size_t)225 * 1024) return true;
+            }
+            const size_t b = vix_smem_bytes(R, ns, t, 32, &WG, &br, &nb);
+            if (WG <= 256 && b <= (size_t)225 * 1024) return true;
+        }
+    return false;
+}
+
+static bool vix_wide(int R, int S) {
+    return tune_get(VS_TUNE_VIX_TILE, R, 0) == 3 || !vix_staged_fits(R, S);
+}
+
+static long long vix_pitcht(int H) { return ((long long)H + 7) & ~7ll; }
+
+static int vix_launch_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
+                           uint8_t *vix_out, unsigned long long *steps, void *ws, size_t ws_bytes,
+                           cudaStream_t s, int NR) {
+    const long long pitcht = vix_pitcht(g.H);
+    // offsets along a line are 32-bit
+    if ((long long)(2 * R + 64) * std::max<long long>(g.pitch, pitcht) >= (1ll << 31)) return VS_ERR_RANGE;
+    const size_t need = (size_t)g.W * (size_t)pitcht * 2 + 256;
+    int16_t *zt = nullptr;
+    if (ws && ws_bytes >= need) {
+        zt = (int16_t *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+        const dim3 tg((unsigned)((g.W + 31) / 32), (unsigned)((g.H + 31) / 32));
+        k_transpose_i16_vix<<<tg, 256, 0, s>>>(g.z, g.pitch, g.H, g.W, zt, pitcht);
+        VS_CUDA_TRY(cudaGetLastError());
+    }
+    VixWide P;
+    P.z = g.z; P.pitch = g.pitch; P.zt = zt; P.pitcht = pitcht;
+    P.H = g.H; P.W = g.W; P.R = R; P.ht = ht; P.hr = hr; P.S = S; P.NR = NR;
+    P.seed = seed; P.out = vix_out; P.steps = steps;
+    const size_t smem = (size_t)(4 * R + 3) * 4;
+    const dim3 grid((unsigned)((g.W + 31) / 32), (unsigned)((g.H + 31) / 32));
+    if (steps) {
+        VS_CUDA_TRY(cudaFuncSetAttribute(k_vix_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_vix_wide<true><<<grid, kVixThreads, smem, s>>>(P);
+    } else {
+        VS_CUDA_TRY(cudaFuncSetAttribute(k_vix_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_vix_wide<false><<<grid, kVixThreads, smem, s>>>(P);
+    }
+    VS_CUDA_TRY(cudaGetLastError());
+    return VS_OK;
+}
+
 static int vix_launch(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
-                      uint8_t *vix_out, unsigned long long *steps, vs_stream_t st) {
+                      uint8_t *vix_out, unsigned long long *steps, void *ws, size_t ws_bytes,
+                      vs_stream_t st) {
     int rc = check_grid(g);
     if (rc) return rc;
     if (!vix_out) return VS_ERR_ARG;
@@ -505,6 +722,9 @@ static int vix_launch(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, u
         nr += 2 * s + 1;
     }
     P.NR = (int)(nr - 1);
+
+    if (vix_wide(R, S))
+        return vix_launch_wide(g, R, ht, hr, S, seed, vix_out, steps, ws, ws_bytes, (cudaStream_t)st, P.NR);
 
     // length-sorted variant when the packed line items can describe R
     if (R <= 511) {
@@ -573,11 +793,22 @@ static int vix_launch(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, u
 
 extern "C" int vs_vix(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
                       uint8_t *vix_out, vs_stream_t st) {
-    return vix_launch(g, R, ht, hr, S, seed, vix_out, nullptr, st);
+    return vix_launch(g, R, ht, hr, S, seed, vix_out, nullptr, nullptr, 0, st);
 }
 
 extern "C" int vs_vix_count(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
                             uint8_t *vix_out, uint64_t *los_steps, vs_stream_t st) {
     if (!los_steps) return VS_ERR_ARG;
-    return vix_launch(g, R, ht, hr, S, seed, vix_out, (unsigned long long *)los_steps, st);
+    return vix_launch(g, R, ht, hr, S, seed, vix_out, (unsigned long long *)los_steps, nullptr, 0, st);
+}
+
+extern "C" size_t vs_vix_workspace(int32_t H, int32_t W, int32_t R, int32_t S) {
+    if (H < 1 || W < 1 || H > kMaxH || W > kMaxH || R < 1 || R > kMaxR || S < 0 || S > 255) return 0;
+    if (!vix_wide(R, S)) return 0;
+    return (size_t)W * (size_t)vix_pitcht(H) * 2 + 256;
+}
+
+extern "C" int vs_vix_ws(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
+                         uint8_t *vix_out, uint64_t *los_steps, void *ws, size_t ws_bytes, vs_stream_t st) {
+    return vix_launch(g, R, ht, hr, S, seed, vix_out, (unsigned long long *)los_steps, ws, ws_bytes, st);
 }

@@ -41,12 +41,13 @@ int make_grid_map(GridMap *gm, const vs_grid &g, int wg, int rows) {
     return r == CUDA_SUCCESS ? VS_OK : VS_ERR_CUDA;
 }
 
-// (op, R) -> value; R <= kMaxR, ops 0..3
-static int g_tune[4][kMaxR + 1];
+// (op, R) -> value; R <= kMaxR, ops 0..4
+constexpr int kTuneOps = 5;
+static int g_tune[kTuneOps][kMaxR + 1];
 static std::mutex g_tune_mu;
 
 int tune_get(int op, int R, int fallback) {
-    if (op < 0 || op >= 4 || R < 1 || R > kMaxR) return fallback;
+    if (op < 0 || op >= kTuneOps || R < 1 || R > kMaxR) return fallback;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const int v = g_tune[op][R];
     return v > 0 ? v : fallback;
@@ -96,12 +97,14 @@ const char *vs_strerror(int code) {
 int vs_version(void) { return 100; }
 
 int vs_tune_set(int32_t op, int32_t R, int32_t value) {
-    if (op < 0 || op >= 4 || R < 1 || R > vs::kMaxR) return VS_ERR_RANGE;
+    if (op < 0 || op >= vs::kTuneOps || R < 1 || R > vs::kMaxR) return VS_ERR_RANGE;
     if (op == VS_TUNE_VIEWSHED_THREADS && value != 0 && value != 128 && value != 256 && value != 512)
         return VS_ERR_RANGE;
-    if (op == VS_TUNE_VIX_TILE && (value < 0 || value > 2)) return VS_ERR_RANGE;
+    if (op == VS_TUNE_VIX_TILE && (value < 0 || value > 3)) return VS_ERR_RANGE;
     if (op == VS_TUNE_SITE_CLUSTER && value != 0 && value != 1 && value != 2 && value != 4 && value != 8 &&
         value != 16)
+        return VS_ERR_RANGE;
+    if ((op == VS_TUNE_VIEWSHED_WIDE || op == VS_TUNE_SITE_LAZY) && value != 0 && value != 1)
         return VS_ERR_RANGE;
     std::lock_guard<std::mutex> lk(vs::g_tune_mu);
     vs::g_tune[op][R] = value;

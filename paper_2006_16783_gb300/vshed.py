@@ -42,7 +42,8 @@ class vs_site_job(ctypes.Structure):
                 ("n_chosen", ctypes.c_void_p)]
 
 
-VS_TUNE_VIEWSHED_THREADS, VS_TUNE_VIX_TILE, VS_TUNE_SITE_CLUSTER = 0, 1, 2
+(VS_TUNE_VIEWSHED_THREADS, VS_TUNE_VIX_TILE, VS_TUNE_SITE_CLUSTER, VS_TUNE_VIEWSHED_WIDE,
+ VS_TUNE_SITE_LAZY) = 0, 1, 2, 3, 4
 
 # name -> (restype, argtypes); the exported symbols of include/vshed.h
 P, i32, i64, u64, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
@@ -59,11 +60,13 @@ SIGNATURES = {
     "vs_site_batch": (ctypes.c_int, [P, i32, P, sz, P]),
     "vs_vix": (ctypes.c_int, [vs_grid, i32, i32, i32, i32, u64, P, P]),
     "vs_vix_count": (ctypes.c_int, [vs_grid, i32, i32, i32, i32, u64, P, P, P]),
+    "vs_vix_workspace": (sz, [i32, i32, i32, i32]),
+    "vs_vix_ws": (ctypes.c_int, [vs_grid, i32, i32, i32, i32, u64, P, P, P, sz, P]),
     "vs_findmax_count": (i64, [i32, i32, i32, i32, i32]),
     "vs_findmax": (ctypes.c_int, [P, i32, i32, i32, i32, P, i64, P]),
     "vs_findmax_f32": (ctypes.c_int, [P, i32, i32, i32, i32, i32, P, i64, P]),
     "vs_bitmap_words": (i64, [i32]),
-    "vs_viewshed_workspace": (sz, [i32, i64]),
+    "vs_viewshed_workspace": (sz, [i32, i32, i32, i64]),
     "vs_viewshed": (ctypes.c_int, [vs_grid, i32, i32, i32, P, i64, P, P, P, sz, P]),
     "vs_site_workspace": (sz, [i64, i32]),
     "vs_site": (ctypes.c_int, [P, P, i64, i32, i32, i32, i32, f64, P, P, P, P, P, sz, P]),
@@ -146,23 +149,40 @@ class Grid:
 
 
 # ------------------------------------------------------------------ stages
-def vix(g, R, ht, hr, S, seed, out=None):
-    """Sampled visibility-index counts (uint8, H x W)."""
+def vix_workspace(H, W, R, S):
+    """Workspace bytes of vs_vix_ws (0 when the staged kernels cover R)."""
+    return lib().vs_vix_workspace(H, W, R, S)
+
+
+def vix(g, R, ht, hr, S, seed, out=None, ws=None):
+    """Sampled visibility-index counts (uint8, H x W).  For ROIs beyond the
+    staged kernels the transposed terrain goes in ``ws`` (a uint8 device
+    buffer of at least vix_workspace() bytes, allocated when missing)."""
+    return _vix(g, R, ht, hr, S, seed, None, out, ws)
+
+
+def vix_count(g, R, ht, hr, S, seed, steps, out=None, ws=None):
+    """vs_vix that also adds the number of LOS crossings it evaluated to the
+    device uint64 counter ``steps`` (an int64 CUDA tensor of one element)."""
+    _need_cuda(steps)
+    return _vix(g, R, ht, hr, S, seed, steps, out, ws)
+
+
+def _vix(g, R, ht, hr, S, seed, steps, out, ws):
     if out is None:
         out = torch.empty((g.H, g.W), dtype=torch.uint8, device=g.storage.device)
     _need_cuda(out)
-    _check("vs_vix", lib().vs_vix(g.c(), R, ht, hr, S, ctypes.c_uint64(seed & (2**64 - 1)), _ptr(out), _stream()))
-    return out
-
-
-def vix_count(g, R, ht, hr, S, seed, steps, out=None):
-    """vs_vix that also adds the number of LOS crossings it evaluated to the
-    device uint64 counter ``steps`` (an int64 CUDA tensor of one element)."""
-    if out is None:
-        out = torch.empty((g.H, g.W), dtype=torch.uint8, device=g.storage.device)
-    _need_cuda(out, steps)
-    _check("vs_vix_count", lib().vs_vix_count(g.c(), R, ht, hr, S, ctypes.c_uint64(seed & (2**64 - 1)),
-                                              _ptr(out), _ptr(steps), _stream()))
+    sd = ctypes.c_uint64(seed & (2**64 - 1))
+    wsb = lib().vs_vix_workspace(g.H, g.W, R, S)
+    if wsb == 0 and steps is None:
+        _check("vs_vix", lib().vs_vix(g.c(), R, ht, hr, S, sd, _ptr(out), _stream()))
+    elif wsb == 0:
+        _check("vs_vix_count", lib().vs_vix_count(g.c(), R, ht, hr, S, sd, _ptr(out), _ptr(steps), _stream()))
+    else:
+        if ws is None or ws.numel() < wsb:
+            ws = torch.empty(wsb, dtype=torch.uint8, device=out.device)
+        _check("vs_vix_ws", lib().vs_vix_ws(g.c(), R, ht, hr, S, sd, _ptr(out), _ptr(steps), _ptr(ws), wsb,
+                                            _stream()))
     return out
 
 
@@ -204,8 +224,16 @@ def words_per_row(R):
     return (2 * R) // 32 + 2
 
 
-def viewshed(g, R, ht, hr, cand, bm=None, area=None):
-    """Viewshed bitmaps uint32 [n, 2R+1, P_R] and areas int32 [n]."""
+def viewshed_workspace(H, W, R, n):
+    """Workspace bytes of vs_viewshed (0 when the ROI window fits in shared
+    memory, else the transposed terrain the banded kernel reads)."""
+    return lib().vs_viewshed_workspace(H, W, R, n)
+
+
+def viewshed(g, R, ht, hr, cand, bm=None, area=None, ws=None):
+    """Viewshed bitmaps uint32 [n, 2R+1, P_R] and areas int32 [n].  ws: an
+    optional uint8 device buffer of at least viewshed_workspace() bytes, to
+    reuse across calls."""
     _need_cuda(cand)
     cand = cand.contiguous()
     n = cand.numel()
@@ -213,8 +241,9 @@ def viewshed(g, R, ht, hr, cand, bm=None, area=None):
         bm = torch.empty((n, 2 * R + 1, words_per_row(R)), dtype=torch.int32, device=cand.device)
     if area is None:
         area = torch.empty(n, dtype=torch.int32, device=cand.device)
-    wsb = lib().vs_viewshed_workspace(R, n)
-    ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=cand.device) if wsb else None
+    wsb = lib().vs_viewshed_workspace(g.H, g.W, R, n)
+    if wsb and (ws is None or ws.numel() < wsb):
+        ws = torch.empty(wsb, dtype=torch.uint8, device=cand.device)
     _check("vs_viewshed", lib().vs_viewshed(g.c(), R, ht, hr, _ptr(cand), n, _ptr(bm), _ptr(area),
                                             _ptr(ws), wsb, _stream()))
     return bm, area

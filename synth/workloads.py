@@ -15,6 +15,9 @@ for the unavailable datasets.  Parameters only -- no siting arithmetic.
     full    46400^2 ridged multifractal (base wavelength 640 posts, 10 octaves,
             0..4000 m, lowest 5% flattened), R=100, h=10, S=10, top-4 per
             464x464 block (40000 candidates), 4096 observers
+    paper   the paper's own US-West regime on the full recipe's terrain:
+            46400^2, R=1000, h_t=100, h_r=10, S=10, top-20 per 334x334 block
+            (386,420 candidates), greedy until 95% coverage
 """
 import math
 from dataclasses import dataclass, field
@@ -42,6 +45,7 @@ class Workload:
     zmax: int = 1000
     lake_frac: float = 0.0
     vix_seed: int = 0x5EED
+    target: float = 0.0        # coverage stop of the site step (0 = off)
     extra: dict = field(default_factory=dict)
 
     def make_terrain(self, device="cpu"):
@@ -75,6 +79,21 @@ FULL = Workload("full_46400sq_R100", 46400, 46400, 100, 10, 10, 10, 464, 4, 4096
 MID = Workload("mid_11600sq_R100", 11600, 11600, 100, 10, 10, 10, 464, 4, 1024, seed=1004,
                kind="ridged", zmax=4000, lake_frac=0.05,
                extra={"octaves": 10, "base_wavelength": 640})
+
+
+# The paper's own US-West run (Sec. "Experiments", Table of the US-West
+# dataset, first column): 46400^2 posts, R = 1000, h_t = 100, h_r = 10, the
+# terrain cut into 139 x 139 blocks (side 334, about R/3) with 20 candidates
+# each (386,420), greedy siting until 95% of the terrain is covered.  The full
+# recipe's ridged terrain stands in for NASADEM US West.  Bitmaps: 386,420 x
+# 2001 rows x 64 words = 198 GB.
+PAPER = Workload("paper_uswest_46400sq_R1000", 46400, 46400, 1000, 100, 10, 10, 334, 20, 20000,
+                 seed=1004, kind="ridged", zmax=4000, lake_frac=0.05, target=0.95,
+                 extra={"octaves": 10, "base_wavelength": 640})
+# the same regime on 16384^2 (49 x 50 blocks, 49,000 candidates, 25 GB of bitmaps)
+PAPER_MID = Workload("paper_regime_16384sq_R1000", 16384, 16384, 1000, 100, 10, 10, 334, 20, 20000,
+                     seed=1004, kind="ridged", zmax=4000, lake_frac=0.05, target=0.95,
+                     extra={"octaves": 10, "base_wavelength": 640})
 
 
 def batch_instances(seed=1002, count=64, max_side=4096):
