@@ -89,9 +89,10 @@ int vs_version(void);
  *     against the terrain in global memory (the path every R takes whose
  *     window does not fit in shared memory, R above ~280) even when the
  *     window would fit; 0 = default.
- *   VS_TUNE_SITE_LAZY: 1 = vs_site runs the lazy greedy (the path of calls
- *     whose gains or windows do not fit in one cluster's shared memory) even
- *     when another loop would fit; 0 = default. */
+ *   VS_TUNE_SITE_LAZY: vs_site runs the lazy greedy (the path of calls whose
+ *     gains or windows do not fit in one cluster's shared memory) even when
+ *     another loop would fit: 1 = on the whole GPU (one cooperative launch,
+ *     the lazy path's default), 2 = in one CTA; 0 = default. */
 enum {
     VS_TUNE_VIEWSHED_THREADS = 0,
     VS_TUNE_VIX_TILE = 1,

@@ -1106,7 +1106,8 @@ __device__ __forceinline__ void lazy_block_best(uint64_t &k, int &c, uint64_t *s
 // this thread's share of popcount(V_c AND NOT C) over c's window clipped to
 // the grid; with commit, C |= V_c.  The clipped window is walked as one flat
 // range of (row, word) pairs, eight pairs per thread in flight.
-__device__ __forceinline__ unsigned lazy_window(const LazyParams &P, int c, int64_t p, bool commit) {
+__device__ __forceinline__ unsigned lazy_window(const LazyParams &P, int c, int64_t p, bool commit,
+                                                int part = 0, int nparts = 1) {
     constexpr int U = 8;
     const int R = P.R, PR = P.PR, WWc = P.WWc;
     const int cx = (int)(p % P.W), cy = (int)(p / P.W);
@@ -1119,19 +1120,23 @@ __device__ __forceinline__ unsigned lazy_window(const LazyParams &P, int c, int6
     uint32_t *C = P.cum + (long long)(cy - R + r_lo) * WWc + (gw0 + w_lo);
     const int nt = blockDim.x;
     const int dr = nt / nw, dw = nt - dr * nw;
-    int r = threadIdx.x / nw, w = threadIdx.x - r * nw;
+    // this part of the flat range: [i_begin, i_end)
+    const int i_begin = (int)((long long)total * part / nparts);
+    const int i_end = (int)((long long)total * (part + 1) / nparts);
+    const int i0 = i_begin + threadIdx.x;
+    int r = i0 / nw, w = i0 - r * nw;
     unsigned sum = 0;
-    for (int i = threadIdx.x; i < total; i += U * nt) {
+    for (int i = i0; i < i_end; i += U * nt) {
         uint32_t v[U], cw[U];
         int off[U];
         int rr = r, ww = w;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             off[u] = -1;
-            if (i + u * nt < total) {
+            if (i + u * nt < i_end) {
                 off[u] = rr * WWc + ww;
                 v[u] = __ldg(V + rr * PR + ww);
-                cw[u] = C[off[u]];
+                cw[u] = __ldcg(C + off[u]);  // L2: other CTAs of k_site_lazy_grid update C
             }
             ww += dw;
             rr += dr;
@@ -1261,6 +1266,166 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_lazy(const LazyParams 
     if (tid == 0) *P.n_chosen = t;
 }
 
+// The lazy greedy on the whole GPU: one cooperative launch, one CTA per SM,
+// each CTA owning a slice of the candidates.  A step is a fixed sequence of
+// phases separated by grid barriers:
+//   A  F = the largest key among exact (fresh) gains;
+//   B  every stale candidate whose bound key is >= F goes on a work list --
+//      only those can beat F, so after B..C the best key is an exact gain;
+//   C  the CTAs evaluate the work list, one window per CTA at a time;
+//   D  the largest key (bound, lowest post) and then the lowest index holding
+//      it (duplicate posts) -- the winner, exactly the sequential argmax;
+//   E  C |= V_winner (the window split over the CTAs), the winner's gain set
+//      to 0, stale flags for the candidates within Chebyshev distance 2R.
+// Arrays other CTAs write during the launch (gains, flags, work list, C) are
+// read through L2 (ld.global.cg), never from a stale L1 line.
+// Keys and counters of a step live in slots indexed by the step's parity; CTA
+// 0 clears the other parity's slots during E.  Barrier waits are bounded: a
+// wait that gives up raises an error flag every CTA checks after each
+// barrier, and the call reports VS_ERR_TIMEOUT in *n_chosen.
+struct LazyCtl {
+    unsigned long long F[2];     // largest fresh key
+    unsigned long long best[2];  // largest key after the evaluations
+    unsigned widx[2];            // 0xFFFFFFFF - lowest index holding best
+    unsigned nwork[2];           // work-list length
+    unsigned next[2];            // work-list cursor
+    unsigned bar_count;
+    unsigned bar_gen;
+    int err;
+};
+static_assert(sizeof(LazyCtl) <= 256, "control block fits its workspace slot");
+
+// grid barrier (all CTAs of a cooperative launch); false when a wait gave up
+__device__ __forceinline__ bool lazy_grid_sync(LazyCtl *ctl, unsigned &gen) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const unsigned g0 = gen;
+        if (atomicAdd(&ctl->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            uint32_t i = 0;
+            while (*(volatile unsigned *)&ctl->bar_gen == g0) {
+                if (++i > kWaitPolls || *(volatile int *)&ctl->err) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        gen = g0 + 1;
+        if (!ok) atomicExch(&ctl->err, 1);
+        s_ok = ok && !*(volatile int *)&ctl->err;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long *s_red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = u64max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) s_red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? s_red[lane] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) v = u64max(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) s_red[32] = v;
+    }
+    __syncthreads();
+    v = s_red[32];
+    __syncthreads();
+    return v;
+}
+
+__global__ void __launch_bounds__(kSiteThreads, 1) k_site_lazy_grid(const LazyParams P, LazyCtl *ctl,
+                                                                   uint32_t *work) {
+    __shared__ unsigned long long s_red[33];
+    __shared__ unsigned s_u[32];
+    __shared__ int s_item;
+    const int tid = threadIdx.x, G = gridDim.x, b = blockIdx.x;
+    const int lo = (int)((long long)P.n * b / G), hi = (int)((long long)P.n * (b + 1) / G);
+    unsigned gen = 0;
+    long long covered = P.need >= 0 ? (long long)*P.covered0 : 0;
+    int t = 0;
+    bool ok = true;
+    for (; t < P.n_obs; ++t) {
+        if (P.need >= 0 && covered >= P.need) break;
+        const int par = t & 1;
+        // A: largest fresh key
+        unsigned long long k = 0;
+        for (int c = lo + tid; c < hi; c += blockDim.x)
+            if (__ldcg(P.fresh + c)) k = u64max(k, lazy_key(__ldcg(P.g + c), P.cand[c]));
+        k = block_max_u64(k, s_red);
+        if (tid == 0 && k) atomicMax(&ctl->F[par], k);
+        if (!(ok = lazy_grid_sync(ctl, gen))) break;
+        const unsigned long long F = *(volatile unsigned long long *)&ctl->F[par];
+        // B: stale bounds that may beat F
+        for (int c = lo + tid; c < hi; c += blockDim.x)
+            if (!__ldcg(P.fresh + c) && lazy_key(__ldcg(P.g + c), P.cand[c]) >= F)
+                work[atomicAdd(&ctl->nwork[par], 1u)] = (uint32_t)c;
+        if (!(ok = lazy_grid_sync(ctl, gen))) break;
+        const unsigned m = *(volatile unsigned *)&ctl->nwork[par];
+        // C: evaluate them, one window per CTA at a time
+        for (;;) {
+            if (tid == 0) s_item = (int)atomicAdd(&ctl->next[par], 1u);
+            __syncthreads();
+            const int it = s_item;
+            __syncthreads();
+            if ((unsigned)it >= m) break;
+            const int c = (int)__ldcg(work + it);
+            const unsigned gnew = lazy_block_sum(lazy_window(P, c, P.cand[c], false), s_u);
+            if (tid == 0) { P.g[c] = gnew; P.fresh[c] = 1; }
+        }
+        if (!(ok = lazy_grid_sync(ctl, gen))) break;
+        // D: the largest key, then the lowest index holding it
+        k = 0;
+        for (int c = lo + tid; c < hi; c += blockDim.x) k = u64max(k, lazy_key(__ldcg(P.g + c), P.cand[c]));
+        k = block_max_u64(k, s_red);
+        if (tid == 0 && k) atomicMax(&ctl->best[par], k);
+        if (!(ok = lazy_grid_sync(ctl, gen))) break;
+        const unsigned long long best = *(volatile unsigned long long *)&ctl->best[par];
+        if ((best >> 32) == 0) break;  // best gain 0: nothing left to cover
+        for (int c = lo + tid; c < hi; c += blockDim.x)
+            if (lazy_key(__ldcg(P.g + c), P.cand[c]) == best) atomicMax(&ctl->widx[par], 0xFFFFFFFFu - (unsigned)c);
+        if (!(ok = lazy_grid_sync(ctl, gen))) break;
+        const int w = (int)(0xFFFFFFFFu - *(volatile unsigned *)&ctl->widx[par]);
+        const int64_t pw = P.cand[w];
+        const uint32_t gw = (uint32_t)(best >> 32);
+        // E: accept
+        lazy_window(P, w, pw, true, b, G);
+        const int cx = (int)(pw % P.W), cy = (int)(pw / P.W), R2 = 2 * P.R;
+        const int x0 = max(0, cx - R2) / P.cs, x1 = min(P.W - 1, cx + R2) / P.cs;
+        const int y0 = max(0, cy - R2) / P.cs, y1 = min(P.H - 1, cy + R2) / P.cs;
+        const int gt = b * blockDim.x + tid, gs = G * blockDim.x;
+        for (int yc = y0; yc <= y1; ++yc)
+            for (int xc = x0; xc <= x1; ++xc) {
+                const int cell = yc * P.ncx + xc;
+                const uint32_t e = P.cstart[cell + 1];
+                for (uint32_t j = P.cstart[cell] + gt; j < e; j += gs) {
+                    const int c2 = (int)P.citems[j];
+                    const int64_t p2 = P.cand[c2];
+                    const int xx = (int)(p2 % P.W), yy = (int)(p2 / P.W);
+                    if (c2 != w && abs(xx - cx) <= R2 && abs(yy - cy) <= R2) P.fresh[c2] = 0;
+                }
+            }
+        if (b == 0 && tid == 0) {
+            P.chosen[t] = pw;
+            P.gains[t] = gw;
+            P.g[w] = 0;  // all of its viewshed is covered now
+            const int q = par ^ 1;
+            ctl->F[q] = 0; ctl->best[q] = 0; ctl->widx[q] = 0; ctl->nwork[q] = 0; ctl->next[q] = 0;
+        }
+        covered += gw;
+        if (!(ok = lazy_grid_sync(ctl, gen))) break;
+    }
+    if (b == 0 && tid == 0) *P.n_chosen = ok ? t : VS_ERR_TIMEOUT;
+}
+
 static size_t site_smem_bytes(int slots, int words) {
     return (size_t)slots * 16 + (size_t)words * 4 + 16;
 }
@@ -1341,6 +1506,23 @@ static int site_lazy(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
     L.n_obs = n_obs; L.need = need; L.chosen = chosen; L.gains = gains; L.cum = cum; L.n_chosen = n_chosen;
     L.g = g0; L.fresh = fresh; L.bs = bs; L.nb = nb; L.cstart = cstart; L.citems = citems;
     L.cs = (int)cs; L.ncx = ncx; L.ncy = ncy; L.covered0 = cov;
+    if (tune_get(VS_TUNE_SITE_LAZY, R, 0) != 2) {
+        // the whole GPU: one CTA per SM in one cooperative launch
+        int dev = 0, sms = 0, per = 0, coop = 0;
+        VS_CUDA_TRY(cudaGetDevice(&dev));
+        VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        VS_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_site_lazy_grid, kSiteThreads, 0));
+        if (coop && per >= 1 && sms >= 1) {
+            LazyCtl *ctl = (LazyCtl *)((char *)ws + 4 * a4);
+            uint32_t *work = (uint32_t *)((char *)ws + 3 * a4);
+            VS_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(LazyCtl), s));
+            void *args[] = {(void *)&L, (void *)&ctl, (void *)&work};
+            VS_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_site_lazy_grid, dim3((unsigned)sms),
+                                                    dim3(kSiteThreads), args, 0, s));
+            return VS_OK;
+        }
+    }
     const size_t smem = (size_t)nb * 12 + 16;
     VS_CUDA_TRY(cudaFuncSetAttribute(k_site_lazy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_site_lazy<<<1, kSiteThreads, smem, s>>>(L);

@@ -171,16 +171,18 @@ def _site(V, bm, cand, H, W, R, n_obs, target=0.0, cum=None):
                   target, cum=cum)
 
 
+@pytest.mark.parametrize("mode", [1, 2])   # the whole GPU, one CTA
 @pytest.mark.parametrize("H,W,R,n,n_obs,target", [
     (300, 340, 20, 900, 200, 0.0),
     (600, 620, 100, 2600, 300, 0.0),
     (600, 620, 100, 2600, 400, 0.55),
     (90, 100, 9, 300, 500, 0.0),      # runs until the best gain is 0
+    (40, 50, 6, 100, 30, 0.0),        # fewer candidates than SMs
 ])
-def test_site_lazy_forced(V, O, H, W, R, n, n_obs, target):
+def test_site_lazy_forced(V, O, H, W, R, n, n_obs, target, mode):
     _, cand, bm = _site_case(O, 11 + R, H, W, R, n)
     ch, gn, C = O.site(bm, cand, H, W, R, n_obs, target)
-    V.tune_set(V.VS_TUNE_SITE_LAZY, R, 1)
+    V.tune_set(V.VS_TUNE_SITE_LAZY, R, mode)
     try:
         gch, ggn, gC, t = _site(V, bm, cand, H, W, R, n_obs, target)
     finally:
@@ -190,13 +192,14 @@ def test_site_lazy_forced(V, O, H, W, R, n, n_obs, target):
     assert (_np(gC).view(np.uint32) == C).all()
 
 
-def test_site_lazy_resume(V, O):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_site_lazy_resume(V, O, mode):
     """Checkpoint / resume: two calls continuing from the returned cum give
     the sequence of one call."""
     H, W, R = 400, 380, 40
     _, cand, bm = _site_case(O, 23, H, W, R, 1200)
     ch, gn, C = O.site(bm, cand, H, W, R, 150)
-    V.tune_set(V.VS_TUNE_SITE_LAZY, R, 1)
+    V.tune_set(V.VS_TUNE_SITE_LAZY, R, mode)
     try:
         c1, g1, cum, t1 = _site(V, bm, cand, H, W, R, 60)
         c2, g2, cum2, t2 = _site(V, bm, cand, H, W, R, 90, cum=cum)
