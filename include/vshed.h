@@ -135,7 +135,7 @@ int vs_vix(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t see
  * NULL) or vs_vix_count (los_steps set) with that workspace; ws may be NULL
  * or smaller, then y-major lines read the terrain with a row stride (same
  * results, slower).  vs_vix and vs_vix_count are vs_vix_ws without a
- * workspace.  Large R needs (2R + 64) * max(pitch, ceil8(H)) < 2^31 (else
+ * workspace.  Large R needs (3R + 128) * max(pitch, ceil8(H)) < 2^31 (else
  * VS_ERR_RANGE). */
 size_t vs_vix_workspace(int32_t H, int32_t W, int32_t R, int32_t S);
 int vs_vix_ws(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,

@@ -588,23 +588,33 @@ __global__ void __launch_bounds__(kVixThreads) k_vix_wide(const VixWide P) {
             const int step32 = 32 * sg * ms + q32 * ns;
             int lhs = j * lts;
             bool vis = true;
-            for (int j0 = 1; j0 < D; j0 += 32) {
-                bool blocked = false;
+            // two chunks of 32 crossings per trip: the second chunk's loads are
+            // in flight before the first chunk's vote
+            for (int j0 = 1; j0 < D; j0 += 64) {
+                int fb = f + r32, offb = off + step32;
+                if (fb >= D) { fb -= D; offb += ns; }
+                int z0a = 0, z1a = 0, z0b = 0, z1b = 0;
                 if (j < D) {
-                    const int z0 = __ldg(bp + off);
-                    const int z1 = f ? (int)__ldg(bp + off + ns) : z0;
-                    blocked = lhs < (z0 - lE) * D + (z1 - z0) * f;
+                    z0a = __ldg(bp + off);
+                    z1a = f ? (int)__ldg(bp + off + ns) : z0a;
                 }
-                const unsigned bb = __ballot_sync(0xffffffffu, blocked);
-                if (bb) {
+                if (j + 32 < D) {
+                    z0b = __ldg(bp + offb);
+                    z1b = fb ? (int)__ldg(bp + offb + ns) : z0b;
+                }
+                const bool ba = j < D && lhs < (z0a - lE) * D + (z1a - z0a) * f;
+                const bool bb2 = j + 32 < D && lhs + 32 * lts < (z0b - lE) * D + (z1b - z0b) * fb;
+                const unsigned va = __ballot_sync(0xffffffffu, ba);
+                const unsigned vb = __ballot_sync(0xffffffffu, bb2);
+                if (va | vb) {
                     vis = false;
-                    if (COUNT) nsteps += (unsigned long long)(j0 + __ffs(bb) - 1);
+                    if (COUNT) nsteps += (unsigned long long)(va ? j0 + __ffs(va) - 1 : j0 + 32 + __ffs(vb) - 1);
                     break;
                 }
-                j += 32;
-                lhs += 32 * lts;
-                off += step32;
-                f += r32;
+                j += 64;
+                lhs += 64 * lts;
+                off = offb + step32;
+                f = fb + r32;
                 if (f >= D) { f -= D; off += ns; }
             }
             if (COUNT && vis && D > 1) nsteps += (unsigned long long)(D - 1);
@@ -675,8 +685,8 @@ static int vix_launch_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, 
                            uint8_t *vix_out, unsigned long long *steps, void *ws, size_t ws_bytes,
                            cudaStream_t s, int NR) {
     const long long pitcht = vix_pitcht(g.H);
-    // offsets along a line are 32-bit
-    if ((long long)(2 * R + 64) * std::max<long long>(g.pitch, pitcht) >= (1ll << 31)) return VS_ERR_RANGE;
+    // offsets along a line (up to crossing D + 95, D <= 1.42 R) are 32-bit
+    if ((long long)(3 * R + 128) * std::max<long long>(g.pitch, pitcht) >= (1ll << 31)) return VS_ERR_RANGE;
     const size_t need = (size_t)g.W * (size_t)pitcht * 2 + 256;
     int16_t *zt = nullptr;
     if (ws && ws_bytes >= need) {
