@@ -547,7 +547,7 @@ def run_paper(args, dist, rank, world, local):
     import __graft_entry__
     __graft_entry__.build()
     import paper_2006_16783_gb300 as V
-    w = WL.PAPER if args.workload == "paper" else WL.PAPER_MID
+    w = {"paper": WL.PAPER, "paper_mid": WL.PAPER_MID, "paper_small": WL.PAPER_SMALL}[args.workload]
     t = time.perf_counter()
     z = w.make_terrain(dev)
     zs, _ = WL.terrain.pad_pitch(z, 8)
@@ -631,7 +631,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="full",
-                    choices=["full", "mid", "scale", "small", "batch", "learn", "paper", "paper_mid"])
+                    choices=["full", "mid", "scale", "small", "batch", "learn", "paper", "paper_mid",
+                             "paper_small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
@@ -656,7 +657,7 @@ def main():
     if args.workload == "learn":
         run_learn(args, rank, local)
         return
-    if args.workload in ("paper", "paper_mid"):
+    if args.workload in ("paper", "paper_mid", "paper_small"):
         if args.impl == "reference":
             if rank == 0:
                 print(json.dumps({"impl": "reference", "unavailable": "the paper-regime workload has no bounded "

@@ -155,18 +155,16 @@ __device__ void vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long 
                 const int gx = xmaj ? gmaj : gmin, gy = xmaj ? gmin : gmaj;
                 if ((unsigned)gx >= (unsigned)J.W || (unsigned)gy >= (unsigned)J.H) break;
                 if (k2 + rnd * rnd > R * R) break;
+                // the straddling posts: the tested cell and, off a post, the
+                // other one (inside the staged window even where it leaves the
+                // grid), both loads issued before the test
                 const int zc = win[a0 + (rb ? amin : 0)];
+                const int zo = f > 0 ? (int)win[a0 + (rb ? 0 : amin)] : zc;
                 const bool vis = (Hk == 0) || ((T)(zc + hre) * R * Hk >= Hn * k);
                 if (vis) atomicOr(&bms[(gy - cy + R) * PRs + ((gx >> 5) - gw0)], 1u << (gx & 31));
                 const int m0 = omin + y0;
                 if (f > 0 && (m0 < 0 || m0 + 1 >= minor_lim)) break;
-                // the straddling posts: the tested cell and, off a post, the other one
-                int z0 = zc, z1 = zc;
-                if (f > 0) {
-                    const int zo = win[a0 + (rb ? 0 : amin)];
-                    z0 = rb ? zo : zc;
-                    z1 = rb ? zc : zo;
-                }
+                const int z0 = rb ? zo : zc, z1 = rb ? zc : zo;
                 const T num = (T)z0 * (R - f) + (T)z1 * f - eyeR;
                 if (Hk == 0 || num * Hk > Hn * k) { Hn = num; Hk = k; }
             }
@@ -259,9 +257,12 @@ __global__ void __launch_bounds__(512) k_viewshed_batch(const __grid_constant__ 
 // the terrain, so that neighbouring rays -- neighbouring threads -- read
 // neighbouring addresses, as the north and south sides (y-major) do in the
 // terrain itself.  Each band's visible cells collect in a shared-memory tile
-// (east / west: every window row x 4 words = 128 columns; north / south: 128
-// window rows x every word) that is then ORed into the candidate's bitmap in
-// global memory.  The arithmetic is that of vs_candidate: the same cells, the
+// that is then ORed into the candidate's bitmap in global memory.  East / west:
+// every window row x 4 words (128 columns), neighbouring rays on neighbouring
+// rows.  North / south: 32 window rows stored by column -- one word per column,
+// bit i = row i of the band -- so that neighbouring rays, which share a row,
+// set bits of neighbouring words rather than the same word; the merge turns
+// each 32 x 32 block back into row words with a warp-shuffle bit transpose.  The arithmetic is that of vs_candidate: the same cells, the
 // same rounding and the same horizon test, so the bitmaps are identical.
 // Values stay in 32 bits with 64-bit products, exact for every accepted input:
 // |z*R + (hr - eye)*R| <= (65535 + 2*100000)*4096 < 2^31 and the interpolated
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(512) k_viewshed_batch(const __grid_constant__ 
 constexpr int kWideThreads = 1024;
 constexpr int kWideTW = 4;    // east / west tile: words per window row
 constexpr int kWideTP = 5;    // its row pitch, odd: neighbouring rows in other banks
-constexpr int kWideBN = 128;  // north / south tile: window rows per band
+constexpr int kWideBN = 32;   // north / south tile: window rows per band (bits of a column word)
 
 struct VsWide {
     const int16_t *z;
@@ -300,12 +301,27 @@ __global__ void __launch_bounds__(256) k_transpose_i16(const int16_t *__restrict
     }
 }
 
+// 32 x 32 bit transpose across a warp: lane l holds row l of a bit matrix
+// (bit i = column i) and gets column l (bit i = row i); five rounds of block
+// swaps between lanes l and l ^ j
+__device__ __forceinline__ uint32_t warp_bit_transpose(uint32_t a) {
+    const int lane = threadIdx.x & 31;
+    uint32_t m = 0x0000FFFFu;
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        const uint32_t o = __shfl_xor_sync(0xffffffffu, a, j);
+        a = (lane & j) ? ((a & ~m) | ((o >> j) & m)) : ((a & m) | ((o << j) & ~m));
+        m ^= m << (j >> 1);
+    }
+    return a;
+}
+
 __global__ void __launch_bounds__(kWideThreads) k_viewshed_wide(const VsWide P) {
     extern __shared__ __align__(16) uint32_t tile[];
     __shared__ int red[32];
     const int tid = threadIdx.x, nt = blockDim.x;
     const long long c = blockIdx.x;
-    const int R = P.R, PR = P.PR, PRs = PR | 1;
+    const int R = P.R, PR = P.PR;
     const int64_t p = P.cand[c];
     uint32_t *out = P.bm + c * (long long)P.words;
     for (int i = tid; i < P.words; i += nt) out[i] = 0u;
@@ -368,7 +384,7 @@ __global__ void __launch_bounds__(kWideThreads) k_viewshed_wide(const VsWide P) 
                     for (int i = tid; i < (rhi - rlo + 1) * kWideTW; i += nt)
                         tile[(rlo + i / kWideTW) * kWideTP + (i % kWideTW)] = 0u;
                 } else {
-                    for (int i = tid; i < nrow * PRs; i += nt) tile[i] = 0u;
+                    for (int i = tid; i < PR * 32; i += nt) tile[i] = 0u;
                 }
                 __syncthreads();
                 if (alive) {
@@ -385,25 +401,24 @@ __global__ void __launch_bounds__(kWideThreads) k_viewshed_wide(const VsWide P) 
                             alive = false;
                             break;
                         }
+                        // both straddling posts loaded before the test; the
+                        // other post only where it lies inside the grid
+                        const int m0 = omin + y0;
+                        const bool stop = f > 0 && (m0 < 0 || m0 + 1 >= minor_lim);
                         const int zc = __ldg(base + a0 + rb);
+                        const int zo = (f > 0 && !stop) ? (int)__ldg(base + a0 + (rb ? 0 : 1)) : zc;
                         const bool vis = (Hk == 0) || ((long long)(zc * R + hreR) * Hk >= (long long)Hn * k);
                         if (vis) {
                             if (xmaj)
                                 atomicOr(&tile[(rnd + R) * kWideTP + ((gmaj >> 5) - bw0)], 1u << (gmaj & 31));
                             else
-                                atomicOr(&tile[(k - klo) * PRs + ((gmin >> 5) - gw0)], 1u << (gmin & 31));
+                                atomicOr(&tile[gmin - 32 * gw0], 1u << (k - klo));
                         }
-                        const int m0 = omin + y0;
-                        if (f > 0 && (m0 < 0 || m0 + 1 >= minor_lim)) {
+                        if (stop) {
                             alive = false;
                             break;
                         }
-                        int z0 = zc, z1 = zc;
-                        if (f > 0) {
-                            const int zo = __ldg(base + a0 + (rb ? 0 : 1));
-                            z0 = rb ? zo : zc;
-                            z1 = rb ? zc : zo;
-                        }
+                        const int z0 = rb ? zo : zc, z1 = rb ? zc : zo;
                         const int num = z0 * (R - f) + z1 * f - eyeR;
                         if (Hk == 0 || (long long)num * Hk > (long long)Hn * k) { Hn = num; Hk = k; }
                     }
@@ -418,10 +433,12 @@ __global__ void __launch_bounds__(kWideThreads) k_viewshed_wide(const VsWide P) 
                         if (t && w >= 0 && w < PR) out[(long long)r * PR + w] |= t;
                     }
                 } else {
-                    for (int i = tid; i < nrow * PR; i += nt) {
-                        const int ri = i / PR, w = i - ri * PR;
-                        const uint32_t t = tile[ri * PRs + w];
-                        if (t) out[(long long)(R + smaj * (klo + ri)) * PR + w] |= t;
+                    // warp per word column: transpose its 32 x 32 block, lane i
+                    // holds window row klo + i
+                    const int lane = tid & 31;
+                    for (int w = tid >> 5; w < PR; w += nt >> 5) {
+                        const uint32_t t = warp_bit_transpose(tile[32 * w + lane]);
+                        if (t && lane < nrow) out[(long long)(R + smaj * (klo + lane)) * PR + w] |= t;
                     }
                 }
             }
@@ -444,7 +461,7 @@ __global__ void __launch_bounds__(kWideThreads) k_viewshed_wide(const VsWide P) 
 
 static size_t wide_smem_bytes(int R) {
     const size_t ew = (size_t)(2 * R + 1) * kWideTP;
-    const size_t ns = (size_t)kWideBN * (words_per_row(R) | 1);
+    const size_t ns = (size_t)32 * words_per_row(R);
     return std::max(ew, ns) * 4;
 }
 

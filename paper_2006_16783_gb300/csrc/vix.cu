@@ -532,8 +532,12 @@ __device__ void vix_tables(int R, int *rowstart, int *hwtab, int *warp_tot) {
     __syncthreads();
 }
 
+// 512 threads = 16 warps = a 32 x 16 tile of posts; three CTAs per SM (48 warps)
+// to hide the cache latency of the line walks
+constexpr int kVixWideThreads = 512;
+
 template <bool COUNT>
-__global__ void __launch_bounds__(kVixThreads) k_vix_wide(const VixWide P) {
+__global__ void __launch_bounds__(kVixWideThreads, 3) k_vix_wide(const VixWide P) {
     extern __shared__ int vix_tab[];
     __shared__ int warp_tot[32];
     const int R = P.R;
@@ -541,7 +545,7 @@ __global__ void __launch_bounds__(kVixThreads) k_vix_wide(const VixWide P) {
     int *hwtab = vix_tab + 2 * R + 2;   // 2R + 1 entries
     vix_tables(R, rowstart, hwtab, warp_tot);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int x0 = blockIdx.x * 32, y = blockIdx.y * 32 + wid;
+    const int x0 = blockIdx.x * 32, y = blockIdx.y * (kVixWideThreads / 32) + wid;
     const int x = x0 + lane;
     if (y >= P.H) return;  // whole warp: no block barrier follows
     const bool mine = x < P.W;
@@ -700,13 +704,14 @@ static int vix_launch_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, 
     P.H = g.H; P.W = g.W; P.R = R; P.ht = ht; P.hr = hr; P.S = S; P.NR = NR;
     P.seed = seed; P.out = vix_out; P.steps = steps;
     const size_t smem = (size_t)(4 * R + 3) * 4;
-    const dim3 grid((unsigned)((g.W + 31) / 32), (unsigned)((g.H + 31) / 32));
+    const int rows = kVixWideThreads / 32;
+    const dim3 grid((unsigned)((g.W + 31) / 32), (unsigned)((g.H + rows - 1) / rows));
     if (steps) {
         VS_CUDA_TRY(cudaFuncSetAttribute(k_vix_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_vix_wide<true><<<grid, kVixThreads, smem, s>>>(P);
+        k_vix_wide<true><<<grid, kVixWideThreads, smem, s>>>(P);
     } else {
         VS_CUDA_TRY(cudaFuncSetAttribute(k_vix_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_vix_wide<false><<<grid, kVixThreads, smem, s>>>(P);
+        k_vix_wide<false><<<grid, kVixWideThreads, smem, s>>>(P);
     }
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;

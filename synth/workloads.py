@@ -90,6 +90,12 @@ MID = Workload("mid_11600sq_R100", 11600, 11600, 100, 10, 10, 10, 464, 4, 1024, 
 PAPER = Workload("paper_uswest_46400sq_R1000", 46400, 46400, 1000, 100, 10, 10, 334, 20, 20000,
                  seed=1004, kind="ridged", zmax=4000, lake_frac=0.05, target=0.95,
                  extra={"octaves": 10, "base_wavelength": 640})
+# the same regime on 4096^2 (13 x 13 blocks, 3,380 candidates, 1.7 GB of bitmaps): a
+# size for profiler captures (the terrain fits in L2; the kernels it is used for
+# are bound by issue and cache latency, not DRAM)
+PAPER_SMALL = Workload("paper_regime_4096sq_R1000", 4096, 4096, 1000, 100, 10, 10, 334, 20, 20000,
+                       seed=1004, kind="ridged", zmax=4000, lake_frac=0.05, target=0.95,
+                       extra={"octaves": 10, "base_wavelength": 640})
 # the same regime on 16384^2 (49 x 50 blocks, 49,000 candidates, 25 GB of bitmaps)
 PAPER_MID = Workload("paper_regime_16384sq_R1000", 16384, 16384, 1000, 100, 10, 10, 334, 20, 20000,
                      seed=1004, kind="ridged", zmax=4000, lake_frac=0.05, target=0.95,
