@@ -624,6 +624,102 @@ def run_paper(args, dist, rank, world, local):
         print(json.dumps(out, default=str))
 
 
+def run_accuracy(args, dist, rank, world, local):
+    """The accuracy study of the paper's closing section (sensitivity of the
+    result to lowered accuracy in the data) and of its R2 / R3 discussion, on
+    the headline workload's recipe:
+      - cells where the ray-sweep viewshed (vs_viewshed, R2-style) and the
+        exact per-cell viewshed (vs_viewshed_r3) disagree, over all candidates;
+      - the exact (R3) coverage of the observers sited with R2 bitmaps against
+        observers sited with R3 bitmaps;
+      - the exact coverage on the true terrain of observers sited on the
+        terrain rounded to q metres (q = 10, 50, 200)."""
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2006_16783_gb300 as V
+    w = WL.FULL if args.accuracy_size == "full" else WL.MID
+    t0 = time.perf_counter()
+    z = w.make_terrain(dev)
+    zs, _ = WL.terrain.pad_pitch(z, 8)
+    del z
+    g = V.Grid(zs, w.W)
+    pipe = Pipeline(V, w, g, dev)
+
+    def site_cov(bm, cand):
+        cum = torch.zeros_like(pipe.cum)
+        res = V.site(bm, cand, w.H, w.W, w.R, w.n_obs, cum=cum, ws=pipe.ws, sync=False)
+        return res
+
+    def union_cov(bm, cand, chosen):
+        """Exact coverage of a fixed observer set: the union of their bitmaps
+        (a greedy run over just those candidates picks every one that adds)."""
+        idx = torch.nonzero(torch.isin(cand, chosen)).reshape(-1)
+        cum = torch.zeros_like(pipe.cum)
+        res = V.site(bm[idx].contiguous(), cand[idx].contiguous(), w.H, w.W, w.R, int(idx.numel()), cum=cum,
+                     ws=pipe.ws, sync=False)
+        return coverage(res)[0]
+
+    # R2 pipeline on the true terrain
+    pipe.step()
+    torch.cuda.synchronize()
+    cand = pipe.cand.clone()
+    bm2 = pipe.bm
+    ch2, gn2, _, n2 = pipe.result
+    ch2 = ch2[:int(n2.item())].clone()
+    cov2_r2 = int(gn2[:int(n2.item())].sum().item())
+    # R3 bitmaps of the same candidates
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    bm3, area3 = V.viewshed_r3(g, w.R, w.ht, w.hr, cand)
+    e1.record()
+    torch.cuda.synchronize()
+    r3_ms = e0.elapsed_time(e1)
+    b2 = bm2.view(torch.int32)
+    b3 = bm3.view(torch.int32)
+    def popc(t):  # bits set, counted on the device (measurement only)
+        u = t.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        c = torch.zeros_like(u)
+        for sh in range(32):
+            c += (u >> sh) & 1
+        return int(c.sum().item())
+    only2 = popc(b2 & ~b3)
+    only3 = popc(b3 & ~b2)
+    both = popc(b2 & b3)
+    res3 = site_cov(bm3, cand)
+    cov3_r3, n3 = coverage(res3)
+    cov2_r3 = union_cov(bm3, cand, ch2)
+    out_q = {}
+    for q in (10, 50, 200):
+        zq = (torch.round(zs.float() / q) * q).clamp(-32768, 32767).to(torch.int16)
+        gq = V.Grid(zq, w.W)
+        pq = Pipeline(V, w, gq, dev)
+        pq.step()
+        torch.cuda.synchronize()
+        chq, gnq, _, nq = pq.result
+        chq = chq[:int(nq.item())]
+        # exact coverage on the true terrain of the observers sited on the rounded one
+        bq3, _ = V.viewshed_r3(g, w.R, w.ht, w.hr, chq.contiguous())
+        cum = torch.zeros_like(pipe.cum)
+        resq = V.site(bq3, chq.contiguous(), w.H, w.W, w.R, int(chq.numel()), cum=cum, ws=pipe.ws, sync=False)
+        out_q[str(q)] = {"observers": int(chq.numel()), "exact_coverage_posts": coverage(resq)[0],
+                         "vs_true_terrain_R2_sited": coverage(resq)[0] / max(cov2_r3, 1)}
+        del pq, gq, zq, bq3
+    out = {"metric": "accuracy study (R2 vs exact R3 viewsheds; rounded elevations)", "workload": w.name,
+           "config": {"H": w.H, "W": w.W, "R": w.R, "ht": w.ht, "hr": w.hr, "candidates": int(cand.numel()),
+                      "n_obs": w.n_obs},
+           "cells": {"R2_and_R3": both, "R2_only": only2, "R3_only": only3,
+                     "disagree_frac": (only2 + only3) / max(both + only2 + only3, 1)},
+           "coverage": {"R2_sited_R2_counted": cov2_r2, "R2_sited_exact": cov2_r3, "R3_sited_exact": cov3_r3,
+                        "R2_sited_vs_R3_sited_exact": cov2_r3 / max(cov3_r3, 1),
+                        "observers_R2": int(ch2.numel()), "observers_R3": n3},
+           "rounded_terrain": out_q, "r3_viewsheds_ms": r3_ms,
+           "r3_viewsheds_per_s": cand.numel() / (r3_ms * 1e-3), "wall_s": time.perf_counter() - t0}
+    if rank == 0:
+        print(json.dumps(out, default=str))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -632,7 +728,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="full",
                     choices=["full", "mid", "scale", "small", "batch", "learn", "paper", "paper_mid",
-                             "paper_small"])
+                             "paper_small", "accuracy"])
+    ap.add_argument("--accuracy-size", default="full", choices=["full", "mid"],
+                    help="terrain of --workload accuracy: the headline recipe at 46400^2 or 11600^2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
@@ -656,6 +754,13 @@ def main():
         return
     if args.workload == "learn":
         run_learn(args, rank, local)
+        return
+    if args.workload == "accuracy":
+        if args.impl == "reference":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the accuracy study has no oracle arm"}))
+            return
+        run_accuracy(args, dist, rank, world, local)
         return
     if args.workload in ("paper", "paper_mid", "paper_small"):
         if args.impl == "reference":

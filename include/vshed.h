@@ -214,6 +214,22 @@ size_t vs_viewshed_workspace(int32_t H, int32_t W, int32_t R, int64_t n);
 int vs_viewshed(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand, int64_t n,
                 uint32_t *bm_out, int32_t *area_out, void *ws, size_t ws_bytes, vs_stream_t st);
 
+/* Exact per-cell viewshed (the "R3" of the siting literature): every cell
+ * of disc(R) inside the grid gets its own line of sight from the observer,
+ * tested exactly as a vix sample (Sec. "Terrain visibility": the LOS against
+ * the terrain interpolated between the two posts it passes between, grazing
+ * lines visible, receiver at z + hr) -- the viewshed of Sec. "Definitions"
+ * read literally, against which vs_viewshed's ray sweep (R2-style) is an
+ * approximation.  Same arguments, output layout and errors as vs_viewshed.
+ * Costs ~0.6*pi*R^3 crossings per candidate (vs_viewshed: ~7R^2 steps): an
+ * accuracy reference, not the siting path.  ws: optional, at least
+ * vs_viewshed_r3_workspace(H, W) bytes for a transposed copy of the terrain
+ * (y-major lines then read contiguous memory); NULL or smaller: strided reads,
+ * same results.  Needs (3R + 128) * max(pitch, ceil8(H)) < 2^31. */
+size_t vs_viewshed_r3_workspace(int32_t H, int32_t W);
+int vs_viewshed_r3(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand, int64_t n,
+                   uint32_t *bm_out, int32_t *area_out, void *ws, size_t ws_bytes, vs_stream_t st);
+
 /* Batched viewsheds: the candidates of up to 64 terrains (different sizes,
  * ROIs, heights) in ONE persistent launch.  jobs is a HOST array read during
  * the call; each job is exactly the arguments of one vs_viewshed call, and

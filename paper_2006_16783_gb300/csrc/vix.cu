@@ -532,6 +532,70 @@ __device__ void vix_tables(int R, int *rowstart, int *hwtab, int *warp_tot) {
     __syncthreads();
 }
 
+// One line of sight from post (ox, oy) with eye E to the post (ox+dx, oy+dy),
+// walked by the whole warp: lane l takes crossings j0 + l, two chunks of 32
+// per trip (the second chunk's loads in flight before the first chunk's vote).
+// ts = z_T + hr - E.  Visible iff j*ts >= (z0 - E)*D + (z1 - z0)*f at every
+// crossing j = 1 .. D-1 (Sec. "Terrain visibility": the LOS against the
+// terrain interpolated linearly between the two posts it passes between).
+// x-major lines read terrain rows, y-major lines the transposed terrain when
+// given (else the terrain with a row stride).  Every lane returns the same
+// result; with COUNT, nsteps grows by the crossings evaluated (the first
+// blocked one, else D - 1), identically in every lane.
+template <bool COUNT>
+__device__ __forceinline__ bool warp_los(const int16_t *z, long long pitch, const int16_t *zt, long long pitcht,
+                                         int ox, int oy, int E, int dx, int dy, int ts,
+                                         unsigned long long &nsteps) {
+    const int lane = threadIdx.x & 31;
+    const int adx = abs(dx), ady = abs(dy);
+    const bool xmaj = adx >= ady;
+    const int D = xmaj ? adx : ady;
+    const int dmin = xmaj ? dy : dx;
+    const int sg = xmaj ? (dx > 0 ? 1 : -1) : (dy > 0 ? 1 : -1);
+    // strides along the major (ms) and minor (ns) axes of the array read
+    const int16_t *bp;
+    int ms, ns;
+    if (xmaj) { bp = z + (long long)oy * pitch + ox; ms = 1; ns = (int)pitch; }
+    else if (zt) { bp = zt + (long long)ox * pitcht + oy; ms = 1; ns = (int)pitcht; }
+    else { bp = z + (long long)oy * pitch + ox; ms = (int)pitch; ns = 1; }
+    // this lane's first crossing j = 1 + lane
+    int j = 1 + lane;
+    const int yq = floordiv(j * dmin, D);
+    int f = j * dmin - yq * D;
+    int off = j * sg * ms + yq * ns;
+    const int q32 = floordiv(32 * dmin, D), r32 = 32 * dmin - q32 * D;
+    const int step32 = 32 * sg * ms + q32 * ns;
+    int lhs = j * ts;
+    for (int j0 = 1; j0 < D; j0 += 64) {
+        int fb = f + r32, offb = off + step32;
+        if (fb >= D) { fb -= D; offb += ns; }
+        int z0a = 0, z1a = 0, z0b = 0, z1b = 0;
+        if (j < D) {
+            z0a = __ldg(bp + off);
+            z1a = f ? (int)__ldg(bp + off + ns) : z0a;
+        }
+        if (j + 32 < D) {
+            z0b = __ldg(bp + offb);
+            z1b = fb ? (int)__ldg(bp + offb + ns) : z0b;
+        }
+        const bool ba = j < D && lhs < (z0a - E) * D + (z1a - z0a) * f;
+        const bool bb = j + 32 < D && lhs + 32 * ts < (z0b - E) * D + (z1b - z0b) * fb;
+        const unsigned va = __ballot_sync(0xffffffffu, ba);
+        const unsigned vb = __ballot_sync(0xffffffffu, bb);
+        if (va | vb) {
+            if (COUNT) nsteps += (unsigned long long)(va ? j0 + __ffs(va) - 1 : j0 + 32 + __ffs(vb) - 1);
+            return false;
+        }
+        j += 64;
+        lhs += 64 * ts;
+        off = offb + step32;
+        f = fb + r32;
+        if (f >= D) { f -= D; off += ns; }
+    }
+    if (COUNT && D > 1) nsteps += (unsigned long long)(D - 1);
+    return true;
+}
+
 // 512 threads = 16 warps = a 32 x 16 tile of posts; three CTAs per SM (48 warps)
 // to hide the cache latency of the line walks
 constexpr int kVixWideThreads = 512;
@@ -571,63 +635,82 @@ __global__ void __launch_bounds__(kVixWideThreads, 3) k_vix_wide(const VixWide P
             todo &= todo - 1;
             const int ldx = __shfl_sync(0xffffffffu, dx, src), ldy = __shfl_sync(0xffffffffu, dy, src);
             const int lE = __shfl_sync(0xffffffffu, E, src), lts = __shfl_sync(0xffffffffu, tsl, src);
-            const int lx = x0 + src;
-            const int adx = abs(ldx), ady = abs(ldy);
-            const bool xmaj = adx >= ady;
-            const int D = xmaj ? adx : ady;
-            const int dmin = xmaj ? ldy : ldx;
-            const int sg = xmaj ? (ldx > 0 ? 1 : -1) : (ldy > 0 ? 1 : -1);
-            // strides along the major (ms) and minor (ns) axes of the array read
-            const int16_t *bp;
-            int ms, ns;
-            if (xmaj) { bp = zrow + lx; ms = 1; ns = (int)P.pitch; }
-            else if (P.zt) { bp = P.zt + (long long)lx * P.pitcht + y; ms = 1; ns = (int)P.pitcht; }
-            else { bp = zrow + lx; ms = (int)P.pitch; ns = 1; }
-            // this lane's first crossing j = 1 + lane
-            int j = 1 + lane;
-            const int yq = floordiv(j * dmin, D);
-            int f = j * dmin - yq * D;
-            int off = j * sg * ms + yq * ns;
-            const int q32 = floordiv(32 * dmin, D), r32 = 32 * dmin - q32 * D;
-            const int step32 = 32 * sg * ms + q32 * ns;
-            int lhs = j * lts;
-            bool vis = true;
-            // two chunks of 32 crossings per trip: the second chunk's loads are
-            // in flight before the first chunk's vote
-            for (int j0 = 1; j0 < D; j0 += 64) {
-                int fb = f + r32, offb = off + step32;
-                if (fb >= D) { fb -= D; offb += ns; }
-                int z0a = 0, z1a = 0, z0b = 0, z1b = 0;
-                if (j < D) {
-                    z0a = __ldg(bp + off);
-                    z1a = f ? (int)__ldg(bp + off + ns) : z0a;
-                }
-                if (j + 32 < D) {
-                    z0b = __ldg(bp + offb);
-                    z1b = fb ? (int)__ldg(bp + offb + ns) : z0b;
-                }
-                const bool ba = j < D && lhs < (z0a - lE) * D + (z1a - z0a) * f;
-                const bool bb2 = j + 32 < D && lhs + 32 * lts < (z0b - lE) * D + (z1b - z0b) * fb;
-                const unsigned va = __ballot_sync(0xffffffffu, ba);
-                const unsigned vb = __ballot_sync(0xffffffffu, bb2);
-                if (va | vb) {
-                    vis = false;
-                    if (COUNT) nsteps += (unsigned long long)(va ? j0 + __ffs(va) - 1 : j0 + 32 + __ffs(vb) - 1);
-                    break;
-                }
-                j += 64;
-                lhs += 64 * lts;
-                off = offb + step32;
-                f = fb + r32;
-                if (f >= D) { f -= D; off += ns; }
-            }
-            if (COUNT && vis && D > 1) nsteps += (unsigned long long)(D - 1);
+            const bool vis = warp_los<COUNT>(P.z, P.pitch, P.zt, P.pitcht, x0 + src, y, lE, ldx, ldy, lts, nsteps);
             if (vis) visbits |= 1u << src;
         }
         cnt += (visbits >> lane) & 1u;
     }
     if (mine) P.out[(size_t)y * P.W + x] = (uint8_t)cnt;
     if (COUNT && lane == 0 && nsteps) atomicAdd(P.steps, nsteps);  // every lane counted the same lines
+}
+
+// ------------------------------------------------------------------ exact per-cell viewshed (R3)
+// Every cell of the ROI disc inside the grid gets its own line of sight from
+// the observer (warp_los: the vix test, target height z + hr) -- the viewshed
+// as defined in Sec. "Definitions", of which the ray sweep of vs_viewshed
+// (R2-style, Sec. "The multiple transmitter siting process", Viewshed) is an
+// approximation.  CTA per candidate; a warp takes one bitmap word at a time --
+// 32 cells of one row, one line each, walked by the whole warp in turn -- and
+// the ballot of their results is the word.  Output layout as vs_viewshed.
+struct VsR3 {
+    const int16_t *z;
+    long long pitch;
+    const int16_t *zt;  // transposed terrain or null
+    long long pitcht;
+    int H, W, R, ht, hr, PR, words;
+    const int64_t *cand;
+    long long n;
+    uint32_t *bm;
+    int32_t *area;
+};
+
+constexpr int kR3Threads = 512;
+
+__global__ void __launch_bounds__(kR3Threads) k_viewshed_r3(const VsR3 P) {
+    __shared__ int red[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const long long c = blockIdx.x;
+    const int R = P.R, PR = P.PR;
+    const int64_t p = P.cand[c];
+    uint32_t *out = P.bm + c * (long long)P.words;
+    if (p < 0 || p >= (int64_t)P.H * P.W) {  // invalid candidate: empty bitmap, area -1
+        for (int i = tid; i < P.words; i += blockDim.x) out[i] = 0u;
+        if (tid == 0) P.area[c] = -1;
+        return;
+    }
+    const int cx = (int)(p % P.W), cy = (int)(p / P.W);
+    const int gw0 = floordiv(cx - R, 32);
+    const int E = (int)P.z[(long long)cy * P.pitch + cx] + P.ht;
+    int cnt = 0;
+    unsigned long long unused = 0;
+    for (int item = wid; item < P.words; item += nw) {
+        const int r = item / PR, w = item - r * PR;
+        const int dy = r - R, y = cy + dy;
+        const int col = 32 * (gw0 + w) + lane, dx = col - cx;
+        const bool in = (unsigned)y < (unsigned)P.H && (unsigned)col < (unsigned)P.W && dx * dx + dy * dy <= R * R;
+        const bool self = dx == 0 && dy == 0;
+        int ts = 0;
+        if (in && !self) ts = (int)__ldg(P.z + (long long)y * P.pitch + col) + P.hr - E;
+        unsigned todo = __ballot_sync(0xffffffffu, in && !self);
+        unsigned bits = __ballot_sync(0xffffffffu, in && self);  // the observer's own cell
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int ldx = __shfl_sync(0xffffffffu, dx, src), lts = __shfl_sync(0xffffffffu, ts, src);
+            if (warp_los<false>(P.z, P.pitch, P.zt, P.pitcht, cx, cy, E, ldx, dy, lts, unused)) bits |= 1u << src;
+        }
+        if (lane == 0) {
+            out[item] = bits;
+            cnt += __popc(bits);
+        }
+    }
+    if (lane == 0) red[wid] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+        int a = 0;
+        for (int i = 0; i < nw; ++i) a += red[i];
+        P.area[c] = a;
+    }
 }
 
 static size_t vix2_smem_bytes(int R, int nsplit, int TX, int TY, int sb, int *WG, int *box_rows,
@@ -826,4 +909,40 @@ extern "C" size_t vs_vix_workspace(int32_t H, int32_t W, int32_t R, int32_t S) {
 extern "C" int vs_vix_ws(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
                          uint8_t *vix_out, uint64_t *los_steps, void *ws, size_t ws_bytes, vs_stream_t st) {
     return vix_launch(g, R, ht, hr, S, seed, vix_out, (unsigned long long *)los_steps, ws, ws_bytes, st);
+}
+
+extern "C" size_t vs_viewshed_r3_workspace(int32_t H, int32_t W) {
+    if (H < 1 || W < 1 || H > kMaxH || W > kMaxH) return 0;
+    return (size_t)W * (size_t)vix_pitcht(H) * 2 + 256;
+}
+
+extern "C" int vs_viewshed_r3(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand, int64_t n,
+                              uint32_t *bm_out, int32_t *area_out, void *ws, size_t ws_bytes, vs_stream_t st) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (R < 1 || R > kMaxR) return VS_ERR_RANGE;
+    if (ht < -100000 || ht > 100000 || hr < -100000 || hr > 100000) return VS_ERR_RANGE;
+    if (n < 0 || n > 0x7fffffffll) return VS_ERR_RANGE;
+    if (n > 0 && (!cand || !bm_out || !area_out)) return VS_ERR_ARG;
+    const long long pitcht = vix_pitcht(g.H);
+    if ((long long)(3 * R + 128) * std::max<long long>(g.pitch, pitcht) >= (1ll << 31)) return VS_ERR_RANGE;
+    if (n == 0) return VS_OK;
+    if ((rc = check_device())) return rc;
+    cudaStream_t s = (cudaStream_t)st;
+    VsR3 P;
+    P.z = g.z; P.pitch = g.pitch; P.zt = nullptr; P.pitcht = pitcht;
+    P.H = g.H; P.W = g.W; P.R = R; P.ht = ht; P.hr = hr;
+    P.PR = (2 * R) / 32 + 2;
+    P.words = (2 * R + 1) * P.PR;
+    P.cand = cand; P.n = n; P.bm = bm_out; P.area = area_out;
+    if (ws && ws_bytes >= vs_viewshed_r3_workspace(g.H, g.W)) {
+        int16_t *zt = (int16_t *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+        const dim3 tg((unsigned)((g.W + 31) / 32), (unsigned)((g.H + 31) / 32));
+        k_transpose_i16_vix<<<tg, 256, 0, s>>>(g.z, g.pitch, g.H, g.W, zt, pitcht);
+        VS_CUDA_TRY(cudaGetLastError());
+        P.zt = zt;
+    }
+    k_viewshed_r3<<<(unsigned)n, kR3Threads, 0, s>>>(P);
+    VS_CUDA_TRY(cudaGetLastError());
+    return VS_OK;
 }

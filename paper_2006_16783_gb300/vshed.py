@@ -68,6 +68,8 @@ SIGNATURES = {
     "vs_bitmap_words": (i64, [i32]),
     "vs_viewshed_workspace": (sz, [i32, i32, i32, i64]),
     "vs_viewshed": (ctypes.c_int, [vs_grid, i32, i32, i32, P, i64, P, P, P, sz, P]),
+    "vs_viewshed_r3_workspace": (sz, [i32, i32]),
+    "vs_viewshed_r3": (ctypes.c_int, [vs_grid, i32, i32, i32, P, i64, P, P, P, sz, P]),
     "vs_site_workspace": (sz, [i64, i32]),
     "vs_site": (ctypes.c_int, [P, P, i64, i32, i32, i32, i32, f64, P, P, P, P, P, sz, P]),
     "vs_site_gains": (ctypes.c_int, [P, P, i64, i32, i32, i32, P, P, P]),
@@ -246,6 +248,25 @@ def viewshed(g, R, ht, hr, cand, bm=None, area=None, ws=None):
         ws = torch.empty(wsb, dtype=torch.uint8, device=cand.device)
     _check("vs_viewshed", lib().vs_viewshed(g.c(), R, ht, hr, _ptr(cand), n, _ptr(bm), _ptr(area),
                                             _ptr(ws), wsb, _stream()))
+    return bm, area
+
+
+def viewshed_r3(g, R, ht, hr, cand, bm=None, area=None, ws=None):
+    """Exact per-cell viewshed (every disc cell its own LOS); same layout as
+    viewshed().  ws: optional uint8 device buffer for the transposed terrain
+    (allocated when missing)."""
+    _need_cuda(cand)
+    cand = cand.contiguous()
+    n = cand.numel()
+    if bm is None:
+        bm = torch.empty((n, 2 * R + 1, words_per_row(R)), dtype=torch.int32, device=cand.device)
+    if area is None:
+        area = torch.empty(n, dtype=torch.int32, device=cand.device)
+    wsb = lib().vs_viewshed_r3_workspace(g.H, g.W)
+    if ws is None or ws.numel() < wsb:
+        ws = torch.empty(wsb, dtype=torch.uint8, device=cand.device)
+    _check("vs_viewshed_r3", lib().vs_viewshed_r3(g.c(), R, ht, hr, _ptr(cand), n, _ptr(bm), _ptr(area),
+                                                  _ptr(ws), wsb, _stream()))
     return bm, area
 
 

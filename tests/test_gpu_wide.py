@@ -251,3 +251,44 @@ def test_paper_regime_pipeline(V, O):
     assert t == len(ch)
     assert _np(gch).tolist() == ch.tolist() and _np(ggn).tolist() == gn.tolist()
     assert (_np(gC).view(np.uint32) == C).all()
+
+
+# ------------------------------------------------------------------ exact per-cell viewshed (R3)
+@pytest.mark.parametrize("H,W,R,ht,hr,zr", [
+    (70, 90, 7, 10, 10, 300),
+    (160, 150, 30, 10, 10, 1200),
+    (260, 300, 100, 100, 10, 2000),
+    (420, 380, 300, 10, 10, 1500),    # beyond the staged windows
+])
+def test_viewshed_r3_parity(V, O, H, W, R, ht, hr, zr):
+    z = T.spectral_fbm(H, W, 0.8, 700 + R, 0, zr).numpy()
+    cand = _posts(H, W, 6, R)
+    g = _grid(V, z)
+    bm, area = V.viewshed_r3(g, R, ht, hr, torch.as_tensor(cand).cuda())
+    got = _np(bm).view(np.uint32)
+    for i, p in enumerate(cand):
+        want = O.viewshed_brute(z, R, ht, hr, int(p))
+        assert (got[i] == want).all(), (i, int(p))
+        assert int(_np(area)[i]) == int(np.unpackbits(want.view(np.uint8)).sum())
+    # without the transposed copy (strided reads): same bitmaps
+    bm2 = torch.empty_like(bm)
+    area2 = torch.empty_like(area)
+    c = torch.as_tensor(cand).cuda()
+    V.vshed._check("vs_viewshed_r3", V.vshed.lib().vs_viewshed_r3(
+        g.c(), R, ht, hr, V.vshed._ptr(c), c.numel(), V.vshed._ptr(bm2), V.vshed._ptr(area2), None, 0,
+        V.vshed._stream()))
+    assert (_np(bm2) == _np(bm)).all() and (_np(area2) == _np(area)).all()
+
+
+def test_viewshed_r3_flat_and_invalid(V, O):
+    """Flat terrain: every disc cell in the grid is visible (grazing lines
+    count); invalid candidates give empty bitmaps and area -1."""
+    H, W, R = 120, 140, 25
+    z = np.full((H, W), 300, np.int16)
+    cand = np.array([60 * W + 70, 0, -1, H * W], np.int64)
+    bm, area = V.viewshed_r3(_grid(V, z), R, 0, 0, torch.as_tensor(cand).cuda())
+    a = _np(area)
+    disc = sum(1 for dy in range(-R, R + 1) for dx in range(-R, R + 1) if dx * dx + dy * dy <= R * R)
+    assert a[0] == disc
+    assert a[1] == sum(1 for dy in range(0, R + 1) for dx in range(0, R + 1) if dx * dx + dy * dy <= R * R)
+    assert a[2] == -1 and a[3] == -1 and not _np(bm[2:]).any()
