@@ -57,6 +57,8 @@ def _load():
         "or_coverage_need": (i64, [f64, i32, i32]),
         "or_cum_popcount": (i64, [P, i32, i32]),
         "or_cum_rebuild": (None, [P, P, i64, i32, i32, i32, P]),
+        "or_intervisible": (ctypes.c_int, [P, i32, i32, i64, i32, i32, i64, i64]),
+        "or_site_ex": (i32, [P, P, i64, i32, i32, i32, i32, f64, P, i64, i32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -230,3 +232,32 @@ def cum_rebuild(bm, cand, H, W, R):
     C = np.zeros((H, cum_words_per_row(W)), np.uint32)
     _load().or_cum_rebuild(_p(bm), _p(cand), cand.shape[0], H, W, R, _p(C))
     return C
+
+
+# ---------------------------------------------------------------- site with constraints
+def intervisible(z, R, ht, pa, pb):
+    """Posts pa and pb within the ROI and the line between their antenna tops
+    (both z + ht) clear of the terrain."""
+    z, H, W, pitch = _grid(z)
+    return bool(_load().or_intervisible(_p(z), H, W, pitch, R, ht, int(pa), int(pb)))
+
+
+def site_ex(bm, cand, H, W, R, n_obs, target=0.0, z=None, ht=0, weight=None, cum=None):
+    """Plain greedy with the optional intervisibility constraint (terrain z
+    given: every transmitter after the first intervisible with one already
+    chosen) and optional uint8 receiver weights (H x W).  Returns (chosen,
+    gains, cum)."""
+    bm = np.ascontiguousarray(bm, dtype=np.uint32)
+    cand = np.ascontiguousarray(cand, dtype=np.int64)
+    n = cand.shape[0]
+    cum = np.zeros((H, cum_words_per_row(W)), np.uint32) if cum is None else np.array(cum, dtype=np.uint32)
+    chosen = np.zeros(max(n_obs, 1), np.int64)
+    gains = np.zeros(max(n_obs, 1), np.int64)
+    zp, pitch = None, 0
+    if z is not None:
+        zp, _, _, pitch = _grid(z)
+    wt = None if weight is None else np.ascontiguousarray(weight, dtype=np.uint8)
+    t = _load().or_site_ex(_p(bm), _p(cand), n, H, W, R, n_obs, float(target),
+                           _p(zp) if zp is not None else None, pitch, ht,
+                           _p(wt) if wt is not None else None, _p(chosen), _p(gains), _p(cum))
+    return chosen[:t], gains[:t], cum

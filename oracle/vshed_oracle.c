@@ -615,3 +615,101 @@ void or_cum_rebuild(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t 
     int64_t words = or_bitmap_words(R);
     for (int64_t c = 0; c < n; c++) or_into(bm + c * words, cand[c], H, W, R, cum);
 }
+
+/* ------------------------------------------------------------------ */
+/* Site with the constraints of Sec. "Prior art" (receivers of a given */
+/* quality; intervisibility, where transmitters must be visible from   */
+/* other transmitters).  Readings taken here:                          */
+/*  - intervisible(a, b): the two posts are within the ROI             */
+/*    (dx^2 + dy^2 <= R^2) and the line between the two antenna tops,  */
+/*    both at z + ht, clears the terrain (the or_los test with the     */
+/*    receiver height set to ht; the test is symmetric in a and b);    */
+/*  - with the constraint, the first transmitter of the call is free   */
+/*    and every later one must be intervisible with one already chosen */
+/*    in this call;                                                    */
+/*  - weighted receivers: post (x, y) weighs weight[y*W + x] (uint8),  */
+/*    the gain of a candidate is the weight of the posts it newly      */
+/*    covers, the coverage stop compares the covered weight with       */
+/*    ceil(target * total weight).                                    */
+/* Plain greedy: every step re-evaluates every eligible candidate;     */
+/* ties as in or_site_plain (largest gain, lowest post, lowest index). */
+/* z == NULL: no intervisibility constraint; weight == NULL: unit      */
+/* weights (then this is or_site_plain).                               */
+/* ------------------------------------------------------------------ */
+static int64_t wgain_of(const uint32_t *V, int64_t p, int32_t H, int32_t W, int32_t R,
+                        const uint32_t *cum, const uint8_t *weight)
+{
+    int64_t PR = (2 * R) / 32 + 2, WW = cum_words_per_row(W);
+    int64_t cx = p % W, cy = p / W, gw0 = floordiv64(cx - R, 32);
+    int64_t g = 0;
+    for (int64_t r = 0; r < 2 * R + 1; r++) {
+        int64_t y = cy - R + r;
+        if (y < 0 || y >= H) continue;
+        for (int64_t w = 0; w < PR; w++) {
+            int64_t gw = gw0 + w;
+            if (gw < 0 || gw >= WW) continue;
+            uint32_t d = V[r * PR + w] & ~cum[y * WW + gw];
+            for (int b = 0; b < 32; b++)
+                if ((d >> b) & 1u) g += weight ? weight[y * W + 32 * gw + b] : 1;
+        }
+    }
+    return g;
+}
+
+static int64_t wcovered(const uint32_t *cum, int32_t H, int32_t W, const uint8_t *weight)
+{
+    int64_t WW = cum_words_per_row(W), c = 0;
+    for (int64_t y = 0; y < H; y++)
+        for (int64_t gw = 0; gw < WW; gw++)
+            for (int b = 0; b < 32; b++)
+                if ((cum[y * WW + gw] >> b) & 1u) c += weight ? weight[y * W + 32 * gw + b] : 1;
+    return c;
+}
+
+int or_intervisible(const int16_t *z, int32_t H, int32_t W, int64_t pitch, int32_t R, int32_t ht,
+                    int64_t pa, int64_t pb)
+{
+    if (pa < 0 || pb < 0 || pa >= (int64_t)H * W || pb >= (int64_t)H * W) return 0;
+    int64_t ax = pa % W, ay = pa / W, bx = pb % W, by = pb / W;
+    int64_t dx = bx - ax, dy = by - ay;
+    if (dx * dx + dy * dy > (int64_t)R * R) return 0;
+    return or_los(z, H, W, pitch, (int32_t)ax, (int32_t)ay, (int32_t)bx, (int32_t)by, ht, ht);
+}
+
+int32_t or_site_ex(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W, int32_t R,
+                   int32_t n_obs, double target, const int16_t *z, int64_t pitch, int32_t ht,
+                   const uint8_t *weight, int64_t *chosen, int64_t *gains, uint32_t *cum)
+{
+    int64_t words = or_bitmap_words(R);
+    int64_t total = weight ? 0 : (int64_t)H * W;
+    if (weight)
+        for (int64_t i = 0; i < (int64_t)H * W; i++) total += weight[i];
+    int64_t need = -1;
+    if (target > 0.0) {
+        double nd = target * (double)total;
+        need = (int64_t)nd;
+        if ((double)need < nd) need += 1;
+    }
+    int64_t covered = wcovered(cum, H, W, weight);
+    uint8_t *elig = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int32_t t = 0;
+    for (; t < n_obs; t++) {
+        if (need >= 0 && covered >= need) break;
+        int64_t best = -1, bestg = -1;
+        for (int64_t c = 0; c < n; c++) {
+            if (cand[c] < 0 || cand[c] >= (int64_t)H * W) continue;
+            if (z && t > 0 && !elig[c]) continue;
+            int64_t g = wgain_of(bm + c * words, cand[c], H, W, R, cum, weight);
+            if (g > bestg || (g == bestg && cand[c] < cand[best])) { best = c; bestg = g; }
+        }
+        if (best < 0 || bestg <= 0) break;
+        chosen[t] = cand[best]; gains[t] = bestg;
+        or_into(bm + best * words, cand[best], H, W, R, cum);
+        covered += bestg;
+        if (z)
+            for (int64_t c = 0; c < n; c++)
+                if (c != best && or_intervisible(z, H, W, pitch, R, ht, cand[best], cand[c])) elig[c] = 1;
+    }
+    free(elig);
+    return t;
+}
