@@ -270,6 +270,33 @@ int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32
             int32_t n_obs, double coverage_target, int64_t *chosen, int64_t *gains,
             uint32_t *cum, int32_t *n_chosen, void *ws, size_t ws_bytes, vs_stream_t st);
 
+/* Site with the constraints the paper names as extensions (Sec. "Prior
+ * art": receivers of a given quality; intervisibility, where transmitters
+ * must be visible from other transmitters).  Readings:
+ *   - intervisibility (terrain.z != NULL): the first transmitter of the call
+ *     is free; every later one must be intervisible with one chosen earlier
+ *     in the call: the posts within the ROI (dx^2 + dy^2 <= R^2) and the line
+ *     between the antenna tops, both at z + ht, clearing the terrain by the
+ *     vix line-of-sight test (symmetric in the two ends).  terrain is the grid
+ *     the bitmaps were computed on (same H, W);
+ *   - weighted receivers (weight != NULL): post (x, y) weighs weight[y*W + x]
+ *     (uint8, pitch W); gains[] are the weights of the newly covered posts and
+ *     the coverage stop compares covered weight with
+ *     ceil(coverage_target * total weight).  Needs (2R+1)^2 * 255 < 2^32.
+ * Ties as in vs_site.  opt == NULL or neither option set: exactly vs_site.
+ * Otherwise the lazy greedy on the whole GPU runs (one cooperative launch;
+ * VS_ERR_DEVICE without cooperative launch support).  ws: at least
+ * vs_site_ex_workspace(n, R) bytes. */
+typedef struct {
+    vs_grid terrain;       /* z == NULL: no intervisibility constraint */
+    int32_t ht;            /* antenna height above the post, both ends */
+    const uint8_t *weight; /* H x W receiver weights, NULL = 1 each     */
+} vs_site_options;
+size_t vs_site_ex_workspace(int64_t n, int32_t R);
+int vs_site_ex(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W, int32_t R,
+               int32_t n_obs, double coverage_target, const vs_site_options *opt, int64_t *chosen,
+               int64_t *gains, uint32_t *cum, int32_t *n_chosen, void *ws, size_t ws_bytes, vs_stream_t st);
+
 /* vs_site for callers that cannot allocate device memory.  The paper has no
  * counterpart; this is a convenience of the library.
  *

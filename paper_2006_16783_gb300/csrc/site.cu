@@ -1013,6 +1013,14 @@ struct LazyParams {
     const uint32_t *citems;  // candidate indices grouped by cell
     int cs, ncx, ncy;        // cell side (>= 2R), cells per row / column
     const unsigned long long *covered0;
+    // options of vs_site_ex (k_site_lazy_grid only)
+    const int16_t *z;        // terrain for the intervisibility constraint, or null
+    long long zpitch;
+    int ht;                  // antenna height above the post (both ends)
+    uint8_t *elig;           // [n] intervisible with a transmitter chosen in this call
+    const uint8_t *weight;   // receiver weights H x W (pitch W), or null = 1 each
+    const unsigned long long *wsum;  // [2]: total weight, weight already covered
+    double target;           // weighted coverage stop (<= 0: off)
 };
 
 __global__ void k_lazy_count(const int64_t *__restrict__ cand, int n, int H, int W, int cs, int ncx,
@@ -1106,6 +1114,7 @@ __device__ __forceinline__ void lazy_block_best(uint64_t &k, int &c, uint64_t *s
 // this thread's share of popcount(V_c AND NOT C) over c's window clipped to
 // the grid; with commit, C |= V_c.  The clipped window is walked as one flat
 // range of (row, word) pairs, eight pairs per thread in flight.
+template <bool WEIGHTS = false>
 __device__ __forceinline__ unsigned lazy_window(const LazyParams &P, int c, int64_t p, bool commit,
                                                 int part = 0, int nparts = 1) {
     constexpr int U = 8;
@@ -1145,9 +1154,19 @@ __device__ __forceinline__ unsigned lazy_window(const LazyParams &P, int c, int6
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (off[u] < 0) continue;
-            const uint32_t d = v[u] & ~cw[u];
-            sum += __popc(d);
+            uint32_t d = v[u] & ~cw[u];
             if (commit && d) C[off[u]] = cw[u] | v[u];
+            if (!WEIGHTS || !P.weight) {
+                sum += __popc(d);
+            } else {  // receiver weights of the newly covered posts
+                const int row = off[u] / WWc, col32 = off[u] - row * WWc;
+                const uint8_t *wr = P.weight + (long long)(cy - R + r_lo + row) * P.W + 32 * (gw0 + w_lo + col32);
+                while (d) {
+                    const int b = __ffs(d) - 1;
+                    d &= d - 1;
+                    sum += wr[b];
+                }
+            }
         }
         r = rr;
         w = ww;
@@ -1342,6 +1361,38 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
     return v;
 }
 
+// Transmitters a and b intervisible: the line between the antenna tops (both
+// z + ht) clears the terrain interpolated between the two posts it passes
+// between at every crossing -- the vix line-of-sight test with the receiver
+// height set to ht (Sec. "Terrain visibility"; symmetric in a and b).  One
+// thread walks the line; 32-bit values (|j * dz| < 2^31 for R <= 4096).
+__device__ __forceinline__ bool tx_intervisible(const int16_t *z, long long pitch, int ax, int ay, int bx, int by,
+                                                int ht) {
+    const int dx = bx - ax, dy = by - ay;
+    const int adx = abs(dx), ady = abs(dy);
+    const bool xmaj = adx >= ady;
+    const int D = xmaj ? adx : ady;
+    if (D <= 1) return true;
+    const int E = (int)z[(long long)ay * pitch + ax] + ht;
+    const int ts = (int)z[(long long)by * pitch + bx] + ht - E;
+    const int dmin = xmaj ? dy : dx;
+    const int q = floordiv(dmin, D), rr = dmin - q * D;
+    const long long ms = xmaj ? (dx > 0 ? 1 : -1) : (dy > 0 ? pitch : -pitch);
+    const long long ns = xmaj ? pitch : 1;
+    const int16_t *a = z + (long long)ay * pitch + ax;
+    int f = 0;
+    for (int j = 1; j < D; ++j) {
+        f += rr;
+        a += ms + q * ns;
+        if (f >= D) { f -= D; a += ns; }
+        const int z0 = a[0];
+        const int z1 = f ? (int)a[ns] : z0;
+        if (j * ts < (z0 - E) * D + (z1 - z0) * f) return false;
+    }
+    return true;
+}
+
+template <bool OPT>  // OPT: the options of vs_site_ex (eligibility, weights) are compiled in
 __global__ void __launch_bounds__(kSiteThreads, 1) k_site_lazy_grid(const LazyParams P, LazyCtl *ctl,
                                                                    uint32_t *work) {
     __shared__ unsigned long long s_red[33];
@@ -1350,23 +1401,36 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_lazy_grid(const LazyPa
     const int tid = threadIdx.x, G = gridDim.x, b = blockIdx.x;
     const int lo = (int)((long long)P.n * b / G), hi = (int)((long long)P.n * (b + 1) / G);
     unsigned gen = 0;
-    long long covered = P.need >= 0 ? (long long)*P.covered0 : 0;
+    long long need = P.need;
+    long long covered = need >= 0 ? (long long)*P.covered0 : 0;
+    if (OPT && P.weight) {  // weighted coverage: the stop compares covered weight
+        covered = (long long)P.wsum[1];
+        need = -1;
+        if (P.target > 0.0) {
+            const double nd = P.target * (double)P.wsum[0];
+            need = (long long)nd;
+            if ((double)need < nd) need += 1;
+        }
+    }
+    const bool con = OPT && P.z != nullptr;
     int t = 0;
     bool ok = true;
     for (; t < P.n_obs; ++t) {
-        if (P.need >= 0 && covered >= P.need) break;
+        if (need >= 0 && covered >= need) break;
         const int par = t & 1;
+        const bool free_pick = !con || t == 0;  // the first transmitter of the call is free
         // A: largest fresh key
         unsigned long long k = 0;
         for (int c = lo + tid; c < hi; c += blockDim.x)
-            if (__ldcg(P.fresh + c)) k = u64max(k, lazy_key(__ldcg(P.g + c), P.cand[c]));
+            if ((free_pick || __ldcg(P.elig + c)) && __ldcg(P.fresh + c))
+                k = u64max(k, lazy_key(__ldcg(P.g + c), P.cand[c]));
         k = block_max_u64(k, s_red);
         if (tid == 0 && k) atomicMax(&ctl->F[par], k);
         if (!(ok = lazy_grid_sync(ctl, gen))) break;
         const unsigned long long F = *(volatile unsigned long long *)&ctl->F[par];
         // B: stale bounds that may beat F
         for (int c = lo + tid; c < hi; c += blockDim.x)
-            if (!__ldcg(P.fresh + c) && lazy_key(__ldcg(P.g + c), P.cand[c]) >= F)
+            if ((free_pick || __ldcg(P.elig + c)) && !__ldcg(P.fresh + c) && lazy_key(__ldcg(P.g + c), P.cand[c]) >= F)
                 work[atomicAdd(&ctl->nwork[par], 1u)] = (uint32_t)c;
         if (!(ok = lazy_grid_sync(ctl, gen))) break;
         const unsigned m = *(volatile unsigned *)&ctl->nwork[par];
@@ -1378,26 +1442,31 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_lazy_grid(const LazyPa
             __syncthreads();
             if ((unsigned)it >= m) break;
             const int c = (int)__ldcg(work + it);
-            const unsigned gnew = lazy_block_sum(lazy_window(P, c, P.cand[c], false), s_u);
+            const int64_t pc = P.cand[c];
+            // a post outside the grid covers nothing (its bound may be the
+            // unknown all-ones of weighted gains)
+            const bool valid = pc >= 0 && pc < (int64_t)P.H * P.W;
+            const unsigned gnew = valid ? lazy_block_sum(lazy_window<OPT>(P, c, pc, false), s_u) : 0u;
             if (tid == 0) { P.g[c] = gnew; P.fresh[c] = 1; }
         }
         if (!(ok = lazy_grid_sync(ctl, gen))) break;
         // D: the largest key, then the lowest index holding it
         k = 0;
-        for (int c = lo + tid; c < hi; c += blockDim.x) k = u64max(k, lazy_key(__ldcg(P.g + c), P.cand[c]));
+        for (int c = lo + tid; c < hi; c += blockDim.x)
+            if (free_pick || __ldcg(P.elig + c)) k = u64max(k, lazy_key(__ldcg(P.g + c), P.cand[c]));
         k = block_max_u64(k, s_red);
         if (tid == 0 && k) atomicMax(&ctl->best[par], k);
         if (!(ok = lazy_grid_sync(ctl, gen))) break;
         const unsigned long long best = *(volatile unsigned long long *)&ctl->best[par];
-        if ((best >> 32) == 0) break;  // best gain 0: nothing left to cover
+        if ((best >> 32) == 0) break;  // best gain 0 (or no eligible candidate): nothing left to cover
         for (int c = lo + tid; c < hi; c += blockDim.x)
-            if (lazy_key(__ldcg(P.g + c), P.cand[c]) == best) atomicMax(&ctl->widx[par], 0xFFFFFFFFu - (unsigned)c);
+            if ((free_pick || __ldcg(P.elig + c)) && lazy_key(__ldcg(P.g + c), P.cand[c]) == best) atomicMax(&ctl->widx[par], 0xFFFFFFFFu - (unsigned)c);
         if (!(ok = lazy_grid_sync(ctl, gen))) break;
         const int w = (int)(0xFFFFFFFFu - *(volatile unsigned *)&ctl->widx[par]);
         const int64_t pw = P.cand[w];
         const uint32_t gw = (uint32_t)(best >> 32);
         // E: accept
-        lazy_window(P, w, pw, true, b, G);
+        lazy_window<OPT>(P, w, pw, true, b, G);
         const int cx = (int)(pw % P.W), cy = (int)(pw / P.W), R2 = 2 * P.R;
         const int x0 = max(0, cx - R2) / P.cs, x1 = min(P.W - 1, cx + R2) / P.cs;
         const int y0 = max(0, cy - R2) / P.cs, y1 = min(P.H - 1, cy + R2) / P.cs;
@@ -1411,6 +1480,10 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_lazy_grid(const LazyPa
                     const int64_t p2 = P.cand[c2];
                     const int xx = (int)(p2 % P.W), yy = (int)(p2 / P.W);
                     if (c2 != w && abs(xx - cx) <= R2 && abs(yy - cy) <= R2) P.fresh[c2] = 0;
+                    // intervisible with the new transmitter: eligible from now on
+                    if (con && c2 != w && (xx - cx) * (xx - cx) + (yy - cy) * (yy - cy) <= P.R * P.R &&
+                        tx_intervisible(P.z, P.zpitch, cx, cy, xx, yy, P.ht))
+                        P.elig[c2] = 1;
                 }
             }
         if (b == 0 && tid == 0) {
@@ -1470,9 +1543,21 @@ extern "C" size_t vs_site_workspace(int64_t n, int32_t R) {
 }
 
 // lazy greedy: bucket the candidates and launch the loop
+// the options of vs_site_ex, resolved on the host
+struct LazyOpts {
+    const int16_t *z;
+    long long zpitch;
+    int ht;
+    const uint8_t *weight;
+    double target;
+    uint8_t *elig;
+    unsigned long long *wsum;
+};
+
 static int site_lazy(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W, int32_t R,
                      int32_t n_obs, long long need, int64_t *chosen, int64_t *gains, uint32_t *cum,
-                     int32_t *n_chosen, uint32_t *g0, void *ws, const unsigned long long *cov, cudaStream_t s) {
+                     int32_t *n_chosen, uint32_t *g0, void *ws, const unsigned long long *cov, cudaStream_t s,
+                     const LazyOpts *opt = nullptr) {
     if (n >= (1ll << 31) - 1) return VS_ERR_RANGE;
     const size_t a4 = align256((size_t)n * 4);
     uint8_t *fresh = (uint8_t *)((char *)ws + a4);
@@ -1490,7 +1575,14 @@ static int site_lazy(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
     int bs = 256;
     while ((n + bs - 1) / bs > 16384) bs *= 2;
     const int nb = (int)((n + bs - 1) / bs);
-    VS_CUDA_TRY(cudaMemsetAsync(fresh, 1, (size_t)n, s));
+    if (opt && opt->weight) {
+        // weighted gains: every bound starts unknown (all ones) and stale, so
+        // the first step evaluates every candidate
+        VS_CUDA_TRY(cudaMemsetAsync(fresh, 0, (size_t)n, s));
+        VS_CUDA_TRY(cudaMemsetAsync(g0, 0xFF, (size_t)n * 4, s));
+    } else {
+        VS_CUDA_TRY(cudaMemsetAsync(fresh, 1, (size_t)n, s));
+    }
     VS_CUDA_TRY(cudaMemsetAsync(cursor, 0, (size_t)ncell * 4, s));
     const unsigned gb = (unsigned)((n + 255) / 256);
     k_lazy_count<<<gb, 256, 0, s>>>(cand, (int)n, H, W, (int)cs, ncx, cursor);
@@ -1506,22 +1598,30 @@ static int site_lazy(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
     L.n_obs = n_obs; L.need = need; L.chosen = chosen; L.gains = gains; L.cum = cum; L.n_chosen = n_chosen;
     L.g = g0; L.fresh = fresh; L.bs = bs; L.nb = nb; L.cstart = cstart; L.citems = citems;
     L.cs = (int)cs; L.ncx = ncx; L.ncy = ncy; L.covered0 = cov;
-    if (tune_get(VS_TUNE_SITE_LAZY, R, 0) != 2) {
+    L.z = opt ? opt->z : nullptr;
+    L.zpitch = opt ? opt->zpitch : 0;
+    L.ht = opt ? opt->ht : 0;
+    L.elig = opt ? opt->elig : nullptr;
+    L.weight = opt ? opt->weight : nullptr;
+    L.wsum = opt ? opt->wsum : nullptr;
+    L.target = opt ? opt->target : 0.0;
+    if (opt || tune_get(VS_TUNE_SITE_LAZY, R, 0) != 2) {
         // the whole GPU: one CTA per SM in one cooperative launch
         int dev = 0, sms = 0, per = 0, coop = 0;
         VS_CUDA_TRY(cudaGetDevice(&dev));
         VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         VS_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-        VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_site_lazy_grid, kSiteThreads, 0));
+        const void *kern = opt ? (const void *)k_site_lazy_grid<true> : (const void *)k_site_lazy_grid<false>;
+        VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kSiteThreads, 0));
         if (coop && per >= 1 && sms >= 1) {
             LazyCtl *ctl = (LazyCtl *)((char *)ws + 4 * a4);
             uint32_t *work = (uint32_t *)((char *)ws + 3 * a4);
             VS_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(LazyCtl), s));
             void *args[] = {(void *)&L, (void *)&ctl, (void *)&work};
-            VS_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_site_lazy_grid, dim3((unsigned)sms),
-                                                    dim3(kSiteThreads), args, 0, s));
+            VS_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3((unsigned)sms), dim3(kSiteThreads), args, 0, s));
             return VS_OK;
         }
+        if (opt) return VS_ERR_DEVICE;  // the options run on the grid kernel only
     }
     const size_t smem = (size_t)nb * 12 + 16;
     VS_CUDA_TRY(cudaFuncSetAttribute(k_site_lazy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1727,6 +1827,97 @@ extern "C" int vs_site(const uint32_t *bm, const int64_t *cand, int64_t n, int32
                        size_t ws_bytes, vs_stream_t st) {
     return site_impl(bm, cand, n, H, W, R, n_obs, coverage_target, chosen, gains, cum, n_chosen, ws,
                      ws_bytes, st, nullptr, nullptr);
+}
+
+// out[0] += total receiver weight, out[1] += weight of the posts set in cum
+__global__ void k_weight_sums(const uint32_t *__restrict__ cum, const uint8_t *__restrict__ weight, int H, int W,
+                              unsigned long long *out) {
+    const int WWc = (W + 31) / 32;
+    const long long nw = (long long)H * WWc, np = (long long)H * W;
+    unsigned long long tot = 0, cov = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += (long long)gridDim.x * blockDim.x)
+        tot += weight[i];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += (long long)gridDim.x * blockDim.x) {
+        uint32_t u = cum[i];
+        const long long y = i / WWc, gw = i - y * WWc;
+        while (u) {
+            const int b = __ffs(u) - 1;
+            u &= u - 1;
+            if (32 * gw + b < W) cov += weight[y * W + 32 * gw + b];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        cov += __shfl_xor_sync(0xffffffffu, cov, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (tot) atomicAdd(&out[0], tot);
+        if (cov) atomicAdd(&out[1], cov);
+    }
+}
+
+extern "C" size_t vs_site_ex_workspace(int64_t n, int32_t R) {
+    if (n < 0) return 0;
+    return vs_site_workspace(n, R) + align256((size_t)n) + 256;  // + eligibility flags, weight sums
+}
+
+extern "C" int vs_site_ex(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W, int32_t R,
+                          int32_t n_obs, double coverage_target, const vs_site_options *opt, int64_t *chosen,
+                          int64_t *gains, uint32_t *cum, int32_t *n_chosen, void *ws, size_t ws_bytes,
+                          vs_stream_t st) {
+    const bool con = opt && opt->terrain.z;
+    const bool wtd = opt && opt->weight;
+    if (!con && !wtd)
+        return vs_site(bm, cand, n, H, W, R, n_obs, coverage_target, chosen, gains, cum, n_chosen, ws, ws_bytes, st);
+    if (n < 0 || n_obs < 0) return VS_ERR_RANGE;
+    if (!cum || !n_chosen || (n > 0 && (!bm || !cand)) || (n_obs > 0 && (!chosen || !gains))) return VS_ERR_ARG;
+    if (H < 1 || W < 1 || H > 65535 || W > 65535 || R < 1 || R > kMaxR) return VS_ERR_RANGE;
+    if (n >= (1ll << 31) - 1) return VS_ERR_RANGE;
+    if (con) {
+        int rc = check_grid(opt->terrain);
+        if (rc) return rc;
+        if (opt->terrain.H != H || opt->terrain.W != W) return VS_ERR_ARG;
+        if (opt->ht < -100000 || opt->ht > 100000) return VS_ERR_RANGE;
+    }
+    if (wtd && (long long)(2 * R + 1) * (2 * R + 1) * 255 >= (1ll << 32)) return VS_ERR_RANGE;  // 32-bit gains
+    if (!ws || ws_bytes < vs_site_ex_workspace(n, R)) return VS_ERR_WS;
+    int rc = check_device();
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)st;
+    if (n == 0) {
+        VS_CUDA_TRY(cudaMemsetAsync(n_chosen, 0, 4, s));
+        return VS_OK;
+    }
+    const size_t a4 = align256((size_t)n * 4);
+    uint32_t *g0 = (uint32_t *)ws;
+    unsigned long long *cov = (unsigned long long *)((char *)ws + 5 * a4);
+    const size_t base = vs_site_workspace(n, R);
+    LazyOpts o;
+    o.z = con ? opt->terrain.z : nullptr;
+    o.zpitch = con ? opt->terrain.pitch : 0;
+    o.ht = con ? opt->ht : 0;
+    o.weight = wtd ? opt->weight : nullptr;
+    o.target = coverage_target;
+    o.elig = (uint8_t *)((char *)ws + base);
+    o.wsum = (unsigned long long *)((char *)ws + base + align256((size_t)n));
+    VS_CUDA_TRY(cudaMemsetAsync(o.elig, 0, (size_t)n, s));
+    long long need = -1;
+    if (wtd) {
+        VS_CUDA_TRY(cudaMemsetAsync(o.wsum, 0, 16, s));
+        k_weight_sums<<<4 * 152, 256, 0, s>>>(cum, o.weight, H, W, o.wsum);
+        VS_CUDA_TRY(cudaGetLastError());
+    } else {
+        if (coverage_target > 0.0) {
+            const double nd = coverage_target * (double)H * (double)W;
+            need = (long long)nd;
+            if ((double)need < nd) need += 1;
+            VS_CUDA_TRY(cudaMemsetAsync(cov, 0, 8, s));
+            k_cum_popcount<<<4 * 152, 256, 0, s>>>(cum, (int64_t)H * ((W + 31) / 32), cov);
+            VS_CUDA_TRY(cudaGetLastError());
+        }
+        if ((rc = vs_site_gains(bm, cand, n, H, W, R, cum, g0, st))) return rc;
+    }
+    return site_lazy(bm, cand, n, H, W, R, n_obs, need, chosen, gains, cum, n_chosen, g0, ws, cov, s, &o);
 }
 
 extern "C" size_t vs_site_batch_workspace(const vs_site_job *jobs, int32_t n_jobs) {

@@ -42,6 +42,10 @@ class vs_site_job(ctypes.Structure):
                 ("n_chosen", ctypes.c_void_p)]
 
 
+class vs_site_options(ctypes.Structure):
+    _fields_ = [("terrain", vs_grid), ("ht", ctypes.c_int32), ("weight", ctypes.c_void_p)]
+
+
 (VS_TUNE_VIEWSHED_THREADS, VS_TUNE_VIX_TILE, VS_TUNE_SITE_CLUSTER, VS_TUNE_VIEWSHED_WIDE,
  VS_TUNE_SITE_LAZY) = 0, 1, 2, 3, 4
 
@@ -73,6 +77,9 @@ SIGNATURES = {
     "vs_site_workspace": (sz, [i64, i32]),
     "vs_site": (ctypes.c_int, [P, P, i64, i32, i32, i32, i32, f64, P, P, P, P, P, sz, P]),
     "vs_site_gains": (ctypes.c_int, [P, P, i64, i32, i32, i32, P, P, P]),
+    "vs_site_ex_workspace": (sz, [i64, i32]),
+    "vs_site_ex": (ctypes.c_int, [P, P, i64, i32, i32, i32, i32, f64, ctypes.POINTER(vs_site_options), P, P, P, P,
+                                  P, sz, P]),
     "vs_site_noalloc": (ctypes.c_int, [P, P, i64, i32, i32, i32, i32, f64, P, P, P, P, P]),
     "vs_cnn_param_count": (ctypes.c_int, []),
     "vs_cnn_packed_bytes": (sz, []),
@@ -268,6 +275,37 @@ def viewshed_r3(g, R, ht, hr, cand, bm=None, area=None, ws=None):
     _check("vs_viewshed_r3", lib().vs_viewshed_r3(g.c(), R, ht, hr, _ptr(cand), n, _ptr(bm), _ptr(area),
                                                   _ptr(ws), wsb, _stream()))
     return bm, area
+
+
+def site_ex(bm, cand, H, W, R, n_obs, target=0.0, grid=None, ht=0, weight=None, cum=None, sync=True):
+    """vs_site with the intervisibility constraint (grid: the terrain the
+    bitmaps were computed on; transmitters after the first must see one
+    chosen earlier, antennas at z + ht) and / or uint8 receiver weights
+    (H x W device tensor).  Same returns as site()."""
+    _need_cuda(bm, cand)
+    dev = cand.device
+    n = cand.numel()
+    if cum is None:
+        cum = torch.zeros((H, (W + 31) // 32), dtype=torch.int32, device=dev)
+    chosen = torch.empty(max(n_obs, 1), dtype=torch.int64, device=dev)
+    gains = torch.empty(max(n_obs, 1), dtype=torch.int64, device=dev)
+    nch = torch.zeros(1, dtype=torch.int32, device=dev)
+    wsb = lib().vs_site_ex_workspace(n, R)
+    ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
+    opt = vs_site_options(grid.c() if grid is not None else vs_grid(0, 0, 0, 0), ht,
+                          weight.data_ptr() if weight is not None else None)
+    if weight is not None:
+        _need_cuda(weight)
+        assert weight.dtype == torch.uint8 and weight.shape == (H, W) and weight.is_contiguous()
+    _check("vs_site_ex", lib().vs_site_ex(_ptr(bm), _ptr(cand), n, H, W, R, n_obs, float(target),
+                                          ctypes.byref(opt), _ptr(chosen), _ptr(gains), _ptr(cum), _ptr(nch),
+                                          _ptr(ws), wsb, _stream()))
+    if not sync:
+        return chosen, gains, cum, nch
+    t = int(nch.item())
+    if t < 0:
+        raise VsError("vs_site_ex", t)
+    return chosen[:t], gains[:t], cum, t
 
 
 def site_workspace(n, R):
