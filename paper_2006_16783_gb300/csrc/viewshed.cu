@@ -46,6 +46,20 @@ __device__ __forceinline__ void ring_cell(int rho, int R, int &ex, int &ey) {
     else { ey = -R;                   ex = -R + 1 + o; }
 }
 
+// Steps of a ray to ring cell (R, e) (or its rotations) inside the disc: the
+// largest k <= R with k^2 + rnd(k)^2 <= R^2, rnd(k) = k*e/R rounded half away
+// from zero.  The left side only grows with k, so a binary search finds it.
+__device__ __forceinline__ int disc_steps(int R, int e) {
+    const int ae = abs(e);
+    int lo = 0, hi = R;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int r = (2 * mid * ae + R) / (2 * R);
+        if (mid * mid + r * r <= R * R) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Everything one viewshed needs, for the single-terrain and the batched
 // launches alike (the tensor map must stay in parameter space).
 struct VsJob {
@@ -80,6 +94,9 @@ __device__ void vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long 
     }
     const int cx = (int)(p % J.W), cy = (int)(p / J.W);
     const int gw0 = floordiv(cx - R, 32);
+    // the whole window inside the grid: no ray meets the grid edge, so a ray
+    // ends only at the disc, after a step count found once per ray
+    const bool interior = cx >= R && cx <= J.W - 1 - R && cy >= R && cy <= J.H - 1 - R;
     if (tid == 0) *s_fail = 0;
     for (int i = tid; i < (2 * R + 1) * PRs; i += blockDim.x) bms[i] = 0;
     __syncthreads();
@@ -142,6 +159,32 @@ __device__ void vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long 
             int f = 0, y0 = 0, gmaj = omaj, k2 = 0;
             T Hn = 0;
             int Hk = 0;
+            if (interior) {
+                const int kmax = disc_steps(R, dmin);
+                // bitmap word of the cell: row and column advance with k and rnd
+                const int rowk = xmaj ? 0 : smaj * PRs, rowr = xmaj ? PRs : 0;
+                const int wbase = R * PRs - gw0;
+                for (int k = 1; k <= kmax; ++k) {
+                    f += rr;
+                    y0 += q;
+                    a0 += astep;
+                    if (f >= R) { f -= R; y0 += 1; a0 += amin; }
+                    const int rb = (2 * f >= thr) ? 1 : 0;  // round half away from zero
+                    const int rnd = y0 + rb;
+                    gmaj += smaj;
+                    const int zc = win[a0 + (rb ? amin : 0)];
+                    const int zo = f > 0 ? (int)win[a0 + (rb ? 0 : amin)] : zc;
+                    const bool vis = (Hk == 0) || ((T)(zc + hre) * R * Hk >= Hn * k);
+                    if (vis) {
+                        const int gx = xmaj ? gmaj : omin + rnd;
+                        atomicOr(&bms[wbase + k * rowk + rnd * rowr + (gx >> 5)], 1u << (gx & 31));
+                    }
+                    const int z0 = rb ? zo : zc, z1 = rb ? zc : zo;
+                    const T num = (T)z0 * (R - f) + (T)z1 * f - eyeR;
+                    if (Hk == 0 || num * Hk > Hn * k) { Hn = num; Hk = k; }
+                }
+                continue;
+            }
             for (int k = 1; k <= R; ++k) {
                 f += rr;
                 y0 += q;
@@ -334,6 +377,8 @@ __global__ void __launch_bounds__(kWideThreads) k_viewshed_wide(const VsWide P) 
     const int eye = (int)P.z[(long long)cy * P.pitch + cx] + P.ht;
     const int eyeR = eye * R;
     const int hreR = (P.hr - eye) * R;
+    // the whole window inside the grid: rays end only at the disc
+    const bool interior = cx >= R && cx <= P.W - 1 - R && cy >= R && cy <= P.H - 1 - R;
 
     for (int side = 0; side < 4; ++side) {  // east, west, north, south
         const bool xmaj = side < 2;
@@ -357,6 +402,7 @@ __global__ void __launch_bounds__(kWideThreads) k_viewshed_wide(const VsWide P) 
             // smaj*k, minor omin + y0); the cell tested is that post or the
             // next one along the minor axis (offset 1 in both arrays)
             int f = 0, y0 = 0, a0 = 0, Hn = 0, Hk = 0;
+            const int kmax = (interior && alive) ? disc_steps(R, e) : R;
             // window rows an east / west pass can touch
             const int rlo = R + min(0, ea), rhi = R + max(0, eb);
             for (int b = 0;; ++b) {
@@ -387,7 +433,32 @@ __global__ void __launch_bounds__(kWideThreads) k_viewshed_wide(const VsWide P) 
                     for (int i = tid; i < PR * 32; i += nt) tile[i] = 0u;
                 }
                 __syncthreads();
-                if (alive) {
+                if (alive && interior) {
+                    const int kend = min(khi, kmax);
+                    for (int k = klo; k <= kend; ++k) {
+                        f += rr;
+                        y0 += q;
+                        a0 += astep;
+                        if (f >= R) { f -= R; y0 += 1; a0 += 1; }
+                        const int rb = (2 * f >= thr) ? 1 : 0;
+                        const int rnd = y0 + rb;
+                        const int zc = __ldg(base + a0 + rb);
+                        const int zo = f > 0 ? (int)__ldg(base + a0 + (rb ? 0 : 1)) : zc;
+                        const bool vis = (Hk == 0) || ((long long)(zc * R + hreR) * Hk >= (long long)Hn * k);
+                        if (vis) {
+                            if (xmaj) {
+                                const int gmaj = omaj + smaj * k;
+                                atomicOr(&tile[(rnd + R) * kWideTP + ((gmaj >> 5) - bw0)], 1u << (gmaj & 31));
+                            } else {
+                                atomicOr(&tile[omin + rnd - 32 * gw0], 1u << (k - klo));
+                            }
+                        }
+                        const int z0 = rb ? zo : zc, z1 = rb ? zc : zo;
+                        const int num = z0 * (R - f) + z1 * f - eyeR;
+                        if (Hk == 0 || (long long)num * Hk > (long long)Hn * k) { Hn = num; Hk = k; }
+                    }
+                    alive = kmax > khi;
+                } else if (alive) {
                     for (int k = klo; k <= khi; ++k) {
                         f += rr;
                         y0 += q;
