@@ -52,7 +52,26 @@ __global__ void __launch_bounds__(kGainThreads) k_site_gains(const uint32_t *__r
     const int gw0 = floordiv(cx - R, 32);
     const uint32_t *V = bm + c * (int64_t)(2 * R + 1) * PR;
     unsigned sum = 0;
-    if (PR <= 32) {
+    const int words = (2 * R + 1) * PR;
+    if ((PR & 3) == 0 && (((uintptr_t)V) & 15) == 0) {
+        // rows of whole 16-byte vectors: a lane reads 4 words of one row per
+        // load, four vectors in flight; the C words beside them one by one
+        const int q4 = PR >> 2, nvec = words >> 2;
+        const uint4 *V4 = (const uint4 *)V;
+#pragma unroll 4
+        for (int i = lane; i < nvec; i += 32) {
+            const uint4 v = __ldg(V4 + i);
+            const int r = i / q4, w = 4 * (i - r * q4);
+            const int y = cy - R + r;
+            if (y < 0 || y >= H) continue;
+            const uint32_t *Cr = cum + (int64_t)y * WWc + gw0 + w;
+            const int g = gw0 + w;
+            const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (g + j >= 0 && g + j < WWc) sum += __popc(vv[j] & ~__ldg(Cr + j));
+        }
+    } else if (PR <= 32) {
         // lanes cover rpi whole rows per iteration
         const int rpi = 32 / PR;
         const int roff = lane / PR, w = lane - roff * PR;
