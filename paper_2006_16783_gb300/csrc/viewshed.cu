@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(512) k_viewshed_batch(const __grid_constant__ 
 // Values stay in 32 bits with 64-bit products, exact for every accepted input:
 // |z*R + (hr - eye)*R| <= (65535 + 2*100000)*4096 < 2^31 and the interpolated
 // numerator |z0*(R-f) + z1*f - eye*R| < 2^31 for R <= 4096.
-constexpr int kWideThreads = 1024;
+constexpr int kWideThreads = 512;  // two CTAs per SM: one's band barriers overlap the other's rays
 constexpr int kWideTW = 4;    // east / west tile: words per window row
 constexpr int kWideTP = 5;    // its row pitch, odd: neighbouring rows in other banks
 constexpr int kWideBN = 32;   // north / south tile: window rows per band (bits of a column word)
@@ -359,7 +359,7 @@ __device__ __forceinline__ uint32_t warp_bit_transpose(uint32_t a) {
     return a;
 }
 
-__global__ void __launch_bounds__(kWideThreads) k_viewshed_wide(const VsWide P) {
+__global__ void __launch_bounds__(kWideThreads, 2) k_viewshed_wide(const VsWide P) {
     extern __shared__ __align__(16) uint32_t tile[];
     __shared__ int red[32];
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -403,8 +403,10 @@ __global__ void __launch_bounds__(kWideThreads) k_viewshed_wide(const VsWide P) 
             // next one along the minor axis (offset 1 in both arrays)
             int f = 0, y0 = 0, a0 = 0, Hn = 0, Hk = 0;
             const int kmax = (interior && alive) ? disc_steps(R, e) : R;
-            // window rows an east / west pass can touch
+            // window rows an east / west pass can touch, word columns of a
+            // north / south one (|rnd| <= |e| along every ray)
             const int rlo = R + min(0, ea), rhi = R + max(0, eb);
+            const int wlo = ((omin + min(0, ea)) >> 5) - gw0, whi = ((omin + max(0, eb)) >> 5) - gw0;
             for (int b = 0;; ++b) {
                 int klo, khi, bw0 = 0;
                 if (xmaj) {
@@ -430,7 +432,7 @@ __global__ void __launch_bounds__(kWideThreads) k_viewshed_wide(const VsWide P) 
                     for (int i = tid; i < (rhi - rlo + 1) * kWideTW; i += nt)
                         tile[(rlo + i / kWideTW) * kWideTP + (i % kWideTW)] = 0u;
                 } else {
-                    for (int i = tid; i < PR * 32; i += nt) tile[i] = 0u;
+                    for (int i = 32 * wlo + tid; i < 32 * (whi + 1); i += nt) tile[i] = 0u;
                 }
                 __syncthreads();
                 if (alive && interior) {
@@ -507,7 +509,7 @@ __global__ void __launch_bounds__(kWideThreads) k_viewshed_wide(const VsWide P) 
                     // warp per word column: transpose its 32 x 32 block, lane i
                     // holds window row klo + i
                     const int lane = tid & 31;
-                    for (int w = tid >> 5; w < PR; w += nt >> 5) {
+                    for (int w = wlo + (tid >> 5); w <= whi; w += nt >> 5) {
                         const uint32_t t = warp_bit_transpose(tile[32 * w + lane]);
                         if (t && lane < nrow) out[(long long)(R + smaj * (klo + lane)) * PR + w] |= t;
                     }
