@@ -128,15 +128,16 @@ int vs_vix(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t see
 /* Large ROIs.  A tile's halo window fits in shared memory up to R ~ 280;
  * beyond that (the paper's runs use R = 500..2000, Sec. "Experiments") a warp
  * walks one line of sight at a time, 32 consecutive crossings per
- * instruction, against the terrain in global memory.  Its y-major lines read
- * a transposed copy of the terrain when the caller provides room for one:
- * vs_vix_workspace(H, W, R, S) bytes (0 when the staged kernels cover R,
- * else W x ceil8(H) int16 plus 256 bytes).  vs_vix_ws is vs_vix (los_steps
- * NULL) or vs_vix_count (los_steps set) with that workspace; ws may be NULL
- * or smaller, then y-major lines read the terrain with a row stride (same
- * results, slower).  vs_vix and vs_vix_count are vs_vix_ws without a
- * workspace.  Large R needs (3R + 128) * max(pitch, ceil8(H)) < 2^31 (else
- * VS_ERR_RANGE). */
+ * instruction, against the terrain in global memory.  With room for them the
+ * call first writes two arrays that hold every post paired with its neighbour
+ * along y (row-major) and along x (transposed), so that a crossing reads both
+ * of its posts with one contiguous 32-bit load: vs_vix_workspace(H, W, R, S)
+ * bytes (0 when the staged kernels cover R, else 8 x H x W plus 512 bytes).
+ * vs_vix_ws is vs_vix (los_steps NULL) or vs_vix_count (los_steps set) with
+ * that workspace; ws may be NULL or smaller, then lines read the terrain in
+ * place (same results, slower).  vs_vix and vs_vix_count are vs_vix_ws
+ * without a workspace.  Without it, large R needs (3R + 128) * pitch < 2^31
+ * (else VS_ERR_RANGE). */
 size_t vs_vix_workspace(int32_t H, int32_t W, int32_t R, int32_t S);
 int vs_vix_ws(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
               uint8_t *vix_out, uint64_t *los_steps, void *ws, size_t ws_bytes, vs_stream_t st);
@@ -223,9 +224,9 @@ int vs_viewshed(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *can
  * approximation.  Same arguments, output layout and errors as vs_viewshed.
  * Costs ~0.6*pi*R^3 crossings per candidate (vs_viewshed: ~7R^2 steps): an
  * accuracy reference, not the siting path.  ws: optional, at least
- * vs_viewshed_r3_workspace(H, W) bytes for a transposed copy of the terrain
- * (y-major lines then read contiguous memory); NULL or smaller: strided reads,
- * same results.  Needs (3R + 128) * max(pitch, ceil8(H)) < 2^31. */
+ * vs_viewshed_r3_workspace(H, W) bytes for the pair arrays of vs_vix_ws;
+ * NULL or smaller: the terrain is read in place, same results.  Without them
+ * it needs (3R + 128) * pitch < 2^31. */
 size_t vs_viewshed_r3_workspace(int32_t H, int32_t W);
 int vs_viewshed_r3(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand, int64_t n,
                    uint32_t *bm_out, int32_t *area_out, void *ws, size_t ws_bytes, vs_stream_t st);

@@ -453,31 +453,16 @@ __global__ void __launch_bounds__(kVixThreads, 1) k_vix2(const __grid_constant__
     }
 }
 
-// zt = transpose of z (32 x 32 tiles through shared memory)
-__global__ void __launch_bounds__(256) k_transpose_i16_vix(const int16_t *__restrict__ z, long long pitch, int H,
-                                                           int W, int16_t *__restrict__ zt, long long pitcht) {
-    __shared__ int t[32][33];
-    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int j = ty; j < 32; j += 8) {
-        const int yy = y0 + j, xx = x0 + tx;
-        if (yy < H && xx < W) t[j][tx] = z[(long long)yy * pitch + xx];
-    }
-    __syncthreads();
-    for (int j = ty; j < 32; j += 8) {
-        const int xx = x0 + j, yy = y0 + tx;
-        if (xx < W && yy < H) zt[(long long)xx * pitcht + yy] = (int16_t)t[tx][j];
-    }
-}
 
 // ------------------------------------------------------------------ wide ROI
 // For ROIs whose halo window does not fit in shared memory (R above ~280; the
 // paper's own runs use R = 500 .. 2000), a warp walks one line of sight at a
 // time, 32 consecutive crossings per instruction (lane l takes crossing
 // j0 + l), against the terrain in global memory, and a warp vote ends the
-// line at its first blocked crossing.  x-major lines read terrain rows;
-// y-major lines read the transposed terrain when the caller gives one (else
-// the terrain with a row stride), so a warp's loads are contiguous.  Each lane
+// line at its first blocked crossing.  With a workspace the walk reads both
+// posts of a crossing with one load from pair arrays laid out so that a
+// warp's loads are contiguous (warp_los_pair); without one, x-major lines
+// read terrain rows and y-major lines the terrain with a row stride.  Each lane
 // draws the samples of its own post (the same generator and offset table as
 // k_vix); the warp then walks its 32 posts' lines one after another.  The
 // test is k_vix's: visible iff j*(z_T + hr - E) >= (z0 - E)*D + (z1 - z0)*f
@@ -485,8 +470,7 @@ __global__ void __launch_bounds__(256) k_transpose_i16_vix(const int16_t *__rest
 struct VixWide {
     const int16_t *z;
     long long pitch;
-    const int16_t *zt;  // transposed terrain zt[x * pitcht + y], or null
-    long long pitcht;
+    const uint32_t *py, *px;  // pair arrays of warp_los_pair, or null
     int H, W, R, ht, hr, S, NR;
     uint64_t seed;
     uint8_t *out;
@@ -596,6 +580,83 @@ __device__ __forceinline__ bool warp_los(const int16_t *z, long long pitch, cons
     return true;
 }
 
+// The same line walk reading both posts of a crossing with one 32-bit load:
+// Py[y*W + x] = z(x, y) | z(x, y+1) << 16 for x-major lines (consecutive
+// crossings = consecutive x, so a warp's loads are contiguous) and
+// Px[x*H + y] = z(x, y) | z(x+1, y) << 16, transposed, for y-major ones.  Half
+// the loads and half the cache lines of warp_los (the walk is bound by L1
+// traffic).  The upper half of a pair past the grid edge is never used: a
+// crossing between two posts has both inside the line's bounding box.
+template <bool COUNT>
+__device__ __forceinline__ bool warp_los_pair(const uint32_t *Py, const uint32_t *Px, int H, int W, int ox, int oy,
+                                              int E, int dx, int dy, int ts, unsigned long long &nsteps) {
+    const int lane = threadIdx.x & 31;
+    const int adx = abs(dx), ady = abs(dy);
+    const bool xmaj = adx >= ady;
+    const int D = xmaj ? adx : ady;
+    const int dmin = xmaj ? dy : dx;
+    const int sg = xmaj ? (dx > 0 ? 1 : -1) : (dy > 0 ? 1 : -1);
+    // element (major m, minor n) of the pair array: x-major Py[n][m], y-major Px[m][n]
+    const uint32_t *bp = xmaj ? Py + (long long)oy * W + ox : Px + (long long)ox * H + oy;
+    const int ns = xmaj ? W : H;  // stride along the minor axis
+    int j = 1 + lane;
+    const int yq = floordiv(j * dmin, D);
+    int f = j * dmin - yq * D;
+    long long off = (long long)j * sg + (long long)yq * ns;
+    const int q32 = floordiv(32 * dmin, D), r32 = 32 * dmin - q32 * D;
+    const long long step32 = 32ll * sg + (long long)q32 * ns;
+    int lhs = j * ts;
+    for (int j0 = 1; j0 < D; j0 += 64) {
+        int fb = f + r32;
+        long long offb = off + step32;
+        if (fb >= D) { fb -= D; offb += ns; }
+        uint32_t pa = 0, pb = 0;
+        if (j < D) pa = __ldg(bp + off);
+        if (j + 32 < D) pb = __ldg(bp + offb);
+        const int z0a = (int16_t)(pa & 0xFFFFu), z1a = f ? (int)(int16_t)(pa >> 16) : z0a;
+        const int z0b = (int16_t)(pb & 0xFFFFu), z1b = fb ? (int)(int16_t)(pb >> 16) : z0b;
+        const bool ba = j < D && lhs < (z0a - E) * D + (z1a - z0a) * f;
+        const bool bb = j + 32 < D && lhs + 32 * ts < (z0b - E) * D + (z1b - z0b) * fb;
+        const unsigned va = __ballot_sync(0xffffffffu, ba);
+        const unsigned vb = __ballot_sync(0xffffffffu, bb);
+        if (va | vb) {
+            if (COUNT) nsteps += (unsigned long long)(va ? j0 + __ffs(va) - 1 : j0 + 32 + __ffs(vb) - 1);
+            return false;
+        }
+        j += 64;
+        lhs += 64 * ts;
+        off = offb + step32;
+        f = fb + r32;
+        if (f >= D) { f -= D; off += ns; }
+    }
+    if (COUNT && D > 1) nsteps += (unsigned long long)(D - 1);
+    return true;
+}
+
+// the pair arrays of warp_los_pair, one 32 x 32 block of posts per CTA: Py
+// written row by row, Px through a shared-memory transpose (both coalesced)
+__global__ void __launch_bounds__(256) k_pairs_i16(const int16_t *__restrict__ z, long long pitch, int H, int W,
+                                                   uint32_t *__restrict__ Py, uint32_t *__restrict__ Px) {
+    __shared__ uint32_t t[32][33];
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int j = ty; j < 32; j += 8) {
+        const int y = y0 + j, x = x0 + tx;
+        if (y < H && x < W) {
+            const uint32_t z0 = (uint16_t)z[(long long)y * pitch + x];
+            const uint32_t zy = y + 1 < H ? (uint16_t)z[(long long)(y + 1) * pitch + x] : 0u;
+            const uint32_t zx = x + 1 < W ? (uint16_t)z[(long long)y * pitch + x + 1] : 0u;
+            Py[(long long)y * W + x] = z0 | (zy << 16);
+            t[j][tx] = z0 | (zx << 16);
+        }
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int x = x0 + j, y = y0 + tx;
+        if (x < W && y < H) Px[(long long)x * H + y] = t[tx][j];
+    }
+}
+
 // 512 threads = 16 warps = a 32 x 16 tile of posts; three CTAs per SM (48 warps)
 // to hide the cache latency of the line walks
 constexpr int kVixWideThreads = 512;
@@ -635,7 +696,8 @@ __global__ void __launch_bounds__(kVixWideThreads, 3) k_vix_wide(const VixWide P
             todo &= todo - 1;
             const int ldx = __shfl_sync(0xffffffffu, dx, src), ldy = __shfl_sync(0xffffffffu, dy, src);
             const int lE = __shfl_sync(0xffffffffu, E, src), lts = __shfl_sync(0xffffffffu, tsl, src);
-            const bool vis = warp_los<COUNT>(P.z, P.pitch, P.zt, P.pitcht, x0 + src, y, lE, ldx, ldy, lts, nsteps);
+            const bool vis = P.py ? warp_los_pair<COUNT>(P.py, P.px, P.H, P.W, x0 + src, y, lE, ldx, ldy, lts, nsteps)
+                                  : warp_los<COUNT>(P.z, P.pitch, nullptr, 0, x0 + src, y, lE, ldx, ldy, lts, nsteps);
             if (vis) visbits |= 1u << src;
         }
         cnt += (visbits >> lane) & 1u;
@@ -655,8 +717,7 @@ __global__ void __launch_bounds__(kVixWideThreads, 3) k_vix_wide(const VixWide P
 struct VsR3 {
     const int16_t *z;
     long long pitch;
-    const int16_t *zt;  // transposed terrain or null
-    long long pitcht;
+    const uint32_t *py, *px;  // pair arrays of warp_los_pair, or null
     int H, W, R, ht, hr, PR, words;
     const int64_t *cand;
     long long n;
@@ -697,7 +758,9 @@ __global__ void __launch_bounds__(kR3Threads) k_viewshed_r3(const VsR3 P) {
             const int src = __ffs(todo) - 1;
             todo &= todo - 1;
             const int ldx = __shfl_sync(0xffffffffu, dx, src), lts = __shfl_sync(0xffffffffu, ts, src);
-            if (warp_los<false>(P.z, P.pitch, P.zt, P.pitcht, cx, cy, E, ldx, dy, lts, unused)) bits |= 1u << src;
+            const bool v = P.py ? warp_los_pair<false>(P.py, P.px, P.H, P.W, cx, cy, E, ldx, dy, lts, unused)
+                                : warp_los<false>(P.z, P.pitch, nullptr, 0, cx, cy, E, ldx, dy, lts, unused);
+            if (v) bits |= 1u << src;
         }
         if (lane == 0) {
             out[item] = bits;
@@ -766,24 +829,34 @@ static bool vix_wide(int R, int S) {
     return tune_get(VS_TUNE_VIX_TILE, R, 0) == 3 || !vix_staged_fits(R, S);
 }
 
-static long long vix_pitcht(int H) { return ((long long)H + 7) & ~7ll; }
+// the two pair arrays of warp_los_pair: 4 bytes per post each
+static size_t pairs_bytes(int H, int W) { return (size_t)H * (size_t)W * 8 + 512; }
+
+// build the pair arrays in the workspace when it is large enough
+static bool pairs_make(const vs_grid &g, void *ws, size_t ws_bytes, cudaStream_t s, uint32_t **py, uint32_t **px) {
+    *py = *px = nullptr;
+    if (!ws || ws_bytes < pairs_bytes(g.H, g.W)) return true;
+    uint32_t *a = (uint32_t *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    uint32_t *b = (uint32_t *)(((uintptr_t)(a + (size_t)g.H * g.W) + 255) & ~(uintptr_t)255);
+    const dim3 tg((unsigned)((g.W + 31) / 32), (unsigned)((g.H + 31) / 32));
+    k_pairs_i16<<<tg, 256, 0, s>>>(g.z, g.pitch, g.H, g.W, a, b);
+    if (cudaGetLastError() != cudaSuccess) return false;
+    *py = a;
+    *px = b;
+    return true;
+}
 
 static int vix_launch_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
                            uint8_t *vix_out, unsigned long long *steps, void *ws, size_t ws_bytes,
                            cudaStream_t s, int NR) {
-    const long long pitcht = vix_pitcht(g.H);
-    // offsets along a line (up to crossing D + 95, D <= 1.42 R) are 32-bit
-    if ((long long)(3 * R + 128) * std::max<long long>(g.pitch, pitcht) >= (1ll << 31)) return VS_ERR_RANGE;
-    const size_t need = (size_t)g.W * (size_t)pitcht * 2 + 256;
-    int16_t *zt = nullptr;
-    if (ws && ws_bytes >= need) {
-        zt = (int16_t *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-        const dim3 tg((unsigned)((g.W + 31) / 32), (unsigned)((g.H + 31) / 32));
-        k_transpose_i16_vix<<<tg, 256, 0, s>>>(g.z, g.pitch, g.H, g.W, zt, pitcht);
-        VS_CUDA_TRY(cudaGetLastError());
-    }
+    uint32_t *py, *px;
+    // without the pair arrays, offsets along a line (up to crossing D + 95,
+    // D <= 1.42 R) in the plain layout are 32-bit
+    if ((!ws || ws_bytes < pairs_bytes(g.H, g.W)) && (long long)(3 * R + 128) * g.pitch >= (1ll << 31))
+        return VS_ERR_RANGE;
+    if (!pairs_make(g, ws, ws_bytes, s, &py, &px)) return VS_ERR_CUDA;
     VixWide P;
-    P.z = g.z; P.pitch = g.pitch; P.zt = zt; P.pitcht = pitcht;
+    P.z = g.z; P.pitch = g.pitch; P.py = py; P.px = px;
     P.H = g.H; P.W = g.W; P.R = R; P.ht = ht; P.hr = hr; P.S = S; P.NR = NR;
     P.seed = seed; P.out = vix_out; P.steps = steps;
     const size_t smem = (size_t)(4 * R + 3) * 4;
@@ -903,7 +976,7 @@ extern "C" int vs_vix_count(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_
 extern "C" size_t vs_vix_workspace(int32_t H, int32_t W, int32_t R, int32_t S) {
     if (H < 1 || W < 1 || H > kMaxH || W > kMaxH || R < 1 || R > kMaxR || S < 0 || S > 255) return 0;
     if (!vix_wide(R, S)) return 0;
-    return (size_t)W * (size_t)vix_pitcht(H) * 2 + 256;
+    return pairs_bytes(H, W);
 }
 
 extern "C" int vs_vix_ws(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
@@ -913,7 +986,7 @@ extern "C" int vs_vix_ws(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S
 
 extern "C" size_t vs_viewshed_r3_workspace(int32_t H, int32_t W) {
     if (H < 1 || W < 1 || H > kMaxH || W > kMaxH) return 0;
-    return (size_t)W * (size_t)vix_pitcht(H) * 2 + 256;
+    return pairs_bytes(H, W);
 }
 
 extern "C" int vs_viewshed_r3(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand, int64_t n,
@@ -924,23 +997,22 @@ extern "C" int vs_viewshed_r3(vs_grid g, int32_t R, int32_t ht, int32_t hr, cons
     if (ht < -100000 || ht > 100000 || hr < -100000 || hr > 100000) return VS_ERR_RANGE;
     if (n < 0 || n > 0x7fffffffll) return VS_ERR_RANGE;
     if (n > 0 && (!cand || !bm_out || !area_out)) return VS_ERR_ARG;
-    const long long pitcht = vix_pitcht(g.H);
-    if ((long long)(3 * R + 128) * std::max<long long>(g.pitch, pitcht) >= (1ll << 31)) return VS_ERR_RANGE;
+    const bool pairs = ws && ws_bytes >= pairs_bytes(g.H, g.W);
+    if (!pairs && (long long)(3 * R + 128) * g.pitch >= (1ll << 31)) return VS_ERR_RANGE;
     if (n == 0) return VS_OK;
     if ((rc = check_device())) return rc;
     cudaStream_t s = (cudaStream_t)st;
     VsR3 P;
-    P.z = g.z; P.pitch = g.pitch; P.zt = nullptr; P.pitcht = pitcht;
+    P.z = g.z; P.pitch = g.pitch; P.py = nullptr; P.px = nullptr;
     P.H = g.H; P.W = g.W; P.R = R; P.ht = ht; P.hr = hr;
     P.PR = (2 * R) / 32 + 2;
     P.words = (2 * R + 1) * P.PR;
     P.cand = cand; P.n = n; P.bm = bm_out; P.area = area_out;
-    if (ws && ws_bytes >= vs_viewshed_r3_workspace(g.H, g.W)) {
-        int16_t *zt = (int16_t *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-        const dim3 tg((unsigned)((g.W + 31) / 32), (unsigned)((g.H + 31) / 32));
-        k_transpose_i16_vix<<<tg, 256, 0, s>>>(g.z, g.pitch, g.H, g.W, zt, pitcht);
-        VS_CUDA_TRY(cudaGetLastError());
-        P.zt = zt;
+    if (pairs) {
+        uint32_t *py, *px;
+        if (!pairs_make(g, ws, ws_bytes, s, &py, &px) || !py) return VS_ERR_CUDA;
+        P.py = py;
+        P.px = px;
     }
     k_viewshed_r3<<<(unsigned)n, kR3Threads, 0, s>>>(P);
     VS_CUDA_TRY(cudaGetLastError());
