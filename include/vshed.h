@@ -200,15 +200,16 @@ int vs_findmax_f32(const float *score, int32_t H, int32_t W, int32_t stride, int
  * Windows that fit in shared memory (R up to ~280 posts) are staged there by
  * TMA.  Larger ROIs -- the paper's own runs use R = 500..2000 (Sec.
  * "Experiments", Tables of the DEM1000 and US-West runs) -- walk the rays in
- * bands of steps against the terrain in global memory; the x-major rays read
- * a transposed copy of the terrain that the call writes into the workspace
- * first.  Both paths give identical bitmaps.
+ * bands of steps against the terrain in global memory, read from two arrays
+ * that pair every post with its neighbour along x and along y (one of them
+ * transposed), which the call writes into the workspace first.  Both paths
+ * give identical bitmaps.
  *
  * ws / ws_bytes: workspace of at least vs_viewshed_workspace(H, W, R, n)
  * bytes: 0 when the window fits in shared memory (ws may then be NULL), else
- * W x ceil8(H) int16 for the transposed terrain plus 256 bytes of alignment
- * (4.3 GB at 46400^2).  Too small: VS_ERR_WS.  With a large R the row pitch
- * must satisfy R * (max(pitch, ceil8(H)) + 1) < 2^31 (else VS_ERR_RANGE).
+ * 8 x H x W plus 512 bytes for the pair arrays (17.2 GB at 46400^2).  Too
+ * small: VS_ERR_WS.  With a large R, R * (max(H, W) + 1) < 2^31 (else
+ * VS_ERR_RANGE).
  * ---------------------------------------------------------------------- */
 int64_t vs_bitmap_words(int32_t R); /* (2R+1) * (floor(2R/32)+2) */
 size_t vs_viewshed_workspace(int32_t H, int32_t W, int32_t R, int64_t n);

@@ -296,10 +296,10 @@ __global__ void __launch_bounds__(512) k_viewshed_batch(const __grid_constant__ 
 // paper's own runs use R = 500 .. 2000) one CTA per candidate walks the rays
 // of each side of the ring side by side, one ray per thread, in bands of
 // steps.  The terrain is read through the L1/L2 caches instead of a staged
-// window.  Rays of the east and west sides (x-major) read a transposed copy of
-// the terrain, so that neighbouring rays -- neighbouring threads -- read
-// neighbouring addresses, as the north and south sides (y-major) do in the
-// terrain itself.  Each band's visible cells collect in a shared-memory tile
+// window, from two arrays that pair every post with its neighbour along a
+// ray's minor axis (one 32-bit load per step); the east / west one is
+// transposed, so that neighbouring rays -- neighbouring threads -- read
+// neighbouring words, as the north / south one is in terrain order.  Each band's visible cells collect in a shared-memory tile
 // that is then ORed into the candidate's bitmap in global memory.  East / west:
 // every window row x 4 words (128 columns), neighbouring rays on neighbouring
 // rows.  North / south: 32 window rows stored by column -- one word per column,
@@ -318,8 +318,11 @@ constexpr int kWideBN = 32;   // north / south tile: window rows per band (bits 
 struct VsWide {
     const int16_t *z;
     long long pitch;
-    const int16_t *zt;  // zt[x * pitcht + y] = z[y * pitch + x]
-    long long pitcht;
+    // each post with its neighbour along a ray's minor axis, one 32-bit load:
+    // pe[x*H + y] = z(x, y) | z(x, y+1) << 16 (east / west rays, transposed so
+    // that neighbouring rays read neighbouring words), pn[y*W + x] = z(x, y) |
+    // z(x+1, y) << 16 (north / south rays); a half past the grid edge is 0
+    const uint32_t *pe, *pn;
     int H, W, R, ht, hr, PR, words;
     const int64_t *cand;
     long long n;
@@ -327,20 +330,27 @@ struct VsWide {
     int32_t *area;
 };
 
-// zt = transpose of z (32 x 32 tiles through shared memory)
-__global__ void __launch_bounds__(256) k_transpose_i16(const int16_t *__restrict__ z, long long pitch, int H,
-                                                       int W, int16_t *__restrict__ zt, long long pitcht) {
-    __shared__ int t[32][33];
+// the pair arrays of k_viewshed_wide, one 32 x 32 block of posts per CTA: pn
+// row by row, pe through a shared-memory transpose (both coalesced)
+__global__ void __launch_bounds__(256) k_vs_pairs(const int16_t *__restrict__ z, long long pitch, int H, int W,
+                                                  uint32_t *__restrict__ pe, uint32_t *__restrict__ pn) {
+    __shared__ uint32_t t[32][33];
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int j = ty; j < 32; j += 8) {
         const int y = y0 + j, x = x0 + tx;
-        if (y < H && x < W) t[j][tx] = z[(long long)y * pitch + x];
+        if (y < H && x < W) {
+            const uint32_t z0 = (uint16_t)z[(long long)y * pitch + x];
+            const uint32_t zx = x + 1 < W ? (uint16_t)z[(long long)y * pitch + x + 1] : 0u;
+            const uint32_t zy = y + 1 < H ? (uint16_t)z[(long long)(y + 1) * pitch + x] : 0u;
+            pn[(long long)y * W + x] = z0 | (zx << 16);
+            t[j][tx] = z0 | (zy << 16);
+        }
     }
     __syncthreads();
     for (int j = ty; j < 32; j += 8) {
         const int x = x0 + j, y = y0 + tx;
-        if (x < W && y < H) zt[(long long)x * pitcht + y] = (int16_t)t[tx][j];
+        if (x < W && y < H) pe[(long long)x * H + y] = t[tx][j];
     }
 }
 
@@ -388,8 +398,8 @@ __global__ void __launch_bounds__(kWideThreads, 2) k_viewshed_wide(const VsWide 
         const int elo = xmaj ? -R : -R + 1, ehi = -elo;
         const int omaj = xmaj ? cx : cy, omin = xmaj ? cy : cx;
         const int major_lim = xmaj ? P.W : P.H, minor_lim = xmaj ? P.H : P.W;
-        const int16_t *base = xmaj ? P.zt + (long long)cx * P.pitcht + cy : P.z + (long long)cy * P.pitch + cx;
-        const int pm = (int)(xmaj ? P.pitcht : P.pitch);
+        const uint32_t *base = xmaj ? P.pe + (long long)cx * P.H + cy : P.pn + (long long)cy * P.W + cx;
+        const int pm = xmaj ? P.H : P.W;
         for (int ea = elo; ea <= ehi; ea += nt) {
             const int eb = min(ehi, ea + nt - 1);
             const int e = ea + tid;  // this thread's ray
@@ -444,8 +454,10 @@ __global__ void __launch_bounds__(kWideThreads, 2) k_viewshed_wide(const VsWide 
                         if (f >= R) { f -= R; y0 += 1; a0 += 1; }
                         const int rb = (2 * f >= thr) ? 1 : 0;
                         const int rnd = y0 + rb;
-                        const int zc = __ldg(base + a0 + rb);
-                        const int zo = f > 0 ? (int)__ldg(base + a0 + (rb ? 0 : 1)) : zc;
+                        // both straddling posts in one load (inside the grid here)
+                        const uint32_t pr = __ldg(base + a0);
+                        const int lo = (int16_t)(pr & 0xFFFFu), hi = (int16_t)(pr >> 16);
+                        const int zc = rb ? hi : lo, zo = rb ? lo : hi;
                         const bool vis = (Hk == 0) || ((long long)(zc * R + hreR) * Hk >= (long long)Hn * k);
                         if (vis) {
                             if (xmaj) {
@@ -474,12 +486,15 @@ __global__ void __launch_bounds__(kWideThreads, 2) k_viewshed_wide(const VsWide 
                             alive = false;
                             break;
                         }
-                        // both straddling posts loaded before the test; the
-                        // other post only where it lies inside the grid
+                        // both straddling posts in one load from the pair of the
+                        // first one; when that post lies outside the grid (the ray
+                        // stops after this test) the pair of the tested cell
                         const int m0 = omin + y0;
                         const bool stop = f > 0 && (m0 < 0 || m0 + 1 >= minor_lim);
-                        const int zc = __ldg(base + a0 + rb);
-                        const int zo = (f > 0 && !stop) ? (int)__ldg(base + a0 + (rb ? 0 : 1)) : zc;
+                        const bool up = rb && !stop;  // tested cell = upper half
+                        const uint32_t pr = __ldg(base + a0 + ((rb && stop) ? 1 : 0));
+                        const int lo = (int16_t)(pr & 0xFFFFu), hi = (int16_t)(pr >> 16);
+                        const int zc = up ? hi : lo, zo = up ? lo : hi;
                         const bool vis = (Hk == 0) || ((long long)(zc * R + hreR) * Hk >= (long long)Hn * k);
                         if (vis) {
                             if (xmaj)
@@ -569,19 +584,20 @@ static int vs_pick_split(int R, int *nsplit, int *WG, int *box_rows, int *nbox, 
 using namespace vs;
 
 // R whose window does not fit in shared memory (or forced by the tuning
-// table) takes the banded kernel, which needs the transposed terrain
+// table) takes the banded kernel, which needs the pair arrays
 static bool vs_wide(int R) {
     if (tune_get(VS_TUNE_VIEWSHED_WIDE, R, 0) == 1) return true;
     int ns = 0, wg = 0, br = 0, nb = 0;
     size_t sm = 0;
     return vs_pick_split(R, &ns, &wg, &br, &nb, &sm) != VS_OK;
 }
-static long long vs_pitcht(int H) { return ((long long)H + 7) & ~7ll; }
+// the two pair arrays of the banded kernel: 4 bytes per post each
+static size_t vs_pairs_bytes(int H, int W) { return (size_t)H * (size_t)W * 8 + 512; }
 
 extern "C" size_t vs_viewshed_workspace(int32_t H, int32_t W, int32_t R, int64_t n) {
     (void)n;
     if (H < 1 || W < 1 || H > kMaxH || W > kMaxH || R < 1 || R > kMaxR || !vs_wide(R)) return 0;
-    return (size_t)W * (size_t)vs_pitcht(H) * 2 + 256;
+    return vs_pairs_bytes(H, W);
 }
 
 static int vs_viewshed_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand,
@@ -592,19 +608,19 @@ static int vs_viewshed_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr,
     if (ht < -100000 || ht > 100000 || hr < -100000 || hr > 100000) return VS_ERR_RANGE;
     if (n < 0 || n > 0x7fffffffll) return VS_ERR_RANGE;
     if (n > 0 && (!cand || !bm_out || !area_out)) return VS_ERR_ARG;
-    const long long pitcht = vs_pitcht(g.H);
     // window offsets of the ray walk are 32-bit
-    if ((long long)R * (std::max<long long>(g.pitch, pitcht) + 1) >= (1ll << 31)) return VS_ERR_RANGE;
+    if ((long long)R * ((long long)std::max(g.H, g.W) + 1) >= (1ll << 31)) return VS_ERR_RANGE;
     const size_t need = vs_viewshed_workspace(g.H, g.W, R, n);
     if (n == 0) return VS_OK;
     if (!ws || ws_bytes < need) return VS_ERR_WS;
     if ((rc = check_device())) return rc;
-    int16_t *zt = (int16_t *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    uint32_t *pe = (uint32_t *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    uint32_t *pn = (uint32_t *)(((uintptr_t)(pe + (size_t)g.H * g.W) + 255) & ~(uintptr_t)255);
     const dim3 tg((unsigned)((g.W + 31) / 32), (unsigned)((g.H + 31) / 32));
-    k_transpose_i16<<<tg, 256, 0, s>>>(g.z, g.pitch, g.H, g.W, zt, pitcht);
+    k_vs_pairs<<<tg, 256, 0, s>>>(g.z, g.pitch, g.H, g.W, pe, pn);
     VS_CUDA_TRY(cudaGetLastError());
     VsWide P;
-    P.z = g.z; P.pitch = g.pitch; P.zt = zt; P.pitcht = pitcht;
+    P.z = g.z; P.pitch = g.pitch; P.pe = pe; P.pn = pn;
     P.H = g.H; P.W = g.W; P.R = R; P.ht = ht; P.hr = hr;
     P.PR = words_per_row(R);
     P.words = (2 * R + 1) * P.PR;
