@@ -660,6 +660,7 @@ __global__ void __launch_bounds__(256) k_pairs_i16(const int16_t *__restrict__ z
 // 512 threads = 16 warps = a 32 x 16 tile of posts; three CTAs per SM (48 warps)
 // to hide the cache latency of the line walks
 constexpr int kVixWideThreads = 512;
+constexpr int kVixStrip = 16;  // tiles per strip of the visiting order
 
 template <bool COUNT>
 __global__ void __launch_bounds__(kVixWideThreads, 3) k_vix_wide(const VixWide P) {
@@ -670,7 +671,14 @@ __global__ void __launch_bounds__(kVixWideThreads, 3) k_vix_wide(const VixWide P
     int *hwtab = vix_tab + 2 * R + 2;   // 2R + 1 entries
     vix_tables(R, rowstart, hwtab, warp_tot);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int x0 = blockIdx.x * 32, y = blockIdx.y * (kVixWideThreads / 32) + wid;
+    // tiles visited in vertical strips of kVixStrip tiles, so that the CTAs
+    // resident at a time cover a compact block of posts whose lines (and the
+    // terrain around it) stay in L2, rather than a long band of rows
+    const int ntx = (P.W + 31) / 32, nty = (P.H + kVixWideThreads / 32 - 1) / (kVixWideThreads / 32);
+    const int b = blockIdx.x, strip = b / (kVixStrip * nty);
+    const int sw = min(kVixStrip, ntx - strip * kVixStrip), idx = b - strip * kVixStrip * nty;
+    const int tyb = idx / sw, txb = strip * kVixStrip + (idx - tyb * sw);
+    const int x0 = txb * 32, y = tyb * (kVixWideThreads / 32) + wid;
     const int x = x0 + lane;
     if (y >= P.H) return;  // whole warp: no block barrier follows
     const bool mine = x < P.W;
@@ -861,7 +869,7 @@ static int vix_launch_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, 
     P.seed = seed; P.out = vix_out; P.steps = steps;
     const size_t smem = (size_t)(4 * R + 3) * 4;
     const int rows = kVixWideThreads / 32;
-    const dim3 grid((unsigned)((g.W + 31) / 32), (unsigned)((g.H + rows - 1) / rows));
+    const dim3 grid((unsigned)(((g.W + 31) / 32) * ((g.H + rows - 1) / rows)));  // one tile per CTA
     if (steps) {
         VS_CUDA_TRY(cudaFuncSetAttribute(k_vix_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_vix_wide<true><<<grid, kVixWideThreads, smem, s>>>(P);
