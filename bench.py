@@ -352,6 +352,33 @@ def site_loop_bytes(cand, chosen, W, R, PR):
     return total
 
 
+def recorded_traffic(patches):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of each stage's
+    kernel, from the ncu capture summarised in profiles/traffic.json; a figure
+    is used only while the source file it was taken on hashes to the recorded
+    SHA-1 (else null).  CNN figures are per patch (times the bench's patches)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "traffic.json")
+    out = {}
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return out
+    import hashlib
+    for key, r in rec.get("stages", {}).items():
+        src = os.path.join(os.path.dirname(path), "..", r["source"])
+        try:
+            sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        except OSError:
+            continue
+        if sha != r["sha1"]:
+            continue
+        if "bytes_per_patch" in r:
+            out[key] = r["bytes_per_patch"] * patches if patches else None
+        else:
+            out[key] = r["bytes_per_launch"]
+    return out
+
+
 def coverage(result):
     ch, gn, _, nch = result
     t = int(nch.item())
@@ -911,6 +938,11 @@ def main():
         roof["cnn_lattice"] = {"bound": "tensor", "achieved": flops / (s_st[0] * 1e-3) / 1e12,
                                "peak": peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]),
                                "unit": "TFLOP/s", "traffic": None}
+    # DRAM bytes per launch from the committed ncu capture, while the kernel
+    # sources are those the counters were taken on
+    for key, tb in recorded_traffic(sur.score.numel() if sur else 0).items():
+        if key in roof:
+            roof[key]["traffic"] = tb
     for r in roof.values():
         r["frac"] = r["achieved"] / r["peak"]
     stage_roof = {"vix": "vix", "findmax": "findmax", "viewshed": "viewshed", "site": "site_loop",
