@@ -85,3 +85,50 @@ def test_binding_refuses_cpu_tensors():
     import paper_2006_16783_gb300 as V
     with pytest.raises(ValueError):
         V.findmax(torch.zeros((4, 4), dtype=torch.uint8), 2, 1)
+
+
+def test_large_roi_size_queries(L):
+    """Workspaces of the large-ROI paths: none while the staged kernels cover
+    R, pair arrays (8 bytes per post) beyond; tuning values checked."""
+    from paper_2006_16783_gb300 import vshed
+    assert L.vs_viewshed_workspace(1000, 1000, 100, 10) == 0
+    assert L.vs_viewshed_workspace(1000, 1000, 280, 10) == 0
+    assert L.vs_viewshed_workspace(1000, 1200, 1000, 10) >= 8 * 1000 * 1200
+    assert L.vs_vix_workspace(1000, 1000, 100, 10) == 0
+    assert L.vs_vix_workspace(1000, 1200, 1000, 10) >= 8 * 1000 * 1200
+    assert L.vs_viewshed_r3_workspace(300, 400) >= 8 * 300 * 400
+    assert L.vs_site_ex_workspace(1000, 100) > L.vs_site_workspace(1000, 100)
+    # forcing the large-ROI kernels at a small R makes them need the workspace
+    assert L.vs_tune_set(vshed.VS_TUNE_VIEWSHED_WIDE, 50, 1) == 0
+    try:
+        assert L.vs_viewshed_workspace(500, 500, 50, 10) > 0
+    finally:
+        L.vs_tune_set(vshed.VS_TUNE_VIEWSHED_WIDE, 50, 0)
+    assert L.vs_viewshed_workspace(500, 500, 50, 10) == 0
+    assert L.vs_tune_set(vshed.VS_TUNE_VIEWSHED_WIDE, 50, 2) == vshed.VS_ERR_RANGE
+    assert L.vs_tune_set(vshed.VS_TUNE_SITE_LAZY, 50, 3) == vshed.VS_ERR_RANGE
+    assert L.vs_tune_set(vshed.VS_TUNE_VIX_TILE, 50, 4) == vshed.VS_ERR_RANGE
+    assert L.vs_tune_set(5, 50, 0) == vshed.VS_ERR_RANGE
+
+
+def test_large_roi_argument_errors_need_no_device(L):
+    from paper_2006_16783_gb300 import vshed
+    g = vshed.vs_grid(300, 320, 320, 4096)
+    d = ctypes.c_void_p(4096)
+    # banded viewshed: workspace missing
+    assert L.vs_viewshed(g, 400, 10, 10, d, 3, d, d, None, 0, None) == vshed.VS_ERR_WS
+    # heights out of range, R out of range
+    assert L.vs_viewshed(g, 400, 200001, 10, d, 3, d, d, None, 0, None) == vshed.VS_ERR_RANGE
+    assert L.vs_viewshed_r3(g, 0, 10, 10, d, 3, d, d, None, 0, None) == vshed.VS_ERR_RANGE
+    assert L.vs_viewshed_r3(g, 5, 10, 10, None, 3, d, d, None, 0, None) == vshed.VS_ERR_ARG
+    # site with options: terrain of another size, workspace missing, weights too
+    # wide for 32-bit gains
+    opt = vshed.vs_site_options(vshed.vs_grid(100, 100, 104, 4096), 10, None)
+    assert L.vs_site_ex(d, d, 3, 300, 320, 20, 5, 0.0, ctypes.byref(opt), d, d, d, d, d, 1 << 20,
+                        None) == vshed.VS_ERR_ARG
+    opt = vshed.vs_site_options(g, 10, None)
+    assert L.vs_site_ex(d, d, 3, 300, 320, 20, 5, 0.0, ctypes.byref(opt), d, d, d, d, None, 0,
+                        None) == vshed.VS_ERR_WS
+    opt = vshed.vs_site_options(vshed.vs_grid(0, 0, 0, 0), 0, 4096)
+    assert L.vs_site_ex(d, d, 3, 300, 320, 2100, 5, 0.0, ctypes.byref(opt), d, d, d, d, d, 1 << 30,
+                        None) == vshed.VS_ERR_RANGE
