@@ -68,6 +68,11 @@ const char *vs_strerror(int code);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int vs_version(void);
 
+/* Number of kernel launches the library has issued in this process (counted
+ * on the host as each launch is made; replays of a captured CUDA graph launch
+ * without passing through the library and are not counted). */
+uint64_t vs_launch_count(void);
+
 /* Launch-shape table used by the kernels, filled by an autotuner (the
  * library's Python autotune module times the candidates and stores the
  * fastest).  The results of every call are independent of these settings.

@@ -1003,6 +1003,7 @@ extern "C" int vs_cnn_pack(const float *master, void *packed, vs_stream_t st) {
     int rc = check_device();
     if (rc) return rc;
     cnn::k_cnn_pack<<<64, 256, 0, (cudaStream_t)st>>>(master, (unsigned char *)packed);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }
@@ -1034,6 +1035,7 @@ static int cnn_forward_launch(vs_grid g, const int64_t *centers, int64_t n, int3
     GridMap gm;  // 72 x 65 post tiles for the staged patches
     if ((rc = make_grid_map(&gm, g, cnn::kStageW / 8, cnn::kPatch))) return rc;
     cnn::k_cnn_forward<<<(unsigned)grid, cnn::kThreads, cnn::kSmemBytes, (cudaStream_t)st>>>(gm.map, P);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }
@@ -1093,6 +1095,7 @@ extern "C" int vs_cnn_backward(const void *save, const float *labels, int64_t B,
     const unsigned char *sv = (const unsigned char *)save;
     cnn::k_cnn_head_bwd<<<(unsigned)((B * 32 + 255) / 256), 256, 0, s>>>(sv, labels, B, 1.0f / (float)B,
                                                                           master, grads, da[4], loss_sum);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     int dev = 0, sms = 0;
     VS_CUDA_TRY(cudaGetDevice(&dev));
@@ -1103,6 +1106,7 @@ extern "C" int vs_cnn_backward(const void *save, const float *labels, int64_t B,
         const unsigned grid = (unsigned)std::min<long long>(B, (long long)sms);
         cnn::k_cnn_conv_bwd<<<grid, cnn::kBwdThreads, smem, s>>>(sv, B, l, da[l], master, grads,
                                                                   l > 0 ? da[l - 1] : nullptr);
+        vs::note_launch();
         VS_CUDA_TRY(cudaGetLastError());
     }
     return VS_OK;
@@ -1118,6 +1122,7 @@ extern "C" int vs_cnn_adam(float *master, float *grads, float *m, float *v, int6
     const int n = cnn::kNParams;
     cnn::k_cnn_adam<<<(n + 255) / 256, 256, 0, (cudaStream_t)st>>>(master, grads, m, v, n, lr, beta1,
                                                                    beta2, eps, c1, c2);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }

@@ -194,17 +194,21 @@ static int findmax_launch(const V *val, int32_t H, int32_t W, int32_t stride, in
     // (the last word must not run past the caller's buffer)
     if (sizeof(V) == 1 && stride == 1 && k <= 8 && (((uintptr_t)val) & 3) == 0 &&
         ((long long)H * W) % 4 == 0) {
-        if (k <= 4)
+        if (k <= 4) {
             k_findmax_u8<4><<<(unsigned)(nby * nbx), kFmThreads, 0, (cudaStream_t)st>>>(
                 (const uint8_t *)val, H, W, block, k, (int)nbx, nullptr, cand_out);
-        else
+            vs::note_launch();
+        } else {
             k_findmax_u8<8><<<(unsigned)(nby * nbx), kFmThreads, 0, (cudaStream_t)st>>>(
                 (const uint8_t *)val, H, W, block, k, (int)nbx, nullptr, cand_out);
+            vs::note_launch();
+        }
         VS_CUDA_TRY(cudaGetLastError());
         return VS_OK;
     }
     k_findmax<V><<<(unsigned)(nby * nbx), kFmThreads, 0, (cudaStream_t)st>>>(
         val, H, W, stride, Ws, block, k, (int)nbx, cand_out);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }

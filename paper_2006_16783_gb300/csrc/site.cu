@@ -1605,11 +1605,14 @@ static int site_lazy(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
     VS_CUDA_TRY(cudaMemsetAsync(cursor, 0, (size_t)ncell * 4, s));
     const unsigned gb = (unsigned)((n + 255) / 256);
     k_lazy_count<<<gb, 256, 0, s>>>(cand, (int)n, H, W, (int)cs, ncx, cursor);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     // counts -> starts, and the cursors (in place) for the scatter
     k_lazy_scan<<<1, 1024, 0, s>>>(cursor, ncell, cstart, cursor);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     k_lazy_scatter<<<gb, 256, 0, s>>>(cand, (int)n, H, W, (int)cs, ncx, cursor, citems);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     LazyParams L;
     L.bm = bm; L.cand = cand; L.n = (int)n; L.H = H; L.W = W; L.R = R;
@@ -1638,6 +1641,7 @@ static int site_lazy(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
             VS_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(LazyCtl), s));
             void *args[] = {(void *)&L, (void *)&ctl, (void *)&work};
             VS_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3((unsigned)sms), dim3(kSiteThreads), args, 0, s));
+            vs::note_launch();
             return VS_OK;
         }
         if (opt) return VS_ERR_DEVICE;  // the options run on the grid kernel only
@@ -1645,6 +1649,7 @@ static int site_lazy(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
     const size_t smem = (size_t)nb * 12 + 16;
     VS_CUDA_TRY(cudaFuncSetAttribute(k_site_lazy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_site_lazy<<<1, kSiteThreads, smem, s>>>(L);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }
@@ -1661,6 +1666,7 @@ extern "C" int vs_site_gains(const uint32_t *bm, const int64_t *cand, int64_t n,
     const int per = kGainThreads / 32;
     k_site_gains<<<(unsigned)((n + per - 1) / per), kGainThreads, 0, (cudaStream_t)st>>>(
         bm, cand, n, H, W, R, cum, gains_out);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }
@@ -1741,6 +1747,7 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
         VS_CUDA_TRY(cudaMemsetAsync(cov, 0, 8, s));
         const int64_t nw = (int64_t)H * P.WWc;
         k_cum_popcount<<<4 * 152, 256, 0, s>>>(cum, nw, cov);
+        vs::note_launch();
         VS_CUDA_TRY(cudaGetLastError());
     }
     if (n > 0 && (rc = vs_site_gains(bm, cand, n, H, W, R, cum, g0, st))) return rc;
@@ -1756,17 +1763,22 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
             const unsigned nch = (unsigned)((n + kRankChunk - 1) / kRankChunk);
             uint64_t *keys = (uint64_t *)slo;
             k_rank_chunks<<<nch, kRankChunk, 0, s>>>(cand, n, (int64_t)H * W, keys, sp);
+            vs::note_launch();
             VS_CUDA_TRY(cudaGetLastError());
             if (nch > 1) {
                 k_rank_cross<<<dim3(nch, nch), kRankChunk, 0, s>>>(keys, n, sp);
+                vs::note_launch();
                 VS_CUDA_TRY(cudaGetLastError());
             }
             k_rank_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sp, n, sorig);
+            vs::note_launch();
             VS_CUDA_TRY(cudaGetLastError());
             k_rank_posts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cand, sorig, n, (int64_t)H * W, sp);
+            vs::note_launch();
             VS_CUDA_TRY(cudaGetLastError());
         }
         k_site_bands<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sp, n, W, R, slo, shi);
+        vs::note_launch();
         VS_CUDA_TRY(cudaGetLastError());
         Site1Params Q1;
         Q1.bm = bm; Q1.n = (int)n; Q1.H = H; Q1.W = W; Q1.R = R; Q1.PR = P.PR; Q1.words = P.words;
@@ -1797,12 +1809,14 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
                 cfg.attrs = at;
                 cfg.numAttrs = 1;
                 VS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_site_loopq, Q1));
+                vs::note_launch();
                 return VS_OK;
             }
         }
         VS_CUDA_TRY(cudaFuncSetAttribute(k_site_loop1, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem1));
         k_site_loop1<<<1, kSiteThreads, smem1, s>>>(Q1);
+        vs::note_launch();
         VS_CUDA_TRY(cudaGetLastError());
         return VS_OK;
     }
@@ -1837,6 +1851,7 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
     cfg.attrs = at;
     cfg.numAttrs = 1;
     VS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_site_loop, P));
+    vs::note_launch();
     return VS_OK;
 }
 
@@ -1924,6 +1939,7 @@ extern "C" int vs_site_ex(const uint32_t *bm, const int64_t *cand, int64_t n, in
     if (wtd) {
         VS_CUDA_TRY(cudaMemsetAsync(o.wsum, 0, 16, s));
         k_weight_sums<<<4 * 152, 256, 0, s>>>(cum, o.weight, H, W, o.wsum);
+        vs::note_launch();
         VS_CUDA_TRY(cudaGetLastError());
     } else {
         if (coverage_target > 0.0) {
@@ -1932,6 +1948,7 @@ extern "C" int vs_site_ex(const uint32_t *bm, const int64_t *cand, int64_t n, in
             if ((double)need < nd) need += 1;
             VS_CUDA_TRY(cudaMemsetAsync(cov, 0, 8, s));
             k_cum_popcount<<<4 * 152, 256, 0, s>>>(cum, (int64_t)H * ((W + 31) / 32), cov);
+            vs::note_launch();
             VS_CUDA_TRY(cudaGetLastError());
         }
         if ((rc = vs_site_gains(bm, cand, n, H, W, R, cum, g0, st))) return rc;
@@ -1983,6 +2000,7 @@ extern "C" int vs_site_batch(const vs_site_job *jobs, int32_t n_jobs, void *ws, 
     VS_CUDA_TRY(cudaFuncSetAttribute(k_site_loop1_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     k_site_loop1_batch<<<nb, kSiteThreads, smem, (cudaStream_t)st>>>(B);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }

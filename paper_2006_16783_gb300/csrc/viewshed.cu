@@ -618,6 +618,7 @@ static int vs_viewshed_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr,
     uint32_t *pn = (uint32_t *)(((uintptr_t)(pe + (size_t)g.H * g.W) + 255) & ~(uintptr_t)255);
     const dim3 tg((unsigned)((g.W + 31) / 32), (unsigned)((g.H + 31) / 32));
     k_vs_pairs<<<tg, 256, 0, s>>>(g.z, g.pitch, g.H, g.W, pe, pn);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     VsWide P;
     P.z = g.z; P.pitch = g.pitch; P.pe = pe; P.pn = pn;
@@ -628,6 +629,7 @@ static int vs_viewshed_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr,
     const size_t smem = wide_smem_bytes(R);
     VS_CUDA_TRY(cudaFuncSetAttribute(k_viewshed_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_viewshed_wide<<<(unsigned)n, kWideThreads, smem, s>>>(P);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }
@@ -675,6 +677,7 @@ extern "C" int vs_viewshed(vs_grid g, int32_t R, int32_t ht, int32_t hr, const i
     VS_CUDA_TRY(cudaFuncSetAttribute(k_viewshed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int threads = tune_get(VS_TUNE_VIEWSHED_THREADS, R, default_threads(R));
     k_viewshed<<<(unsigned)n, threads, smem, (cudaStream_t)st>>>(J);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }
@@ -729,6 +732,7 @@ extern "C" int vs_viewshed_batch(const vs_viewshed_job *jobs, int32_t n_jobs, vo
     VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_viewshed_batch, threads, smem));
     const long long grid = std::min<long long>(total, (long long)sms * std::max(per, 1));
     k_viewshed_batch<<<(unsigned)grid, threads, smem, s>>>(B);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }

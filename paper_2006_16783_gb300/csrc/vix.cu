@@ -848,6 +848,7 @@ static bool pairs_make(const vs_grid &g, void *ws, size_t ws_bytes, cudaStream_t
     uint32_t *b = (uint32_t *)(((uintptr_t)(a + (size_t)g.H * g.W) + 255) & ~(uintptr_t)255);
     const dim3 tg((unsigned)((g.W + 31) / 32), (unsigned)((g.H + 31) / 32));
     k_pairs_i16<<<tg, 256, 0, s>>>(g.z, g.pitch, g.H, g.W, a, b);
+    vs::note_launch();
     if (cudaGetLastError() != cudaSuccess) return false;
     *py = a;
     *px = b;
@@ -873,9 +874,11 @@ static int vix_launch_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, 
     if (steps) {
         VS_CUDA_TRY(cudaFuncSetAttribute(k_vix_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_vix_wide<true><<<grid, kVixWideThreads, smem, s>>>(P);
+        vs::note_launch();
     } else {
         VS_CUDA_TRY(cudaFuncSetAttribute(k_vix_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_vix_wide<false><<<grid, kVixWideThreads, smem, s>>>(P);
+        vs::note_launch();
     }
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
@@ -927,9 +930,11 @@ static int vix_launch(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, u
                 if (steps) {
                     VS_CUDA_TRY(cudaFuncSetAttribute(k_vix2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
                     k_vix2<true><<<grid, kVixThreads, b, (cudaStream_t)st>>>(gm.map, Q);
+                    vs::note_launch();
                 } else {
                     VS_CUDA_TRY(cudaFuncSetAttribute(k_vix2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
                     k_vix2<false><<<grid, kVixThreads, b, (cudaStream_t)st>>>(gm.map, Q);
+                    vs::note_launch();
                 }
                 VS_CUDA_TRY(cudaGetLastError());
                 return VS_OK;
@@ -962,9 +967,11 @@ static int vix_launch(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, u
     if (steps) {
         VS_CUDA_TRY(cudaFuncSetAttribute(k_vix<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_vix<true><<<grid, kVixThreads, smem, (cudaStream_t)st>>>(gm.map, P);
+        vs::note_launch();
     } else {
         VS_CUDA_TRY(cudaFuncSetAttribute(k_vix<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_vix<false><<<grid, kVixThreads, smem, (cudaStream_t)st>>>(gm.map, P);
+        vs::note_launch();
     }
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
@@ -1023,6 +1030,7 @@ extern "C" int vs_viewshed_r3(vs_grid g, int32_t R, int32_t ht, int32_t hr, cons
         P.px = px;
     }
     k_viewshed_r3<<<(unsigned)n, kR3Threads, 0, s>>>(P);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }

@@ -1,6 +1,7 @@
 // vs_api.cu -- host-side helpers of the C ABI: error strings, argument
 // checks, the TMA tensor-map builder and the size queries.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string.h>
 
@@ -53,6 +54,9 @@ int tune_get(int op, int R, int fallback) {
     return v > 0 ? v : fallback;
 }
 
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1ull, std::memory_order_relaxed); }
+
 int check_grid(const vs_grid &g) {
     if (!g.z) return VS_ERR_ARG;
     if (g.H < 1 || g.W < 1 || g.H > kMaxH || g.W > kMaxH) return VS_ERR_RANGE;
@@ -95,6 +99,8 @@ const char *vs_strerror(int code) {
 }
 
 int vs_version(void) { return 100; }
+
+uint64_t vs_launch_count(void) { return (uint64_t)vs::g_launches.load(std::memory_order_relaxed); }
 
 int vs_tune_set(int32_t op, int32_t R, int32_t value) {
     if (op < 0 || op >= vs::kTuneOps || R < 1 || R > vs::kMaxR) return VS_ERR_RANGE;
@@ -159,6 +165,7 @@ extern "C" int vs_selftest_wait_timeout(int32_t *status, uint32_t polls, vs_stre
     int rc = vs::check_device();
     if (rc) return rc;
     k_selftest_wait<<<1, 32, 0, (cudaStream_t)st>>>(status, polls);
+    vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;
 }

@@ -103,6 +103,9 @@ int make_grid_map(GridMap *gm, const vs_grid &g, int wg, int rows);
 // the stored value for (op, R) or `fallback`
 int tune_get(int op, int R, int fallback);
 
+// counts the kernel launches the library issues (vs_launch_count)
+void note_launch();
+
 // argument checks shared by several entry points
 int check_grid(const vs_grid &g);
 int check_device();  // current device is sm_103 (cached per device)

@@ -55,6 +55,7 @@ P, i32, i64, u64, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ct
 SIGNATURES = {
     "vs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "vs_version": (ctypes.c_int, []),
+    "vs_launch_count": (u64, []),
     "vs_selftest_wait_timeout": (ctypes.c_int, [P, ctypes.c_uint32, P]),
     "vs_tune_set": (ctypes.c_int, [i32, i32, i32]),
     "vs_tune_get": (ctypes.c_int, [i32, i32]),
@@ -417,6 +418,11 @@ def cnn_adam(master, grads, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-
 
 
 # ------------------------------------------------------------------ batching and tuning
+def launch_count():
+    """Kernel launches the library has issued in this process."""
+    return int(lib().vs_launch_count())
+
+
 def tune_set(op, R, value):
     _check("vs_tune_set", lib().vs_tune_set(op, R, value))
 
