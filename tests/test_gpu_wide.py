@@ -292,3 +292,36 @@ def test_viewshed_r3_flat_and_invalid(V, O):
     assert a[0] == disc
     assert a[1] == sum(1 for dy in range(0, R + 1) for dx in range(0, R + 1) if dx * dx + dy * dy <= R * R)
     assert a[2] == -1 and a[3] == -1 and not _np(bm[2:]).any()
+
+
+# ------------------------------------------------------------------ extreme values
+@pytest.mark.parametrize("R,ht,hr", [(4096, 100000, -100000), (700, -100000, 100000), (1500, 100000, 100000)])
+def test_wide_extreme_values(V, O, R, ht, hr):
+    """int16 extremes, the largest heights and the largest ROI: the 32-bit
+    values with 64-bit products of the large-ROI kernels stay exact."""
+    H, W = 150, 170
+    rng = np.random.default_rng(R)
+    z = rng.integers(-32768, 32768, (H, W)).astype(np.int16)
+    z[:, 40] = 32767                       # a wall of the highest posts
+    z[70, :] = -32768                      # a trench of the lowest
+    cand = _posts(H, W, 5, R)
+    _viewshed_vs_oracle(V, O, z, R, ht, hr, cand)
+    want = O.vix(z, R, ht, hr, 10, 99, threads=8)
+    got = _np(V.vix(_grid(V, z), R, ht, hr, 10, 99))
+    assert (got == want).all()
+    bm, _ = V.viewshed_r3(_grid(V, z), min(R, 200), ht, hr, torch.as_tensor(cand[:4]).cuda())
+    for i, p in enumerate(cand[:4]):
+        assert (_np(bm[i]).view(np.uint32) == O.viewshed_brute(z, min(R, 200), ht, hr, int(p))).all()
+
+
+def test_launch_count_counts_library_kernels(V):
+    """vs_launch_count grows by the kernels one call issues (a staged
+    viewshed: one launch)."""
+    H, W, R = 120, 130, 20
+    z = T.spectral_fbm(H, W, 0.8, 3, 0, 500).numpy()
+    g = _grid(V, z)
+    c = torch.tensor([5, 700, 4000], dtype=torch.int64).cuda()
+    V.viewshed(g, R, 10, 10, c)
+    n0 = V.launch_count()
+    V.viewshed(g, R, 10, 10, c)
+    assert V.launch_count() - n0 == 1
