@@ -356,7 +356,7 @@ def recorded_traffic(patches):
     """dram__bytes_read.sum + dram__bytes_write.sum per launch of each stage's
     kernel, from the ncu capture summarised in profiles/traffic.json; a figure
     is used only while the source file it was taken on hashes to the recorded
-    SHA-1 (else null).  CNN figures are per patch (times the bench's patches)."""
+    SHA-1 (else null); the CNN's figure only for the lattice it was taken on."""
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "traffic.json")
     out = {}
     try:
@@ -372,8 +372,8 @@ def recorded_traffic(patches):
             continue
         if sha != r["sha1"]:
             continue
-        if "bytes_per_patch" in r:
-            out[key] = r["bytes_per_patch"] * patches if patches else None
+        if "patches" in r:  # a lattice figure: valid for the same number of patches only
+            out[key] = r["bytes_per_launch"] if patches == r["patches"] else None
         else:
             out[key] = r["bytes_per_launch"]
     return out
