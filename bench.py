@@ -634,6 +634,8 @@ def run_paper(args, dist, rank, world, local):
     covered, nobs = coverage(res)
     los = int(steps_ctr.item()) if args.warmup else None
     steps_vs = interior_ray_steps(w.R) * n
+    sur_out = paper_surrogate(args, V, w, g, dev, vixbuf, bm, area, cum, sws, ws, nobs, ms, dist) \
+        if args.paper_surrogate else None
     out = {"metric": "paper-regime siting s (vix + findmax + viewshed + site to 95% coverage)",
            "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -649,8 +651,97 @@ def run_paper(args, dist, rank, world, local):
            "paper_context_s": {"vix": 130, "findmax": 9, "viewshed": 1706, "site": 3510,
                                "note": "the paper's US-West R=1000 run, 32-way CPU parallelism"},
            "clocks": clk, "gpu_launches": n_launch, "terrain_gen_s": gen_s}
+    if sur_out:
+        out["surrogate"] = sur_out
     if rank == 0:
         print(json.dumps(out, default=str))
+
+
+def paper_surrogate(args, V, w, g, dev, vixbuf, bm, area, cum, sws, ws, nobs_plain, ms_plain, dist):
+    """The learned proposal in the paper's regime: the network is trained on
+    exact R = 1000 visibility indices of another terrain of the recipe, with a
+    patch that spans the ROI (patch step 30: 65 posts 30 apart cover ~2R); it
+    scores a lattice (stride 64 gives >= 20 lattice posts per 334-post block),
+    findmax_f32 keeps 20 per block, and the exact viewshed and site steps run
+    to the same 95 % coverage.  Reported beside the plain pipeline."""
+    from paper_2006_16783_gb300 import surrogate as S
+    P = args.paper_patch_step
+    strides = [int(x) for x in str(args.paper_stride).split(",")]
+    t0 = time.perf_counter()
+    side = min(8192, w.H, w.W)
+    wtr = WL.scaled(w, side, side, name=w.name + "_train", seed=w.seed + 7)
+    ztr = wtr.make_terrain(dev)
+    ztr_s, _ = WL.terrain.pad_pitch(ztr, 8)
+    del ztr
+    gtr = V.Grid(ztr_s, side)
+    margin = 32 * P  # training patches inside the grid
+    posts = S.sample_posts(side, side, args.train_posts, margin, 11, dev)
+    labels = S.exact_vix(gtr, posts, w.R, w.ht, w.hr)
+    torch.cuda.synchronize()
+    label_s = time.perf_counter() - t0
+    tr = S.Trainer(S.init_master(0), batch=512, lr=2e-3, patch_step=P)
+    t1 = time.perf_counter()
+    loss = tr.fit([(gtr, posts, labels)], epochs=args.epochs, seed=3, log=lambda m: print(m, file=sys.stderr))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    del gtr, ztr_s, posts, labels
+    # held-out error on the bench terrain, beside the 10-sample vix
+    pt = S.sample_posts(w.H, w.W, 20000, margin, 5, dev)
+    lt = S.exact_vix(g, pt, w.R, w.ht, w.hr, ws=ws)
+    mae = float((tr.predict(g, pt) - lt).abs().mean())
+    mae_vix = float((vixbuf.reshape(-1)[pt].float() / w.S - lt).abs().mean())
+    common = {"patch_step": P, "train_terrain": "%dx%d, seed %d" % (side, side, w.seed + 7),
+              "train_posts": args.train_posts, "epochs": args.epochs, "train_loss_last_epoch": loss,
+              "label_s": label_s, "train_s": train_s, "mae_heldout": mae, "mae_sampled_vix": mae_vix,
+              "mae_posts": int(pt.numel()), "observers_plain": nobs_plain, "by_stride": {}}
+    for stride in strides:
+        common["by_stride"][str(stride)] = _paper_surrogate_run(args, V, w, g, dev, tr, P, stride, bm, area, cum,
+                                                                sws, ws, ms_plain, dist)
+    return common
+
+
+def _paper_surrogate_run(args, V, w, g, dev, tr, P, stride, bm, area, cum, sws, ws, ms_plain, dist):
+    """One lattice stride of the paper-regime proposal, timed like the plain pipeline."""
+    ns = V.findmax_count(w.H, w.W, stride, w.block, w.k)
+    assert ns <= bm.shape[0]
+    score = torch.empty(((w.H + stride - 1) // stride, (w.W + stride - 1) // stride), dtype=torch.float32,
+                        device=dev)
+    cand = torch.empty(ns, dtype=torch.int64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+
+    def step():
+        ev[0].record()
+        V.cnn_score_lattice(g, stride, tr.packed, out=score, patch_step=P)
+        ev[1].record()
+        V.findmax_f32(score, w.H, w.W, stride, w.block, w.k, out=cand)
+        ev[2].record()
+        V.viewshed(g, w.R, w.ht, w.hr, cand, bm=bm[:ns], area=area[:ns], ws=ws)
+        ev[3].record()
+        cum.zero_()
+        r = V.site(bm[:ns], cand, w.H, w.W, w.R, w.n_obs, w.target, cum=cum, ws=sws, sync=False)
+        ev[4].record()
+        return r
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stages, walls = [], []
+    n0 = V.launch_count()
+    for _ in range(args.steps):
+        res = step()
+        torch.cuda.synchronize()
+        stages.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+        walls.append(ev[0].elapsed_time(ev[4]))
+    n_launch = V.launch_count() - n0
+    ms = max_over_ranks(statistics.median(walls), dist, dev)
+    st = [statistics.median(x[i] for x in stages) for i in range(4)]
+    covered, nobs = coverage(res)
+    return {"s_per_step": ms / 1000.0, "stages_ms": dict(zip(["cnn_lattice", "findmax_f32", "viewshed", "site"], st)),
+            "speedup_vs_plain": ms_plain / ms, "candidates": ns, "observers": nobs,
+            "coverage_posts": covered, "coverage_frac": covered / float(w.H * w.W),
+            "patches_per_step": score.numel(), "gpu_launches": n_launch}
 
 
 def run_accuracy(args, dist, rank, world, local):
@@ -758,6 +849,12 @@ def main():
     ap.add_argument("--workload", default="full",
                     choices=["full", "mid", "scale", "small", "batch", "learn", "paper", "paper_mid",
                              "paper_small", "accuracy"])
+    ap.add_argument("--paper-surrogate", action="store_true",
+                    help="--workload paper*: also run the learned proposal trained on exact R-vix labels")
+    ap.add_argument("--paper-patch-step", type=int, default=30,
+                    help="post spacing of the CNN patch in the paper regime (65 posts 30 apart span ~2R)")
+    ap.add_argument("--paper-stride", default="64",
+                    help="lattice stride(s) of the paper-regime proposal, comma-separated")
     ap.add_argument("--accuracy-size", default="full", choices=["full", "mid"],
                     help="terrain of --workload accuracy: the headline recipe at 46400^2 or 11600^2")
     ap.add_argument("--no-cpu-baseline", action="store_true")

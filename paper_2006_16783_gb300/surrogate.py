@@ -37,17 +37,24 @@ def disc_in_grid(posts, H, W, R):
     return out
 
 
-def exact_vix(g, posts, R, ht, hr, chunk=100000):
-    """Exact visibility index of every listed post (fp32 in [0, 1])."""
+def exact_vix(g, posts, R, ht, hr, chunk=100000, max_bitmap_bytes=2 << 30, ws=None):
+    """Exact visibility index of every listed post (fp32 in [0, 1]).  The
+    viewsheds are computed in chunks whose bitmaps stay under
+    ``max_bitmap_bytes`` (512 KB per post at R = 1000)."""
+    words = (2 * R + 1) * V.words_per_row(R)
+    chunk = max(1, min(chunk, max_bitmap_bytes // (4 * words)))
     out = torch.empty(posts.numel(), dtype=torch.float32, device=posts.device)
     bm = torch.empty((min(chunk, posts.numel()), 2 * R + 1, V.words_per_row(R)), dtype=torch.int32,
                      device=posts.device)
     area = torch.empty(min(chunk, posts.numel()), dtype=torch.int32, device=posts.device)
+    wsb = V.viewshed_workspace(g.H, g.W, R, min(chunk, posts.numel()))
+    if wsb and (ws is None or ws.numel() < wsb):
+        ws = torch.empty(wsb, dtype=torch.uint8, device=posts.device)
     den = disc_in_grid(posts, g.H, g.W, R)
     for i in range(0, posts.numel(), chunk):
         p = posts[i:i + chunk].contiguous()
         n = p.numel()
-        V.viewshed(g, R, ht, hr, p, bm=bm[:n], area=area[:n])
+        V.viewshed(g, R, ht, hr, p, bm=bm[:n], area=area[:n], ws=ws)
         out[i:i + n] = area[:n].float() / den[i:i + n].float()
     return out
 
