@@ -1,0 +1,61 @@
+"""Host-side accounting of the benchmark (CPU only): the ray-step count
+behind the viewshed roofline, the greedy loop's byte count, and the rule that
+a recorded DRAM-traffic figure is reported only for the source it was
+measured on."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import bench
+
+
+@pytest.mark.parametrize("R,lo,hi", [(50, 6.95, 6.99), (100, 6.99, 7.03), (200, 7.01, 7.05)])
+def test_interior_ray_steps_about_7_R2(R, lo, hi):
+    """Rays to the 8R ring cells cut at the disc take ~7.0 R^2 steps."""
+    assert lo * R * R <= bench.interior_ray_steps(R) <= hi * R * R
+
+
+def test_interior_ray_steps_brute_force():
+    """Against a direct walk of every ring ray (R small)."""
+    for R in (1, 2, 3, 7, 12):
+        n = 0
+        for ex, ey in ([(R, e) for e in range(-R + 1, R + 1)] + [(e, R) for e in range(-R, R)] +
+                       [(-R, e) for e in range(-R, R)] + [(e, -R) for e in range(-R + 1, R + 1)]):
+            dmin = ey if abs(ex) >= abs(ey) else ex
+            for k in range(1, R + 1):
+                a = (2 * abs(k * dmin) + R) // (2 * R)
+                if k * k + a * a > R * R:
+                    break
+                n += 1
+        assert bench.interior_ray_steps(R) == n
+
+
+def test_site_loop_bytes_isolated_winners():
+    """Winners far apart: each step moves its own window (V and C read, C
+    written) and refreshes nobody."""
+    W, R, PR = 10000, 10, 2
+    cand = np.array([0 * W + 100, 5000 * W + 5000, 9000 * W + 200], np.int64)
+    words = (2 * R + 1) * PR
+    assert bench.site_loop_bytes(cand, cand[:2], W, R, PR) == 2 * 3 * words * 4
+
+
+def test_recorded_traffic_follows_the_source(tmp_path, monkeypatch):
+    root = tmp_path
+    (root / "profiles").mkdir()
+    src = root / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    sha = hashlib.sha1(src.read_bytes()).hexdigest()
+    rec = {"stages": {"site_loop": {"bytes_per_launch": 123.0, "source": "k.cu", "sha1": sha},
+                      "cnn_lattice": {"bytes_per_launch": 7.0, "patches": 10, "source": "k.cu", "sha1": sha},
+                      "vix": {"bytes_per_launch": 5.0, "source": "k.cu", "sha1": "0" * 40}}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "__file__", str(root / "bench.py"))
+    got = bench.recorded_traffic(10)
+    assert got["site_loop"] == 123.0 and got["cnn_lattice"] == 7.0
+    assert "vix" not in got                       # another source than the one measured
+    assert bench.recorded_traffic(11)["cnn_lattice"] is None   # another lattice
+    src.write_text("__global__ void k() { }\n")   # the kernel changed
+    assert bench.recorded_traffic(10) == {}
