@@ -58,6 +58,11 @@ def test_size_queries(L):
     # stride-4 lattice {0,4,8}^2 in 8 x 8 blocks: 4, 2 / 2, 1 lattice posts
     assert L.vs_findmax_count(10, 10, 4, 8, 2) == 2 + 2 + 2 + 1
     assert L.vs_site_workspace(40000, 100) >= 40000 * 4
+    # the paper's US-West run (Sec. "Experiments"): 139 x 139 blocks of 20 potential
+    # transmitters, 386,420 in all, for R = 1000 (block side 334 ~ R/3); R = 2000:
+    # 70 x 70 blocks, 98,000
+    assert L.vs_findmax_count(46400, 46400, 1, 334, 20) == 386420
+    assert L.vs_findmax_count(46400, 46400, 1, 667, 20) == 98000
 
 
 def test_argument_errors_need_no_device(L):
