@@ -574,7 +574,8 @@ def run_paper(args, dist, rank, world, local):
     import __graft_entry__
     __graft_entry__.build()
     import paper_2006_16783_gb300 as V
-    w = {"paper": WL.PAPER, "paper_mid": WL.PAPER_MID, "paper_small": WL.PAPER_SMALL}[args.workload]
+    w = {"paper": WL.PAPER, "paper_mid": WL.PAPER_MID, "paper_small": WL.PAPER_SMALL,
+         "paper_r2000": WL.PAPER_R2000}[args.workload]
     t = time.perf_counter()
     z = w.make_terrain(dev)
     zs, _ = WL.terrain.pad_pitch(z, 8)
@@ -848,7 +849,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="full",
                     choices=["full", "mid", "scale", "small", "batch", "learn", "paper", "paper_mid",
-                             "paper_small", "accuracy"])
+                             "paper_small", "paper_r2000", "accuracy"])
     ap.add_argument("--paper-surrogate", action="store_true",
                     help="--workload paper*: also run the learned proposal trained on exact R-vix labels")
     ap.add_argument("--paper-patch-step", type=int, default=30,
@@ -888,7 +889,7 @@ def main():
             return
         run_accuracy(args, dist, rank, world, local)
         return
-    if args.workload in ("paper", "paper_mid", "paper_small"):
+    if args.workload in ("paper", "paper_mid", "paper_small", "paper_r2000"):
         if args.impl == "reference":
             if rank == 0:
                 print(json.dumps({"impl": "reference", "unavailable": "the paper-regime workload has no bounded "

@@ -90,6 +90,11 @@ MID = Workload("mid_11600sq_R100", 11600, 11600, 100, 10, 10, 10, 464, 4, 1024, 
 PAPER = Workload("paper_uswest_46400sq_R1000", 46400, 46400, 1000, 100, 10, 10, 334, 20, 20000,
                  seed=1004, kind="ridged", zmax=4000, lake_frac=0.05, target=0.95,
                  extra={"octaves": 10, "base_wavelength": 640})
+# the paper's second US-West column: R = 2000, 70 x 70 blocks (side 667 ~ R/3) of 20
+# candidates (98,000), 95 % coverage.  Bitmaps: 98,000 x 4001 rows x 127 words = 199 GB.
+PAPER_R2000 = Workload("paper_uswest_46400sq_R2000", 46400, 46400, 2000, 100, 10, 10, 667, 20, 20000,
+                       seed=1004, kind="ridged", zmax=4000, lake_frac=0.05, target=0.95,
+                       extra={"octaves": 10, "base_wavelength": 640})
 # the same regime on 4096^2 (13 x 13 blocks, 3,380 candidates, 1.7 GB of bitmaps): a
 # size for profiler captures (the terrain fits in L2; the kernels it is used for
 # are bound by issue and cache latency, not DRAM)
