@@ -702,8 +702,13 @@ def paper_surrogate(args, V, w, g, dev, vixbuf, bm, area, cum, sws, ws, nobs_pla
 
 
 def _paper_surrogate_run(args, V, w, g, dev, tr, P, stride, bm, area, cum, sws, ws, ms_plain, dist):
-    """One lattice stride of the paper-regime proposal, timed like the plain pipeline."""
-    ns = V.findmax_count(w.H, w.W, stride, w.block, w.k)
+    """One lattice stride of the paper-regime proposal, timed like the plain
+    pipeline.  --paper-block / --paper-k replace the findmax blocks of the
+    proposal (e.g. the top 1 of every 75^2 block instead of the top 20 of
+    every 334^2 block: about as many candidates, spread evenly)."""
+    blk = args.paper_block or w.block
+    kk = args.paper_k or w.k
+    ns = V.findmax_count(w.H, w.W, stride, blk, kk)
     assert ns <= bm.shape[0]
     score = torch.empty(((w.H + stride - 1) // stride, (w.W + stride - 1) // stride), dtype=torch.float32,
                         device=dev)
@@ -714,7 +719,7 @@ def _paper_surrogate_run(args, V, w, g, dev, tr, P, stride, bm, area, cum, sws, 
         ev[0].record()
         V.cnn_score_lattice(g, stride, tr.packed, out=score, patch_step=P)
         ev[1].record()
-        V.findmax_f32(score, w.H, w.W, stride, w.block, w.k, out=cand)
+        V.findmax_f32(score, w.H, w.W, stride, blk, kk, out=cand)
         ev[2].record()
         V.viewshed(g, w.R, w.ht, w.hr, cand, bm=bm[:ns], area=area[:ns], ws=ws)
         ev[3].record()
@@ -742,7 +747,7 @@ def _paper_surrogate_run(args, V, w, g, dev, tr, P, stride, bm, area, cum, sws, 
     return {"s_per_step": ms / 1000.0, "stages_ms": dict(zip(["cnn_lattice", "findmax_f32", "viewshed", "site"], st)),
             "speedup_vs_plain": ms_plain / ms, "candidates": ns, "observers": nobs,
             "coverage_posts": covered, "coverage_frac": covered / float(w.H * w.W),
-            "patches_per_step": score.numel(), "gpu_launches": n_launch}
+            "patches_per_step": score.numel(), "proposal_block": blk, "proposal_k": kk, "gpu_launches": n_launch}
 
 
 def run_accuracy(args, dist, rank, world, local):
@@ -854,6 +859,9 @@ def main():
                     help="--workload paper*: also run the learned proposal trained on exact R-vix labels")
     ap.add_argument("--paper-patch-step", type=int, default=30,
                     help="post spacing of the CNN patch in the paper regime (65 posts 30 apart span ~2R)")
+    ap.add_argument("--paper-block", type=int, default=0,
+                    help="findmax block of the paper-regime proposal (0 = the workload's)")
+    ap.add_argument("--paper-k", type=int, default=0, help="candidates per block of that proposal (0 = the workload's)")
     ap.add_argument("--paper-stride", default="64",
                     help="lattice stride(s) of the paper-regime proposal, comma-separated")
     ap.add_argument("--accuracy-size", default="full", choices=["full", "mid"],
