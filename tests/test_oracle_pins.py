@@ -173,6 +173,38 @@ def test_vix_sample_definition(O):
         assert v[y, x] == c
 
 
+GAMMA = 0x9E3779B97F4A7C15
+
+
+def test_vix_sample_mapping_golden(O):
+    """Each of the five hand-worked rows of tests/golden/vix_samples_R5.txt
+    (published SplitMix64 output -> top 32 bits -> offset index -> offset)
+    fixes which receiver a sample tests: on flat terrain (everything visible)
+    lowering that one receiver post hides the sample, so a single-sample vix
+    drops from 1 to 0; with all five samples of one post, the count is five
+    minus the lowered receivers among them."""
+    rows = _read_golden("vix_samples_R5.txt")
+    R, H, W, cx, cy = 5, 15, 15, 7, 7
+    p = cy * W + cx
+    dx_t, dy_t = O.offsets(R)
+    assert len(dx_t) == 80
+    for m, u, hi, NR, idx, dx, dy in rows:
+        assert O.splitmix64_nth(1234567, m) == u and u >> 32 == hi and NR == len(dx_t)
+        assert (int(dx_t[idx]), int(dy_t[idx])) == (dx, dy)
+        seed1 = (1234567 + GAMMA * (m - p)) % 2 ** 64      # S = 1: sample 0 of post p is output m
+        z = np.zeros((H, W), np.int16)
+        assert O.vix(z, R, 0, 0, 1, seed1)[cy, cx] == 1
+        z[cy + dy, cx + dx] = -100
+        assert O.vix(z, R, 0, 0, 1, seed1)[cy, cx] == 0
+    seed5 = (1234567 - GAMMA * (p * 5)) % 2 ** 64           # S = 5: samples 0..4 are outputs 0..4
+    for hidden in ([0, 2], [1, 3, 4], [4], []):
+        z = np.zeros((H, W), np.int16)
+        for m in hidden:
+            _, _, _, _, _, dx, dy = rows[m]
+            z[cy + dy, cx + dx] = -100
+        assert O.vix(z, R, 0, 0, 5, seed5)[cy, cx] == 5 - len(hidden)
+
+
 def test_vix_threads_agree(O):
     z = T.spectral_fbm(48, 40, 0.8, 3).numpy()
     a = O.vix(z, 8, 10, 10, 10, 1)
@@ -236,6 +268,27 @@ def test_findmax_f32_stride(O):
             items.sort()
             out += [p for _, p in items[:2]]
     assert got.tolist() == out
+
+
+def _f32(bits):
+    return np.array([bits], np.uint32).view(np.float32)[0]
+
+
+def test_findmax_f32_total_order(O):
+    """Float scores rank by the IEEE-754 totalOrder predicate (IEEE 754-2008
+    Sec. 5.10): -NaN < -inf < negative numbers < -0 < +0 < positive numbers
+    < +inf < +NaN.  So +0 beats -0 although they compare equal (a numeric
+    tie would go to the lower post), a positive NaN beats +inf and a
+    negative NaN loses to -inf."""
+    pnan, nnan = _f32(0x7FC00000), _f32(0xFFC00000)
+    vals = np.array([[-0.0, 0.0, pnan, nnan, np.inf, -np.inf, 1.5, -1.5]], np.float32)
+    got = O.findmax_f32(vals, 1, 8, 1, 8, 8).tolist()
+    assert got == [2, 4, 6, 1, 0, 7, 5, 3]
+    assert O.findmax_f32(vals[:, :2].copy(), 1, 2, 1, 2, 1).tolist() == [1]
+    same = np.array([[0.0, 0.0, -0.0, -0.0]], np.float32)  # equal keys: lower post first
+    assert O.findmax_f32(same, 1, 4, 1, 4, 4).tolist() == [0, 1, 2, 3]
+    neg = np.array([[nnan, -np.inf]], np.float32)
+    assert O.findmax_f32(neg, 1, 2, 1, 2, 1).tolist() == [1]
 
 
 # ------------------------------------------------------------------ viewshed
