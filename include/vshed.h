@@ -97,13 +97,19 @@ uint64_t vs_launch_count(void);
  *   VS_TUNE_SITE_LAZY: vs_site runs the lazy greedy (the path of calls whose
  *     gains or windows do not fit in one cluster's shared memory) even when
  *     another loop would fit: 1 = on the whole GPU (one cooperative launch,
- *     the lazy path's default), 2 = in one CTA; 0 = default. */
+ *     the lazy path's default), 2 = in one CTA; 0 = default.
+ *   VS_TUNE_SITE_MULTI: the leader cluster's rounds of several greedy steps
+ *     (the candidates taken in key order while each lies more than 2R from
+ *     every other winner of the round; same results as one step at a time):
+ *     0 = default (on whenever the leader cluster runs and the gains fit),
+ *     1 = off (one step per round). */
 enum {
     VS_TUNE_VIEWSHED_THREADS = 0,
     VS_TUNE_VIX_TILE = 1,
     VS_TUNE_SITE_CLUSTER = 2,
     VS_TUNE_VIEWSHED_WIDE = 3,
-    VS_TUNE_SITE_LAZY = 4
+    VS_TUNE_SITE_LAZY = 4,
+    VS_TUNE_SITE_MULTI = 5
 };
 int vs_tune_set(int32_t op, int32_t R, int32_t value);
 int vs_tune_get(int32_t op, int32_t R);
@@ -265,8 +271,11 @@ int vs_viewshed_batch(const vs_viewshed_job *jobs, int32_t n_jobs, void *ws, siz
  * gains[], and ORs V_c into cum.  It stops after n_obs observers, when the
  * best gain is 0, or -- when coverage_target > 0 -- as soon as
  * popcount(cum) >= ceil(coverage_target * H * W) before a step.
- * *n_chosen (device int32) receives the number chosen.  Calling again with the
- * returned cum continues the same greedy sequence (checkpoint / resume).
+ * *n_chosen (device int32) receives the number chosen, or a negative VS_ERR_*
+ * code when the device reports a failure (VS_ERR_TIMEOUT: a bounded wait of
+ * the lazy greedy's grid barrier gave up; chosen[] and cum are then
+ * incomplete).  Calling again with the returned cum continues the same greedy
+ * sequence (checkpoint / resume).
  *
  * bm, cand, n, R describe the candidates exactly as vs_viewshed wrote them.
  * chosen and gains have room for n_obs int64 entries.  Requires W, H <= 65535.
@@ -319,11 +328,14 @@ int vs_site_ex(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, in
  *
  *  - Same arguments, results and errors as vs_site, minus the workspace.
  *  - Limit: vs_site_workspace(n, R) must not exceed VS_SITE_NOALLOC_MAX_BYTES
- *    (1 MiB, i.e. up to 52,416 candidates); larger calls return
+ *    (1 MiB, i.e. up to 37,439 candidates, for any R); larger calls return
  *    VS_ERR_RANGE and launch nothing.
  *  - The first call on each device looks up the array's device address (a
  *    runtime query, with that device current); make that first call before
- *    any stream capture.
+ *    any stream capture.  The address belongs to the device's current CUDA
+ *    context: a call made after that context changed (e.g. after the caller's
+ *    cudaDeviceReset) looks it up again, so it too should come before any
+ *    stream capture.
  *  - Every call on a device shares the one array and leaves its contents
  *    behind; the call re-initialises everything it reads.  Calls whose work
  *    overlaps on the GPU (other streams, other host threads) race on the

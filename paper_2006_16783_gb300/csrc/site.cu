@@ -992,6 +992,449 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_loopq(const Site1Param
     cl.sync();  // no CTA leaves while another may still address its shared memory
 }
 
+// ------------------------------------------------------------------ multi-winner leader cluster
+// Several greedy steps per round, with results identical to one step at a
+// time.  After a round's refresh every cached gain is exact.  The leader then
+// takes candidates in decreasing key order (gain, then lowest slot) and
+// accepts each while it lies more than 2R (Chebyshev distance of the posts)
+// from every candidate already accepted in this round, stopping at the first
+// that does not (or at n_obs, the coverage stop, a zero gain, or the round's
+// capacity).  Every accepted candidate is exactly the next sequential argmax:
+// its window is disjoint from the windows accepted before it in the round,
+// so its gain is unchanged by them (Sec. "The multiple transmitter siting
+// process", Site: a gain can only shrink as coverage grows, so no other
+// candidate can have risen above it), and every other key can only have
+// fallen.  The accepted windows are disjoint, so their newly covered bits
+// (deltas) are disjoint too and the refreshes they cause add up.
+//
+// Roles: the leader (rank 0) holds the gains; each of its threads caches the
+// two best keys of its run of slots and their posts, so warp 0 picks the
+// round's winners with no block barrier (the owner of a winner promotes its
+// second key; a run whose second key is used up is rescanned by the warp).
+// The leader then compacts the winners' bands (slots within 2R rows) into a
+// list of (candidate, winner) pairs whose windows meet.  The workers (ranks
+// 1..Q-1) own window rows r = rank-1 (mod Q-1): on a round's first list they
+// compute every winner's delta rows and OR the winners into C (atomically: two
+// disjoint windows can share a boundary word of C), then every list adds
+// popc(V_c AND delta) over its overlap rows into the leader's sums, which the
+// leader subtracts from the gains.  A list holds at most kMultiList pairs; a
+// round whose pairs do not fit takes several lists.
+constexpr int kMultiList = 1024;   // (candidate, winner) pairs per list
+constexpr int kMultiMaxL = 64;     // winners per round
+constexpr int kMultiItems = 8;     // band slots per leader thread and pass
+
+struct SiteMParams {
+    Site1Params b;
+    int Lmax;     // winners per round: <= kMultiMaxL and the workers' delta rows
+    int nrow;     // window rows per worker: ceil((2R+1) / (Q-1))
+};
+
+struct SiteMHeader {
+    int stop, first, last, tot, L, pad0, pad1, pad2;
+};
+
+__device__ __forceinline__ uint64_t slot_key(uint32_t g, int i) {
+    return g ? (((uint64_t)g << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)i)) : 0ull;
+}
+__device__ __forceinline__ int key_slot(uint64_t k) { return (int)(0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFu)); }
+
+__global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParams M) {
+    const Site1Params &P = M.b;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), Q = (int)cl.num_blocks(), Qw = Q - 1;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int n = P.n, R = P.R, PR = P.PR, W = P.W, H = P.H, WWc = P.WWc;
+    const int cs = (n + kSiteThreads - 1) / kSiteThreads;
+    const int my0 = min(n, tid * cs), my1 = min(n, my0 + cs);
+    const int nrow = M.nrow;
+    extern __shared__ __align__(16) unsigned char smem[];
+    // leader: gains, then the list's slots and sums
+    uint32_t *s_gain = (uint32_t *)smem;
+    int *s_list = (int *)(s_gain + ((n + 3) & ~3));
+    unsigned *s_sum = (unsigned *)(s_list + kMultiList);
+    // worker: delta rows of every winner, list row prefix, partial sums
+    uint32_t *s_dloc = (uint32_t *)smem;
+    int *s_cpref = (int *)(s_dloc + (size_t)M.Lmax * nrow * PR);
+    unsigned *s_part = (unsigned *)(s_cpref + kMultiList + 4);
+    __shared__ SiteMHeader s_hdr;
+    __shared__ int4 s_win[kMultiMaxL];      // per winner: wx, wy, wgw0, bitmap index (broadcast)
+    __shared__ int4 s_geo[kMultiList];      // per pair (broadcast)
+    // leader selection state
+    __shared__ uint64_t s_tkey[kSiteThreads], s_tkey2[kSiteThreads];
+    __shared__ uint32_t s_tpost[kSiteThreads], s_tpost2[kSiteThreads];
+    __shared__ unsigned char s_t2ok[kSiteThreads], s_dirty[kSiteThreads];
+    __shared__ uint64_t s_wkey[32];
+    __shared__ int s_wslot[kMultiMaxL], s_wx[kMultiMaxL], s_wy[kMultiMaxL];
+    __shared__ uint32_t s_wpost[kMultiMaxL], s_wgain[kMultiMaxL];
+    __shared__ int s_blo[kMultiMaxL], s_bpref[kMultiMaxL + 1];
+    __shared__ int s_wa[32], s_wb[32];
+    __shared__ int s_nL, s_cut;
+
+    const uint32_t *sp = P.sp;
+    if (rank == 0) {
+        for (int i = tid; i < n; i += kSiteThreads)
+            s_gain[i] = (sp[i] == 0xFFFFFFFFu) ? 0u : P.gain0[P.sorig[i]];
+        s_dirty[tid] = 1;
+    }
+    __syncthreads();
+    long long covered = (rank == 0 && P.need >= 0) ? (long long)*P.covered0 : 0;
+    int t = 0, L = 0, cursor = 0, NI = 0;
+    bool in_round = false, first = false;
+    cl.sync();
+
+    for (;;) {
+        // ================================================ leader
+        if (rank == 0) {
+            bool stop = false;
+            if (!in_round) {
+                // ---- the two best keys of every dirty run and their posts
+                if (s_dirty[tid]) {
+                    s_dirty[tid] = 0;
+                    uint64_t a1 = 0ull, a2 = 0ull, c1 = 0ull, c2 = 0ull;  // two chains
+                    int i = my0;
+                    for (; i + 2 <= my1; i += 2) {
+                        const uint64_t ka = slot_key(s_gain[i], i), kb = slot_key(s_gain[i + 1], i + 1);
+                        if (ka > a1) { a2 = a1; a1 = ka; } else if (ka > a2) a2 = ka;
+                        if (kb > c1) { c2 = c1; c1 = kb; } else if (kb > c2) c2 = kb;
+                    }
+                    if (i < my1) {
+                        const uint64_t ka = slot_key(s_gain[i], i);
+                        if (ka > a1) { a2 = a1; a1 = ka; } else if (ka > a2) a2 = ka;
+                    }
+                    const uint64_t b1 = u64max(a1, c1);
+                    const uint64_t b2 = u64max(a1 > c1 ? a2 : c2, a1 > c1 ? c1 : a1);
+                    const uint32_t p1 = b1 ? sp[key_slot(b1)] : 0u;
+                    const uint32_t p2 = b2 ? sp[key_slot(b2)] : 0u;
+                    s_tkey[tid] = b1;
+                    s_tkey2[tid] = b2;
+                    s_tpost[tid] = p1;
+                    s_tpost2[tid] = p2;
+                    s_t2ok[tid] = 1;
+                }
+                __syncthreads();
+                {
+                    uint64_t k = s_tkey[tid];
+                    for (int o = 16; o > 0; o >>= 1) k = u64max(k, __shfl_xor_sync(0xffffffffu, k, o));
+                    if (lane == 0) s_wkey[wid] = k;
+                }
+                __syncthreads();
+                // ---- warp 0 picks the round's winners
+                if (wid == 0) {
+                    int nl = 0;
+                    for (;;) {
+                        if (t + nl >= P.n_obs || nl >= M.Lmax) break;
+                        if (P.need >= 0 && covered >= P.need) break;
+                        uint64_t k = s_wkey[lane];
+                        for (int o = 16; o > 0; o >>= 1) k = u64max(k, __shfl_xor_sync(0xffffffffu, k, o));
+                        const uint32_t g = (uint32_t)(k >> 32);
+                        if (g == 0u) break;
+                        const int slot = key_slot(k);
+                        const int own = slot / cs;
+                        const uint32_t post = s_tpost[own];
+                        const int x = (int)(post % (uint32_t)W), y = (int)(post / (uint32_t)W);
+                        bool conf = false;
+                        for (int a = lane; a < nl; a += 32)
+                            conf |= abs(x - s_wx[a]) <= 2 * R && abs(y - s_wy[a]) <= 2 * R;
+                        if (__any_sync(0xffffffffu, conf)) break;
+                        if (lane == 0) {
+                            s_wslot[nl] = slot;
+                            s_wpost[nl] = post;
+                            s_wgain[nl] = g;
+                            s_wx[nl] = x;
+                            s_wy[nl] = y;
+                            s_gain[slot] = 0u;
+                        }
+                        ++nl;
+                        covered += g;
+                        __syncwarp();
+                        // the owner's next best key
+                        if (s_t2ok[own]) {
+                            __syncwarp();
+                            if (lane == 0) {
+                                s_tkey[own] = s_tkey2[own];
+                                s_tpost[own] = s_tpost2[own];
+                                s_t2ok[own] = 0;
+                            }
+                        } else {
+                            const int r0 = min(n, own * cs), r1 = min(n, r0 + cs);
+                            uint64_t b = 0ull;
+                            for (int i = r0 + lane; i < r1; i += 32) b = u64max(b, slot_key(s_gain[i], i));
+                            for (int o = 16; o > 0; o >>= 1) b = u64max(b, __shfl_xor_sync(0xffffffffu, b, o));
+                            if (lane == 0) {
+                                s_tkey[own] = b;
+                                s_tpost[own] = b ? sp[key_slot(b)] : 0u;
+                            }
+                        }
+                        __syncwarp();
+                        uint64_t kk = s_tkey[(own & ~31) + lane];
+                        for (int o = 16; o > 0; o >>= 1) kk = u64max(kk, __shfl_xor_sync(0xffffffffu, kk, o));
+                        if (lane == 0) s_wkey[own >> 5] = kk;
+                        __syncwarp();
+                    }
+                    if (lane == 0) s_nL = nl;
+                }
+                __syncthreads();
+                L = s_nL;
+                if (L == 0) {
+                    stop = true;
+                } else {
+                    // ---- winner metadata and band sizes
+                    if (tid < L) {
+                        const int slot = s_wslot[tid];
+                        const int lo = (int)P.slo[slot], hi = (int)P.shi[slot];
+                        const int wx = s_wx[tid];
+                        s_win[tid] = make_int4(wx, s_wy[tid], floordiv(wx - R, 32), (int)P.sorig[slot]);
+                        s_blo[tid] = lo;
+                        s_bpref[tid] = hi - lo;
+                    }
+                    __syncthreads();
+                    if (wid == 0) {  // exclusive prefix of the band sizes (L <= 64)
+                        const int a = lane < L ? s_bpref[lane] : 0;
+                        const int b = lane + 32 < L ? s_bpref[lane + 32] : 0;
+                        const int ia = warp_incl_scan(a, lane);
+                        const int ta = __shfl_sync(0xffffffffu, ia, 31);
+                        const int ib = warp_incl_scan(b, lane) + ta;
+                        __syncwarp();
+                        if (lane < L) s_bpref[lane] = ia - a;
+                        if (lane + 32 < L) s_bpref[lane + 32] = ib - b;
+                        if (lane == 31) s_bpref[L] = ib;
+                    }
+                    // the winners' geometry into every worker
+                    for (int e = tid; e < L * Qw; e += kSiteThreads) {
+                        const int j = e % L, q = 1 + e / L;
+                        *cl.map_shared_rank(&s_win[j], q) = s_win[j];
+                    }
+                    __syncthreads();
+                    NI = s_bpref[L];
+                    cursor = 0;
+                    in_round = true;
+                    first = true;
+                }
+            }
+            // ---- compaction of band slots [cursor, NI) into the list
+            int tot = 0;
+            if (!stop) {
+                while (cursor < NI && tot < kMultiList) {
+                    const int chunk = min(NI - cursor, kMultiItems * kSiteThreads);
+                    const int per = (chunk + kSiteThreads - 1) / kSiteThreads;
+                    const int e0 = cursor + tid * per, e1 = min(cursor + chunk, e0 + per);
+                    uint32_t ip[kMultiItems], io[kMultiItems];
+                    int jfirst = 0;
+                    if (e0 < e1) {  // winner of the first item: last j with s_bpref[j] <= e0
+                        int hi2 = L - 1;
+                        while (jfirst < hi2) {
+                            const int m = (jfirst + hi2 + 1) >> 1;
+                            if (s_bpref[m] <= e0) jfirst = m; else hi2 = m - 1;
+                        }
+                    }
+                    {
+                        int j = jfirst;
+#pragma unroll
+                        for (int q = 0; q < kMultiItems; ++q) {
+                            const int e = e0 + q;
+                            ip[q] = 0xFFFFFFFFu;
+                            io[q] = 0u;
+                            if (e < e1) {
+                                while (s_bpref[j + 1] <= e) ++j;
+                                const int i = s_blo[j] + (e - s_bpref[j]);
+                                if (s_gain[i] != 0u) {
+                                    ip[q] = sp[i];
+                                    io[q] = P.sorig[i];
+                                }
+                            }
+                        }
+                    }
+                    // pass 1: which items' windows meet their winner's
+                    unsigned affm = 0u;
+                    {
+                        int j = jfirst;
+#pragma unroll
+                        for (int q = 0; q < kMultiItems; ++q) {
+                            const int e = e0 + q;
+                            if (e < e1) {
+                                while (s_bpref[j + 1] <= e) ++j;
+                                if (ip[q] != 0xFFFFFFFFu) {
+                                    const int4 wv = s_win[j];
+                                    const int cx = (int)(ip[q] % (uint32_t)W), cy = (int)(ip[q] / (uint32_t)W);
+                                    if (abs(cx - wv.x) <= 2 * R && abs(cy - wv.y) <= 2 * R) {
+                                        const int cgw0 = floordiv(cx - R, 32);
+                                        const int ya = max(max(cy, wv.y) - R, 0), yb = min(min(cy, wv.y) + R, H - 1);
+                                        const int ga = max(max(cgw0, wv.z), 0), gb = min(min(cgw0, wv.z) + PR - 1, WWc - 1);
+                                        if (ya <= yb && ga <= gb) affm |= 1u << q;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    const int cnt = __popc(affm);
+                    // block exclusive scan of the counts
+                    const int inc = warp_incl_scan(cnt, lane);
+                    if (lane == 31) s_wa[wid] = inc;
+                    if (tid == 0) s_cut = 0x7fffffff;
+                    __syncthreads();
+                    const int wv = s_wa[lane];
+                    const int iw = warp_incl_scan(wv, lane);
+                    const int base = tot + __shfl_sync(0xffffffffu, iw - wv, wid) + inc - cnt;
+                    const int T = __shfl_sync(0xffffffffu, iw, 31);
+                    // pass 2: the affected items' pairs, in item order
+                    int li = base;
+                    if (affm) {
+                        int j = jfirst;
+#pragma unroll
+                        for (int q = 0; q < kMultiItems; ++q) {
+                            const int e = e0 + q;
+                            if (e < e1) while (s_bpref[j + 1] <= e) ++j;
+                            if (affm & (1u << q)) {
+                                if (li < kMultiList) {
+                                    const int4 wv = s_win[j];
+                                    const int wy = wv.y, wgw0 = wv.z;
+                                    const int cx = (int)(ip[q] % (uint32_t)W), cy = (int)(ip[q] / (uint32_t)W);
+                                    const int cgw0 = floordiv(cx - R, 32);
+                                    const int ya = max(max(cy, wy) - R, 0), yb = min(min(cy, wy) + R, H - 1);
+                                    const int ga = max(max(cgw0, wgw0), 0), gb = min(min(cgw0, wgw0) + PR - 1, WWc - 1);
+                                    const int ra = ya - (wy - R), rb = yb - (wy - R);
+                                    const uint32_t vrow0 = io[q] * (uint32_t)P.words + (uint32_t)((ya - cy + R) * PR);
+                                    const int4 geo = make_int4(ra | (rb << 16),
+                                                               (gb - ga + 1) | ((ga - cgw0) << 10) | ((ga - wgw0) << 20),
+                                                               (int)vrow0, j);
+                                    s_list[li] = s_blo[j] + (e - s_bpref[j]);
+                                    s_sum[li] = 0u;
+                                    for (int r = 1; r < Q; ++r) *cl.map_shared_rank(&s_geo[li], r) = geo;
+                                } else {
+                                    atomicMin(&s_cut, e);
+                                }
+                                ++li;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    if (tot + T > kMultiList) {
+                        cursor = s_cut;  // the first slot whose pair did not fit
+                        tot = kMultiList;
+                    } else {
+                        cursor += chunk;
+                        tot += T;
+                    }
+                    __syncthreads();  // s_cut and s_wa are reused by the next pass
+                }
+            }
+            if (tid < Q) {
+                SiteMHeader h;
+                h.stop = stop ? 1 : 0;
+                h.first = first ? 1 : 0;
+                h.last = (cursor >= NI) ? 1 : 0;
+                h.tot = tot;
+                h.L = L;
+                h.pad0 = h.pad1 = h.pad2 = 0;
+                *cl.map_shared_rank(&s_hdr, tid) = h;
+            }
+        }
+        cl.sync();  // A: header, winners and list are in every CTA
+        const SiteMHeader h = s_hdr;
+        if (h.stop) break;
+        // ================================================ workers
+        if (rank > 0) {
+            const int wr = rank - 1, tot = h.tot, Lr = h.L;
+            int cnt = 0;
+            if (tid < tot) {
+                const int ra = s_geo[tid].x & 0xFFFF, rb = s_geo[tid].x >> 16;
+                const int r0 = ra + ((wr - ra) % Qw + Qw) % Qw;
+                cnt = (r0 <= rb) ? (rb - r0) / Qw + 1 : 0;
+                s_part[tid] = 0u;
+            }
+            const int inc = warp_incl_scan(cnt, lane);
+            if (lane == 31) s_wb[wid] = inc;
+            __syncthreads();
+            {
+                const int wv = s_wb[lane];
+                const int iw = warp_incl_scan(wv, lane);
+                const int wbase = __shfl_sync(0xffffffffu, iw - wv, wid);
+                const int rows_all = __shfl_sync(0xffffffffu, iw, 31);
+                if (tid < tot) s_cpref[tid] = wbase + inc - cnt;
+                if (tid == 0) s_cpref[tot] = rows_all;
+            }
+            // ---- this worker's window rows of every winner (a round's first list)
+            if (h.first) {
+                const int per_w = nrow * PR;
+                for (int e = tid; e < Lr * per_w; e += kSiteThreads) {
+                    const int j = e / per_w, rem = e - j * per_w;
+                    const int il = rem / PR, w = rem - il * PR;
+                    const int r = wr + Qw * il;
+                    const int4 wv = s_win[j];
+                    uint32_t d = 0u;
+                    if (r <= 2 * R) {
+                        const int y = wv.y - R + r, gw = wv.z + w;
+                        if (y >= 0 && y < H && gw >= 0 && gw < WWc) {
+                            uint32_t *cp = P.cum + (int64_t)y * WWc + gw;
+                            const uint32_t v = __ldg(P.bm + (int64_t)(uint32_t)wv.w * P.words + r * PR + w);
+                            const uint32_t old = *cp;
+                            d = v & ~old;
+                            if (d) atomicOr(cp, v);
+                        }
+                    }
+                    s_dloc[e] = d;
+                }
+            }
+            __syncthreads();  // s_cpref, s_part and s_dloc published
+            const int TT = s_cpref[tot];
+            for (int e = tid; e < TT; e += kSiteThreads) {
+                int l = 0, h2 = tot - 1;  // last l with s_cpref[l] <= e
+                while (l < h2) {
+                    const int m = (l + h2 + 1) >> 1;
+                    if (s_cpref[m] <= e) l = m; else h2 = m - 1;
+                }
+                const int4 gq = s_geo[l];
+                const int ra = gq.x & 0xFFFF;
+                const int r = ra + ((wr - ra) % Qw + Qw) % Qw + Qw * (e - s_cpref[l]);
+                const int nwd = gq.y & 0x3FF, c0 = (gq.y >> 10) & 0x3FF, dw0 = gq.y >> 20;
+                const uint32_t *dl = s_dloc + ((size_t)gq.w * nrow + (r - wr) / Qw) * PR + dw0;
+                uint32_t any = 0u;
+                for (int jw = 0; jw < nwd; ++jw) any |= dl[jw];
+                if (!any) continue;
+                const uint4 *vr = (const uint4 *)(P.bm + (uint32_t)gq.z + (uint32_t)((r - ra) * PR));
+                unsigned sum = 0;
+                for (int q4 = 0; q4 < PR / 4; ++q4) {
+                    const uint4 v = __ldg(vr + q4);
+                    const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int t4 = 0; t4 < 4; ++t4) {
+                        const int jw = 4 * q4 + t4 - c0;
+                        if (jw >= 0 && jw < nwd) sum += __popc(vv[t4] & dl[jw]);
+                    }
+                }
+                if (sum) atomicAdd(&s_part[l], sum);
+            }
+            __syncthreads();
+            if (tid < tot && s_part[tid]) atomicAdd(cl.map_shared_rank(&s_sum[tid], 0), s_part[tid]);
+        }
+        cl.sync();  // B: every partial refresh is in the leader's sums
+        // ================================================ leader: lower the gains
+        if (rank == 0) {
+            for (int q = tid; q < h.tot; q += kSiteThreads) {
+                const unsigned d = s_sum[q];
+                if (d) {
+                    const int ci = s_list[q];
+                    atomicSub(&s_gain[ci], d);
+                    s_dirty[ci / cs] = 1;
+                }
+            }
+            first = false;
+            if (h.last) {
+                if (tid < L) {
+                    P.chosen[t + tid] = (int64_t)s_wpost[tid];
+                    P.gains[t + tid] = (int64_t)s_wgain[tid];
+                    s_dirty[s_wslot[tid] / cs] = 1;
+                }
+                t += L;
+                in_round = false;
+            }
+            __syncthreads();
+        }
+    }
+    if (rank == 0 && tid == 0) *P.n_chosen = t;
+    cl.sync();  // no CTA leaves while another may still address its shared memory
+}
+
 // many independent greedy loops (one per terrain) in one launch: CTA j runs job j
 constexpr int kSiteMaxJobs = 64;
 struct Site1Batch {
@@ -1711,6 +2154,54 @@ static bool siteq_launchable(size_t smem, int q) {
     return nclus >= 1;
 }
 
+// multi-winner leader cluster of q CTAs (q - 1 workers): VS_OK when launched,
+// a negative code on a CUDA error, 1 when the call does not fit it
+static int launch_site_multi(const Site1Params &Q1, int q, cudaStream_t s) {
+    if (q < 2 || q > 16) return 1;
+    const int nrow = (2 * Q1.R + 1 + (q - 1) - 1) / (q - 1);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_site_multi) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    const long long budget = (long long)kSmemLimit - (long long)fa.sharedSizeBytes - 256;
+    const long long lead = (long long)((Q1.n + 3) & ~3) * 4 + (long long)kMultiList * 8;
+    const long long per = (long long)nrow * Q1.PR * 4;
+    const long long fixed = (long long)(kMultiList + 4) * 4 + (long long)kMultiList * 4;
+    if (lead > budget || per <= 0 || budget - fixed < per) return 1;
+    const int Lmax = (int)std::min<long long>(kMultiMaxL, (budget - fixed) / per);
+    const size_t dyn = (size_t)std::max(lead, fixed + (long long)Lmax * per);
+    if (cudaFuncSetAttribute(k_site_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess ||
+        cudaFuncSetAttribute(k_site_multi, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(q);
+    cfg.blockDim = dim3(kSiteThreads);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = q;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclus = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclus, k_site_multi, &cfg) != cudaSuccess || nclus < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    SiteMParams M;
+    M.b = Q1;
+    M.Lmax = Lmax;
+    M.nrow = nrow;
+    VS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_site_multi, M));
+    vs::note_launch();
+    return VS_OK;
+}
+
 static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W,
                      int32_t R, int32_t n_obs, double coverage_target, int64_t *chosen,
                      int64_t *gains, uint32_t *cum, int32_t *n_chosen, void *ws,
@@ -1793,6 +2284,11 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
         }
         // leader cluster: bitmap rows must be whole 16-byte vectors
         const int qc = (qtune == 0) ? 8 : qtune;
+        if (qc >= 2 && Q1.vec_rows && tune_get(VS_TUNE_SITE_MULTI, R, 0) != 1 &&
+            (uint64_t)n * (uint64_t)P.words < (1ull << 32)) {
+            const int mrc = launch_site_multi(Q1, qc, s);
+            if (mrc <= 0) return mrc;  // launched, or a CUDA error; > 0: does not fit
+        }
         if (qc >= 2 && Q1.vec_rows && (uintptr_t)cum % 16 == 0) {
             const size_t smemq = siteq_smem_bytes(n, R, P.PR, qc);
             if (siteq_fits(smemq) && siteq_launchable(smemq, qc)) {
@@ -2012,8 +2508,42 @@ extern "C" int vs_site_batch(const vs_site_job *jobs, int32_t n_jobs, void *ws, 
 namespace {
 constexpr size_t kSiteNoAllocBytes = 1u << 20;  // VS_SITE_NOALLOC_MAX_BYTES in vshed.h
 static __device__ __align__(256) unsigned char g_site_scratch[kSiteNoAllocBytes];
+
+// The array's device address is only valid in the context it was looked up
+// in: a caller's cudaDeviceReset destroys the primary context, and the array
+// may sit elsewhere in the next one.  So the cached address is tagged with the
+// context's process-unique ID (cuCtxGetId) and looked up again when it changes.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    void *ptr;
+};
 std::mutex g_scratch_mu;
-void *g_scratch_ptr[64];  // device address of g_site_scratch, per device ordinal
+ScratchSlot g_scratch[64];  // per device ordinal
+
+// ID of the calling thread's current context; false when none is current or
+// the driver does not offer the query
+bool current_ctx_id(unsigned long long *id) {
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) ==
+                cudaSuccess && qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) ==
+                cudaSuccess && qb == cudaDriverEntryPointSuccess) {
+            get_cur = (CtxGetCurrentFn)a;
+            get_id = (CtxGetIdFn)b;
+        }
+    });
+    if (!get_cur || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 }  // namespace
 
 extern "C" int vs_site_noalloc(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H,
@@ -2027,15 +2557,21 @@ extern "C" int vs_site_noalloc(const uint32_t *bm, const int64_t *cand, int64_t 
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return VS_ERR_DEVICE;
     void *scratch = nullptr;
     {
-        // one-time set-up per device, with that device current: the host-side
-        // name of the array is not a device address, so ask the runtime for it
+        // set-up per device (and again per context), with that device current:
+        // the host-side name of the array is not a device address, so ask the
+        // runtime for it
         std::lock_guard<std::mutex> lk(g_scratch_mu);
-        if (!g_scratch_ptr[dev]) {
+        unsigned long long id = 0;
+        const bool have_id = current_ctx_id(&id);
+        ScratchSlot &sl = g_scratch[dev];
+        if (!sl.ptr || (have_id && id != sl.ctx_id)) {
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_site_scratch) != cudaSuccess || !p) return VS_ERR_CUDA;
-            g_scratch_ptr[dev] = p;
+            unsigned long long id2 = 0;
+            sl.ptr = p;
+            sl.ctx_id = current_ctx_id(&id2) ? id2 : 0;  // the lookup made the context current
         }
-        scratch = g_scratch_ptr[dev];
+        scratch = sl.ptr;
     }
     return vs_site(bm, cand, n, H, W, R, n_obs, coverage_target, chosen, gains, cum, n_chosen,
                    scratch, kSiteNoAllocBytes, st);

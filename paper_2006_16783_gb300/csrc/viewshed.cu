@@ -74,9 +74,11 @@ struct VsJob {
 
 // One candidate: stage the window (per sector), walk the rays of the sector,
 // OR visible cells into the shared bitmap, write bitmap and area.  `phase` is
-// the parity of the CTA's window barrier, carried across candidates.
+// the parity of the CTA's window barrier, carried across candidates.  Returns
+// true when a window copy did not land within two bounded waits: the barrier
+// can then no longer be trusted and the CTA must take no further candidate.
 template <typename T>
-__device__ void vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long c, unsigned char *smem,
+__device__ bool vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long c, unsigned char *smem,
                              uint64_t *bar, uint32_t &phase, int *s_fail, int *red) {
     const int R = J.R, PR = J.PR;
     const int PRs = PR | 1;  // odd row pitch of the shared bitmap: rays on nearby rows hit other banks
@@ -90,7 +92,7 @@ __device__ void vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long 
     if (p < 0 || p >= (int64_t)J.H * J.W) {  // invalid candidate: empty bitmap, area -1
         for (int i = tid; i < J.words; i += blockDim.x) out[i] = 0;
         if (tid == 0) J.area[c] = -1;
-        return;
+        return false;
     }
     const int cx = (int)(p % J.W), cy = (int)(p / J.W);
     const int gw0 = floordiv(cx - R, 32);
@@ -122,9 +124,14 @@ __device__ void vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long 
         if (!mbar_wait(bar, phase)) *s_fail = 1;
         __syncthreads();
         if (*s_fail) {
-            // give the copy in flight a second bounded chance to land before the
-            // CTA moves on, then report the candidate as timed out
-            mbar_wait(bar, phase);
+            // give the copy in flight a second bounded chance to land, then
+            // report the candidate as timed out; when that wait gives up too,
+            // the barrier's phase may still complete later, so the CTA must not
+            // reuse it (s_fail = 2: the caller stops taking candidates)
+            const bool ok2 = mbar_wait(bar, phase);
+            __syncthreads();
+            if (tid == 0 && !ok2) *s_fail = 2;
+            __syncthreads();
             phase ^= 1u;
             break;
         }
@@ -216,6 +223,7 @@ __device__ void vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long 
     }
 
     const bool fail = *s_fail != 0;
+    const bool dead = *s_fail == 2;
     if (tid == 0 && !fail) atomicOr(&bms[R * PRs + ((cx >> 5) - gw0)], 1u << (cx & 31));
     __syncthreads();
     int cnt = 0;
@@ -234,6 +242,7 @@ __device__ void vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long 
         J.area[c] = fail ? VS_ERR_TIMEOUT : a;
     }
     __syncthreads();  // red[] and the bitmap are reused by the next candidate
+    return dead;
 }
 
 __device__ __forceinline__ unsigned char *vs_smem_base(unsigned char *raw) {
@@ -286,8 +295,9 @@ __global__ void __launch_bounds__(512) k_viewshed_batch(const __grid_constant__ 
         int j = 0;
         while (j + 1 < B.njobs && B.job[j + 1].item0 <= it) ++j;
         const VsJob &J = B.job[j];
-        if (J.wide) vs_candidate<long long>(&J.map, J, it - J.item0, smem, &bar, phase, &s_fail, red);
-        else vs_candidate<int>(&J.map, J, it - J.item0, smem, &bar, phase, &s_fail, red);
+        const bool dead = J.wide ? vs_candidate<long long>(&J.map, J, it - J.item0, smem, &bar, phase, &s_fail, red)
+                                 : vs_candidate<int>(&J.map, J, it - J.item0, smem, &bar, phase, &s_fail, red);
+        if (dead) break;  // a copy may still land in this CTA's window: take no more items
     }
 }
 

@@ -42,8 +42,8 @@ int make_grid_map(GridMap *gm, const vs_grid &g, int wg, int rows) {
     return r == CUDA_SUCCESS ? VS_OK : VS_ERR_CUDA;
 }
 
-// (op, R) -> value; R <= kMaxR, ops 0..4
-constexpr int kTuneOps = 5;
+// (op, R) -> value; R <= kMaxR, ops 0..5
+constexpr int kTuneOps = 6;
 static int g_tune[kTuneOps][kMaxR + 1];
 static std::mutex g_tune_mu;
 

@@ -137,3 +137,15 @@ def test_large_roi_argument_errors_need_no_device(L):
     opt = vshed.vs_site_options(vshed.vs_grid(0, 0, 0, 0), 0, 4096)
     assert L.vs_site_ex(d, d, 3, 300, 320, 2100, 5, 0.0, ctypes.byref(opt), d, d, d, d, d, 1 << 30,
                         None) == vshed.VS_ERR_RANGE
+
+
+def test_site_noalloc_limit(L):
+    """vs_site_noalloc's static scratch (VS_SITE_NOALLOC_MAX_BYTES = 1 MiB)
+    holds the workspace of up to 37,439 candidates at any R; one more needs
+    more than the array and is refused before anything runs."""
+    for R in (1, 9, 40, 100, 1000):
+        assert L.vs_site_workspace(37439, R) <= 1 << 20 < L.vs_site_workspace(37440, R)
+    from paper_2006_16783_gb300 import vshed
+    dummy = ctypes.c_void_p(256)
+    rc = L.vs_site_noalloc(dummy, dummy, 37440, 300, 300, 9, 10, 0.0, dummy, dummy, dummy, dummy, None)
+    assert rc == vshed.VS_ERR_RANGE

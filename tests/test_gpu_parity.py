@@ -81,11 +81,12 @@ def test_findmax_f32_parity(V, O, H, W, s, b, k):
     sc[1, 1] = -0.0
     sc[2, 2] = 0.0
     sc[0, 1] = 0.0                                         # +0 beside -0 in one block
+    hs, ws = sc.shape
     bits = sc.view(np.uint32)
-    bits[3, 3] = 0x7FC00000                                # +NaN: above +inf
-    bits[4, 1] = 0xFFC00000                                # -NaN: below -inf
-    sc[5, 2] = np.inf
-    sc[2, 5] = -np.inf
+    bits[hs - 1, ws - 1] = 0x7FC00000                      # +NaN: above +inf
+    bits[hs - 1, 0] = 0xFFC00000                           # -NaN: below -inf
+    sc[0, ws - 1] = np.inf
+    sc[hs - 2, 1] = -np.inf
     want = O.findmax_f32(sc, H, W, s, b, k)
     got = _np(V.findmax_f32(torch.as_tensor(sc).cuda(), H, W, s, b, k))
     assert got.tolist() == want.tolist()
