@@ -52,6 +52,7 @@ def _load():
         "or_bitmap_words": (i64, [i32]),
         "or_viewshed": (ctypes.c_int, [P, i32, i32, i64, i32, i32, i32, P, i64, P, P, i32]),
         "or_viewshed_brute": (ctypes.c_int, [P, i32, i32, i64, i32, i32, i32, i64, P]),
+        "or_exact_vix": (ctypes.c_int, [P, i32, i32, i64, i32, i32, i32, P, i64, P, i32]),
         "or_site_plain": (i32, [P, P, i64, i32, i32, i32, i32, f64, P, P, P]),
         "or_site_lazy": (i32, [P, P, i64, i32, i32, i32, i32, f64, P, P, P]),
         "or_coverage_need": (i64, [f64, i32, i32]),
@@ -180,6 +181,19 @@ def viewshed(z, R, ht, hr, cand, threads=1):
     if rc != 0:
         raise ValueError("or_viewshed: bad arguments (%d)" % rc)
     return bm, area
+
+
+def exact_vix(z, R, ht, hr, posts, threads=1):
+    """Exact visibility index of each post (Sec. "Definitions"): its
+    viewshed's area over the ROI's lattice points inside the grid (float32;
+    -1 for a post outside the grid)."""
+    z, H, W, pitch = _grid(z)
+    posts = np.ascontiguousarray(posts, dtype=np.int64)
+    out = np.zeros(posts.shape[0], np.float32)
+    rc = _load().or_exact_vix(_p(z), H, W, pitch, R, ht, hr, _p(posts), posts.shape[0], _p(out), threads)
+    if rc != 0:
+        raise ValueError("or_exact_vix: bad arguments (%d)" % rc)
+    return out
 
 
 def viewshed_brute(z, R, ht, hr, p):

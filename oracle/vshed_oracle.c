@@ -452,6 +452,49 @@ int or_viewshed_brute(const int16_t *z, int32_t H, int32_t W, int64_t pitch,
 }
 
 /* ------------------------------------------------------------------ */
+/* Exact visibility index (Sec. "Definitions": the visibility index of */
+/* a transmitter is the fraction of the receivers within its ROI that  */
+/* it sees, i.e. the normalised area of its viewshed).  Numerator: the */
+/* area of the post's ray-sweep viewshed (or_viewshed).  Denominator:  */
+/* the receivers of the ROI, the lattice points (dx,dy) with           */
+/* dx^2+dy^2 <= R^2 whose post lies inside the grid, counted one by    */
+/* one.  out[i] = the quotient in double, rounded to float; a post     */
+/* outside the grid gives -1.                                          */
+/* ------------------------------------------------------------------ */
+int or_exact_vix(const int16_t *z, int32_t H, int32_t W, int64_t pitch,
+                 int32_t R, int32_t ht, int32_t hr, const int64_t *posts, int64_t n,
+                 float *out, int32_t threads)
+{
+    if (H < 1 || W < 1 || R < 1 || pitch < W || n < 0) return -1;
+    int64_t words = or_bitmap_words(R);
+    int64_t chunk = 256;
+    uint32_t *bm = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(words * chunk));
+    int32_t *area = (int32_t *)malloc(sizeof(int32_t) * (size_t)chunk);
+    int64_t *valid = (int64_t *)malloc(sizeof(int64_t) * (size_t)chunk);
+    for (int64_t i0 = 0; i0 < n; i0 += chunk) {
+        int64_t m = n - i0 < chunk ? n - i0 : chunk, nv = 0;
+        for (int64_t i = 0; i < m; i++) {
+            int64_t p = posts[i0 + i];
+            if (p >= 0 && p < (int64_t)H * W) valid[nv++] = p;
+        }
+        memset(bm, 0, sizeof(uint32_t) * (size_t)(words * chunk));
+        or_viewshed(z, H, W, pitch, R, ht, hr, valid, nv, bm, area, threads);
+        int64_t v = 0;
+        for (int64_t i = 0; i < m; i++) {
+            int64_t p = posts[i0 + i];
+            if (p < 0 || p >= (int64_t)H * W) { out[i0 + i] = -1.0f; continue; }
+            int64_t ox = p % W, oy = p / W, den = 0;
+            for (int64_t dy = -R; dy <= R; dy++)
+                for (int64_t dx = -R; dx <= R; dx++)
+                    if (dx * dx + dy * dy <= (int64_t)R * R && in_grid(H, W, ox + dx, oy + dy)) den++;
+            out[i0 + i] = (float)((double)area[v++] / (double)den);
+        }
+    }
+    free(bm); free(area); free(valid);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Site stage (Sec. "The multiple transmitter siting process", Site):  */
 /* greedy; each step adds the candidate whose viewshed grows the        */
 /* cumulative viewshed C the most: gain_c = popcount(V_c AND NOT C),    */

@@ -531,3 +531,55 @@ def test_site_greedy_bound_vs_optimum(O):
         s = list(sub)
         best = max(best, O.cum_popcount(O.cum_rebuild(bm[s], cand[s], H, W, 6), H, W))
     assert gains.sum() >= (1 - 1 / math.e) * best
+
+
+# ------------------------------------------------------------------ exact visibility index
+def _disc_rows_in_grid(R, x, y, H, W):
+    """|disc(R) around (x, y) inside the grid| by rows: each row dy holds the
+    columns x - h .. x + h, h = isqrt(R^2 - dy^2), clipped to the grid."""
+    n = 0
+    for dy in range(-R, R + 1):
+        if 0 <= y + dy < H:
+            h = math.isqrt(R * R - dy * dy)
+            n += max(0, min(W - 1, x + h) - max(0, x - h) + 1)
+    return n
+
+
+def test_exact_vix_flat_is_one(O):
+    # flat terrain: every receiver of the ROI inside the grid is visible (for
+    # these radii every ray that leaves the grid has reached its last
+    # in-grid cell: the viewshed is disc x grid, as pinned above); and a
+    # window inside the grid at any R
+    z = np.full((37, 45), 120, np.int16)
+    H, W = z.shape
+    posts = np.array([0, W - 1, (H - 1) * W, H * W - 1, 18 * W + 22, 3 * W + 40], np.int64)
+    for R in (2, 7, 12):
+        assert (O.exact_vix(z, R, 10, 10, posts) == 1.0).all()
+    z = np.full((90, 95), -7, np.int16)
+    assert (O.exact_vix(z, 40, 10, 10, np.array([45 * 95 + 47], np.int64)) == 1.0).all()
+
+
+@pytest.mark.parametrize("R", [2, 5, 13, 40])
+def test_exact_vix_walled_observer(O, R):
+    """An observer walled in by its eight neighbours (1000 above a flat floor)
+    sees itself and the walls only: every ray's first step is visible, the
+    interpolated wall then hides every later step.  Visibility index = the
+    in-grid cells of its 3 x 3 block over the ROI's receivers in the grid."""
+    H, W = 31, 26
+    for (x, y) in [(12, 15), (0, 0), (25, 30), (0, 14), (11, 0), (25, 7)]:
+        z = np.zeros((H, W), np.int16)
+        seen = 0
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if 0 <= x + dx < W and 0 <= y + dy < H:
+                    seen += 1
+                    if dx or dy:
+                        z[y + dy, x + dx] = 1000
+        got = O.exact_vix(z, R, 10, 10, np.array([y * W + x], np.int64))[0]
+        want = np.float32(seen / _disc_rows_in_grid(R, x, y, H, W))
+        assert got == want, (x, y, got, want)
+
+
+def test_exact_vix_outside_grid(O):
+    z = np.zeros((10, 10), np.int16)
+    assert O.exact_vix(z, 3, 10, 10, np.array([-1, 100, 5], np.int64)).tolist() == [-1.0, -1.0, 1.0]
