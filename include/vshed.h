@@ -243,6 +243,23 @@ size_t vs_viewshed_r3_workspace(int32_t H, int32_t W);
 int vs_viewshed_r3(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand, int64_t n,
                    uint32_t *bm_out, int32_t *area_out, void *ws, size_t ws_bytes, vs_stream_t st);
 
+/* Exact visibility index of each listed post (Sec. "Definitions": the
+ * visibility index of a transmitter is the fraction of the receivers within
+ * its ROI that it sees; here the label the learned proposal is trained on):
+ *   out[i] = area of the post's vs_viewshed bitmap
+ *            / |{(dx,dy): dx^2+dy^2 <= R^2, post + (dx,dy) inside the grid}|,
+ * the quotient of the two integers rounded once to float (round to nearest
+ * even).  posts[n]: int64 post indices (device); out[n]: float (device).  A
+ * post outside the grid gives -1; a timed-out device wait gives
+ * VS_ERR_TIMEOUT (as a float).  No bitmap is returned.  ws: at least
+ * vs_exact_vix_workspace(H, W, R, n) bytes (4 bytes per post, plus for ROIs
+ * beyond shared memory the pair arrays of vs_viewshed and a bitmap buffer of
+ * at most 1 GiB through which the posts are processed in chunks).  Errors as
+ * vs_viewshed. */
+size_t vs_exact_vix_workspace(int32_t H, int32_t W, int32_t R, int64_t n);
+int vs_exact_vix(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *posts, int64_t n,
+                 float *out, void *ws, size_t ws_bytes, vs_stream_t st);
+
 /* Batched viewsheds: the candidates of up to 64 terrains (different sizes,
  * ROIs, heights) in ONE persistent launch.  jobs is a HOST array read during
  * the call; each job is exactly the arguments of one vs_viewshed call, and

@@ -88,9 +88,10 @@ __device__ bool vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long 
     uint32_t *bms = (uint32_t *)(smem + ((win_elems * 2 + 127) & ~127));
     const int tid = threadIdx.x;
     const int64_t p = J.cand[c];
-    uint32_t *out = J.bm + c * (int64_t)J.words;
+    uint32_t *out = J.bm ? J.bm + c * (int64_t)J.words : nullptr;  // NULL: areas only
     if (p < 0 || p >= (int64_t)J.H * J.W) {  // invalid candidate: empty bitmap, area -1
-        for (int i = tid; i < J.words; i += blockDim.x) out[i] = 0;
+        if (out)
+            for (int i = tid; i < J.words; i += blockDim.x) out[i] = 0;
         if (tid == 0) J.area[c] = -1;
         return false;
     }
@@ -230,7 +231,7 @@ __device__ bool vs_candidate(const CUtensorMap *tmap, const VsJob &J, long long 
     for (int i = tid; i < J.words; i += blockDim.x) {
         const int r = i / PR;
         const uint32_t w = fail ? 0u : bms[r * PRs + (i - r * PR)];
-        out[i] = w;
+        if (out) out[i] = w;
         cnt += __popc(w);
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -612,7 +613,7 @@ extern "C" size_t vs_viewshed_workspace(int32_t H, int32_t W, int32_t R, int64_t
 
 static int vs_viewshed_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand,
                             int64_t n, uint32_t *bm_out, int32_t *area_out, void *ws, size_t ws_bytes,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool pairs_ready = false) {
     int rc = check_grid(g);
     if (rc) return rc;
     if (ht < -100000 || ht > 100000 || hr < -100000 || hr > 100000) return VS_ERR_RANGE;
@@ -626,10 +627,12 @@ static int vs_viewshed_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr,
     if ((rc = check_device())) return rc;
     uint32_t *pe = (uint32_t *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     uint32_t *pn = (uint32_t *)(((uintptr_t)(pe + (size_t)g.H * g.W) + 255) & ~(uintptr_t)255);
-    const dim3 tg((unsigned)((g.W + 31) / 32), (unsigned)((g.H + 31) / 32));
-    k_vs_pairs<<<tg, 256, 0, s>>>(g.z, g.pitch, g.H, g.W, pe, pn);
-    vs::note_launch();
-    VS_CUDA_TRY(cudaGetLastError());
+    if (!pairs_ready) {
+        const dim3 tg((unsigned)((g.W + 31) / 32), (unsigned)((g.H + 31) / 32));
+        k_vs_pairs<<<tg, 256, 0, s>>>(g.z, g.pitch, g.H, g.W, pe, pn);
+        vs::note_launch();
+        VS_CUDA_TRY(cudaGetLastError());
+    }
     VsWide P;
     P.z = g.z; P.pitch = g.pitch; P.pe = pe; P.pn = pn;
     P.H = g.H; P.W = g.W; P.R = R; P.ht = ht; P.hr = hr;
@@ -651,13 +654,14 @@ static int default_threads(int R) {
 }
 
 static int vs_make_job(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, const int64_t *cand,
-                       int64_t n, uint32_t *bm_out, int32_t *area_out, VsJob *J, size_t *smem) {
+                       int64_t n, uint32_t *bm_out, int32_t *area_out, VsJob *J, size_t *smem,
+                       bool areas_only = false) {
     int rc = check_grid(g);
     if (rc) return rc;
     if (R < 1 || R > kMaxR) return VS_ERR_RANGE;
     if (ht < -100000 || ht > 100000 || hr < -100000 || hr > 100000) return VS_ERR_RANGE;
     if (n < 0 || n > 0x7fffffffll) return VS_ERR_RANGE;
-    if (n > 0 && (!cand || !bm_out || !area_out)) return VS_ERR_ARG;
+    if (n > 0 && (!cand || (!bm_out && !areas_only) || !area_out)) return VS_ERR_ARG;
     memset(J, 0, sizeof(*J));
     J->H = g.H; J->W = g.W; J->R = R; J->ht = ht; J->hr = hr;
     J->cand = cand; J->n = n; J->bm = bm_out; J->area = area_out;
@@ -742,6 +746,98 @@ extern "C" int vs_viewshed_batch(const vs_viewshed_job *jobs, int32_t n_jobs, vo
     VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_viewshed_batch, threads, smem));
     const long long grid = std::min<long long>(total, (long long)sms * std::max(per, 1));
     k_viewshed_batch<<<(unsigned)grid, threads, smem, s>>>(B);
+    vs::note_launch();
+    VS_CUDA_TRY(cudaGetLastError());
+    return VS_OK;
+}
+
+// ------------------------------------------------------------------ exact visibility index
+// The label of the learned proposal (Sec. "Definitions": the visibility index
+// is the fraction of the receivers within the ROI that the transmitter sees).
+// Numerator: the viewshed's area (areas-only viewshed launch for windows that
+// fit in shared memory; the banded kernel, in chunks through a bitmap buffer,
+// for large ROIs).  Denominator: the lattice points of disc(R) whose post is
+// inside the grid, summed by rows (isqrt of R^2 - dy^2, clipped to the grid).
+namespace vs {
+// out[i] = area[i] / den(post i), the quotient of two integers rounded once to
+// float (divided in double, then rounded to float: with 53 >= 2*24 + 2
+// significand bits the second rounding cannot differ from a direct one); a
+// negative area (post outside the grid, timed-out wait) is passed through
+__global__ void k_exact_vix(const int64_t *__restrict__ posts, int64_t n, int H, int W, int R,
+                            const int32_t *__restrict__ area, float *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int a = area[i];
+    if (a < 0) {
+        out[i] = (float)a;
+        return;
+    }
+    const int64_t p = posts[i];
+    const int cx = (int)(p % W), cy = (int)(p / W);
+    long long den = 0;
+    const int y0 = max(-R, -cy), y1 = min(R, H - 1 - cy);
+    for (int dy = y0; dy <= y1; ++dy) {
+        const int h = isqrt_exact(R * R - dy * dy);
+        den += min(W - 1, cx + h) - max(0, cx - h) + 1;
+    }
+    out[i] = __double2float_rn(__ddiv_rn((double)a, (double)den));
+}
+}  // namespace vs
+
+static constexpr size_t kLabelBitmapBytes = (size_t)1 << 30;  // bitmap chunk of the banded path
+
+static inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// candidates per banded chunk: bitmaps within kLabelBitmapBytes
+static int64_t label_chunk(int32_t R, int64_t n) {
+    const int64_t words = (int64_t)(2 * R + 1) * words_per_row(R);
+    return std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)(kLabelBitmapBytes / (4 * (size_t)words))));
+}
+
+extern "C" size_t vs_exact_vix_workspace(int32_t H, int32_t W, int32_t R, int64_t n) {
+    if (H < 1 || W < 1 || H > kMaxH || W > kMaxH || R < 1 || R > kMaxR || n < 0) return 0;
+    size_t b = al256((size_t)n * 4) + 256;
+    if (vs_wide(R)) {
+        const int64_t words = (int64_t)(2 * R + 1) * words_per_row(R);
+        b += al256(vs_pairs_bytes(H, W)) + al256((size_t)label_chunk(R, n) * words * 4);
+    }
+    return b;
+}
+
+extern "C" int vs_exact_vix(vs_grid g, int32_t R, int32_t ht, int32_t hr, const int64_t *posts, int64_t n,
+                            float *out, void *ws, size_t ws_bytes, vs_stream_t st) {
+    if (R < 1 || R > kMaxR) return VS_ERR_RANGE;
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (ht < -100000 || ht > 100000 || hr < -100000 || hr > 100000) return VS_ERR_RANGE;
+    if (n < 0 || n > 0x7fffffffll) return VS_ERR_RANGE;
+    if (n == 0) return VS_OK;
+    if (!posts || !out) return VS_ERR_ARG;
+    if (!ws || ws_bytes < vs_exact_vix_workspace(g.H, g.W, R, n)) return VS_ERR_WS;
+    if ((rc = check_device())) return rc;
+    cudaStream_t s = (cudaStream_t)st;
+    char *w = (char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    int32_t *area = (int32_t *)w;
+    w += al256((size_t)n * 4);
+    if (vs_wide(R)) {
+        const size_t pb = al256(vs_pairs_bytes(g.H, g.W));
+        uint32_t *bm = (uint32_t *)(w + pb);
+        const int64_t chunk = label_chunk(R, n);
+        for (int64_t i = 0; i < n; i += chunk) {
+            const int64_t m = std::min(chunk, n - i);
+            if ((rc = vs_viewshed_wide(g, R, ht, hr, posts + i, m, bm, area + i, w, pb, s, i > 0))) return rc;
+        }
+    } else {
+        VsJob J;
+        size_t smem = 0;
+        if ((rc = vs_make_job(g, R, ht, hr, posts, n, nullptr, area, &J, &smem, true))) return rc;
+        VS_CUDA_TRY(cudaFuncSetAttribute(k_viewshed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int threads = tune_get(VS_TUNE_VIEWSHED_THREADS, R, default_threads(R));
+        k_viewshed<<<(unsigned)n, threads, smem, s>>>(J);
+        vs::note_launch();
+        VS_CUDA_TRY(cudaGetLastError());
+    }
+    k_exact_vix<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(posts, n, g.H, g.W, R, area, out);
     vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;

@@ -112,6 +112,7 @@ int vs_tune_set(int32_t op, int32_t R, int32_t value) {
         return VS_ERR_RANGE;
     if (op == VS_TUNE_VIEWSHED_WIDE && value != 0 && value != 1) return VS_ERR_RANGE;
     if (op == VS_TUNE_SITE_LAZY && (value < 0 || value > 2)) return VS_ERR_RANGE;
+    if (op == VS_TUNE_SITE_MULTI && value != 0 && value != 1) return VS_ERR_RANGE;
     std::lock_guard<std::mutex> lk(vs::g_tune_mu);
     vs::g_tune[op][R] = value;
     return VS_OK;

@@ -17,45 +17,16 @@ import torch
 from . import vshed as V
 
 
-def disc_in_grid(posts, H, W, R):
-    """|{(dx,dy): dx^2+dy^2 <= R^2, post+(dx,dy) inside the grid}| per post."""
-    dev = posts.device
-    dy = torch.arange(-R, R + 1, device=dev)
-    hw = torch.sqrt((R * R - dy * dy).double()).floor().long()
-    # exact integer square root
-    hw = torch.where((hw + 1) * (hw + 1) <= R * R - dy * dy, hw + 1, hw)
-    hw = torch.where(hw * hw > R * R - dy * dy, hw - 1, hw)
-    out = torch.empty(posts.numel(), dtype=torch.int64, device=dev)
-    for i in range(0, posts.numel(), 1 << 18):
-        p = posts[i:i + (1 << 18)]
-        cy, cx = (p // W)[:, None], (p % W)[:, None]
-        y = cy + dy[None, :]
-        lo = torch.clamp(cx - hw[None, :], min=0)
-        hi = torch.clamp(cx + hw[None, :], max=W - 1)
-        n = torch.clamp(hi - lo + 1, min=0) * ((y >= 0) & (y < H))
-        out[i:i + (1 << 18)] = n.sum(1)
-    return out
-
-
-def exact_vix(g, posts, R, ht, hr, chunk=100000, max_bitmap_bytes=2 << 30, ws=None):
-    """Exact visibility index of every listed post (fp32 in [0, 1]).  The
-    viewsheds are computed in chunks whose bitmaps stay under
-    ``max_bitmap_bytes`` (512 KB per post at R = 1000)."""
-    words = (2 * R + 1) * V.words_per_row(R)
-    chunk = max(1, min(chunk, max_bitmap_bytes // (4 * words)))
+def exact_vix(g, posts, R, ht, hr, chunk=1 << 20, ws=None):
+    """Exact visibility index of every listed post (fp32 in [0, 1]), computed
+    by vs_exact_vix in chunks of ``chunk`` posts (one workspace reused)."""
     out = torch.empty(posts.numel(), dtype=torch.float32, device=posts.device)
-    bm = torch.empty((min(chunk, posts.numel()), 2 * R + 1, V.words_per_row(R)), dtype=torch.int32,
-                     device=posts.device)
-    area = torch.empty(min(chunk, posts.numel()), dtype=torch.int32, device=posts.device)
-    wsb = V.viewshed_workspace(g.H, g.W, R, min(chunk, posts.numel()))
-    if wsb and (ws is None or ws.numel() < wsb):
-        ws = torch.empty(wsb, dtype=torch.uint8, device=posts.device)
-    den = disc_in_grid(posts, g.H, g.W, R)
+    wsb = V.lib().vs_exact_vix_workspace(g.H, g.W, R, min(chunk, posts.numel()))
+    if ws is None or ws.numel() < wsb:
+        ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=posts.device)
     for i in range(0, posts.numel(), chunk):
         p = posts[i:i + chunk].contiguous()
-        n = p.numel()
-        V.viewshed(g, R, ht, hr, p, bm=bm[:n], area=area[:n], ws=ws)
-        out[i:i + n] = area[:n].float() / den[i:i + n].float()
+        V.exact_vix(g, R, ht, hr, p, out=out[i:i + p.numel()], ws=ws)
     return out
 
 

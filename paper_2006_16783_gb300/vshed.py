@@ -75,6 +75,8 @@ SIGNATURES = {
     "vs_viewshed": (ctypes.c_int, [vs_grid, i32, i32, i32, P, i64, P, P, P, sz, P]),
     "vs_viewshed_r3_workspace": (sz, [i32, i32]),
     "vs_viewshed_r3": (ctypes.c_int, [vs_grid, i32, i32, i32, P, i64, P, P, P, sz, P]),
+    "vs_exact_vix_workspace": (sz, [i32, i32, i32, i64]),
+    "vs_exact_vix": (ctypes.c_int, [vs_grid, i32, i32, i32, P, i64, P, P, sz, P]),
     "vs_site_workspace": (sz, [i64, i32]),
     "vs_site": (ctypes.c_int, [P, P, i64, i32, i32, i32, i32, f64, P, P, P, P, P, sz, P]),
     "vs_site_gains": (ctypes.c_int, [P, P, i64, i32, i32, i32, P, P, P]),
@@ -276,6 +278,23 @@ def viewshed_r3(g, R, ht, hr, cand, bm=None, area=None, ws=None):
     _check("vs_viewshed_r3", lib().vs_viewshed_r3(g.c(), R, ht, hr, _ptr(cand), n, _ptr(bm), _ptr(area),
                                                   _ptr(ws), wsb, _stream()))
     return bm, area
+
+
+def exact_vix(g, R, ht, hr, posts, out=None, ws=None):
+    """Exact visibility index of each post (float32; -1 outside the grid):
+    viewshed area over the ROI's receivers inside the grid.  ws: optional
+    uint8 device buffer of at least vs_exact_vix_workspace bytes."""
+    _need_cuda(posts)
+    posts = posts.contiguous()
+    n = posts.numel()
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=posts.device)
+    wsb = lib().vs_exact_vix_workspace(g.H, g.W, R, n)
+    if ws is None or ws.numel() < wsb:
+        ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=posts.device)
+    _check("vs_exact_vix", lib().vs_exact_vix(g.c(), R, ht, hr, _ptr(posts), n, _ptr(out), _ptr(ws), wsb,
+                                              _stream()))
+    return out
 
 
 def site_ex(bm, cand, H, W, R, n_obs, target=0.0, grid=None, ht=0, weight=None, cum=None, sync=True):

@@ -113,7 +113,8 @@ def test_large_roi_size_queries(L):
     assert L.vs_tune_set(vshed.VS_TUNE_VIEWSHED_WIDE, 50, 2) == vshed.VS_ERR_RANGE
     assert L.vs_tune_set(vshed.VS_TUNE_SITE_LAZY, 50, 3) == vshed.VS_ERR_RANGE
     assert L.vs_tune_set(vshed.VS_TUNE_VIX_TILE, 50, 4) == vshed.VS_ERR_RANGE
-    assert L.vs_tune_set(5, 50, 0) == vshed.VS_ERR_RANGE
+    assert L.vs_tune_set(vshed.VS_TUNE_SITE_MULTI, 50, 2) == vshed.VS_ERR_RANGE
+    assert L.vs_tune_set(6, 50, 0) == vshed.VS_ERR_RANGE
 
 
 def test_large_roi_argument_errors_need_no_device(L):
@@ -149,3 +150,16 @@ def test_site_noalloc_limit(L):
     dummy = ctypes.c_void_p(256)
     rc = L.vs_site_noalloc(dummy, dummy, 37440, 300, 300, 9, 10, 0.0, dummy, dummy, dummy, dummy, None)
     assert rc == vshed.VS_ERR_RANGE
+
+
+def test_exact_vix_queries_need_no_device(L):
+    from paper_2006_16783_gb300 import vshed
+    assert L.vs_exact_vix_workspace(1000, 1000, 100, 500) >= 4 * 500
+    assert L.vs_exact_vix_workspace(1000, 1200, 1000, 10) >= 8 * 1000 * 1200 + 10 * 4 * 2001 * 64
+    assert L.vs_exact_vix_workspace(1000, 1000, 0, 10) == 0
+    g = vshed.vs_grid(100, 100, 104, None)
+    dummy = ctypes.c_void_p(256)
+    assert L.vs_exact_vix(g, 10, 10, 10, dummy, 5, dummy, dummy, 1 << 20, None) == vshed.VS_ERR_ARG
+    g = vshed.vs_grid(100, 100, 104, dummy)
+    assert L.vs_exact_vix(g, 0, 10, 10, dummy, 5, dummy, dummy, 1 << 20, None) == vshed.VS_ERR_RANGE
+    assert L.vs_exact_vix(g, 10, 10, 10, dummy, 5, dummy, None, 0, None) == vshed.VS_ERR_WS

@@ -20,19 +20,29 @@ def V():
     return V
 
 
-def test_exact_labels_match_oracle(V, O):
+@pytest.mark.parametrize("H,W,R,wide", [(260, 240, 30, 0), (97, 300, 100, 0), (260, 240, 30, 1),
+                                         (700, 650, 300, 0)])
+def test_exact_labels_match_oracle(V, O, H, W, R, wide):
+    """vs_exact_vix (labels of the learned proposal) bit for bit against the
+    oracle's exact visibility index: interior, edge and corner posts, a grid
+    narrower than the ROI, the banded large-ROI path (forced at R = 30, and
+    R = 300 beyond shared memory), posts outside the grid."""
     from paper_2006_16783_gb300 import surrogate as S
-    H, W, R = 260, 240, 30
-    z = T.spectral_fbm(H, W, 0.8, 17, 0, 800).numpy()
+    z = T.spectral_fbm(H, W, 0.8, 17 + R, 0, 800).numpy()
     g = V.Grid.from_tensor(torch.as_tensor(z), "cuda")
     posts = S.sample_posts(H, W, 300, 0, 5, "cuda")
-    lab = S.exact_vix(g, posts, R, 10, 10).cpu().numpy()
-    ph = posts.cpu().numpy()
-    bm, area = O.viewshed(z, R, 10, 10, ph, threads=8)
-    den = np.array([sum(1 for dy in range(-R, R + 1) for dx in range(-R, R + 1)
-                        if dx * dx + dy * dy <= R * R and 0 <= p // W + dy < H and 0 <= p % W + dx < W)
-                    for p in ph[:40]])
-    assert np.allclose(lab[:40], area[:40] / den, rtol=0, atol=1e-6)
+    edge = torch.tensor([0, W - 1, (H - 1) * W, H * W - 1, W // 2, (H // 2) * W, -3, H * W],
+                        dtype=torch.int64, device="cuda")
+    posts = torch.cat([posts, edge])
+    if wide:
+        V.tune_set(V.VS_TUNE_VIEWSHED_WIDE, R, 1)
+    try:
+        lab = S.exact_vix(g, posts, R, 10, 10, chunk=128).cpu().numpy()
+    finally:
+        V.tune_set(V.VS_TUNE_VIEWSHED_WIDE, R, 0)
+    want = O.exact_vix(z, R, 10, 10, posts.cpu().numpy(), threads=8)
+    assert lab.view(np.uint32).tolist() == want.view(np.uint32).tolist()
+    assert lab[-2] == -1.0 and lab[-1] == -1.0
 
 
 @pytest.mark.slow
