@@ -109,6 +109,20 @@ def forward(params, x0, keep=False):
     return y
 
 
+def layer_pre(params, l, a, absolute=False):
+    """Pre-activation of conv layer l (0-based) on input a (B, cin, H, W):
+    (B, Ho, Wo, 32) in fp64 from the bf16-rounded weights, plus the bias.
+    With absolute=True: the sum of the absolute values of the same terms
+    (|w| |a| over the taps, + |bias|), the scale of any rounding error of a
+    lower-precision accumulation of that sum."""
+    ci, co, s = LAYERS[l]
+    cols = _im2col(np.asarray(a, dtype=np.float64), s)
+    w = bf16(params["w%d" % l]).reshape(co, ci * 9)
+    if absolute:
+        return np.abs(cols) @ np.abs(w).T + np.abs(params["b%d" % l])
+    return cols @ w.T + params["b%d" % l]
+
+
 def loss_and_grads(params, x0, label):
     """L1 loss and gradients of every parameter (dict like params)."""
     B = x0.shape[0]

@@ -1027,6 +1027,7 @@ struct SiteMParams {
     Site1Params b;
     int Lmax;     // winners per round: <= kMultiMaxL and the workers' delta rows
     int nrow;     // window rows per worker: ceil((2R+1) / (Q-1))
+    unsigned long long *stats;  // rounds, lists, rescans of used-up runs (spare workspace bytes)
 };
 
 struct SiteMHeader {
@@ -1080,6 +1081,7 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
     long long covered = (rank == 0 && P.need >= 0) ? (long long)*P.covered0 : 0;
     int t = 0, L = 0, cursor = 0, NI = 0;
     bool in_round = false, first = false;
+    unsigned long long n_rounds = 0, n_lists = 0, n_rescans = 0;  // leader thread 0's counts
     cl.sync();
 
     for (;;) {
@@ -1118,24 +1120,33 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
                     if (lane == 0) s_wkey[wid] = k;
                 }
                 __syncthreads();
-                // ---- warp 0 picks the round's winners
+                // ---- warp 0 picks the round's winners.  Lane j holds warp j's best
+                // key as (gain, ~slot) and the coordinates of winners j and j + 32;
+                // the 64-bit max is two 32-bit warp reductions (gain, then ~slot
+                // among the lanes holding that gain).
                 if (wid == 0) {
+                    const uint64_t k0 = s_wkey[lane];
+                    uint32_t khi = (uint32_t)(k0 >> 32), klo = (uint32_t)k0;
+                    int ax = 0, ay = 0, bx = 0, by = 0;
                     int nl = 0;
                     for (;;) {
                         if (t + nl >= P.n_obs || nl >= M.Lmax) break;
                         if (P.need >= 0 && covered >= P.need) break;
-                        uint64_t k = s_wkey[lane];
-                        for (int o = 16; o > 0; o >>= 1) k = u64max(k, __shfl_xor_sync(0xffffffffu, k, o));
-                        const uint32_t g = (uint32_t)(k >> 32);
+                        const uint32_t g = __reduce_max_sync(0xffffffffu, khi);
                         if (g == 0u) break;
-                        const int slot = key_slot(k);
+                        const uint32_t lo = __reduce_max_sync(0xffffffffu, khi == g ? klo : 0u);
+                        const int slot = (int)(0xFFFFFFFFu - lo);
                         const int own = slot / cs;
                         const uint32_t post = s_tpost[own];
                         const int x = (int)(post % (uint32_t)W), y = (int)(post / (uint32_t)W);
-                        bool conf = false;
-                        for (int a = lane; a < nl; a += 32)
-                            conf |= abs(x - s_wx[a]) <= 2 * R && abs(y - s_wy[a]) <= 2 * R;
+                        const bool conf = (lane < nl && abs(x - ax) <= 2 * R && abs(y - ay) <= 2 * R) ||
+                                          (lane + 32 < nl && abs(x - bx) <= 2 * R && abs(y - by) <= 2 * R);
                         if (__any_sync(0xffffffffu, conf)) break;
+                        if (lane == (nl & 31)) {
+                            if (nl < 32) { ax = x; ay = y; } else { bx = x; by = y; }
+                        }
+                        const bool t2 = s_t2ok[own] != 0;
+                        __syncwarp();  // every lane has read the owner's state before lane 0 changes it
                         if (lane == 0) {
                             s_wslot[nl] = slot;
                             s_wpost[nl] = post;
@@ -1143,33 +1154,35 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
                             s_wx[nl] = x;
                             s_wy[nl] = y;
                             s_gain[slot] = 0u;
-                        }
-                        ++nl;
-                        covered += g;
-                        __syncwarp();
-                        // the owner's next best key
-                        if (s_t2ok[own]) {
-                            __syncwarp();
-                            if (lane == 0) {
+                            if (t2) {  // the owner's second key becomes its best
                                 s_tkey[own] = s_tkey2[own];
                                 s_tpost[own] = s_tpost2[own];
                                 s_t2ok[own] = 0;
                             }
-                        } else {
-                            const int r0 = min(n, own * cs), r1 = min(n, r0 + cs);
-                            uint64_t b = 0ull;
-                            for (int i = r0 + lane; i < r1; i += 32) b = u64max(b, slot_key(s_gain[i], i));
-                            for (int o = 16; o > 0; o >>= 1) b = u64max(b, __shfl_xor_sync(0xffffffffu, b, o));
-                            if (lane == 0) {
-                                s_tkey[own] = b;
-                                s_tpost[own] = b ? sp[key_slot(b)] : 0u;
-                            }
                         }
+                        ++nl;
+                        covered += g;
                         __syncwarp();
-                        uint64_t kk = s_tkey[(own & ~31) + lane];
-                        for (int o = 16; o > 0; o >>= 1) kk = u64max(kk, __shfl_xor_sync(0xffffffffu, kk, o));
-                        if (lane == 0) s_wkey[own >> 5] = kk;
-                        __syncwarp();
+                        if (!t2) {  // its run is rescanned (its second key was used up)
+                            if (lane == 0) ++n_rescans;
+                            const int r0 = min(n, own * cs), r1 = min(n, r0 + cs);
+                            uint64_t bk = 0ull;
+                            for (int i = r0 + lane; i < r1; i += 32) bk = u64max(bk, slot_key(s_gain[i], i));
+                            const uint32_t bh = __reduce_max_sync(0xffffffffu, (uint32_t)(bk >> 32));
+                            const uint32_t bl = __reduce_max_sync(0xffffffffu, (uint32_t)(bk >> 32) == bh ? (uint32_t)bk : 0u);
+                            if (lane == 0) {
+                                const uint64_t kb = ((uint64_t)bh << 32) | bl;
+                                s_tkey[own] = kb;
+                                s_tpost[own] = kb ? sp[key_slot(kb)] : 0u;
+                            }
+                            __syncwarp();
+                        }
+                        // the owner warp's best key
+                        const int ow = own >> 5;
+                        const uint64_t kk = s_tkey[(ow << 5) + lane];
+                        const uint32_t hh = __reduce_max_sync(0xffffffffu, (uint32_t)(kk >> 32));
+                        const uint32_t ll = __reduce_max_sync(0xffffffffu, (uint32_t)(kk >> 32) == hh ? (uint32_t)kk : 0u);
+                        if (lane == ow) { khi = hh; klo = ll; }
                     }
                     if (lane == 0) s_nL = nl;
                 }
@@ -1209,6 +1222,7 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
                     cursor = 0;
                     in_round = true;
                     first = true;
+                    ++n_rounds;
                 }
             }
             // ---- compaction of band slots [cursor, NI) into the list
@@ -1318,6 +1332,7 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
                     __syncthreads();  // s_cut and s_wa are reused by the next pass
                 }
             }
+            if (!stop) ++n_lists;
             if (tid < Q) {
                 SiteMHeader h;
                 h.stop = stop ? 1 : 0;
@@ -1353,6 +1368,34 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
                 if (tid < tot) s_cpref[tid] = wbase + inc - cnt;
                 if (tid == 0) s_cpref[tot] = rows_all;
             }
+            __syncthreads();  // s_cpref and the zeroed s_part
+            const int TT = s_cpref[tot];
+            // row item e of this worker: its pair, window row and bitmap row
+            auto row_item = [&](int e, int &l, int &r, const uint4 *&vr) {
+                l = 0;
+                int h2 = tot - 1;  // last l with s_cpref[l] <= e
+                while (l < h2) {
+                    const int m = (l + h2 + 1) >> 1;
+                    if (s_cpref[m] <= e) l = m; else h2 = m - 1;
+                }
+                const int4 gq = s_geo[l];
+                const int ra = gq.x & 0xFFFF;
+                r = ra + ((wr - ra) % Qw + Qw) % Qw + Qw * (e - s_cpref[l]);
+                vr = (const uint4 *)(P.bm + (uint32_t)gq.z + (uint32_t)((r - ra) * PR));
+            };
+            // the first refresh row of each thread is loaded beside the window's
+            // words (only the popcounts need the new coverage)
+            constexpr int kPreVec = 2;  // rows of up to 8 words (R = 100: 8)
+            const bool pre = tid < TT && PR / 4 <= kPreVec;
+            uint4 pv[kPreVec];
+            int pl = 0, prr = 0;
+            if (pre) {
+                const uint4 *vr;
+                row_item(tid, pl, prr, vr);
+#pragma unroll
+                for (int q4 = 0; q4 < kPreVec; ++q4)
+                    if (q4 < PR / 4) pv[q4] = __ldg(vr + q4);
+            }
             // ---- this worker's window rows of every winner (a round's first list)
             if (h.first) {
                 const int per_w = nrow * PR;
@@ -1375,33 +1418,44 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
                     s_dloc[e] = d;
                 }
             }
-            __syncthreads();  // s_cpref, s_part and s_dloc published
-            const int TT = s_cpref[tot];
-            for (int e = tid; e < TT; e += kSiteThreads) {
-                int l = 0, h2 = tot - 1;  // last l with s_cpref[l] <= e
-                while (l < h2) {
-                    const int m = (l + h2 + 1) >> 1;
-                    if (s_cpref[m] <= e) l = m; else h2 = m - 1;
+            __syncthreads();  // s_dloc published
+            // popc(V_c AND delta) over the overlap words of one refresh row
+            auto row_sum = [&](const uint32_t *dl, int c0, int nwd, int q4, const uint4 &v) {
+                const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+                unsigned sum = 0;
+#pragma unroll
+                for (int t4 = 0; t4 < 4; ++t4) {
+                    const int jw = 4 * q4 + t4 - c0;
+                    if (jw >= 0 && jw < nwd) sum += __popc(vv[t4] & dl[jw]);
                 }
+                return sum;
+            };
+            auto row_delta = [&](int l, int r, int &c0, int &nwd) {
                 const int4 gq = s_geo[l];
-                const int ra = gq.x & 0xFFFF;
-                const int r = ra + ((wr - ra) % Qw + Qw) % Qw + Qw * (e - s_cpref[l]);
-                const int nwd = gq.y & 0x3FF, c0 = (gq.y >> 10) & 0x3FF, dw0 = gq.y >> 20;
-                const uint32_t *dl = s_dloc + ((size_t)gq.w * nrow + (r - wr) / Qw) * PR + dw0;
+                nwd = gq.y & 0x3FF;
+                c0 = (gq.y >> 10) & 0x3FF;
+                const int dw0 = gq.y >> 20;
+                return s_dloc + ((size_t)gq.w * nrow + (r - wr) / Qw) * PR + dw0;
+            };
+            if (pre) {
+                int c0, nwd;
+                const uint32_t *dl = row_delta(pl, prr, c0, nwd);
+                unsigned sum = 0;
+#pragma unroll
+                for (int q4 = 0; q4 < kPreVec; ++q4)
+                    if (q4 < PR / 4) sum += row_sum(dl, c0, nwd, q4, pv[q4]);
+                if (sum) atomicAdd(&s_part[pl], sum);
+            }
+            for (int e = tid + (pre ? kSiteThreads : 0); e < TT; e += kSiteThreads) {
+                int l, r, c0, nwd;
+                const uint4 *vr;
+                row_item(e, l, r, vr);
+                const uint32_t *dl = row_delta(l, r, c0, nwd);
                 uint32_t any = 0u;
                 for (int jw = 0; jw < nwd; ++jw) any |= dl[jw];
                 if (!any) continue;
-                const uint4 *vr = (const uint4 *)(P.bm + (uint32_t)gq.z + (uint32_t)((r - ra) * PR));
                 unsigned sum = 0;
-                for (int q4 = 0; q4 < PR / 4; ++q4) {
-                    const uint4 v = __ldg(vr + q4);
-                    const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int t4 = 0; t4 < 4; ++t4) {
-                        const int jw = 4 * q4 + t4 - c0;
-                        if (jw >= 0 && jw < nwd) sum += __popc(vv[t4] & dl[jw]);
-                    }
-                }
+                for (int q4 = 0; q4 < PR / 4; ++q4) sum += row_sum(dl, c0, nwd, q4, __ldg(vr + q4));
                 if (sum) atomicAdd(&s_part[l], sum);
             }
             __syncthreads();
@@ -1431,7 +1485,12 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
             __syncthreads();
         }
     }
-    if (rank == 0 && tid == 0) *P.n_chosen = t;
+    if (rank == 0 && tid == 0) {
+        *P.n_chosen = t;
+        M.stats[0] = n_rounds;
+        M.stats[1] = n_lists;
+        M.stats[2] = n_rescans;
+    }
     cl.sync();  // no CTA leaves while another may still address its shared memory
 }
 
@@ -2156,7 +2215,7 @@ static bool siteq_launchable(size_t smem, int q) {
 
 // multi-winner leader cluster of q CTAs (q - 1 workers): VS_OK when launched,
 // a negative code on a CUDA error, 1 when the call does not fit it
-static int launch_site_multi(const Site1Params &Q1, int q, cudaStream_t s) {
+static int launch_site_multi(const Site1Params &Q1, int q, unsigned long long *stats, cudaStream_t s) {
     if (q < 2 || q > 16) return 1;
     const int nrow = (2 * Q1.R + 1 + (q - 1) - 1) / (q - 1);
     cudaFuncAttributes fa;
@@ -2197,6 +2256,7 @@ static int launch_site_multi(const Site1Params &Q1, int q, cudaStream_t s) {
     M.b = Q1;
     M.Lmax = Lmax;
     M.nrow = nrow;
+    M.stats = stats;
     VS_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_site_multi, M));
     vs::note_launch();
     return VS_OK;
@@ -2286,7 +2346,9 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
         const int qc = (qtune == 0) ? 8 : qtune;
         if (qc >= 2 && Q1.vec_rows && tune_get(VS_TUNE_SITE_MULTI, R, 0) != 1 &&
             (uint64_t)n * (uint64_t)P.words < (1ull << 32)) {
-            const int mrc = launch_site_multi(Q1, qc, s);
+            // three counters of the loop in the workspace's spare bytes, after
+            // the coverage count (diagnostics, read by nothing in the library)
+            const int mrc = launch_site_multi(Q1, qc, cov + 1, s);
             if (mrc <= 0) return mrc;  // launched, or a CUDA error; > 0: does not fit
         }
         if (qc >= 2 && Q1.vec_rows && (uintptr_t)cum % 16 == 0) {

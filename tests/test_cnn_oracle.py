@@ -99,3 +99,20 @@ def test_extract_patch_slices_and_clamps():
                 y = min(max(cy + (r - 32) * s, 0), 299)
                 x = min(max(cx + (c - 32) * s, 0), 279)
                 assert p[r, c] == z[y, x]
+
+
+@pytest.mark.parametrize("l", [0, 1, 4])
+def test_layer_pre_matches_direct_loop(l):
+    """layer_pre (the per-layer check of the tensor-core forward) against the
+    direct 7-loop convolution with bf16-rounded weights; absolute=True against
+    the same loop on absolute values."""
+    rng = np.random.default_rng(10 + l)
+    p = C.init_params(l)
+    p["b%d" % l] = rng.normal(0, 0.1, 32)
+    ci, co, s = C.LAYERS[l]
+    x = C.bf16(rng.normal(size=(2, ci, 9, 8)))
+    w = C.bf16(p["w%d" % l])
+    assert np.allclose(C.layer_pre(p, l, x), _direct_conv(x, w, p["b%d" % l], s), rtol=0, atol=1e-12)
+    got = C.layer_pre(p, l, x, absolute=True)
+    want = _direct_conv(np.abs(x), np.abs(w), np.abs(p["b%d" % l]), s)
+    assert np.allclose(got, want, rtol=0, atol=1e-12)

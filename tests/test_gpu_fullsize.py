@@ -103,3 +103,65 @@ def test_batch_full_size_sampled(V, O):
         obm, oarea = O.viewshed(zh, w.R, w.ht, w.hr, c, threads=16)
         assert (j["area"].cpu().numpy()[sel] == oarea).all(), w.name
         assert (j["bm"].cpu().numpy()[sel].view(np.uint32) == obm).all(), w.name
+
+
+def _downstream_matches_oracle(O, zh, w, cand, bm, area, res):
+    """Every candidate's bitmap and area, then the whole greedy (observers,
+    gains, cumulative viewshed) against the oracle on the oracle's bitmaps."""
+    c = cand.cpu().numpy()
+    obm, oarea = O.viewshed(zh, w.R, w.ht, w.hr, c, threads=16)
+    assert (area.cpu().numpy() == oarea).all()
+    assert (bm.cpu().numpy().view(np.uint32) == obm).all()
+    och, ogn, oC = O.site(obm, c, w.H, w.W, w.R, w.n_obs)
+    chosen, gains, cum, t = res
+    t = int(t.item()) if torch.is_tensor(t) else t
+    assert t == len(och)
+    assert chosen[:t].cpu().numpy().tolist() == och.tolist()
+    assert gains[:t].cpu().numpy().tolist() == ogn.tolist()
+    assert (cum.cpu().numpy().view(np.uint32) == oC).all()
+
+
+def _plain(V, O, w, g, zh):
+    v = V.vix(g, w.R, w.ht, w.hr, w.S, w.vix_seed)
+    cand = V.findmax(v, w.block, w.k)
+    ocand = O.findmax(v.cpu().numpy(), w.block, w.k)
+    del v
+    assert cand.cpu().numpy().tolist() == ocand.tolist()
+    bm, area = V.viewshed(g, w.R, w.ht, w.hr, cand)
+    res = V.site(bm, cand, w.H, w.W, w.R, w.n_obs)
+    torch.cuda.synchronize()
+    _downstream_matches_oracle(O, zh, w, cand, bm, area, res)
+
+
+def test_headline_pipelines_full_size(V, O):
+    """The 46400^2 headline configuration end to end, in the bench's launch
+    configuration: the plain pipeline (vix map -> findmax over the whole map
+    compared with the oracle's findmax on the same map -> 40,000 viewsheds ->
+    4096 observers) and the surrogate pipeline (CNN scores of the stride-64
+    lattice, patch step 3 -> findmax_f32 compared with the oracle's on the
+    same scores -> 40,000 viewsheds -> 4096 observers).  Every candidate,
+    bitmap, area, observer, gain and the cumulative viewshed is compared; only
+    the vix map itself is sampled (test_full_size_sampled_parity)."""
+    from paper_2006_16783_gb300 import surrogate as S
+    w = WL.FULL
+    g, zh = _terrain(V, w)
+    _plain(V, O, w, g, zh)
+    packed = V.cnn_pack(S.init_master(0))
+    stride, step = 64, 3
+    score = V.cnn_score_lattice(g, stride, packed, patch_step=step)
+    cand = V.findmax_f32(score, w.H, w.W, stride, w.block, w.k)
+    ocand = O.findmax_f32(score.cpu().numpy(), w.H, w.W, stride, w.block, w.k)
+    assert len(ocand) == 40000 and cand.cpu().numpy().tolist() == ocand.tolist()
+    bm, area = V.viewshed(g, w.R, w.ht, w.hr, cand)
+    res = V.site(bm, cand, w.H, w.W, w.R, w.n_obs)
+    torch.cuda.synchronize()
+    _downstream_matches_oracle(O, zh, w, cand, bm, area, res)
+
+
+def test_scale_pipeline_full_size(V, O):
+    """16384^2, R = 200, S = 20, top-2 per 256^2 block (8192 candidates, bitmap
+    rows of 14 words: the one-CTA greedy), 2048 observers: the whole plain
+    pipeline against the oracle as above."""
+    w = WL.SCALE
+    g, zh = _terrain(V, w)
+    _plain(V, O, w, g, zh)
