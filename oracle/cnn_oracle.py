@@ -123,13 +123,17 @@ def layer_pre(params, l, a, absolute=False):
     return cols @ w.T + params["b%d" % l]
 
 
-def loss_and_grads(params, x0, label):
-    """L1 loss and gradients of every parameter (dict like params)."""
+def loss_and_grads(params, x0, label, scale=False):
+    """L1 loss and gradients of every parameter (dict like params).  With
+    scale=True also, per gradient element, the sum of the absolute values of
+    the terms it adds up (the scale of the rounding error of a lower-precision
+    evaluation of the same sums)."""
     B = x0.shape[0]
     y, (cache, a5, g, logit) = forward(params, x0, keep=True)
     loss = np.abs(y - label).mean()
     dlogit = np.sign(y - label) * y * (1.0 - y) / B
     grads = {"fw": g.T @ dlogit, "fb": np.array([dlogit.sum()])}
+    sc = {"fw": np.abs(g).T @ np.abs(dlogit), "fb": np.array([np.abs(dlogit).sum()])}
     dg = dlogit[:, None] * params["fw"][None, :]           # (B, 32)
     Ho, Wo = a5.shape[2], a5.shape[3]
     da = np.broadcast_to(dg[:, :, None, None] / (Ho * Wo), a5.shape).copy()
@@ -139,10 +143,15 @@ def loss_and_grads(params, x0, label):
         dz = bf16(da.transpose(0, 2, 3, 1) * (pre > 0))     # (B, Ho, Wo, co)
         grads["w%d" % l] = np.einsum("bhwk,bhwo->ok", cols, dz).reshape(co, ci, 3, 3)
         grads["b%d" % l] = dz.sum(axis=(0, 1, 2))
+        if scale:
+            sc["w%d" % l] = np.einsum("bhwk,bhwo->ok", np.abs(cols), np.abs(dz)).reshape(co, ci, 3, 3)
+            sc["b%d" % l] = np.abs(dz).sum(axis=(0, 1, 2))
         if l > 0:
             w = bf16(params["w%d" % l]).reshape(co, ci * 9)
             dcols = dz @ w                                  # (B, Ho, Wo, ci*9)
             da = _col2im(dcols, a_in.shape, s)
+    if scale:
+        return loss, grads, sc
     return loss, grads
 
 

@@ -42,19 +42,12 @@
 #include <cuda_bf16.h>
 
 #include "vs_common.cuh"
+#include "cnn_layout.cuh"
 
 namespace vs {
 namespace cnn {
 
 constexpr int kThreads = 512;  // 16 warps
-constexpr int kPatch = 65;
-
-// ---- master parameter layout (fp32): w_l [32][cin][3][3], b_l [32], fw [32], fb
-constexpr int kNParams = 288 + 32 + 4 * (9216 + 32) + 33;
-__host__ __device__ constexpr int off_w(int l) { return l == 0 ? 0 : 320 + (l - 1) * 9248; }
-__host__ __device__ constexpr int off_b(int l) { return l == 0 ? 288 : 320 + (l - 1) * 9248 + 9216; }
-constexpr int kOffFw = 320 + 4 * 9248;
-
 // ---- packed layout (bytes): B operands (bf16), biases (fp32), fc (fp32)
 constexpr int kB1Bytes = 1024;                 // 32 x 16
 constexpr int kBlBytes = 9 * 2 * 1024;         // per 32->32 layer: 9 taps x 2 K-steps
@@ -64,14 +57,6 @@ constexpr int kPkBias = kB1Bytes + 4 * kBlBytes;  // 5 x 32 floats
 constexpr int kPkFc = kPkBias + 5 * 32 * 4;       // 32 + 1 floats (padded to 36)
 constexpr int kPackedBytes = kPkFc + 36 * 4;
 
-// ---- activations saved for the backward pass, per patch (bytes)
-constexpr int kA1 = 33 * 33 * 32 * 2, kA2 = 17 * 17 * 32 * 2, kA3 = 9 * 9 * 32 * 2,
-              kA4 = 5 * 5 * 32 * 2, kA5 = 5 * 5 * 32 * 2;
-constexpr int kSvA1 = 0, kSvA2 = kSvA1 + kA1, kSvA3 = kSvA2 + kA2, kSvA4 = kSvA3 + kA3,
-              kSvA5 = kSvA4 + kA4, kSvHead = kSvA5 + kA5;  // head: g[32], logit, y (fp32)
-constexpr int kSaveBytes = ((kSvHead + 34 * 4) + 127) & ~127;
-constexpr int kSvInput = kSaveBytes;                       // x0: 65x65 bf16
-constexpr int kSaveBytesTotal = kSaveBytes + ((kPatch * kPatch * 2 + 127) & ~127);
 
 // ---- shared-memory plan of the forward kernel (bytes, 128-aligned)
 constexpr int kPln2 = 18 * 18, kPln3 = 10 * 10, kPln4 = 6 * 6, kPln5 = 7 * 7;
@@ -838,141 +823,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
 // over the patches it owns and adds it to the global gradient once, so the
 // global atomics do not scale with the batch.  Products take bf16-valued
 // operands (saved activations, bf16-rounded weights, bf16-rounded
-// pre-activation gradients) and accumulate in FP32 on the CUDA cores.
-constexpr int kBwdThreads = 256;
-
-struct LayerGeo {
-    int Hin, Win, Cin, Hout, Wout, stride;
-    int sv_in, sv_out;  // byte offsets of the layer's input / output in a save record
-};
-
-__host__ __device__ inline LayerGeo layer_geo(int l) {
-    const int hin[5] = {65, 33, 17, 9, 5}, hout[5] = {33, 17, 9, 5, 5};
-    const int svin[5] = {kSvInput, kSvA1, kSvA2, kSvA3, kSvA4};
-    const int svout[5] = {kSvA1, kSvA2, kSvA3, kSvA4, kSvA5};
-    LayerGeo g;
-    g.Hin = g.Win = hin[l];
-    g.Cin = l == 0 ? 1 : 32;
-    g.Hout = g.Wout = hout[l];
-    g.stride = l == 4 ? 1 : 2;
-    g.sv_in = svin[l];
-    g.sv_out = svout[l];
-    return g;
-}
-
-// dL/dlogit = sign(y - label) * y (1 - y) / B (L1 loss through the sigmoid);
-// fc gradients; dL/da5 = dL/dg / 25 on every pooled pixel.  One warp per patch.
-__global__ void k_cnn_head_bwd(const unsigned char *__restrict__ save, const float *__restrict__ labels,
-                               long long B, float inv_batch, const float *__restrict__ master,
-                               float *__restrict__ grads, float *__restrict__ da5,
-                               float *__restrict__ loss_sum) {
-    const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int c = threadIdx.x & 31;
-    if (b >= B) return;
-    const float *hd = (const float *)(save + b * (long long)kSaveBytesTotal + kSvHead);
-    const float y = hd[33], lab = labels[b];
-    const float sgn = (y > lab) ? 1.f : ((y < lab) ? -1.f : 0.f);
-    const float dlogit = sgn * y * (1.f - y) * inv_batch;
-    atomicAdd(&grads[kOffFw + c], dlogit * hd[c]);
-    if (c == 0) {
-        atomicAdd(&grads[kOffFw + 32], dlogit);
-        atomicAdd(loss_sum, fabsf(y - lab));
-    }
-    const float d = dlogit * master[kOffFw + c] * (1.0f / 25.0f);
-    for (int pix = 0; pix < 25; ++pix) da5[(b * 25 + pix) * 32 + c] = d;
-}
-
-__global__ void __launch_bounds__(kBwdThreads) k_cnn_conv_bwd(const unsigned char *__restrict__ save,
-                                                              long long B, int l,
-                                                              const float *__restrict__ da_out,
-                                                              const float *__restrict__ master,
-                                                              float *__restrict__ grads,
-                                                              float *__restrict__ da_in) {
-    extern __shared__ __align__(16) unsigned char smb[];
-    const LayerGeo G = layer_geo(l);
-    const int nW = 32 * G.Cin * 9;
-    const int nin = G.Hin * G.Win * G.Cin, nout = G.Hout * G.Wout * 32;
-    float *Wr = (float *)smb;                         // nW, bf16-rounded weights
-    float *dW = Wr + nW;                              // nW partial gradient
-    float *db = dW + nW;                              // 32
-    __nv_bfloat16 *ain = (__nv_bfloat16 *)(db + 32);  // nin
-    __nv_bfloat16 *dz = ain + ((nin + 7) & ~7);       // nout
-    const int tid = threadIdx.x;
-    for (int i = tid; i < nW; i += blockDim.x) {
-        Wr[i] = bf16_round(master[off_w(l) + i]);
-        dW[i] = 0.f;
-    }
-    if (tid < 32) db[tid] = 0.f;
-    __syncthreads();
-    const int s = G.stride;
-    for (long long b = blockIdx.x; b < B; b += gridDim.x) {
-        const unsigned char *rec = save + b * (long long)kSaveBytesTotal;
-        const __nv_bfloat16 *gin = (const __nv_bfloat16 *)(rec + G.sv_in);
-        const __nv_bfloat16 *gout = (const __nv_bfloat16 *)(rec + G.sv_out);
-        for (int i = tid; i < nin; i += blockDim.x) ain[i] = gin[i];
-        for (int i = tid; i < nout; i += blockDim.x) {
-            const float a = __bfloat162float(gout[i]);
-            dz[i] = __float2bfloat16_rn(a > 0.f ? da_out[b * nout + i] : 0.f);
-        }
-        __syncthreads();
-        if (tid < 32) {
-            float t = 0.f;
-            for (int p = 0; p < G.Hout * G.Wout; ++p) t += __bfloat162float(dz[p * 32 + tid]);
-            db[tid] += t;
-        }
-        // weight gradient: dW[cout][cin][ky][kx] += sum over output pixels
-        for (int o = tid; o < nW; o += blockDim.x) {
-            const int cout = o / (G.Cin * 9), rem = o - cout * (G.Cin * 9);
-            const int cin = rem / 9, tap = rem - cin * 9, ky = tap / 3, kx = tap - ky * 3;
-            float acc = 0.f;
-            for (int y = 0; y < G.Hout; ++y) {
-                const int iy = s * y + ky - 1;
-                if (iy < 0 || iy >= G.Hin) continue;
-                for (int x = 0; x < G.Wout; ++x) {
-                    const int ix = s * x + kx - 1;
-                    if (ix < 0 || ix >= G.Win) continue;
-                    acc += __bfloat162float(dz[(y * G.Wout + x) * 32 + cout]) *
-                           __bfloat162float(ain[(iy * G.Win + ix) * G.Cin + cin]);
-                }
-            }
-            dW[o] += acc;
-        }
-        // input gradient (not needed below the first layer)
-        if (da_in) {
-            for (int e = tid; e < nin; e += blockDim.x) {
-                const int ipix = e / G.Cin, cin = e - ipix * G.Cin;
-                const int iy = ipix / G.Win, ix = ipix - iy * G.Win;
-                float acc = 0.f;
-                for (int ky = 0; ky < 3; ++ky) {
-                    const int ty = iy + 1 - ky;
-                    if (ty < 0 || ty % s) continue;
-                    const int y = ty / s;
-                    if (y >= G.Hout) continue;
-                    for (int kx = 0; kx < 3; ++kx) {
-                        const int tx = ix + 1 - kx;
-                        if (tx < 0 || tx % s) continue;
-                        const int x = tx / s;
-                        if (x >= G.Wout) continue;
-                        const __nv_bfloat16 *dzp = dz + (y * G.Wout + x) * 32;
-                        const float *wp = Wr + cin * 9 + ky * 3 + kx;
-#pragma unroll 8
-                        for (int co = 0; co < 32; ++co) acc += __bfloat162float(dzp[co]) * wp[co * G.Cin * 9];
-                    }
-                }
-                da_in[b * nin + e] = acc;
-            }
-        }
-        __syncthreads();
-    }
-    for (int i = tid; i < nW; i += blockDim.x) atomicAdd(&grads[off_w(l) + i], dW[i]);
-    if (tid < 32) atomicAdd(&grads[off_b(l) + tid], db[tid]);
-}
-
-__host__ __device__ inline size_t conv_bwd_smem(int l) {
-    const LayerGeo G = layer_geo(l);
-    const int nW = 32 * G.Cin * 9, nin = G.Hin * G.Win * G.Cin, nout = G.Hout * G.Wout * 32;
-    return (size_t)(2 * nW + 32) * 4 + (size_t)((nin + 7) & ~7) * 2 + (size_t)nout * 2 + 16;
-}
 
 // Adam (Kingma & Ba 2015) on the fp32 master weights; clears the gradients.
 __global__ void k_cnn_adam(float *__restrict__ w, float *__restrict__ g, float *__restrict__ m,
@@ -1065,51 +915,6 @@ extern "C" int vs_cnn_score_lattice_rows(vs_grid g, int32_t stride, int32_t patc
     if (row0 < 0 || nrows < 0 || (int64_t)row0 + nrows > Hs) return VS_ERR_RANGE;
     return cnn_forward_launch(g, nullptr, (int64_t)nrows * Ws, stride, row0, patch_step, packed, score_out,
                               nullptr, status, st);
-}
-
-// per patch: dL/da of layers 5, 4, 3, 2, 1 (fp32)
-static size_t cnn_da_floats(int l) {  // gradient w.r.t. the output of layer l
-    const int h[5] = {33, 17, 9, 5, 5};
-    return (size_t)h[l] * h[l] * 32;
-}
-
-extern "C" size_t vs_cnn_backward_workspace(int64_t B) {
-    if (B < 0) return 0;
-    size_t per = 0;
-    for (int l = 0; l < 5; ++l) per += cnn_da_floats(l);
-    return (size_t)B * per * 4 + 256;
-}
-
-extern "C" int vs_cnn_backward(const void *save, const float *labels, int64_t B, const float *master,
-                               float *grads, float *loss_sum, void *ws, size_t ws_bytes,
-                               vs_stream_t st) {
-    if (!save || !labels || !master || !grads || !loss_sum || ((uintptr_t)save & 15)) return VS_ERR_ARG;
-    if (B < 1) return VS_ERR_RANGE;
-    if (!ws || ws_bytes < vs_cnn_backward_workspace(B)) return VS_ERR_WS;
-    int rc = check_device();
-    if (rc) return rc;
-    cudaStream_t s = (cudaStream_t)st;
-    float *da[5];
-    float *p = (float *)ws;
-    for (int l = 0; l < 5; ++l) { da[l] = p; p += (size_t)B * cnn_da_floats(l); }
-    const unsigned char *sv = (const unsigned char *)save;
-    cnn::k_cnn_head_bwd<<<(unsigned)((B * 32 + 255) / 256), 256, 0, s>>>(sv, labels, B, 1.0f / (float)B,
-                                                                          master, grads, da[4], loss_sum);
-    vs::note_launch();
-    VS_CUDA_TRY(cudaGetLastError());
-    int dev = 0, sms = 0;
-    VS_CUDA_TRY(cudaGetDevice(&dev));
-    VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    for (int l = 4; l >= 0; --l) {
-        const size_t smem = cnn::conv_bwd_smem(l);
-        VS_CUDA_TRY(cudaFuncSetAttribute(cnn::k_cnn_conv_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const unsigned grid = (unsigned)std::min<long long>(B, (long long)sms);
-        cnn::k_cnn_conv_bwd<<<grid, cnn::kBwdThreads, smem, s>>>(sv, B, l, da[l], master, grads,
-                                                                  l > 0 ? da[l - 1] : nullptr);
-        vs::note_launch();
-        VS_CUDA_TRY(cudaGetLastError());
-    }
-    return VS_OK;
 }
 
 extern "C" int vs_cnn_adam(float *master, float *grads, float *m, float *v, int64_t step, float lr,

@@ -207,16 +207,22 @@ def test_cnn_strided_patches(V, step):
         V.cnn_forward(g, cen, packed, patch_step=0)
 
 
-def test_cnn_backward_matches_oracle(V):
-    """Gradients of the batch L1 loss, per parameter tensor, against the
-    oracle's fp64 backward on the same bf16-rounded operands."""
+@pytest.mark.parametrize("B,seed", [(12, 4), (37, 5)])
+def test_cnn_backward_matches_oracle(V, B, seed):
+    """Gradients of the batch L1 loss, element by element, against the
+    oracle's fp64 backward on the same bf16-rounded operands: every element
+    within 1e-2 of its value plus 2^-6 of the sum of the absolute values of
+    the terms it adds up -- room for pre-activation gradients whose bf16
+    rounding goes the other way after FP32 accumulation (one bf16 step,
+    2^-8, per term and layer), not for a wrong tap, channel or patch."""
     from oracle import cnn_oracle as C
     H, W = 200, 210
     z = T.spectral_fbm(H, W, 0.8, 91, 0, 1200).numpy()
     g = V.Grid.from_tensor(torch.as_tensor(z), "cuda")
     p = _params(11)
-    rng = np.random.default_rng(4)
-    pts = [(int(a), int(b)) for a, b in zip(rng.integers(0, H, 12), rng.integers(0, W, 12))]
+    rng = np.random.default_rng(seed)
+    pts = [(int(a), int(b)) for a, b in zip(rng.integers(0, H, B), rng.integers(0, W, B))]
+    pts[:3] = [(0, 0), (H - 1, W - 1), (100, 0)]
     labels = rng.random(len(pts)).astype(np.float32)
     master = torch.as_tensor(C.flatten_params(p)).cuda()
     packed = V.cnn_pack(master)
@@ -228,12 +234,13 @@ def test_cnn_backward_matches_oracle(V):
     V.cnn_backward(save, torch.as_tensor(labels).cuda(), master, grads, loss)
     gg = C.unflatten_params(grads.cpu().numpy())
     x0 = np.stack([C.normalize_patch(C.extract_patch(z, cy, cx)) for cy, cx in pts])
-    want_loss, want = C.loss_and_grads(p, x0, labels.astype(np.float64))
+    want_loss, want, scale = C.loss_and_grads(p, x0, labels.astype(np.float64), scale=True)
     assert abs(loss.item() / len(pts) - want_loss) < 5e-3
     for k in want:
-        a, b = gg[k].ravel(), want[k].ravel()
-        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
-        assert rel < 3e-2, (k, rel)
+        a, b, sc = gg[k].ravel(), want[k].ravel(), scale[k].ravel()
+        bad = np.abs(a - b) > 1e-2 * np.abs(b) + 2.0 ** -6 * sc
+        assert not bad.any(), (k, int(bad.sum()), np.flatnonzero(bad)[:5].tolist(),
+                               a[bad][:5].tolist(), b[bad][:5].tolist())
 
 
 def test_cnn_adam_step(V):
