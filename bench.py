@@ -875,14 +875,14 @@ def main():
     ap.add_argument("--patch-step", type=int, default=3,
                     help="post spacing inside the CNN's 65x65 input patch")
     ap.add_argument("--train-posts", type=int, default=None,
-                    help="training posts (default 500000; 4000000 for --workload learn)")
-    ap.add_argument("--epochs", type=int, default=None, help="default 3; 6 for --workload learn")
+                    help="training posts (default 4000000; 500000 for the paper-regime proposal)")
+    ap.add_argument("--epochs", type=int, default=None, help="default 6; 3 for the paper-regime proposal")
     args = ap.parse_args()
-    learn = args.workload == "learn"
+    paper = args.workload.startswith("paper")
     if args.train_posts is None:
-        args.train_posts = 4000000 if learn else 500000
+        args.train_posts = 500000 if paper else 4000000
     if args.epochs is None:
-        args.epochs = 6 if learn else 3
+        args.epochs = 3 if paper else 6
     dist, rank, world, local = dist_init()
     if args.workload == "batch":
         run_batch(args, dist, rank, world, local)
