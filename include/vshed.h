@@ -102,14 +102,20 @@ uint64_t vs_launch_count(void);
  *     (the candidates taken in key order while each lies more than 2R from
  *     every other winner of the round; same results as one step at a time):
  *     0 = default (on whenever the leader cluster runs and the gains fit),
- *     1 = off (one step per round). */
+ *     1 = off (one step per round).
+ *   VS_TUNE_SITE_BARRIER_TEST: a test of the failure path, not a launch
+ *     shape: v > 0 (up to 2^20) makes one CTA of the whole-GPU lazy greedy
+ *     skip its arrival at the first grid barrier and every barrier wait give
+ *     up after v polls, so that the call reports VS_ERR_TIMEOUT in *n_chosen
+ *     (the GPU and the next call are unaffected); 0 = off. */
 enum {
     VS_TUNE_VIEWSHED_THREADS = 0,
     VS_TUNE_VIX_TILE = 1,
     VS_TUNE_SITE_CLUSTER = 2,
     VS_TUNE_VIEWSHED_WIDE = 3,
     VS_TUNE_SITE_LAZY = 4,
-    VS_TUNE_SITE_MULTI = 5
+    VS_TUNE_SITE_MULTI = 5,
+    VS_TUNE_SITE_BARRIER_TEST = 6
 };
 int vs_tune_set(int32_t op, int32_t R, int32_t value);
 int vs_tune_get(int32_t op, int32_t R);

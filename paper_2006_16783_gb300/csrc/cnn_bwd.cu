@@ -64,10 +64,10 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// where D[m][n] goes: mode 0 (weight gradient, rows m = tap * cin + c)
-// atomically adds into out[n * 9 * cin + c * 9 + tap] for m < mvalid (the
-// launch is split over K); mode 1 (data gradient) stores out[m * 32 + n] for
-// m < mvalid.  a_rows: rows of each A tile held in memory and copied (128, or
+// where D[m][n] goes: mode 0 (weight gradient, split over K) stores the
+// split's partial sum at out[(split * mvalid + m) * 32 + n] for m < mvalid
+// (k_wgrad_reduce adds the splits in a fixed order); mode 1 (data gradient)
+// stores out[m * 32 + n] for m < mvalid.  a_rows: rows of each A tile held in memory and copied (128, or
 // 16 for the first layer's 9 taps: the MMA still computes 128 rows, those it
 // reads from whatever the shared buffer holds only reach discarded outputs).
 struct GemmArgs {
@@ -174,19 +174,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const GemmArgs G) {
               "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
             : "r"(ta), "r"(ta + 16u)
             : "memory");
-        if (ok && !s_fail && nc > 0 && m < G.mvalid) {
-            if (G.mode == 0) {
-                const int tap = (int)m / G.cin, c = (int)m - tap * G.cin;
-                float *o = G.out + c * 9 + tap;
+        if (nc > 0 && m < G.mvalid) {
+            // a wait that gave up leaves NaN in the outputs, so that the
+            // failure shows in the gradients instead of passing silently
+            const bool good = ok && !s_fail;
+            const long long row = G.mode == 0 ? (long long)ks * G.mvalid + m : m;
+            float4 *o = (float4 *)(G.out + row * 32);
 #pragma unroll
-                for (int n = 0; n < 32; ++n) atomicAdd(o + n * 9 * G.cin, __uint_as_float(v[n]));
-            } else {
-                float4 *o = (float4 *)(G.out + m * 32);
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    o[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                                       __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
-            }
+            for (int q = 0; q < 8; ++q)
+                o[q] = good ? make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                          __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]))
+                            : make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
+                                          __int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
         }
         if ((!ok || s_fail) && G.status && tid == 0) atomicExch(G.status, VS_ERR_TIMEOUT);
     }
@@ -202,11 +201,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const GemmArgs G) {
 }
 
 // ------------------------------------------------------------------ head
-// dL/dlogit = sign(y - label) * y (1 - y) / B (L1 loss through the sigmoid);
-// fc gradients; dL/da5 = dL/dg / 25 on every pooled pixel.  One warp per patch.
+// dL/dlogit = sign(y - label) * y (1 - y) / B (L1 loss through the sigmoid)
+// and |y - label| per patch into hd2[b] (k_head_reduce sums them, and the fc
+// gradients, in patch order); dL/da5 = dL/dg / 25 on every pooled pixel.
+// One warp per patch.
 __global__ void k_head_bwd(const unsigned char *__restrict__ save, const float *__restrict__ labels,
                            long long B, float inv_batch, const float *__restrict__ master,
-                           float *__restrict__ grads, float *__restrict__ da5, float *__restrict__ loss_sum) {
+                           float2 *__restrict__ hd2, float *__restrict__ da5) {
     const long long b = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int c = threadIdx.x & 31;
     if (b >= B) return;
@@ -214,13 +215,42 @@ __global__ void k_head_bwd(const unsigned char *__restrict__ save, const float *
     const float y = hd[33], lab = labels[b];
     const float sgn = (y > lab) ? 1.f : ((y < lab) ? -1.f : 0.f);
     const float dlogit = sgn * y * (1.f - y) * inv_batch;
-    atomicAdd(&grads[kOffFw + c], dlogit * hd[c]);
-    if (c == 0) {
-        atomicAdd(&grads[kOffFw + 32], dlogit);
-        atomicAdd(loss_sum, fabsf(y - lab));
-    }
+    if (c == 0) hd2[b] = make_float2(dlogit, fabsf(y - lab));
     const float d = dlogit * master[kOffFw + c] * (1.0f / 25.0f);
     for (int pix = 0; pix < 25; ++pix) da5[(b * 25 + pix) * 32 + c] = d;
+}
+
+// fc gradients (sum over patches of dlogit * pooled features, and of dlogit)
+// and the loss sum, each added in patch order by one thread
+__global__ void k_head_reduce(const unsigned char *__restrict__ save, const float2 *__restrict__ hd2, long long B,
+                              float *__restrict__ grads, float *__restrict__ loss_sum) {
+    const int c = threadIdx.x;
+    float acc = 0.f;
+    for (long long b = 0; b < B; ++b) {
+        const float2 h = hd2[b];
+        if (c < 32) acc += h.x * ((const float *)(save + b * (long long)kSaveBytesTotal + kSvHead))[c];
+        else if (c == 32) acc += h.x;
+        else acc += h.y;
+    }
+    if (c < 33) grads[kOffFw + c] += acc;
+    else if (c == 33) *loss_sum += acc;
+}
+
+// out[map(i)] += sum over r < nrows of part[r * n + i], in row order:
+// mode 0, the weight gradient of a layer (i = m * 32 + n, m = tap * cin + c
+// -> w[n][c][tap]); mode 1, the bias (i = channel)
+__global__ void k_ordered_sum(const float *__restrict__ part, int nrows, int n, int mode, int cin,
+                              float *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float acc = 0.f;
+    for (int r = 0; r < nrows; ++r) acc += part[(long long)r * n + i];
+    if (mode == 0) {
+        const int m = i >> 5, nn = i & 31, tap = m / cin, c = m - tap * cin;
+        out[(nn * cin + c) * 9 + tap] += acc;
+    } else {
+        out[i] += acc;
+    }
 }
 
 // ------------------------------------------------------------------ dz
@@ -234,13 +264,11 @@ __global__ void __launch_bounds__(kDzThreads) k_bwd_dz(const unsigned char *__re
                                                        int l, const float *__restrict__ da,
                                                        __nv_bfloat16 *__restrict__ dz_plain,
                                                        unsigned char *__restrict__ dzT, long long kpad,
-                                                       float *__restrict__ grads) {
-    __shared__ float s_db[32];
+                                                       float *__restrict__ bias_part) {
+    __shared__ float s_acc[kDzThreads][9];
     const LayerGeo G = layer_geo(l);
     const int P = G.Hout * G.Wout;
     const long long K = B * P;
-    if (threadIdx.x < 32) s_db[threadIdx.x] = 0.f;
-    __syncthreads();
     float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int j = threadIdx.x & 3;
     for (long long k = ((long long)blockIdx.x * kDzThreads + threadIdx.x) >> 2; k < kpad;
@@ -270,10 +298,16 @@ __global__ void __launch_bounds__(kDzThreads) k_bwd_dz(const unsigned char *__re
             for (int i = 0; i < 8; ++i) *(__nv_bfloat16 *)(tile + tile_off(8 * j + i, (int)(k & 63))) = d8[i];
         }
     }
+    // the block's partial bias gradient, summed over its threads in a fixed order
 #pragma unroll
-    for (int i = 0; i < 8; ++i) atomicAdd(&s_db[8 * j + i], acc[i]);
+    for (int i = 0; i < 8; ++i) s_acc[threadIdx.x][i] = acc[i];
     __syncthreads();
-    if (threadIdx.x < 32) atomicAdd(&grads[off_b(l) + threadIdx.x], s_db[threadIdx.x]);
+    if (threadIdx.x < 32) {
+        const int jj = threadIdx.x >> 3, ii = threadIdx.x & 7;
+        float t = 0.f;
+        for (int q = jj; q < kDzThreads; q += 4) t += s_acc[q][ii];
+        bias_part[blockIdx.x * 32 + threadIdx.x] = t;
+    }
 }
 
 // ------------------------------------------------------------------ im2col^T of a layer's input
@@ -381,8 +415,12 @@ using namespace vs;
 
 namespace {
 
+constexpr int kDzGrid = 1024;     // blocks of k_bwd_dz (rows of its bias partials)
+constexpr int kMaxKSplit = 256;   // splits of a weight-gradient GEMM
+
 struct BwdLayout {
     long long B;
+    size_t off_hd2, off_bpart, off_wpart;
     long long kc[5];       // weight-gradient K chunks of 64 per layer (l >= 1)
     long long mt_col[5];   // data-gradient row tiles of 128 per layer (l >= 1)
     size_t off_da[5], off_dz[5], off_dzT[5], off_wT, off_scratch, total;
@@ -405,6 +443,12 @@ BwdLayout bwd_layout(long long B) {
     }
     L.off_wT = o;
     o += al256((size_t)4 * 5 * cnnb::kTileB);
+    L.off_hd2 = o;
+    o += al256((size_t)B * 8);
+    L.off_bpart = o;
+    o += al256((size_t)kDzGrid * 32 * 4);
+    L.off_wpart = o;
+    o += al256((size_t)kMaxKSplit * 288 * 32 * 4);
     // the A operands of one layer at a time: im2col^T (3 row tiles) and the
     // transposed convolution's im2col (5 K chunks per row tile)
     size_t scratch = al256((size_t)L.kc[0] * 16 * 128);  // the first layer: 16-row A tiles
@@ -453,19 +497,27 @@ extern "C" int vs_cnn_backward(const void *save, const float *labels, int64_t B,
     auto dz = [&](int l) { return (__nv_bfloat16 *)(w + L.off_dz[l]); };
     unsigned char *wT = w + L.off_wT;
     // head: loss, fc gradients, dL/da5
-    cnnb::k_head_bwd<<<(unsigned)((B * 32 + 255) / 256), 256, 0, s>>>(sv, labels, B, 1.0f / (float)B, master,
-                                                                       grads, da(4), loss_sum);
+    float2 *hd2 = (float2 *)(w + L.off_hd2);
+    float *bpart = (float *)(w + L.off_bpart), *wpart = (float *)(w + L.off_wpart);
+    cnnb::k_head_bwd<<<(unsigned)((B * 32 + 255) / 256), 256, 0, s>>>(sv, labels, B, 1.0f / (float)B, master, hd2,
+                                                                       da(4));
+    vs::note_launch();
+    VS_CUDA_TRY(cudaGetLastError());
+    cnnb::k_head_reduce<<<1, 34, 0, s>>>(sv, hd2, B, grads, loss_sum);
     vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     cnnb::k_bwd_wT<<<(4 * 32 * 320 + 255) / 256, 256, 0, s>>>(master, wT);
     vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
-    const unsigned grid_el = (unsigned)(4 * sms);
+    const unsigned grid_el = (unsigned)std::min(4 * sms, kDzGrid);
     for (int l = 4; l >= 0; --l) {
         const cnn::LayerGeo G = cnn::layer_geo(l);
         const int a_rows = l == 0 ? 16 : 128, mtiles = l == 0 ? 1 : 3;
         cnnb::k_bwd_dz<<<grid_el, cnnb::kDzThreads, 0, s>>>(sv, B, l, da(l), l >= 1 ? dz(l) : nullptr,
-                                                             w + L.off_dzT[l], L.kc[l] * 64, grads);
+                                                             w + L.off_dzT[l], L.kc[l] * 64, bpart);
+        vs::note_launch();
+        VS_CUDA_TRY(cudaGetLastError());
+        cnnb::k_ordered_sum<<<1, 32, 0, s>>>(bpart, (int)grid_el, 32, 1, 1, grads + cnn::off_b(l));
         vs::note_launch();
         VS_CUDA_TRY(cudaGetLastError());
         unsigned char *acolT = w + L.off_scratch;
@@ -478,14 +530,19 @@ extern "C" int vs_cnn_backward(const void *save, const float *labels, int64_t B,
         gw.B = w + L.off_dzT[l];
         gw.mtiles = mtiles;
         gw.kchunks = (int)L.kc[l];
-        gw.ksplit = (int)std::max<long long>(1, std::min<long long>(L.kc[l], (2LL * sms + mtiles - 1) / mtiles));
+        gw.ksplit = (int)std::max<long long>(
+            1, std::min<long long>(std::min<long long>(L.kc[l], kMaxKSplit), (2LL * sms + mtiles - 1) / mtiles));
         gw.a_rows = a_rows;
-        gw.out = grads + cnn::off_w(l);
+        gw.out = wpart;
         gw.mvalid = 9 * G.Cin;
         gw.cin = G.Cin;
         gw.mode = 0;
         gw.status = nullptr;
         if ((rc = launch_gemm(gw, sms, s))) return rc;
+        const int nw = 9 * G.Cin * 32;
+        cnnb::k_ordered_sum<<<(nw + 255) / 256, 256, 0, s>>>(wpart, gw.ksplit, nw, 0, G.Cin, grads + cnn::off_w(l));
+        vs::note_launch();
+        VS_CUDA_TRY(cudaGetLastError());
         if (l == 0) break;
         // data gradient of the layer's input: D[(patch, input pixel)][cin], K = (tap, cout)
         unsigned char *dzcol = acolT + al256((size_t)3 * L.kc[l] * cnnb::kTileA);

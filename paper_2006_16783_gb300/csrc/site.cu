@@ -1542,6 +1542,11 @@ struct LazyParams {
     const uint8_t *weight;   // receiver weights H x W (pitch W), or null = 1 each
     const unsigned long long *wsum;  // [2]: total weight, weight already covered
     double target;           // weighted coverage stop (<= 0: off)
+    // failure-path test (VS_TUNE_SITE_BARRIER_TEST): CTA 1 skips its arrival at
+    // the first grid barrier, and every barrier wait gives up after bar_polls
+    // polls (0 = the library's default limit)
+    int bar_skip;
+    unsigned bar_polls;
 };
 
 __global__ void k_lazy_count(const int64_t *__restrict__ cand, int n, int H, int W, int cs, int ncx,
@@ -1836,21 +1841,23 @@ struct LazyCtl {
 static_assert(sizeof(LazyCtl) <= 256, "control block fits its workspace slot");
 
 // grid barrier (all CTAs of a cooperative launch); false when a wait gave up
-__device__ __forceinline__ bool lazy_grid_sync(LazyCtl *ctl, unsigned &gen) {
+__device__ __forceinline__ bool lazy_grid_sync(LazyCtl *ctl, unsigned &gen, int skip = 0, unsigned polls = 0) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         __threadfence();
         const unsigned g0 = gen;
-        if (atomicAdd(&ctl->bar_count, 1u) == gridDim.x - 1) {
+        const uint32_t limit = polls ? polls : kWaitPolls;
+        const bool arrive = !(skip && blockIdx.x == 1 && g0 == 0);
+        if (arrive && atomicAdd(&ctl->bar_count, 1u) == gridDim.x - 1) {
             atomicExch(&ctl->bar_count, 0u);
             __threadfence();
             atomicAdd(&ctl->bar_gen, 1u);
         } else {
             uint32_t i = 0;
             while (*(volatile unsigned *)&ctl->bar_gen == g0) {
-                if (++i > kWaitPolls || *(volatile int *)&ctl->err) {
+                if (++i > limit || *(volatile int *)&ctl->err) {
                     ok = 0;
                     break;
                 }
@@ -1947,13 +1954,13 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_lazy_grid(const LazyPa
                 k = u64max(k, lazy_key(__ldcg(P.g + c), P.cand[c]));
         k = block_max_u64(k, s_red);
         if (tid == 0 && k) atomicMax(&ctl->F[par], k);
-        if (!(ok = lazy_grid_sync(ctl, gen))) break;
+        if (!(ok = lazy_grid_sync(ctl, gen, P.bar_skip, P.bar_polls))) break;
         const unsigned long long F = *(volatile unsigned long long *)&ctl->F[par];
         // B: stale bounds that may beat F
         for (int c = lo + tid; c < hi; c += blockDim.x)
             if ((free_pick || __ldcg(P.elig + c)) && !__ldcg(P.fresh + c) && lazy_key(__ldcg(P.g + c), P.cand[c]) >= F)
                 work[atomicAdd(&ctl->nwork[par], 1u)] = (uint32_t)c;
-        if (!(ok = lazy_grid_sync(ctl, gen))) break;
+        if (!(ok = lazy_grid_sync(ctl, gen, P.bar_skip, P.bar_polls))) break;
         const unsigned m = *(volatile unsigned *)&ctl->nwork[par];
         // C: evaluate them, one window per CTA at a time
         for (;;) {
@@ -1970,19 +1977,19 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_lazy_grid(const LazyPa
             const unsigned gnew = valid ? lazy_block_sum(lazy_window<OPT>(P, c, pc, false), s_u) : 0u;
             if (tid == 0) { P.g[c] = gnew; P.fresh[c] = 1; }
         }
-        if (!(ok = lazy_grid_sync(ctl, gen))) break;
+        if (!(ok = lazy_grid_sync(ctl, gen, P.bar_skip, P.bar_polls))) break;
         // D: the largest key, then the lowest index holding it
         k = 0;
         for (int c = lo + tid; c < hi; c += blockDim.x)
             if (free_pick || __ldcg(P.elig + c)) k = u64max(k, lazy_key(__ldcg(P.g + c), P.cand[c]));
         k = block_max_u64(k, s_red);
         if (tid == 0 && k) atomicMax(&ctl->best[par], k);
-        if (!(ok = lazy_grid_sync(ctl, gen))) break;
+        if (!(ok = lazy_grid_sync(ctl, gen, P.bar_skip, P.bar_polls))) break;
         const unsigned long long best = *(volatile unsigned long long *)&ctl->best[par];
         if ((best >> 32) == 0) break;  // best gain 0 (or no eligible candidate): nothing left to cover
         for (int c = lo + tid; c < hi; c += blockDim.x)
             if ((free_pick || __ldcg(P.elig + c)) && lazy_key(__ldcg(P.g + c), P.cand[c]) == best) atomicMax(&ctl->widx[par], 0xFFFFFFFFu - (unsigned)c);
-        if (!(ok = lazy_grid_sync(ctl, gen))) break;
+        if (!(ok = lazy_grid_sync(ctl, gen, P.bar_skip, P.bar_polls))) break;
         const int w = (int)(0xFFFFFFFFu - *(volatile unsigned *)&ctl->widx[par]);
         const int64_t pw = P.cand[w];
         const uint32_t gw = (uint32_t)(best >> 32);
@@ -2015,7 +2022,7 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_lazy_grid(const LazyPa
             ctl->F[q] = 0; ctl->best[q] = 0; ctl->widx[q] = 0; ctl->nwork[q] = 0; ctl->next[q] = 0;
         }
         covered += gw;
-        if (!(ok = lazy_grid_sync(ctl, gen))) break;
+        if (!(ok = lazy_grid_sync(ctl, gen, P.bar_skip, P.bar_polls))) break;
     }
     if (b == 0 && tid == 0) *P.n_chosen = ok ? t : VS_ERR_TIMEOUT;
 }
@@ -2129,6 +2136,11 @@ static int site_lazy(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
     L.weight = opt ? opt->weight : nullptr;
     L.wsum = opt ? opt->wsum : nullptr;
     L.target = opt ? opt->target : 0.0;
+    {
+        const int bt = tune_get(VS_TUNE_SITE_BARRIER_TEST, R, 0);
+        L.bar_skip = bt > 0 ? 1 : 0;
+        L.bar_polls = bt > 0 ? (unsigned)bt : 0u;
+    }
     if (opt || tune_get(VS_TUNE_SITE_LAZY, R, 0) != 2) {
         // the whole GPU: one CTA per SM in one cooperative launch
         int dev = 0, sms = 0, per = 0, coop = 0;

@@ -42,8 +42,8 @@ int make_grid_map(GridMap *gm, const vs_grid &g, int wg, int rows) {
     return r == CUDA_SUCCESS ? VS_OK : VS_ERR_CUDA;
 }
 
-// (op, R) -> value; R <= kMaxR, ops 0..5
-constexpr int kTuneOps = 6;
+// (op, R) -> value; R <= kMaxR, ops 0..6
+constexpr int kTuneOps = 7;
 static int g_tune[kTuneOps][kMaxR + 1];
 static std::mutex g_tune_mu;
 
@@ -113,6 +113,7 @@ int vs_tune_set(int32_t op, int32_t R, int32_t value) {
     if (op == VS_TUNE_VIEWSHED_WIDE && value != 0 && value != 1) return VS_ERR_RANGE;
     if (op == VS_TUNE_SITE_LAZY && (value < 0 || value > 2)) return VS_ERR_RANGE;
     if (op == VS_TUNE_SITE_MULTI && value != 0 && value != 1) return VS_ERR_RANGE;
+    if (op == VS_TUNE_SITE_BARRIER_TEST && (value < 0 || value > (1 << 20))) return VS_ERR_RANGE;
     std::lock_guard<std::mutex> lk(vs::g_tune_mu);
     vs::g_tune[op][R] = value;
     return VS_OK;

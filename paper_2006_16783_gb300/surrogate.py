@@ -70,6 +70,7 @@ class Trainer:
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.ws = None
         self.step = 0
+        self.epochs_done = 0
 
     def train_step(self, g, posts, labels):
         B = posts.numel()
@@ -82,13 +83,17 @@ class Trainer:
         V.cnn_adam(self.master, self.grads, self.m, self.v, self.step, lr=lr)
         V.cnn_pack(self.master, self.packed)
 
-    def fit(self, data, epochs, seed=0, lr_decay=0.5, log=None):
-        """data: list of (grid, posts, labels).  Returns the mean training
-        loss of the last epoch."""
-        gen = torch.Generator(device="cpu").manual_seed(seed)
+    def fit(self, data, epochs, seed=0, lr_decay=0.5, log=None, first_epoch=0):
+        """data: list of (grid, posts, labels).  Epochs first_epoch .. epochs-1
+        run with learning rate lr * lr_decay^epoch, each on a shuffle drawn
+        from its own seed (seed, epoch), so that training resumed at an
+        epoch boundary from a checkpoint (checkpoint / from_checkpoint) continues
+        exactly as an uninterrupted run.  Returns the mean training loss of
+        the last epoch."""
         last = None
         base_lr = self.lr
-        for ep in range(epochs):
+        for ep in range(first_epoch, epochs):
+            gen = torch.Generator(device="cpu").manual_seed(seed * 1000003 + ep)
             self.lr = base_lr * (lr_decay ** ep)
             self.loss.zero_()
             seen = 0
@@ -106,10 +111,36 @@ class Trainer:
                 self.train_step(g, posts[idx].contiguous(), labels[idx].contiguous())
                 seen += idx.numel()
             last = float(self.loss.item()) / max(seen, 1)
+            self.epochs_done = ep + 1
             if log:
                 log("epoch %d: mean |y - label| = %.4f (%.1f s)" % (ep, last, time.time() - t0))
         self.lr = base_lr
         return last
+
+    def checkpoint(self):
+        """Checkpoint of the training state (host copies): fp32 master
+        weights, Adam moments, Adam step, learning rate, batch size, patch
+        step and the number of epochs done."""
+        return {"master": self.master.cpu().clone(), "m": self.m.cpu().clone(), "v": self.v.cpu().clone(),
+                "step": self.step, "lr": self.lr, "batch": self.batch, "patch_step": self.patch_step,
+                "epochs_done": self.epochs_done}
+
+    def save_checkpoint(self, path):
+        torch.save(self.checkpoint(), path)
+
+    @classmethod
+    def from_checkpoint(cls, st, device="cuda"):
+        """A trainer that continues from a checkpoint made by checkpoint()."""
+        tr = cls(st["master"].to(device).clone(), batch=st["batch"], lr=st["lr"], patch_step=st["patch_step"])
+        tr.m.copy_(st["m"].to(device))
+        tr.v.copy_(st["v"].to(device))
+        tr.step = int(st["step"])
+        tr.epochs_done = int(st["epochs_done"])
+        return tr
+
+    @classmethod
+    def load_checkpoint(cls, path, device="cuda"):
+        return cls.from_checkpoint(torch.load(path, map_location="cpu"), device)
 
     def predict(self, g, posts, chunk=1 << 20):
         out = torch.empty(posts.numel(), dtype=torch.float32, device=posts.device)

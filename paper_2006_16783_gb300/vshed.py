@@ -47,7 +47,7 @@ class vs_site_options(ctypes.Structure):
 
 
 (VS_TUNE_VIEWSHED_THREADS, VS_TUNE_VIX_TILE, VS_TUNE_SITE_CLUSTER, VS_TUNE_VIEWSHED_WIDE,
- VS_TUNE_SITE_LAZY, VS_TUNE_SITE_MULTI) = 0, 1, 2, 3, 4, 5
+ VS_TUNE_SITE_LAZY, VS_TUNE_SITE_MULTI, VS_TUNE_SITE_BARRIER_TEST) = 0, 1, 2, 3, 4, 5, 6
 
 # name -> (restype, argtypes); the exported symbols of include/vshed.h
 P, i32, i64, u64, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,

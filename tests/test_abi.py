@@ -114,7 +114,8 @@ def test_large_roi_size_queries(L):
     assert L.vs_tune_set(vshed.VS_TUNE_SITE_LAZY, 50, 3) == vshed.VS_ERR_RANGE
     assert L.vs_tune_set(vshed.VS_TUNE_VIX_TILE, 50, 4) == vshed.VS_ERR_RANGE
     assert L.vs_tune_set(vshed.VS_TUNE_SITE_MULTI, 50, 2) == vshed.VS_ERR_RANGE
-    assert L.vs_tune_set(6, 50, 0) == vshed.VS_ERR_RANGE
+    assert L.vs_tune_set(vshed.VS_TUNE_SITE_BARRIER_TEST, 50, (1 << 20) + 1) == vshed.VS_ERR_RANGE
+    assert L.vs_tune_set(7, 50, 0) == vshed.VS_ERR_RANGE
 
 
 def test_large_roi_argument_errors_need_no_device(L):

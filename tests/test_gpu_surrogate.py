@@ -59,11 +59,60 @@ def test_training_reduces_loss_and_beats_sampling(V):
     gt = V.Grid(zt.contiguous())
     pt = S.sample_posts(H, W, 20000, 32, 9, "cuda")
     lt = S.exact_vix(gt, pt, R, 10, 10)
-    tr = S.Trainer(S.init_master(0), batch=256, lr=2e-3)
+    # patch step 2: the 65 x 65 input spans +-64 posts, the whole R = 50 ROI
+    tr = S.Trainer(S.init_master(0), batch=256, lr=2e-3, patch_step=2)
     base = float((tr.predict(gt, pt) - lt).abs().mean())
-    tr.fit(data, epochs=3, seed=1)
+    tr.fit(data, epochs=6, seed=1)
     mae = float((tr.predict(gt, pt) - lt).abs().mean())
     sampled = float((S.sampled_vix_fraction(gt, pt, R, 10, 10, 10, 77) - lt).abs().mean())
     print("held-out MAE: untrained %.4f, trained %.4f, sampled vix (S=10) %.4f" % (base, mae, sampled))
     assert mae < 0.7 * base
     assert mae < sampled
+
+
+def test_backward_is_deterministic(V):
+    """No floating-point atomics in the backward: the same batch gives
+    bit-identical gradients and loss on every call."""
+    from paper_2006_16783_gb300 import surrogate as S
+    H = W = 260
+    z = T.spectral_fbm(H, W, 0.8, 8, 0, 900)
+    g = V.Grid.from_tensor(z, "cuda")
+    posts = S.sample_posts(H, W, 300, 0, 2, "cuda")
+    labels = torch.rand(posts.numel(), device="cuda")
+    master = S.init_master(1)
+    packed = V.cnn_pack(master)
+    save = torch.empty(posts.numel() * V.cnn_save_bytes(), dtype=torch.uint8, device="cuda")
+    V.cnn_forward(g, posts, packed, save=save, patch_step=2)
+    outs = []
+    for _ in range(3):
+        gr = torch.zeros_like(master)
+        loss = torch.zeros(1, device="cuda")
+        V.cnn_backward(save, labels, master, gr, loss)
+        outs.append((gr, loss))
+    for gr, loss in outs[1:]:
+        assert torch.equal(gr, outs[0][0]) and torch.equal(loss, outs[0][1])
+
+
+def test_trainer_checkpoint_resume_bit_identical(V, tmp_path):
+    """Three epochs in one run, and one epoch + checkpoint to a file + a new
+    trainer loaded from it + the remaining two: identical weights, Adam
+    moments and step."""
+    from paper_2006_16783_gb300 import surrogate as S
+    H = W = 300
+    z = T.spectral_fbm(H, W, 0.8, 12, 0, 900)
+    g = V.Grid.from_tensor(z, "cuda")
+    posts = S.sample_posts(H, W, 2000, 32, 4, "cuda")
+    labels = S.exact_vix(g, posts, 30, 10, 10)
+    data = [(g, posts, labels)]
+    a = S.Trainer(S.init_master(0), batch=256, lr=2e-3, patch_step=2)
+    a.fit(data, epochs=3, seed=7)
+    b = S.Trainer(S.init_master(0), batch=256, lr=2e-3, patch_step=2)
+    b.fit(data, epochs=1, seed=7)
+    path = str(tmp_path / "trainer.pt")
+    b.save_checkpoint(path)
+    c = S.Trainer.load_checkpoint(path)
+    assert c.epochs_done == 1 and c.step == b.step
+    c.fit(data, epochs=3, seed=7, first_epoch=c.epochs_done)
+    assert c.step == a.step
+    assert torch.equal(c.master, a.master)
+    assert torch.equal(c.m, a.m) and torch.equal(c.v, a.v)
