@@ -173,50 +173,61 @@ class Pipeline:
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(z_host, w, budget_s=20.0, threads=None):
-    """Time the CPU oracle on a bounded sample of the workload and extrapolate
-    linearly to the whole workload.  Returns (seconds, description, threads)."""
+def oracle_sample(z_host, w, cand=None, threads=None):
+    """Time the CPU oracle on a bounded sample of the workload, on all host
+    threads and on one thread.  vix: a tile of posts, extrapolated linearly to
+    the grid; viewshed: every candidate (the pipeline's own when given, else
+    as many seeded interior posts) on all threads, a sample of them on one;
+    site: the oracle's greedy over all those candidates for 1 and for 64
+    steps (its set-up, the initial gains of every candidate, and the first 64
+    steps), the per-step cost extrapolated to n_obs steps.  Returns
+    (seconds on all threads, description, threads, seconds on one thread)."""
     from oracle import oracle as O
     threads = threads or os.cpu_count() or 1
     H, W = w.H, w.W
     rng = np.random.default_rng(12345)
-    # vix: a square tile of posts in the middle of the terrain
+
+    def vix_tile(side, nthr):
+        y0, x0 = (H - side) // 2, (W - side) // 2
+        posts = ((np.arange(y0, y0 + side)[:, None] * W) + np.arange(x0, x0 + side)[None, :]).ravel()
+        ths = [threading.Thread(target=O.vix_posts, args=(z_host, w.R, w.ht, w.hr, w.S, w.vix_seed, c, W))
+               for c in np.array_split(posts, nthr)]
+        t = time.perf_counter()
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        return (time.perf_counter() - t) * (H * W) / len(posts)
+
     side = 512 if H * W > 4e6 else min(H, W)
-    y0, x0 = (H - side) // 2, (W - side) // 2
-    posts = ((np.arange(y0, y0 + side)[:, None] * W) + np.arange(x0, x0 + side)[None, :]).ravel()
-    chunks = np.array_split(posts, threads)
-    t = time.perf_counter()
-    ths = [threading.Thread(target=O.vix_posts, args=(z_host, w.R, w.ht, w.hr, w.S, w.vix_seed, c, W))
-           for c in chunks]
-    for th in ths:
-        th.start()
-    for th in ths:
-        th.join()
-    t_vix = (time.perf_counter() - t) * (H * W) / len(posts)
-    # viewsheds of seeded interior candidates
-    nv = 400
-    cy = rng.integers(w.R, H - w.R, nv)
-    cx = rng.integers(w.R, W - w.R, nv)
-    cand = (cy * W + cx).astype(np.int64)
-    t = time.perf_counter()
-    bm, area = O.viewshed(z_host, w.R, w.ht, w.hr, cand, threads=threads)
+    t_vix = vix_tile(side, threads)
+    t_vix1 = vix_tile(min(side, 128), 1)
     n_full = WL.FULL.n_candidates() if w is WL.FULL else w.n_candidates()
-    t_vs = (time.perf_counter() - t) * n_full / nv
-    # site: heap set-up and per-step cost on the sample, scaled to the workload
+    if cand is None:
+        cand = (rng.integers(w.R, H - w.R, n_full) * W + rng.integers(w.R, W - w.R, n_full)).astype(np.int64)
+    cand = np.asarray(cand, np.int64)
+    t = time.perf_counter()
+    bm, _ = O.viewshed(z_host, w.R, w.ht, w.hr, cand, threads=threads)
+    t_vs = (time.perf_counter() - t) * n_full / len(cand)
+    ns = min(256, len(cand))
+    t = time.perf_counter()
+    O.viewshed(z_host, w.R, w.ht, w.hr, cand[:ns], threads=1)
+    t_vs1 = (time.perf_counter() - t) * n_full / ns
     t = time.perf_counter()
     O.site(bm, cand, H, W, w.R, 1)
     t0 = time.perf_counter() - t
     t = time.perf_counter()
-    ch, gn, C = O.site(bm, cand, H, W, w.R, 64)
+    ch, _, _ = O.site(bm, cand, H, W, w.R, 64)
     t1 = time.perf_counter() - t
     per_step = max(t1 - t0, 0.0) / max(len(ch) - 1, 1)
-    t_site = t0 * n_full / nv + per_step * w.n_obs
-    total = t_vix + t_vs + t_site
-    desc = ("oracle on %d threads: vix of a %dx%d post tile, %d viewsheds, site of those %d candidates "
-            "(1 and 64 steps); extrapolated linearly to %dx%d posts, %d candidates, %d observers "
-            "(vix %.1f s, viewshed %.1f s, site %.1f s)" % (
-                threads, side, side, nv, nv, H, W, n_full, w.n_obs, t_vix, t_vs, t_site))
-    return total, desc, threads
+    t_site = t0 + per_step * (w.n_obs - 1)
+    total, total1 = t_vix + t_vs + t_site, t_vix1 + t_vs1 + t_site
+    desc = ("oracle on %d threads (and on 1): vix of a %dx%d post tile (%dx%d on 1 thread), the %d candidates' "
+            "viewsheds (%d on 1 thread), the greedy over all %d for its first 64 steps; extrapolated linearly to "
+            "%dx%d posts and %d observers (vix %.1f s, viewshed %.1f s, site %.1f s; 1 thread: vix %.1f s, "
+            "viewshed %.1f s)" % (threads, side, side, min(side, 128), min(side, 128), len(cand), ns, len(cand),
+                                  H, W, w.n_obs, t_vix, t_vs, t_site, t_vix1, t_vs1))
+    return total, desc, threads, total1
 
 
 # ------------------------------------------------------------------ learned proposal
@@ -352,30 +363,27 @@ def site_loop_bytes(cand, chosen, W, R, PR):
     return total
 
 
-def recorded_traffic(patches):
-    """dram__bytes_read.sum + dram__bytes_write.sum per launch of each stage's
-    kernel, from the ncu capture summarised in profiles/traffic.json; a figure
-    is used only while the source file it was taken on hashes to the recorded
-    SHA-1 (else null); the CNN's figure only for the lattice it was taken on."""
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "traffic.json")
+def recorded_counters():
+    """Per-unit figures of the headline kernels from the committed ncu capture
+    on the mid workload (profiles/counters_mid_11600sq_R100.json): thread
+    instructions and DRAM bytes per work unit (LOS crossing, ray step,
+    candidate) and the issue-active share.  A kernel's figures are used only
+    while its source file hashes to the recorded SHA-1."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "counters_mid_11600sq_R100.json")
     out = {}
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
         return out
     import hashlib
-    for key, r in rec.get("stages", {}).items():
+    for key, r in rec.get("kernels", {}).items():
         src = os.path.join(os.path.dirname(path), "..", r["source"])
         try:
             sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
         except OSError:
             continue
-        if sha != r["sha1"]:
-            continue
-        if "patches" in r:  # a lattice figure: valid for the same number of patches only
-            out[key] = r["bytes_per_launch"] if patches == r["patches"] else None
-        else:
-            out[key] = r["bytes_per_launch"]
+        if sha == r["sha1"]:
+            out[key] = r
     return out
 
 
@@ -424,10 +432,10 @@ def run_reference(args, w, rank):
     for _ in range(args.warmup):
         oracle_sample(z, w)
     vals = []
-    desc = threads = None
+    desc = threads = v1 = None
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, desc, threads = oracle_sample(z, w)
+        v, desc, threads, v1 = oracle_sample(z, w)
         vals.append(v)
     wall = time.perf_counter() - t0
     value = statistics.median(vals)
@@ -437,7 +445,8 @@ def run_reference(args, w, rank):
            "data": "synthetic", "config": {"workload": w.name, "H": w.H, "W": w.W, "R": w.R,
                                            "ht": w.ht, "hr": w.hr, "S": w.S, "block": w.block,
                                            "k": w.k, "n_obs": w.n_obs},
-           "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc},
+           "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc,
+                            "single_thread_value": v1},
            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -979,7 +988,16 @@ def main():
     gw0 = np.floor_divide(cxh - w.R, 32)
     WWc = (w.W + 31) // 32
     words_in = np.minimum(gw0 + PR - 1, WWc - 1) - np.maximum(gw0, 0) + 1
-    gain_bytes = plain.n * (2 * w.R + 1) * PR * 4 + int((rows_in * words_in).sum()) * 4 + plain.n * 4
+    # algorithmic bytes of the dense pass: every bitmap, the cumulative
+    # viewshed under the union of the candidates' windows (each word read
+    # once), and 8 bytes of key per candidate
+    cover = np.zeros((w.H, WWc), bool)
+    for y_, x_ in zip(cyh, cxh):
+        g0 = (int(x_) - w.R) // 32
+        cover[max(0, int(y_) - w.R):min(w.H, int(y_) + w.R + 1), max(0, g0):min(WWc, g0 + PR)] = True
+    union_words = int(cover.sum())
+    del cover
+    gain_bytes = plain.n * (2 * w.R + 1) * PR * 4 + union_words * 4 + plain.n * 8
 
     # ---- e2e: the headline pipeline through the same C-ABI calls on a terrain
     # copied in from pinned host memory every step, results copied back
@@ -1023,14 +1041,34 @@ def main():
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     issue_peak = sms * 4 * 32 * mhz * 1e6 / 1e9            # G thread-instr / s
+    # vix and viewshed: thread instructions issued per work unit counted by
+    # ncu on the mid workload (the current kernel sources), times this run's
+    # units, over the live stage time, against the issue peak; beside it the
+    # same rate for a minimal instruction sequence (OPS_PER_*)
+    cnt = recorded_counters()
+
+    def issue_roof(key, units, t_ms, min_ops):
+        r = {"bound": "alu", "peak": issue_peak, "unit": "Gop/s", "units": units,
+             "min_inst_per_unit": min_ops,
+             "algorithmic_frac": units * min_ops / (t_ms * 1e-3) / 1e9 / issue_peak}
+        c = cnt.get(key)
+        if c:
+            r["inst_per_unit"] = c["thread_inst_per_unit"]
+            r["achieved"] = units * c["thread_inst_per_unit"] / (t_ms * 1e-3) / 1e9
+            r["issue_active_mid_pct"] = c["issue_active_pct"]
+            r["traffic"] = units * c["dram_bytes_per_unit"]
+            r["traffic_source"] = "ncu on the mid workload, scaled by units"
+        else:  # the kernel changed since the capture: the minimal sequence only
+            r["achieved"] = units * min_ops / (t_ms * 1e-3) / 1e9
+            r["traffic"] = None
+        return r
+
     roof = {
-        "vix": {"bound": "alu", "achieved": los_steps * OPS_PER_LOS_STEP / (p_st[0] * 1e-3) / 1e9,
-                "peak": issue_peak, "unit": "Gop/s", "traffic": None},
-        "viewshed": {"bound": "alu",
-                     "achieved": plain.n * interior_ray_steps(w.R) * OPS_PER_RAY_STEP / (p_st[2] * 1e-3) / 1e9,
-                     "peak": issue_peak, "unit": "Gop/s", "traffic": None},
+        "vix": issue_roof("vix", los_steps, p_st[0], OPS_PER_LOS_STEP),
+        "viewshed": issue_roof("viewshed", plain.n * interior_ray_steps(w.R), p_st[2], OPS_PER_RAY_STEP),
         "site_gains": {"bound": "hbm", "achieved": gain_bytes / (gains_ms * 1e-3) / 1e9,
-                       "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None},
+                       "peak": peaks["hbm_gbs"], "unit": "GB/s", "bytes": gain_bytes,
+                       "traffic": (plain.n * cnt["site_gains"]["dram_bytes_per_unit"]) if "site_gains" in cnt else None},
         "findmax": {"bound": "hbm", "achieved": (w.H * w.W + plain.n * 8) / (p_st[1] * 1e-3) / 1e9,
                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": None},
     }
@@ -1050,11 +1088,6 @@ def main():
         roof["cnn_lattice"] = {"bound": "tensor", "achieved": flops / (s_st[0] * 1e-3) / 1e12,
                                "peak": peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]),
                                "unit": "TFLOP/s", "traffic": None}
-    # DRAM bytes per launch from the committed ncu capture, while the kernel
-    # sources are those the counters were taken on
-    for key, tb in recorded_traffic(sur.score.numel() if sur else 0).items():
-        if key in roof:
-            roof[key]["traffic"] = tb
     for r in roof.values():
         r["frac"] = r["achieved"] / r["peak"]
     stage_roof = {"vix": "vix", "findmax": "findmax", "viewshed": "viewshed", "site": "site_loop",
@@ -1103,15 +1136,19 @@ def main():
         out["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         zh_np = zs[:, :w.W].cpu().numpy() if pitch != w.W else zs.cpu().numpy()
-        v, desc, threads = oracle_sample(zh_np, w)
+        v, desc, threads, v1 = oracle_sample(zh_np, w, cand=head.cand.cpu().numpy())
         if head is sur:
             # the surrogate pipeline's oracle: numpy CNN per lattice patch instead of vix
             per_patch = cnn_oracle_sample(zh_np, w, sur.stride, args.patch_step)
             t_vix = float(desc.split("(vix ")[1].split(" s")[0])
+            t_vix1 = float(desc.split("1 thread: vix ")[1].split(" s")[0])
             v = v - t_vix + per_patch * sur.score.numel()
+            v1 = v1 - t_vix1 + per_patch * sur.score.numel()
             desc += ("; surrogate pipeline: vix replaced by the numpy CNN oracle on %d lattice patches "
-                     "(%.2f ms per patch on one thread, 24 patches timed)" % (sur.score.numel(), per_patch * 1e3))
-        out["cpu_baseline"] = {"value": v, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc}
+                     "(%.2f ms per patch on one thread, 24 patches timed; one thread in both figures)"
+                     % (sur.score.numel(), per_patch * 1e3))
+        out["cpu_baseline"] = {"value": v, "unit": "s", "cores": threads, "kind": "oracle", "sample": desc,
+                               "single_thread_value": v1}
     if rank == 0:
         print(json.dumps(out))
     if dist:

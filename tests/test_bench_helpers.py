@@ -1,7 +1,6 @@
 """Host-side accounting of the benchmark (CPU only): the ray-step count
 behind the viewshed roofline, the greedy loop's byte count, and the rule that
-a recorded DRAM-traffic figure is reported only for the source it was
-measured on."""
+recorded ncu counters are used only for the source they were measured on."""
 import hashlib
 import json
 import os
@@ -42,20 +41,31 @@ def test_site_loop_bytes_isolated_winners():
     assert bench.site_loop_bytes(cand, cand[:2], W, R, PR) == 2 * 3 * words * 4
 
 
-def test_recorded_traffic_follows_the_source(tmp_path, monkeypatch):
+def test_recorded_counters_follow_the_source(tmp_path, monkeypatch):
+    """Per-unit counters from the mid-workload capture are used only while
+    the kernel's source file is the one they were measured on."""
     root = tmp_path
     (root / "profiles").mkdir()
     src = root / "k.cu"
     src.write_text("__global__ void k() {}\n")
     sha = hashlib.sha1(src.read_bytes()).hexdigest()
-    rec = {"stages": {"site_loop": {"bytes_per_launch": 123.0, "source": "k.cu", "sha1": sha},
-                      "cnn_lattice": {"bytes_per_launch": 7.0, "patches": 10, "source": "k.cu", "sha1": sha},
-                      "vix": {"bytes_per_launch": 5.0, "source": "k.cu", "sha1": "0" * 40}}}
-    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    rec = {"kernels": {"viewshed": {"thread_inst_per_unit": 63.5, "dram_bytes_per_unit": 0.5,
+                                    "issue_active_pct": 76.0, "source": "k.cu", "sha1": sha},
+                       "vix": {"thread_inst_per_unit": 29.0, "dram_bytes_per_unit": 0.01,
+                               "issue_active_pct": 68.0, "source": "k.cu", "sha1": "0" * 40}}}
+    (root / "profiles" / "counters_mid_11600sq_R100.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "__file__", str(root / "bench.py"))
-    got = bench.recorded_traffic(10)
-    assert got["site_loop"] == 123.0 and got["cnn_lattice"] == 7.0
+    got = bench.recorded_counters()
+    assert got["viewshed"]["thread_inst_per_unit"] == 63.5
     assert "vix" not in got                       # another source than the one measured
-    assert bench.recorded_traffic(11)["cnn_lattice"] is None   # another lattice
     src.write_text("__global__ void k() { }\n")   # the kernel changed
-    assert bench.recorded_traffic(10) == {}
+    assert bench.recorded_counters() == {}
+
+
+def test_committed_counters_record():
+    """The committed capture's per-unit figures are consistent with its raw counts."""
+    rec = json.load(open(os.path.join(os.path.dirname(bench.__file__), "profiles",
+                                      "counters_mid_11600sq_R100.json")))
+    for k, r in rec["kernels"].items():
+        assert abs(r["thread_inst_per_unit"] - r["thread_inst"] / r["units"]) < 1e-9 * r["thread_inst_per_unit"]
+        assert r["units"] > 0 and 0 < r["issue_active_pct"] <= 100
