@@ -369,6 +369,31 @@ int vs_site_noalloc(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t 
                     int32_t R, int32_t n_obs, double coverage_target, int64_t *chosen,
                     int64_t *gains, uint32_t *cum, int32_t *n_chosen, vs_stream_t st);
 
+/* Site with the candidates split over several ranks (the paper's parallel
+ * Site loop over candidates, divided between processes, one GPU each; Sec.
+ * "The multiple transmitter siting process", Site).  Each rank holds its own
+ * candidates (bm, cand, n as vs_viewshed wrote them), their exact gains
+ * (device uint32 [n], initialised with vs_site_gains) and a full copy of the
+ * cumulative viewshed cum.  One greedy step on one rank:
+ *   - win_post >= 0: the step's winner, whose bitmap win_bm (device,
+ *     vs_bitmap_words(R) words, vs_viewshed's layout) every rank received
+ *     from the rank that owns it, is ORed into cum, and every local candidate
+ *     whose window meets the winner's loses popcount(V_c AND delta), delta =
+ *     win_bm AND NOT cum before the update; win_local is the winner's index
+ *     among this rank's candidates (its gain becomes 0), -1 on other ranks.
+ *     win_post < 0: no winner yet (the first step).
+ *   - *best_key (device uint64) = the largest (gain << 32) | (0xFFFFFFFF -
+ *     post) over this rank's candidates, 0 when every gain is 0.
+ * The caller takes the largest key over the ranks (an all-reduce of one
+ * 8-byte value); its rank finds the lowest index holding it and broadcasts
+ * that bitmap.  The sequence of winners is the single-rank greedy's (posts are
+ * unique across ranks).  ws: vs_site_shard_workspace(R) bytes.  Requires
+ * W, H <= 65535. */
+size_t vs_site_shard_workspace(int32_t R);
+int vs_site_shard_step(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t H, int32_t W, int32_t R,
+                       uint32_t *gains, uint32_t *cum, const uint32_t *win_bm, int64_t win_post,
+                       int64_t win_local, uint64_t *best_key, void *ws, size_t ws_bytes, vs_stream_t st);
+
 /* Batched site: up to 64 independent greedy problems (one per terrain), each
  * exactly the arguments of one vs_site call minus the workspace, with the
  * same results.  The greedy loops of every job small enough for one CTA's

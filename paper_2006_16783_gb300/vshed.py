@@ -77,6 +77,8 @@ SIGNATURES = {
     "vs_viewshed_r3": (ctypes.c_int, [vs_grid, i32, i32, i32, P, i64, P, P, P, sz, P]),
     "vs_exact_vix_workspace": (sz, [i32, i32, i32, i64]),
     "vs_exact_vix": (ctypes.c_int, [vs_grid, i32, i32, i32, P, i64, P, P, sz, P]),
+    "vs_site_shard_workspace": (sz, [i32]),
+    "vs_site_shard_step": (ctypes.c_int, [P, P, i64, i32, i32, i32, P, P, P, i64, i64, P, P, sz, P]),
     "vs_site_workspace": (sz, [i64, i32]),
     "vs_site": (ctypes.c_int, [P, P, i64, i32, i32, i32, i32, f64, P, P, P, P, P, sz, P]),
     "vs_site_gains": (ctypes.c_int, [P, P, i64, i32, i32, i32, P, P, P]),
@@ -295,6 +297,18 @@ def exact_vix(g, R, ht, hr, posts, out=None, ws=None):
     _check("vs_exact_vix", lib().vs_exact_vix(g.c(), R, ht, hr, _ptr(posts), n, _ptr(out), _ptr(ws), wsb,
                                               _stream()))
     return out
+
+
+def site_shard_step(bm, cand, H, W, R, gains, cum, win_bm, win_post, win_local, best_key, ws):
+    """One greedy step on this rank's share of the candidates (vs_site_shard_step):
+    apply the broadcast winner (win_post < 0: none) and write the rank's best
+    key into best_key (uint64 as int64, one element)."""
+    _need_cuda(cand, gains, cum, best_key, ws)
+    n = cand.numel()
+    _check("vs_site_shard_step", lib().vs_site_shard_step(
+        _ptr(bm) if n else None, _ptr(cand) if n else None, n, H, W, R, _ptr(gains) if n else None, _ptr(cum),
+        _ptr(win_bm) if win_bm is not None else None, int(win_post), int(win_local), _ptr(best_key), _ptr(ws),
+        ws.numel(), _stream()))
 
 
 def site_ex(bm, cand, H, W, R, n_obs, target=0.0, grid=None, ht=0, weight=None, cum=None, sync=True):
