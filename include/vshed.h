@@ -159,6 +159,22 @@ size_t vs_vix_workspace(int32_t H, int32_t W, int32_t R, int32_t S);
 int vs_vix_ws(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
               uint8_t *vix_out, uint64_t *los_steps, void *ws, size_t ws_bytes, vs_stream_t st);
 
+/* Batched vix: up to 64 terrains (different sizes, ROIs, heights, sample
+ * counts, seeds) in ONE persistent launch over (terrain, tile) items; each job
+ * is exactly the arguments of one vs_vix call and gets its results.  Each
+ * job's halo window must fit in shared memory (R up to ~280; else
+ * VS_ERR_RANGE).  jobs is a HOST array read during the call; ws:
+ * vs_vix_batch_workspace bytes (a work counter, re-initialised by every call;
+ * calls that overlap on the GPU need separate workspaces). */
+typedef struct {
+    vs_grid g;
+    int32_t R, ht, hr, S;
+    uint64_t seed;
+    uint8_t *vix_out;  /* H x W, device */
+} vs_vix_job;
+size_t vs_vix_batch_workspace(int32_t n_jobs);
+int vs_vix_batch(const vs_vix_job *jobs, int32_t n_jobs, void *ws, size_t ws_bytes, vs_stream_t st);
+
 /* vs_vix plus work accounting: *los_steps (device uint64, accumulated, not
  * cleared) grows by the number of LOS crossings evaluated -- j = 1..D-1 for a
  * visible sample, j = 1..j_block for a blocked one (the test ends at the first
@@ -190,6 +206,17 @@ int vs_findmax(const uint8_t *vix, int32_t H, int32_t W, int32_t block, int32_t 
                int64_t *cand_out, int64_t cap, vs_stream_t st);
 int vs_findmax_f32(const float *score, int32_t H, int32_t W, int32_t stride, int32_t block,
                    int32_t k, int64_t *cand_out, int64_t cap, vs_stream_t st);
+
+/* Batched findmax: up to 64 uint8 maps (one per terrain) in ONE launch, each
+ * job exactly the arguments of one vs_findmax call and with its results.  jobs
+ * is a HOST array read during the call. */
+typedef struct {
+    const uint8_t *vix;  /* H x W uint8 map (pitch W), device */
+    int32_t H, W, block, k;
+    int64_t *cand_out;   /* device, cap entries */
+    int64_t cap;
+} vs_findmax_job;
+int vs_findmax_batch(const vs_findmax_job *jobs, int32_t n_jobs, vs_stream_t st);
 
 /* ------------------------------------------------------------------------
  * Viewshed (Sec. "The multiple transmitter siting process", Viewshed; the

@@ -1,7 +1,10 @@
-"""Many terrains sited together: per-terrain vix and findmax launches, all
-viewsheds in one persistent launch (vs_viewshed_batch), all greedy loops in
-one launch (vs_site_batch), the whole sequence captured once in a CUDA graph
-and replayed.  Launch shapes come from the autotuner (autotune.py)."""
+"""Many terrains sited together in a constant number of launches, whatever
+the number of terrains: every terrain's vix in one persistent launch
+(vs_vix_batch), every findmax in one launch (vs_findmax_batch), every
+viewshed in one persistent launch (vs_viewshed_batch), every greedy problem's
+preparation in six launches and every greedy loop in one (vs_site_batch), the
+cumulative viewsheds zeroed by one fill; the whole sequence captured once in a
+CUDA graph and replayed.  Launch shapes come from the autotuner (autotune.py)."""
 import torch
 
 from . import vshed as V
@@ -16,7 +19,12 @@ class BatchedSiting:
         self.inst = instances
         dev = torch.device(device)
         self.vs_jobs, self.site_jobs_, self.bufs = [], [], []
-        for it in instances:
+        self.vix_jobs, self.fm_jobs = [], []
+        # every terrain's cumulative viewshed in one buffer (zeroed by one fill)
+        sizes = [it["grid"].H * ((it["grid"].W + 31) // 32) for it in instances]
+        self.cum_all = torch.zeros(max(sum(sizes), 1), dtype=torch.int32, device=dev)
+        offs = [sum(sizes[:i]) for i in range(len(sizes))]
+        for it, o, sz in zip(instances, offs, sizes):
             g, R = it["grid"], it["R"]
             n = V.findmax_count(g.H, g.W, 1, it["block"], it["k"])
             b = {
@@ -24,12 +32,15 @@ class BatchedSiting:
                 "cand": torch.empty(n, dtype=torch.int64, device=dev),
                 "bm": torch.empty((n, 2 * R + 1, V.words_per_row(R)), dtype=torch.int32, device=dev),
                 "area": torch.empty(n, dtype=torch.int32, device=dev),
-                "cum": torch.zeros((g.H, (g.W + 31) // 32), dtype=torch.int32, device=dev),
+                "cum": self.cum_all[o:o + sz].view(g.H, (g.W + 31) // 32),
                 "chosen": torch.empty(max(it["n_obs"], 1), dtype=torch.int64, device=dev),
                 "gains": torch.empty(max(it["n_obs"], 1), dtype=torch.int64, device=dev),
                 "n_chosen": torch.zeros(1, dtype=torch.int32, device=dev),
             }
             self.bufs.append(b)
+            self.vix_jobs.append({"g": g, "R": R, "ht": it["ht"], "hr": it["hr"], "S": it["S"], "seed": it["seed"],
+                                  "out": b["vix"]})
+            self.fm_jobs.append({"vix": b["vix"], "block": it["block"], "k": it["k"], "out": b["cand"]})
             self.vs_jobs.append({"g": g, "R": R, "ht": it["ht"], "hr": it["hr"], "cand": b["cand"],
                                  "bm": b["bm"], "area": b["area"]})
             self.site_jobs_.append({"bm": b["bm"], "cand": b["cand"], "H": g.H, "W": g.W, "R": R,
@@ -37,17 +48,17 @@ class BatchedSiting:
                                     "cum": b["cum"], "n_chosen": b["n_chosen"]})
         self.vs_ws = torch.empty(max(V.lib().vs_viewshed_batch_workspace(len(instances)), 256),
                                  dtype=torch.uint8, device=dev)
+        self.vix_ws = torch.empty(max(V.lib().vs_vix_batch_workspace(len(instances)), 256),
+                                  dtype=torch.uint8, device=dev)
         self.site_ws = torch.empty(max(V.site_batch_workspace(self.site_jobs_), 256), dtype=torch.uint8,
                                    device=dev)
         self.graph = None
 
     def run(self):
-        for it, b in zip(self.inst, self.bufs):
-            V.vix(it["grid"], it["R"], it["ht"], it["hr"], it["S"], it["seed"], out=b["vix"])
-            V.findmax(b["vix"], it["block"], it["k"], out=b["cand"])
+        V.vix_batch(self.vix_jobs, self.vix_ws)
+        V.findmax_batch(self.fm_jobs)
         V.viewshed_batch(self.vs_jobs, self.vs_ws)
-        for b in self.bufs:
-            b["cum"].zero_()
+        self.cum_all.zero_()
         V.site_batch(self.site_jobs_, self.site_ws)
 
     def capture(self):

@@ -8,6 +8,8 @@
 // rounds hit L2.  The CTA's output position is the sum of
 // min(k, block size) over the blocks before it, computed in parallel.
 #include <algorithm>
+#include <cstring>
+#include <mutex>
 
 #include "vs_common.cuh"
 
@@ -45,13 +47,13 @@ __device__ __forceinline__ uint64_t block_max_u64(uint64_t v, uint64_t *red) {
     return v;
 }
 
+// block blk (row-major over blocks) of one map; the CTA's threads all take part
 template <typename V>
-__global__ void __launch_bounds__(kFmThreads) k_findmax(const V *val, int H, int W, int stride,
-                                                        int Ws, int b, int k, int nbx,
-                                                        int64_t *out) {
-    __shared__ uint64_t red[32];
-    __shared__ long long s_off;
-    const int by = blockIdx.x / nbx, bx = blockIdx.x - (blockIdx.x / nbx) * nbx;
+__device__ __forceinline__ void findmax_block(const V *val, int H, int W, int stride, int Ws, int b, int k,
+                                              int nbx, int blk, int64_t *out, uint64_t *red,
+                                              long long *s_offp) {
+    long long &s_off = *s_offp;
+    const int by = blk / nbx, bx = blk - (blk / nbx) * nbx;
     const long long i0 = ((long long)by * b + stride - 1) / stride;
     const long long i1 = llmin(((long long)(by + 1) * b + stride - 1) / stride,
                                              (H + stride - 1) / stride);
@@ -62,7 +64,7 @@ __global__ void __launch_bounds__(kFmThreads) k_findmax(const V *val, int H, int
     // output offset: sum of min(k, size) over the blocks before this one
     {
         long long acc = 0;
-        for (int q = threadIdx.x; q < (int)blockIdx.x; q += blockDim.x) {
+        for (int q = threadIdx.x; q < blk; q += blockDim.x) {
             const int qy = q / nbx, qx = q - (q / nbx) * nbx;
             const long long ny = lattice_count((long long)qy * b, llmin(H, (long long)(qy + 1) * b), stride);
             const long long nx = lattice_count((long long)qx * b, llmin(W, (long long)(qx + 1) * b), stride);
@@ -98,6 +100,38 @@ __global__ void __launch_bounds__(kFmThreads) k_findmax(const V *val, int H, int
         if (threadIdx.x == 0) out[off + r] = (int64_t)(0xFFFFFFFFu - (uint32_t)(best & 0xFFFFFFFFu));
         bound = best;
     }
+    __syncthreads();  // red and s_off are reused by the CTA's next block
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kFmThreads) k_findmax(const V *val, int H, int W, int stride,
+                                                        int Ws, int b, int k, int nbx,
+                                                        int64_t *out) {
+    __shared__ uint64_t red[32];
+    __shared__ long long s_off;
+    findmax_block<V>(val, H, W, stride, Ws, b, k, nbx, (int)blockIdx.x, out, red, &s_off);
+}
+
+// Many uint8 maps in one launch: the blocks of every job are numbered job by
+// job and CTA i takes block i.
+constexpr int kFmMaxJobs = 64;
+struct FmJob {
+    const uint8_t *val;
+    int H, W, b, k, nbx;
+    int64_t *out;
+    long long blk0;  // first CTA of the job
+};
+struct FmBatch {
+    FmJob job[kFmMaxJobs];
+    int njobs;
+};
+__global__ void __launch_bounds__(kFmThreads) k_findmax_batch(const __grid_constant__ FmBatch B) {
+    __shared__ uint64_t red[32];
+    __shared__ long long s_off;
+    int j = 0;
+    while (j + 1 < B.njobs && B.job[j + 1].blk0 <= (long long)blockIdx.x) ++j;
+    const FmJob &J = B.job[j];
+    findmax_block<uint8_t>(J.val, J.H, J.W, 1, J.W, J.b, J.k, J.nbx, (int)(blockIdx.x - J.blk0), J.out, red, &s_off);
 }
 
 // Single pass for uint8 maps and k <= KM: every thread keeps its own KM
@@ -222,4 +256,38 @@ extern "C" int vs_findmax_f32(const float *score, int32_t H, int32_t W, int32_t 
                               int32_t block, int32_t k, int64_t *cand_out, int64_t cap,
                               vs_stream_t st) {
     return findmax_launch<float>(score, H, W, stride, block, k, cand_out, cap, st);
+}
+
+extern "C" int vs_findmax_batch(const vs_findmax_job *jobs, int32_t n_jobs, vs_stream_t st) {
+    if (n_jobs < 0 || n_jobs > kFmMaxJobs) return VS_ERR_RANGE;
+    if (n_jobs == 0) return VS_OK;
+    if (!jobs) return VS_ERR_ARG;
+    static FmBatch B;  // built on the host, copied into the launch's parameters
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    memset(&B, 0, sizeof(B));
+    long long total = 0;
+    int nj = 0;
+    for (int i = 0; i < n_jobs; ++i) {
+        const vs_findmax_job &q = jobs[i];
+        if (!q.vix || !q.cand_out) return VS_ERR_ARG;
+        if (q.H < 1 || q.W < 1 || q.block < 1 || q.k < 1) return VS_ERR_RANGE;
+        if ((long long)q.H * q.W >= (1ll << 32) - 1) return VS_ERR_RANGE;
+        const int64_t need = vs_findmax_count(q.H, q.W, 1, q.block, q.k);
+        if (need < 0) return (int)need;
+        if (q.cap < need) return VS_ERR_RANGE;
+        const long long nby = (q.H + (long long)q.block - 1) / q.block, nbx = (q.W + (long long)q.block - 1) / q.block;
+        FmJob &J = B.job[nj++];
+        J.val = q.vix; J.H = q.H; J.W = q.W; J.b = q.block; J.k = q.k; J.nbx = (int)nbx; J.out = q.cand_out;
+        J.blk0 = total;
+        total += nby * nbx;
+    }
+    if (total > 0x7fffffffll) return VS_ERR_RANGE;
+    B.njobs = nj;
+    int rc = check_device();
+    if (rc) return rc;
+    k_findmax_batch<<<(unsigned)total, kFmThreads, 0, (cudaStream_t)st>>>(B);
+    vs::note_launch();
+    VS_CUDA_TRY(cudaGetLastError());
+    return VS_OK;
 }

@@ -34,13 +34,11 @@ constexpr int kSiteThreads = 1024;
 constexpr int kGainThreads = 256;
 
 // ------------------------------------------------------------------ dense gain pass
-__global__ void __launch_bounds__(kGainThreads) k_site_gains(const uint32_t *__restrict__ bm,
-                                                             const int64_t *__restrict__ cand,
-                                                             int64_t n, int H, int W, int R,
-                                                             const uint32_t *__restrict__ cum,
-                                                             uint32_t *__restrict__ gains) {
+// one warp computes candidate c's gain
+__device__ __forceinline__ void site_gain_warp(const uint32_t *__restrict__ bm, const int64_t *__restrict__ cand,
+                                               int64_t n, int H, int W, int R, const uint32_t *__restrict__ cum,
+                                               uint32_t *__restrict__ gains, int64_t c) {
     const int lane = threadIdx.x & 31;
-    const int64_t c = (int64_t)blockIdx.x * (kGainThreads / 32) + (threadIdx.x >> 5);
     if (c >= n) return;
     const int64_t p = cand[c];
     if (p < 0 || p >= (int64_t)H * W) {
@@ -100,6 +98,15 @@ __global__ void __launch_bounds__(kGainThreads) k_site_gains(const uint32_t *__r
     }
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) gains[c] = sum;
+}
+
+__global__ void __launch_bounds__(kGainThreads) k_site_gains(const uint32_t *__restrict__ bm,
+                                                             const int64_t *__restrict__ cand,
+                                                             int64_t n, int H, int W, int R,
+                                                             const uint32_t *__restrict__ cum,
+                                                             uint32_t *__restrict__ gains) {
+    site_gain_warp(bm, cand, n, H, W, R, cum, gains,
+                   (int64_t)blockIdx.x * (kGainThreads / 32) + (threadIdx.x >> 5));
 }
 
 __global__ void k_cum_popcount(const uint32_t *__restrict__ cum, int64_t nwords,
@@ -308,11 +315,11 @@ __device__ __forceinline__ uint64_t slot_key(const int64_t *cand, int64_t c, int
 }
 
 // sorted chunks into keys[]; rank[c] = position of candidate c in its chunk
-__global__ void __launch_bounds__(kRankChunk) k_rank_chunks(const int64_t *__restrict__ cand, int64_t n, int64_t HW,
-                                                           uint64_t *__restrict__ keys, uint32_t *__restrict__ rank) {
-    __shared__ uint64_t sk[kRankChunk];
+__device__ __forceinline__ void rank_chunk(const int64_t *__restrict__ cand, int64_t n, int64_t HW,
+                                           uint64_t *__restrict__ keys, uint32_t *__restrict__ rank, int64_t blk,
+                                           uint64_t *sk) {
     const int t = threadIdx.x;
-    const int64_t c = (int64_t)blockIdx.x * kRankChunk + t;
+    const int64_t c = blk * kRankChunk + t;
     sk[t] = (c < n) ? slot_key(cand, c, HW) : ~0ull;
     __syncthreads();
     for (int size = 2; size <= kRankChunk; size <<= 1)
@@ -330,30 +337,44 @@ __global__ void __launch_bounds__(kRankChunk) k_rank_chunks(const int64_t *__res
         }
     if (c < n) {
         const uint64_t k = sk[t];  // padding (~0) sorts after every real key
-        keys[(int64_t)blockIdx.x * kRankChunk + t] = k;
+        keys[blk * kRankChunk + t] = k;
         rank[(uint32_t)k] = (uint32_t)t;
     }
+    __syncthreads();  // sk is reused by the CTA's next chunk
+}
+
+__global__ void __launch_bounds__(kRankChunk) k_rank_chunks(const int64_t *__restrict__ cand, int64_t n, int64_t HW,
+                                                           uint64_t *__restrict__ keys, uint32_t *__restrict__ rank) {
+    __shared__ uint64_t sk[kRankChunk];
+    rank_chunk(cand, n, HW, keys, rank, blockIdx.x, sk);
 }
 
 // rank[c] += number of keys of chunk blockIdx.y below candidate c's key, for
 // the keys of chunk blockIdx.x
-__global__ void __launch_bounds__(kRankChunk) k_rank_cross(const uint64_t *__restrict__ keys, int64_t n,
-                                                          uint32_t *__restrict__ rank) {
-    if (blockIdx.x == blockIdx.y) return;
-    __shared__ uint64_t sk[kRankChunk];
+__device__ __forceinline__ void rank_cross(const uint64_t *__restrict__ keys, int64_t n, uint32_t *__restrict__ rank,
+                                           int64_t bx, int64_t by, uint64_t *sk) {
+    if (bx == by) return;
     const int t = threadIdx.x;
-    const int64_t b0 = (int64_t)blockIdx.y * kRankChunk, a0 = (int64_t)blockIdx.x * kRankChunk;
+    const int64_t b0 = by * kRankChunk, a0 = bx * kRankChunk;
     const int mb = (int)min((int64_t)kRankChunk, n - b0);
     if (t < mb) sk[t] = keys[b0 + t];
     __syncthreads();
-    if (a0 + t >= n) return;
-    const uint64_t k = keys[a0 + t];
-    int lo = 0, hi = mb;  // first key of chunk y not below k
-    while (lo < hi) {
-        const int m = (lo + hi) >> 1;
-        if (sk[m] < k) lo = m + 1; else hi = m;
+    if (a0 + t < n) {
+        const uint64_t k = keys[a0 + t];
+        int lo = 0, hi = mb;  // first key of chunk y not below k
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (sk[m] < k) lo = m + 1; else hi = m;
+        }
+        if (lo) atomicAdd(&rank[(uint32_t)k], (uint32_t)lo);
     }
-    if (lo) atomicAdd(&rank[(uint32_t)k], (uint32_t)lo);
+    __syncthreads();  // sk is reused by the CTA's next pair of chunks
+}
+
+__global__ void __launch_bounds__(kRankChunk) k_rank_cross(const uint64_t *__restrict__ keys, int64_t n,
+                                                          uint32_t *__restrict__ rank) {
+    __shared__ uint64_t sk[kRankChunk];
+    rank_cross(keys, n, rank, blockIdx.x, blockIdx.y, sk);
 }
 
 __global__ void k_rank_scatter(const uint32_t *__restrict__ rank, int64_t n, uint32_t *__restrict__ sorig) {
@@ -368,9 +389,8 @@ __global__ void k_rank_posts(const int64_t *__restrict__ cand, const uint32_t *_
 }
 
 // for every slot, the slot range holding the candidates within 2R rows
-__global__ void k_site_bands(const uint32_t *__restrict__ sp, int64_t n, int W, int R,
-                             uint32_t *__restrict__ slo, uint32_t *__restrict__ shi) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void site_band(const uint32_t *__restrict__ sp, int64_t n, int W, int R,
+                                          uint32_t *__restrict__ slo, uint32_t *__restrict__ shi, int64_t i) {
     if (i >= n) return;
     const uint32_t p = sp[i];
     if (p == 0xFFFFFFFFu) { slo[i] = (uint32_t)i; shi[i] = (uint32_t)i; return; }
@@ -386,6 +406,11 @@ __global__ void k_site_bands(const uint32_t *__restrict__ sp, int64_t n, int W, 
     shi[i] = (uint32_t)lo;
 }
 
+__global__ void k_site_bands(const uint32_t *__restrict__ sp, int64_t n, int W, int R,
+                             uint32_t *__restrict__ slo, uint32_t *__restrict__ shi) {
+    site_band(sp, n, W, R, slo, shi, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 struct Site1Params {
     const uint32_t *bm;
     int n;
@@ -399,6 +424,7 @@ struct Site1Params {
     const uint32_t *sp, *sorig, *slo, *shi;  // slot order
     const unsigned long long *covered0;
     int vec_rows;            // bitmap rows are whole 16-byte vectors (PR % 4 == 0, bm 16-byte aligned)
+    uint32_t *gbuf;          // gains in global memory (jobs whose gains exceed shared memory), or null
 };
 
 __device__ __forceinline__ uint64_t u64max(uint64_t a, uint64_t b) { return a > b ? a : b; }
@@ -427,8 +453,9 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 // (about 0.55 per cycle measured) bound the refresh.
 __device__ __forceinline__ void site1_body(const Site1Params &P) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t *s_gain = (uint32_t *)smem;                  // n
-    uint32_t *s_delta = s_gain + ((P.n + 3) & ~3);        // words
+    // the gains in shared memory, or (too many candidates for it) in global memory
+    uint32_t *s_gain = P.gbuf ? P.gbuf : (uint32_t *)smem;                          // n
+    uint32_t *s_delta = P.gbuf ? (uint32_t *)smem : s_gain + ((P.n + 3) & ~3);    // words
     int *s_list = (int *)(s_delta + ((P.words + 3) & ~3)); // kSiteThreads
     __shared__ uint64_t s_red[32];
     __shared__ int s_wcnt[32], s_wsum[32];
@@ -1503,6 +1530,62 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_loop1_batch(const __gr
     site1_body(B.job[blockIdx.x]);
 }
 
+// The preparation of many greedy problems in six launches, one per step for
+// every job (a job's blocks of a step follow the previous job's): 0 dense
+// gains (and the coverage count zeroed), 1 slot-order chunks (and the
+// coverage count of the starting cumulative viewshed), 2 cross-chunk ranks,
+// 3 scatter to slots, 4 slot posts, 5 bands.  Each step's body is the one the
+// single-problem launches use.
+constexpr int kPrepPhases = 6;
+constexpr int kCovBlocks = 16;
+struct PrepJob {
+    const uint32_t *bm;
+    const int64_t *cand;
+    int64_t n;
+    int H, W, R, count_cov;
+    const uint32_t *cum;
+    uint32_t *g0, *sp, *sorig, *slo, *shi;
+    unsigned long long *cov;
+    int64_t nch;
+    long long blk0[kPrepPhases];
+};
+struct PrepBatch {
+    PrepJob job[kSiteMaxJobs];
+    int njobs;
+};
+__global__ void __launch_bounds__(kRankChunk) k_site_prep_batch(const __grid_constant__ PrepBatch B, int phase) {
+    __shared__ uint64_t sk[kRankChunk];
+    int j = 0;
+    while (j + 1 < B.njobs && B.job[j + 1].blk0[phase] <= (long long)blockIdx.x) ++j;
+    const PrepJob &J = B.job[j];
+    const int64_t b = (int64_t)blockIdx.x - J.blk0[phase];
+    const int64_t HW = (int64_t)J.H * J.W;
+    if (phase == 0) {
+        if (b == 0 && threadIdx.x == 0 && J.count_cov) *J.cov = 0ull;
+        site_gain_warp(J.bm, J.cand, J.n, J.H, J.W, J.R, J.cum, J.g0, b * (blockDim.x / 32) + (threadIdx.x >> 5));
+    } else if (phase == 1) {
+        if (b < J.nch) {
+            rank_chunk(J.cand, J.n, HW, (uint64_t *)J.slo, J.sp, b, sk);
+        } else if (J.count_cov) {  // popcount of the starting cumulative viewshed
+            const int64_t nw = (int64_t)J.H * ((J.W + 31) / 32);
+            unsigned long long v = 0;
+            for (int64_t i = (b - J.nch) * blockDim.x + threadIdx.x; i < nw; i += (int64_t)kCovBlocks * blockDim.x)
+                v += __popc(J.cum[i]);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0 && v) atomicAdd(J.cov, v);
+        }
+    } else if (phase == 2) {
+        rank_cross((const uint64_t *)J.slo, J.n, J.sp, b % J.nch, b / J.nch, sk);
+    } else {
+        const int64_t i = b * blockDim.x + threadIdx.x;
+        if (i < J.n) {
+            if (phase == 3) J.sorig[J.sp[i]] = (uint32_t)i;
+            else if (phase == 4) J.sp[i] = (uint32_t)(slot_key(J.cand, J.sorig[i], HW) >> 32);
+        }
+        if (phase == 5) site_band(J.sp, J.n, J.W, J.R, J.slo, J.shi, i);
+    }
+}
+
 // ------------------------------------------------------------------ lazy greedy
 // For calls whose gains or windows do not fit in one cluster's shared memory
 // (the paper's own regime: R = 1000, ~386,000 candidates, 512 KB bitmaps),
@@ -2349,6 +2432,7 @@ static int site_impl(const uint32_t *bm, const int64_t *cand, int64_t n, int32_t
         Q1.cum = cum; Q1.n_chosen = n_chosen; Q1.gain0 = g0; Q1.sp = sp; Q1.sorig = sorig;
         Q1.slo = slo; Q1.shi = shi; Q1.covered0 = cov;
         Q1.vec_rows = (P.PR % 4 == 0 && ((uintptr_t)bm & 15) == 0) ? 1 : 0;
+        Q1.gbuf = nullptr;
         if (job_out) {  // batched call: the caller launches the loop
             *job_out = Q1;
             *smem_out = smem1;
@@ -2526,11 +2610,20 @@ extern "C" int vs_site_ex(const uint32_t *bm, const int64_t *cand, int64_t n, in
     return site_lazy(bm, cand, n, H, W, R, n_obs, need, chosen, gains, cum, n_chosen, g0, ws, cov, s, &o);
 }
 
+// a batch job whose gains do not fit one CTA's shared memory keeps them in
+// global memory, after its workspace
+static bool site_batch_global(int64_t n, int R) {
+    return n > 0 && !site1_fits(n, (2 * R + 1) * words_per_row(R));
+}
+
 extern "C" size_t vs_site_batch_workspace(const vs_site_job *jobs, int32_t n_jobs) {
     if (!jobs || n_jobs < 0) return 0;
     size_t t = 0;
-    for (int i = 0; i < n_jobs; ++i) t += align256(vs_site_workspace(jobs[i].n, jobs[i].R));
-    return t;
+    for (int i = 0; i < n_jobs; ++i) {
+        t += align256(vs_site_workspace(jobs[i].n, jobs[i].R));
+        if (site_batch_global(jobs[i].n, jobs[i].R)) t += align256((size_t)jobs[i].n * 4);
+    }
+    return t + 256;
 }
 
 extern "C" int vs_site_batch(const vs_site_job *jobs, int32_t n_jobs, void *ws, size_t ws_bytes,
@@ -2542,34 +2635,82 @@ extern "C" int vs_site_batch(const vs_site_job *jobs, int32_t n_jobs, void *ws, 
     int rc = check_device();
     if (rc) return rc;
     static Site1Batch B;
+    static PrepBatch PB;
     static std::mutex mu;
     std::lock_guard<std::mutex> lk(mu);
     memset(&B, 0, sizeof(B));
+    memset(&PB, 0, sizeof(PB));
     size_t smem = 0, off = 0;
-    int nb = 0;
+    long long nblk[kPrepPhases] = {0, 0, 0, 0, 0, 0};
     for (int i = 0; i < n_jobs; ++i) {
         const vs_site_job &q = jobs[i];
-        const size_t wsb = align256(vs_site_workspace(q.n, q.R));
-        void *wsj = (char *)ws + off;
-        off += wsb;
-        const int words = (2 * q.R + 1) * words_per_row(q.R);
-        if (q.n > 0 && site1_fits(q.n, words)) {
-            size_t sm = 0;
-            if ((rc = site_impl(q.bm, q.cand, q.n, q.H, q.W, q.R, q.n_obs, q.coverage_target, q.chosen,
-                                q.gains, q.cum, q.n_chosen, wsj, wsb, st, &B.job[nb], &sm)))
-                return rc;
-            smem = std::max(smem, sm);
-            ++nb;
-        } else {  // empty or too large for one CTA: the ordinary call
-            if ((rc = site_impl(q.bm, q.cand, q.n, q.H, q.W, q.R, q.n_obs, q.coverage_target, q.chosen,
-                                q.gains, q.cum, q.n_chosen, wsj, wsb, st, nullptr, nullptr)))
-                return rc;
+        const int64_t n = q.n;
+        if (n < 0 || q.n_obs < 0) return VS_ERR_RANGE;
+        if (!q.cum || !q.n_chosen || (n > 0 && (!q.bm || !q.cand)) || (q.n_obs > 0 && (!q.chosen || !q.gains)))
+            return VS_ERR_ARG;
+        if (q.H < 1 || q.W < 1 || q.H > 65535 || q.W > 65535 || q.R < 1 || q.R > kMaxR) return VS_ERR_RANGE;
+        if (n >= (1 << 30)) return VS_ERR_RANGE;
+        char *wsj = (char *)ws + off;
+        const size_t a4 = align256((size_t)n * 4);
+        off += align256(vs_site_workspace(n, q.R));
+        const bool global = site_batch_global(n, q.R);
+        uint32_t *gbuf = nullptr;
+        if (global) {
+            gbuf = (uint32_t *)((char *)ws + off);
+            off += align256((size_t)n * 4);
+        }
+        Site1Params &Q1 = B.job[i];
+        const int PR = words_per_row(q.R), words = (2 * q.R + 1) * PR;
+        Q1.bm = q.bm; Q1.n = (int)n; Q1.H = q.H; Q1.W = q.W; Q1.R = q.R; Q1.PR = PR; Q1.words = words;
+        Q1.WWc = (q.W + 31) / 32; Q1.n_obs = q.n_obs; Q1.chosen = q.chosen; Q1.gains = q.gains;
+        Q1.cum = q.cum; Q1.n_chosen = q.n_chosen;
+        Q1.gain0 = (uint32_t *)wsj;
+        Q1.sp = (uint32_t *)(wsj + a4);
+        Q1.sorig = (uint32_t *)(wsj + 2 * a4);
+        Q1.slo = (uint32_t *)(wsj + 3 * a4);
+        Q1.shi = (uint32_t *)(wsj + 4 * a4);
+        Q1.covered0 = (unsigned long long *)(wsj + 5 * a4);
+        Q1.need = -1;
+        if (q.coverage_target > 0.0) {
+            const double need = q.coverage_target * (double)q.H * (double)q.W;
+            long long nn = (long long)need;
+            if ((double)nn < need) nn += 1;
+            Q1.need = nn;
+        }
+        Q1.vec_rows = (PR % 4 == 0 && ((uintptr_t)q.bm & 15) == 0) ? 1 : 0;
+        Q1.gbuf = gbuf;
+        smem = std::max(smem, global ? site1_smem_bytes(0, words) : site1_smem_bytes(n, words));
+        PrepJob &J = PB.job[i];
+        J.bm = q.bm; J.cand = q.cand; J.n = n; J.H = q.H; J.W = q.W; J.R = q.R;
+        J.count_cov = Q1.need >= 0 ? 1 : 0;
+        J.cum = q.cum; J.g0 = (uint32_t *)Q1.gain0; J.sp = (uint32_t *)Q1.sp; J.sorig = (uint32_t *)Q1.sorig;
+        J.slo = (uint32_t *)Q1.slo; J.shi = (uint32_t *)Q1.shi;
+        J.cov = (unsigned long long *)Q1.covered0;
+        J.nch = (n + kRankChunk - 1) / kRankChunk;
+        const long long cnt[kPrepPhases] = {(n + 7) / 8, J.nch + (J.count_cov ? kCovBlocks : 0),
+                                             J.nch > 1 ? J.nch * J.nch : 0, (n + 1023) / 1024, (n + 1023) / 1024,
+                                             (n + 1023) / 1024};
+        for (int ph = 0; ph < kPrepPhases; ++ph) {
+            J.blk0[ph] = nblk[ph];
+            nblk[ph] += cnt[ph];
         }
     }
-    if (nb == 0) return VS_OK;
+    PB.njobs = n_jobs;
+    cudaStream_t s = (cudaStream_t)st;
+    // phases 0 (a warp per candidate, 8 per block) and 3..5 (one thread per
+    // candidate) use 256 or 1024 threads; 1 and 2 one 1024-key chunk per block
+    const int threads[kPrepPhases] = {256, 1024, 1024, 1024, 1024, 1024};
+    // every step is launched (one idle block when no job has work in it), so
+    // that the number of launches does not depend on the jobs
+    for (int ph = 0; ph < kPrepPhases; ++ph) {
+        if (nblk[ph] > 0x7fffffffll) return VS_ERR_RANGE;
+        k_site_prep_batch<<<(unsigned)std::max(nblk[ph], 1ll), threads[ph], 0, s>>>(PB, ph);
+        vs::note_launch();
+        VS_CUDA_TRY(cudaGetLastError());
+    }
     VS_CUDA_TRY(cudaFuncSetAttribute(k_site_loop1_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-    k_site_loop1_batch<<<nb, kSiteThreads, smem, (cudaStream_t)st>>>(B);
+    k_site_loop1_batch<<<n_jobs, kSiteThreads, smem, s>>>(B);
     vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;

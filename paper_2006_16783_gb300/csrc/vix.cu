@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include <mutex>
+#include <cstring>
 #include "vs_common.cuh"
 
 namespace vs {
@@ -233,12 +235,15 @@ __device__ __forceinline__ void vix_offset(uint64_t state, unsigned NR, int R, c
     if (dy == 0 && dx >= 0) dx += 1;
 }
 
+// one tile of posts (left column tx0, top row ty0) of one terrain; the CTA's
+// mbarrier and its phase parity are carried across tiles.  Returns true when a
+// window copy did not land within two bounded waits (the barrier can then no
+// longer be trusted: the CTA must take no further tile).
 template <bool COUNT>
-__global__ void __launch_bounds__(kVixThreads, 1) k_vix2(const __grid_constant__ CUtensorMap tmap,
-                                                         const Vix2Params Q) {
+__device__ bool vix2_tile(const CUtensorMap *tmapp, const Vix2Params &Q, int tx0, int ty0, unsigned char *smem,
+                          uint64_t *bar, uint32_t &phase, int *warp_tot, int *s_failp) {
     const VixParams &P = Q.b;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    int &s_fail = *s_failp;
     const int R = P.R, TX = P.TX, TY = P.TY, lgTX = Q.lgTX;
     const int WW = P.WG * 8;
     const int nposts = TX * TY;
@@ -249,16 +254,9 @@ __global__ void __launch_bounds__(kVixThreads, 1) k_vix2(const __grid_constant__
     int *hist = cnt + nposts;                      // R + 2 entries
     int *rowstart = hist + ((R + 2 + 3) & ~3);      // 2R + 2 entries
     int *hwtab = rowstart + (2 * R + 2);            // 2R + 1 entries
-    uint64_t *bar = (uint64_t *)(hwtab + ((2 * R + 1 + 1) & ~1));
-    __shared__ int warp_tot[32];
-    __shared__ int s_fail;
 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        s_fail = 0;
-    }
+    if (tid == 0) s_fail = 0;
     for (int i = tid; i < nposts; i += blockDim.x) cnt[i] = 0;
     // ---- row table of OFF_R (as in k_vix)
     {
@@ -313,15 +311,20 @@ __global__ void __launch_bounds__(kVixThreads, 1) k_vix2(const __grid_constant__
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, (uint32_t)(win_elems * 2));
             for (int b = 0; b < P.nbox; ++b)
-                tma_load_3d(win + (size_t)b * P.box_rows * WW, &tmap, 0, wx0 / 8,
+                tma_load_3d(win + (size_t)b * P.box_rows * WW, tmapp, 0, wx0 / 8,
                             wy0 + b * P.box_rows, bar);
         }
-        if (!mbar_wait(bar, (uint32_t)(sec & 1))) s_fail = 1;
+        if (!mbar_wait(bar, phase & 1u)) s_fail = 1;
         __syncthreads();
         if (s_fail) {
-            mbar_wait(bar, (uint32_t)(sec & 1));
+            const bool ok2 = mbar_wait(bar, phase & 1u);
+            __syncthreads();
+            if (tid == 0 && !ok2) s_fail = 2;
+            __syncthreads();
+            phase ^= 1u;
             break;
         }
+        phase ^= 1u;
         for (int s0 = 0; s0 < P.S; s0 += Q.sb) {
             const int nb = min(Q.sb, P.S - s0);
             // ---- pass A: how many lines of each length
@@ -450,6 +453,66 @@ __global__ void __launch_bounds__(kVixThreads, 1) k_vix2(const __grid_constant__
     if (COUNT) {
         for (int o = 16; o > 0; o >>= 1) nsteps += __shfl_xor_sync(0xffffffffu, nsteps, o);
         if (lane == 0 && nsteps) atomicAdd(P.steps, nsteps);
+    }
+    const bool dead = s_fail == 2;
+    __syncthreads();  // shared memory is reused by the CTA's next tile
+    return dead;
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(kVixThreads, 1) k_vix2(const __grid_constant__ CUtensorMap tmap,
+                                                         const Vix2Params Q) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    __shared__ uint64_t bar;
+    __shared__ int warp_tot[32];
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    vix2_tile<COUNT>(&tmap, Q, blockIdx.x * Q.b.TX, blockIdx.y * Q.b.TY, smem, &bar, phase, warp_tot, &s_fail);
+}
+
+// Batched vix of many terrains in one persistent launch: items (job, tile)
+// are numbered job by job (jobs ordered by decreasing R, so the costly ones
+// start first) and pulled from a global counter; each job's TMA descriptor
+// and parameters sit in the launch's parameters.
+constexpr int kVixMaxJobs = 64;
+struct Vix2Job {
+    CUtensorMap map;
+    Vix2Params Q;
+    int tiles_x;
+    long long item0;
+};
+struct Vix2Batch {
+    Vix2Job job[kVixMaxJobs];
+    int njobs;
+    long long total;
+    unsigned long long *counter;
+};
+__global__ void __launch_bounds__(kVixThreads, 1) k_vix2_batch(const __grid_constant__ Vix2Batch B) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    __shared__ uint64_t bar;
+    __shared__ int warp_tot[32];
+    __shared__ int s_fail;
+    __shared__ long long s_item;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(B.counter, 1ull);
+        __syncthreads();
+        const long long it = s_item;
+        __syncthreads();
+        if (it >= B.total) break;
+        int j = 0;
+        while (j + 1 < B.njobs && B.job[j + 1].item0 <= it) ++j;
+        const Vix2Job &J = B.job[j];
+        const long long t = it - J.item0;
+        const int tx = (int)(t % J.tiles_x), ty = (int)(t / J.tiles_x);
+        if (vix2_tile<false>(&J.map, J.Q, tx * J.Q.b.TX, ty * J.Q.b.TY, smem, &bar, phase, warp_tot, &s_fail))
+            break;  // a copy may still land in this CTA's window: take no more items
     }
 }
 
@@ -884,6 +947,46 @@ static int vix_launch_wide(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, 
     return VS_OK;
 }
 
+// the parameters common to the vix kernels; NR = |disc(R)| - 1
+static void vix_params(const vs_grid &g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
+                       uint8_t *vix_out, VixParams *P) {
+    memset(P, 0, sizeof(*P));
+    P->H = g.H; P->W = g.W; P->R = R; P->ht = ht; P->hr = hr; P->S = S; P->seed = seed; P->out = vix_out;
+    long long nr = 0;
+    for (int dy = -R; dy <= R; ++dy) {
+        long long v = (long long)R * R - (long long)dy * dy, s = (long long)std::sqrt((double)v);
+        while (s * s > v) --s;
+        while ((s + 1) * (s + 1) <= v) ++s;
+        nr += 2 * s + 1;
+    }
+    P->NR = (int)(nr - 1);
+}
+
+// tile, passes and sample batch of the length-sorted kernel for P's R and S:
+// the largest tile whose staged window fits, fewest passes first; false when
+// none fits in shared memory
+static bool vix2_pick(const VixParams &P, unsigned long long *steps, Vix2Params *Q, size_t *smem) {
+    const int R = P.R;
+    const int pref = tune_get(VS_TUNE_VIX_TILE, R, 0);
+    const int tiles2[2][2] = {{pref == 2 ? 32 : 64, 32}, {32, 32}};
+    const int sb = std::min(P.S, kVixSB);
+    for (int ns : {1, 2, 4}) {
+        for (auto &t : tiles2) {
+            int WG, br, nb;
+            const size_t b = vix2_smem_bytes(R, ns, t[0], t[1], std::max(sb, 1), &WG, &br, &nb);
+            if (WG > 256 || b > (size_t)225 * 1024) continue;
+            Q->b = P;
+            Q->b.nsplit = ns; Q->b.TX = t[0]; Q->b.TY = t[1]; Q->b.WG = WG; Q->b.box_rows = br;
+            Q->b.nbox = nb; Q->b.steps = steps;
+            Q->lgTX = (t[0] == 64) ? 6 : 5;
+            Q->sb = std::max(sb, 1);
+            *smem = b;
+            return true;
+        }
+    }
+    return false;
+}
+
 static int vix_launch(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, uint64_t seed,
                       uint8_t *vix_out, unsigned long long *steps, void *ws, size_t ws_bytes,
                       vs_stream_t st) {
@@ -895,51 +998,29 @@ static int vix_launch(vs_grid g, int32_t R, int32_t ht, int32_t hr, int32_t S, u
     if ((rc = check_device())) return rc;
 
     VixParams P;
-    P.H = g.H; P.W = g.W; P.R = R; P.ht = ht; P.hr = hr; P.S = S; P.seed = seed; P.out = vix_out;
-    long long nr = 0;
-    for (int dy = -R; dy <= R; ++dy) {
-        long long v = (long long)R * R - (long long)dy * dy, s = (long long)std::sqrt((double)v);
-        while (s * s > v) --s;
-        while ((s + 1) * (s + 1) <= v) ++s;
-        nr += 2 * s + 1;
-    }
-    P.NR = (int)(nr - 1);
+    vix_params(g, R, ht, hr, S, seed, vix_out, &P);
 
     if (vix_wide(R, S))
         return vix_launch_wide(g, R, ht, hr, S, seed, vix_out, steps, ws, ws_bytes, (cudaStream_t)st, P.NR);
 
     // length-sorted variant when the packed line items can describe R
-    if (R <= 511) {
-        const int pref = tune_get(VS_TUNE_VIX_TILE, R, 0);
-        const int tiles2[2][2] = {{pref == 2 ? 32 : 64, 32}, {32, 32}};
-        const int sb = std::min(S, kVixSB);
-        for (int ns : {1, 2, 4}) {
-            for (auto &t : tiles2) {
-                int WG, br, nb;
-                size_t b = vix2_smem_bytes(R, ns, t[0], t[1], std::max(sb, 1), &WG, &br, &nb);
-                if (WG > 256 || b > (size_t)225 * 1024) continue;
-                Vix2Params Q;
-                Q.b = P;
-                Q.b.nsplit = ns; Q.b.TX = t[0]; Q.b.TY = t[1]; Q.b.WG = WG; Q.b.box_rows = br;
-                Q.b.nbox = nb; Q.b.steps = steps;
-                Q.lgTX = (t[0] == 64) ? 6 : 5;
-                Q.sb = std::max(sb, 1);
-                GridMap gm;
-                if ((rc = make_grid_map(&gm, g, WG, br))) return rc;
-                dim3 grid((g.W + t[0] - 1) / t[0], (g.H + t[1] - 1) / t[1]);
-                if (steps) {
-                    VS_CUDA_TRY(cudaFuncSetAttribute(k_vix2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
-                    k_vix2<true><<<grid, kVixThreads, b, (cudaStream_t)st>>>(gm.map, Q);
-                    vs::note_launch();
-                } else {
-                    VS_CUDA_TRY(cudaFuncSetAttribute(k_vix2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
-                    k_vix2<false><<<grid, kVixThreads, b, (cudaStream_t)st>>>(gm.map, Q);
-                    vs::note_launch();
-                }
-                VS_CUDA_TRY(cudaGetLastError());
-                return VS_OK;
-            }
+    Vix2Params Q;
+    size_t b = 0;
+    if (R <= 511 && vix2_pick(P, steps, &Q, &b)) {
+        GridMap gm;
+        if ((rc = make_grid_map(&gm, g, Q.b.WG, Q.b.box_rows))) return rc;
+        dim3 grid((g.W + Q.b.TX - 1) / Q.b.TX, (g.H + Q.b.TY - 1) / Q.b.TY);
+        if (steps) {
+            VS_CUDA_TRY(cudaFuncSetAttribute(k_vix2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+            k_vix2<true><<<grid, kVixThreads, b, (cudaStream_t)st>>>(gm.map, Q);
+            vs::note_launch();
+        } else {
+            VS_CUDA_TRY(cudaFuncSetAttribute(k_vix2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+            k_vix2<false><<<grid, kVixThreads, b, (cudaStream_t)st>>>(gm.map, Q);
+            vs::note_launch();
         }
+        VS_CUDA_TRY(cudaGetLastError());
+        return VS_OK;
     }
 
     // tile / split choice: the largest tile whose staged window fits, fewest
@@ -1030,6 +1111,67 @@ extern "C" int vs_viewshed_r3(vs_grid g, int32_t R, int32_t ht, int32_t hr, cons
         P.px = px;
     }
     k_viewshed_r3<<<(unsigned)n, kR3Threads, 0, s>>>(P);
+    vs::note_launch();
+    VS_CUDA_TRY(cudaGetLastError());
+    return VS_OK;
+}
+
+extern "C" size_t vs_vix_batch_workspace(int32_t n_jobs) {
+    (void)n_jobs;
+    return 256;
+}
+
+extern "C" int vs_vix_batch(const vs_vix_job *jobs, int32_t n_jobs, void *ws, size_t ws_bytes, vs_stream_t st) {
+    if (n_jobs < 0 || n_jobs > kVixMaxJobs) return VS_ERR_RANGE;
+    if (n_jobs == 0) return VS_OK;
+    if (!jobs) return VS_ERR_ARG;
+    if (!ws || ws_bytes < vs_vix_batch_workspace(n_jobs)) return VS_ERR_WS;
+    int rc = check_device();
+    if (rc) return rc;
+    // largest ROI first: the longest items start early, the short ones fill the tail
+    int order[kVixMaxJobs];
+    for (int i = 0; i < n_jobs; ++i) order[i] = i;
+    std::stable_sort(order, order + n_jobs, [&](int a, int b) { return jobs[a].R > jobs[b].R; });
+    static Vix2Batch B;  // large: built on the host, copied into the launch's parameters
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    memset(&B, 0, sizeof(B));
+    size_t smem = 0;
+    long long total = 0;
+    int nj = 0;
+    for (int i = 0; i < n_jobs; ++i) {
+        const vs_vix_job &q = jobs[order[i]];
+        if ((rc = check_grid(q.g))) return rc;
+        if (!q.vix_out) return VS_ERR_ARG;
+        if (q.R < 1 || q.R > 511 || q.S < 0 || q.S > 255) return VS_ERR_RANGE;
+        if (q.ht < -100000 || q.ht > 100000 || q.hr < -100000 || q.hr > 100000) return VS_ERR_RANGE;
+        VixParams P;
+        vix_params(q.g, q.R, q.ht, q.hr, q.S, q.seed, q.vix_out, &P);
+        Vix2Job &J = B.job[nj];
+        size_t b = 0;
+        if (!vix2_pick(P, nullptr, &J.Q, &b)) return VS_ERR_RANGE;  // window beyond shared memory
+        GridMap gm;
+        if ((rc = make_grid_map(&gm, q.g, J.Q.b.WG, J.Q.b.box_rows))) return rc;
+        J.map = gm.map;
+        J.tiles_x = (q.g.W + J.Q.b.TX - 1) / J.Q.b.TX;
+        const long long tiles = (long long)J.tiles_x * ((q.g.H + J.Q.b.TY - 1) / J.Q.b.TY);
+        J.item0 = total;
+        total += tiles;
+        smem = std::max(smem, b);
+        ++nj;
+    }
+    B.njobs = nj;
+    B.total = total;
+    B.counter = (unsigned long long *)ws;
+    cudaStream_t s = (cudaStream_t)st;
+    VS_CUDA_TRY(cudaMemsetAsync(ws, 0, 8, s));
+    VS_CUDA_TRY(cudaFuncSetAttribute(k_vix2_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per = 0;
+    VS_CUDA_TRY(cudaGetDevice(&dev));
+    VS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    VS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_vix2_batch, kVixThreads, smem));
+    const long long grid = std::min<long long>(total, (long long)sms * std::max(per, 1));
+    k_vix2_batch<<<(unsigned)grid, kVixThreads, smem, s>>>(B);
     vs::note_launch();
     VS_CUDA_TRY(cudaGetLastError());
     return VS_OK;

@@ -42,6 +42,17 @@ class vs_site_job(ctypes.Structure):
                 ("n_chosen", ctypes.c_void_p)]
 
 
+class vs_vix_job(ctypes.Structure):
+    _fields_ = [("g", vs_grid), ("R", ctypes.c_int32), ("ht", ctypes.c_int32), ("hr", ctypes.c_int32),
+                ("S", ctypes.c_int32), ("seed", ctypes.c_uint64), ("vix_out", ctypes.c_void_p)]
+
+
+class vs_findmax_job(ctypes.Structure):
+    _fields_ = [("vix", ctypes.c_void_p), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("k", ctypes.c_int32), ("cand_out", ctypes.c_void_p),
+                ("cap", ctypes.c_int64)]
+
+
 class vs_site_options(ctypes.Structure):
     _fields_ = [("terrain", vs_grid), ("ht", ctypes.c_int32), ("weight", ctypes.c_void_p)]
 
@@ -77,6 +88,9 @@ SIGNATURES = {
     "vs_viewshed_r3": (ctypes.c_int, [vs_grid, i32, i32, i32, P, i64, P, P, P, sz, P]),
     "vs_exact_vix_workspace": (sz, [i32, i32, i32, i64]),
     "vs_exact_vix": (ctypes.c_int, [vs_grid, i32, i32, i32, P, i64, P, P, sz, P]),
+    "vs_vix_batch_workspace": (sz, [i32]),
+    "vs_vix_batch": (ctypes.c_int, [P, i32, P, sz, P]),
+    "vs_findmax_batch": (ctypes.c_int, [P, i32, P]),
     "vs_site_shard_workspace": (sz, [i32]),
     "vs_site_shard_step": (ctypes.c_int, [P, P, i64, i32, i32, i32, P, P, P, i64, i64, P, P, sz, P]),
     "vs_site_workspace": (sz, [i64, i32]),
@@ -462,6 +476,32 @@ def tune_set(op, R, value):
 
 def tune_get(op, R):
     return lib().vs_tune_get(op, R)
+
+
+def vix_batch(jobs, ws):
+    """jobs: list of dicts (g, R, ht, hr, S, seed, out) -> one persistent launch."""
+    arr = (vs_vix_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        _need_cuda(j["out"])
+        arr[i].g = j["g"].c()
+        arr[i].R, arr[i].ht, arr[i].hr, arr[i].S = j["R"], j["ht"], j["hr"], j["S"]
+        arr[i].seed = j["seed"] % (1 << 64)
+        arr[i].vix_out = j["out"].data_ptr()
+    _check("vs_vix_batch", lib().vs_vix_batch(ctypes.cast(arr, ctypes.c_void_p), len(jobs), _ptr(ws),
+                                              ws.numel(), _stream()))
+
+
+def findmax_batch(jobs):
+    """jobs: list of dicts (vix (H x W uint8), block, k, out) -> one launch."""
+    arr = (vs_findmax_job * len(jobs))()
+    for i, j in enumerate(jobs):
+        _need_cuda(j["vix"], j["out"])
+        H, W = j["vix"].shape
+        arr[i].vix = j["vix"].data_ptr()
+        arr[i].H, arr[i].W, arr[i].block, arr[i].k = H, W, j["block"], j["k"]
+        arr[i].cand_out = j["out"].data_ptr()
+        arr[i].cap = j["out"].numel()
+    _check("vs_findmax_batch", lib().vs_findmax_batch(ctypes.cast(arr, ctypes.c_void_p), len(jobs), _stream()))
 
 
 def viewshed_batch(jobs, ws):

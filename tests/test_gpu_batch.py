@@ -1,6 +1,8 @@
-"""Batched multi-terrain siting (one persistent viewshed launch, one site
-launch, the whole sequence captured in a CUDA graph) against the oracle run
-terrain by terrain, and the autotuner's launch shapes leaving results
+"""Batched multi-terrain siting (one persistent vix launch, one findmax
+launch, one persistent viewshed launch, the greedy problems' preparation in
+six launches and their loops in one, the whole sequence captured in a CUDA
+graph) against the oracle run terrain by terrain; the launch count does not
+grow with the number of terrains; the autotuner's launch shapes leave results
 unchanged."""
 import numpy as np
 import pytest
@@ -43,12 +45,13 @@ def _oracle(O, z, it):
     bm, area = O.viewshed(z, it["R"], it["ht"], it["hr"], cand, threads=8)
     H, W = z.shape
     ch, gn, C = O.site(bm, cand, H, W, it["R"], it["n_obs"])
-    return cand, bm, ch, gn, C
+    return v, cand, bm, ch, gn, C
 
 
 def _check(V, O, bs, zs):
     for it, z, b, (ch, gn, C) in zip(bs.inst, zs, bs.bufs, bs.results()):
-        cand, bm, och, ogn, oC = _oracle(O, z, it)
+        v, cand, bm, och, ogn, oC = _oracle(O, z, it)
+        assert (b["vix"].cpu().numpy() == v).all()
         assert b["cand"].cpu().numpy().tolist() == cand.tolist()
         assert (b["bm"].cpu().numpy().view(np.uint32) == bm).all()
         assert ch.cpu().numpy().tolist() == och.tolist()
@@ -92,3 +95,47 @@ def test_autotuner_keeps_results(V):
     assert best in (128, 256, 512) and V.tune_get(V.VS_TUNE_VIEWSHED_THREADS, 30) == best
     V.tune_set(V.VS_TUNE_VIEWSHED_THREADS, 30, 0)
     V.tune_set(V.VS_TUNE_VIX_TILE, 30, 0)
+
+
+def test_batch_launch_count_is_constant(V):
+    """One siting of 3 terrains and of 6 terrains issue the same number of launches."""
+    from paper_2006_16783_gb300.batch import BatchedSiting
+    inst, _ = _instances(V)
+    counts = []
+    for m in (3, 6):
+        bs = BatchedSiting(inst[:m])
+        bs.run()
+        torch.cuda.synchronize()
+        c0 = V.launch_count()
+        bs.run()
+        counts.append(V.launch_count() - c0)
+    assert counts[0] == counts[1] <= 10, counts
+
+
+def test_site_batch_global_gains_job(V, O):
+    """A job whose gains exceed one CTA's shared memory (55,000 candidates)
+    runs inside the batched launch with its gains in global memory, beside a
+    small job with a coverage stop; both equal the oracle."""
+    H, W = 400, 380
+    jobs, want = [], []
+    for n, R, seed, target in ((55000, 3, 1, 0.0), (700, 12, 2, 0.3)):
+        z = T.spectral_fbm(H, W, 0.8, 90 + seed, 0, 600).numpy()
+        rng = np.random.default_rng(seed)
+        cand = rng.choice(H * W, n, replace=False).astype(np.int64)
+        bm, _ = O.viewshed(z, R, 10, 10, cand, threads=8)
+        want.append(O.site(bm, cand, H, W, R, 400, target=target))
+        jobs.append({"bm": torch.as_tensor(bm.view(np.int32)).cuda(), "cand": torch.as_tensor(cand).cuda(),
+                     "H": H, "W": W, "R": R, "n_obs": 400, "target": target,
+                     "chosen": torch.empty(400, dtype=torch.int64, device="cuda"),
+                     "gains": torch.empty(400, dtype=torch.int64, device="cuda"),
+                     "cum": torch.zeros((H, (W + 31) // 32), dtype=torch.int32, device="cuda"),
+                     "n_chosen": torch.zeros(1, dtype=torch.int32, device="cuda")})
+    ws = torch.empty(V.site_batch_workspace(jobs), dtype=torch.uint8, device="cuda")
+    V.site_batch(jobs, ws)
+    torch.cuda.synchronize()
+    for j, (ch, gn, C) in zip(jobs, want):
+        t = int(j["n_chosen"].item())
+        assert t == len(ch)
+        assert j["chosen"][:t].cpu().numpy().tolist() == ch.tolist()
+        assert j["gains"][:t].cpu().numpy().tolist() == gn.tolist()
+        assert (j["cum"].cpu().numpy().view(np.uint32) == C).all()

@@ -165,3 +165,35 @@ def test_scale_pipeline_full_size(V, O):
     w = WL.SCALE
     g, zh = _terrain(V, w)
     _plain(V, O, w, g, zh)
+
+
+def test_batch_pipeline_full_size(V, O):
+    """The 64-terrain batched workload at its full sizes through BatchedSiting
+    (the bench's launch configuration): per terrain the vix map on 300
+    sampled posts, findmax over the whole map, and the greedy (observers,
+    gains, cumulative viewshed) against the oracle on the pipeline's bitmaps
+    (whose viewsheds test_batch_full_size_sampled checks)."""
+    from paper_2006_16783_gb300.batch import BatchedSiting
+    ws_ = WL.batch_instances()
+    inst, zs = [], []
+    for w in ws_:
+        z = w.make_terrain("cuda")
+        g = V.Grid.from_tensor(z, "cuda")
+        inst.append({"grid": g, "R": w.R, "ht": w.ht, "hr": w.hr, "S": w.S, "seed": w.vix_seed,
+                     "block": w.block, "k": w.k, "n_obs": w.n_obs})
+        zs.append(z.cpu().numpy())
+        del z
+    bs = BatchedSiting(inst)
+    bs.run()
+    torch.cuda.synchronize()
+    for w, it, zh, b, (ch, gn, C) in zip(ws_, inst, zs, bs.bufs, bs.results()):
+        v = b["vix"].cpu().numpy()
+        posts = _seeded_posts(w.H, w.W, 300, 7)
+        assert (v.reshape(-1)[posts] == O.vix_posts(zh, w.R, w.ht, w.hr, w.S, w.vix_seed, posts)).all(), w.name
+        cand = O.findmax(v, w.block, w.k)
+        assert b["cand"].cpu().numpy().tolist() == cand.tolist(), w.name
+        bm = b["bm"].cpu().numpy().view(np.uint32)
+        och, ogn, oC = O.site(bm, cand, w.H, w.W, w.R, w.n_obs)
+        assert ch.cpu().numpy().tolist() == och.tolist(), w.name
+        assert gn.cpu().numpy().tolist() == ogn.tolist(), w.name
+        assert (C.cpu().numpy().view(np.uint32) == oC).all(), w.name
