@@ -14,29 +14,36 @@
 //   global average pool -> fc 32->1 -> sigmoid
 //
 // Forward kernel: one persistent 512-thread CTA per SM works through patches
-// entirely in shared memory, its warps split into roles (epilogue, front end,
-// MMA issue; see the role table below) that hand work to each other through
-// mbarriers.  Every convolution is an implicit GEMM on the 5th-generation
-// tensor cores: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32), M = 128 output
-// pixels, N = 32 channels, K = 16 per instruction, the FP32 accumulator in
-// tensor memory (32 columns per tile), read back with tcgen05.ld for the
-// bias + ReLU + BF16 epilogue.  Operands are read straight from shared
-// memory through matrix descriptors (no swizzle, K-major 8x16-byte core
-// matrices):
-//   * A stride-2 layer's input is stored as four parity planes (even/odd row
-//     x even/odd column) in blocks of 8 channels, each plane with a zero
-//     border row/column and a row pitch of (output width + 1) pixels.  For
-//     output pixel m = y*pitch + x, tap (ky,kx) reads plane
+// entirely on chip, its warps split into roles (conv1 group, conv2..5 group,
+// front end, MMA issue; see the role table below) that hand work to each
+// other through mbarriers, with two patches in flight: the conv1 group and
+// the conv1/conv2 MMAs of patch k+1 run beside the conv3..5 chain of patch k,
+// whose MMAs the conv2..5 group issues itself (two MMA issuers share the
+// tensor core).
+// Every convolution is an implicit GEMM on the 5th-generation tensor cores:
+// tcgen05.mma kind::f16 (BF16 x BF16 -> FP32), M = 128 output pixels,
+// N = 32 channels, K = 16 per instruction, the FP32 accumulator in tensor
+// memory (32 columns per tile), read back with tcgen05.ld for the bias +
+// ReLU + BF16 epilogue.  Operands:
+//   * A stride-2 layer's input is stored in shared memory as four parity
+//     planes (even/odd row x even/odd column) in blocks of 8 channels, each
+//     plane with a zero border row/column and a row pitch of (output width
+//     + 1) pixels.  For output pixel m = y*pitch + x, tap (ky,kx) reads plane
 //     (ky != 1, kx != 1) at m + (ky != 0)*pitch + (kx != 0): every tap of a
 //     128-pixel tile is one contiguous run of 16-byte rows, i.e. a plain
-//     descriptor (leading offset = next 8-channel block, stride offset =
-//     next 8 pixels).  The one junk column per row is discarded.
+//     matrix descriptor (no swizzle, K-major 8x16-byte core matrices; leading
+//     offset = next 8-channel block, stride offset = next 8 pixels).  The one
+//     junk column per row is discarded.
 //   * The stride-1 last layer uses one plane with a border on all sides.
-//   * The 1-channel first layer uses an explicit im2col tile (K = 9 taps
-//     padded to 16).
-// At N = 32 an MMA costs a fixed ~46 cycles whatever N <= 64 (measured), so
-// the 117 MMAs of a patch bound the kernel at ~6K cycles per patch and SM;
-// the rest of a patch's chain is epilogue and hand-off latency.
+//   * The 1-channel first layer takes A from tensor memory: the conv1 group
+//     writes each output pixel's 9 taps (K padded to 16) into its TMEM lane
+//     with tcgen05.st, so the im2col tile needs no shared memory.
+//   * B (the weights) always comes from shared memory.
+// At N = 32 an MMA with A in shared memory costs ~46 cycles whatever N <= 64
+// (measured): it is bound by the shared-memory operand reads, so the 108
+// MMAs of conv2..5 bound the kernel at ~5K cycles per patch and SM; the rest
+// of a patch's time is the epilogue / hand-off latency of the conv3..5 chain,
+// which the second patch in flight overlaps.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -61,31 +68,34 @@ constexpr int kPackedBytes = kPkFc + 36 * 4;
 // ---- shared-memory plan of the forward kernel (bytes, 128-aligned)
 constexpr int kPln2 = 18 * 18, kPln3 = 10 * 10, kPln4 = 6 * 6, kPln5 = 7 * 7;
 constexpr int kSmW = 0;
-constexpr int kSmP2 = ((kSmW + kPackedBytes) + 127) & ~127;
+constexpr int kSmP2 = ((kSmW + kPackedBytes) + 127) & ~127;  // conv2 input planes
 constexpr int kP2Bytes = (16 * kPln2 + 96) * 16;
-constexpr int kSmU = ((kSmP2 + kP2Bytes) + 127) & ~127;  // conv1 im2col tile
-constexpr int kA1Bytes = 1152 * 32;
-constexpr int kUBytes = kA1Bytes;
-// conv3..5 inputs reuse the start of the conv2 input region (dead once every
-// conv2 MMA has completed)
+// conv3..5 input planes, each followed by the cells that the last taps'
+// descriptors run over (read as zero, never written)
+constexpr int kSmP345 = ((kSmP2 + kP2Bytes) + 127) & ~127;
 constexpr int kP3Off = 0, kP3Bytes = (16 * kPln3 + 40) * 16;
 constexpr int kP4Off = kP3Off + kP3Bytes, kP4Bytes = (16 * kPln4 + 104) * 16;
 constexpr int kP5Off = kP4Off + kP4Bytes, kP5Bytes = (4 * kPln5 + 100) * 16;
 constexpr int kP345Bytes = kP5Off + kP5Bytes;
-static_assert(kP345Bytes <= kP2Bytes, "conv3..5 planes must fit in the conv2 input region");
-constexpr int kSmPatch = ((kSmU + kUBytes) + 127) & ~127;   // 67x67 bf16, zero border
+constexpr int kSmPatch = ((kSmP345 + kP345Bytes) + 127) & ~127;  // 67x67 bf16, zero border
 constexpr int kPatchBytes = ((67 * 67 * 2) + 127) & ~127;
-constexpr int kSmGap = kSmPatch + kPatchBytes;              // 25 x 32 floats
-constexpr int kSmStage = ((kSmGap + 25 * 32 * 4) + 127) & ~127;  // TMA-staged patch
-constexpr int kStageW = 72;                                  // 65 columns + 8-alignment slack
+constexpr int kNGap = 3;  // pooling buffers (ring), each [32 channels][25 pixels] fp32
+constexpr int kGapBytes = 25 * 32 * 4;
+constexpr int kSmGap = kSmPatch + kPatchBytes;
+constexpr int kSmStage = ((kSmGap + kNGap * kGapBytes) + 127) & ~127;  // TMA-staged patch
+constexpr int kStageW = 72;                                   // 65 columns + 8-alignment slack
 constexpr int kStageBytes = ((kPatch * kStageW * 2) + 127) & ~127;
 constexpr int kSmEnd = kSmStage + kStageBytes;
-constexpr int kSmemBytes = kSmEnd + 128;                    // + base alignment slack
+constexpr int kSmemBytes = kSmEnd + 128;                     // + base alignment slack
+static_assert(kSmemBytes + 512 <= kSmemLimit, "forward plan exceeds shared memory");
 
-// instruction descriptor: kind::f16, A = B = BF16, D = F32, K-major A and B,
-// N = 32, M = 128
+// instruction descriptors: kind::f16, A = B = BF16, D = F32, K-major A and
+// B, N = 32, M = 128 or 64.  An M = 64 tile's row r lands in TMEM lane
+// 32 * (r / 16) + r % 16 (lanes 0..15 of each quarter).
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) |
                             ((128u >> 4) << 24);
+constexpr uint32_t kIdesc64 = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) |
+                              ((64u >> 4) << 24);
 
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
@@ -202,42 +212,58 @@ __device__ __forceinline__ bool patch_inside(const FwdParams &P, int cy, int cx)
 }
 
 // ---- warp roles of the forward kernel (16 warps)
-//   warps 0..7   epilogue: TMEM -> bias + ReLU + bf16 -> the next layer's
-//                planes, and the pooling buffer (thread: one accumulator row,
-//                16 channels)
-//   warps 8..14  front: a later patch's posts, mean, normalisation and
-//                im2col, and the head (pool, fc, sigmoid) of an earlier one
-//   warp 15      MMA issue (one lane)
-// so the front end and the head run beside the chain conv1 epilogue -> conv2
-// -> epilogue -> conv3 -> ... -> conv5 epilogue, which alternates between the
-// tensor core and the epilogue warps.
-constexpr int kEpiWarps = 8, kFrontWarps = 7, kMmaWarp = kEpiWarps + kFrontWarps;
-constexpr int kEpiThreads = kEpiWarps * 32, kFrontThreads = kFrontWarps * 32;
+//   warps 0..3   conv1 group: patch k's conv1 operand (im2col: 9 taps of an
+//                output pixel into its TMEM lane) and conv1 epilogue (TMEM ->
+//                bias + ReLU + bf16 -> conv2 input planes); thread: one
+//                accumulator row, 32 channels
+//   warps 4..7   conv2..5 group: the conv2 epilogue, then conv3, conv4 and
+//                conv5 (their MMAs issued by one thread of the group once
+//                the group has written the layer's input) and epilogues
+//                (-> conv3, conv4, conv5 input planes, pooling buffer);
+//                thread: one accumulator row, 32 channels
+//   warps 8..14  front: a later patch's posts, mean and normalisation, and
+//                the head (pool, fc, sigmoid) of an earlier one
+//   warp 15      MMA issue (one lane): conv1 and conv2 of each patch, so
+//                that they run beside the conv3..5 chain of the patch before
+constexpr int kAWarps = 4, kBWarps = 4, kFrontWarps = 7;
+constexpr int kBWarp0 = kAWarps, kFrontWarp0 = kAWarps + kBWarps, kMmaWarp = kFrontWarp0 + kFrontWarps;
+constexpr int kAThreads = kAWarps * 32, kBThreads = kBWarps * 32, kFrontThreads = kFrontWarps * 32;
+constexpr int kRowsFront = (kPatch + kFrontWarps - 1) / kFrontWarps;  // window rows per front warp
 static_assert((kMmaWarp + 1) * 32 == kThreads, "role split must cover the CTA");
-constexpr int kPerFront = (kPatch * kPatch + kFrontThreads - 1) / kFrontThreads;  // posts per front thread
-constexpr int kRowsFront = (1152 + kFrontThreads - 1) / kFrontThreads;           // im2col rows per front thread
+static_assert(kAWarps == 4 && kBWarps == 4, "TMEM lane quarters: warp w reads lanes 32*(w%4)..+31");
 
-// Tensor memory: every accumulator tile of a patch has its own 32 columns
-// (conv1 tiles 0..8, conv2 tiles 0..2, conv3, conv4, conv5: 15 x 32 = 480 of
-// the 512 columns).
+// Tensor memory (512 columns): conv1 tiles 0..8, conv2 tiles 0..2 and one
+// tile that conv3, conv4 and conv5 take in turn (32 FP32 columns each), and
+// the conv1 A operand (8 columns of bf16 pairs per tile).
 constexpr int kTmemCols = 512;
-constexpr int kColL2 = 9 * 32, kColL3 = 12 * 32, kColL4 = 13 * 32, kColL5 = 14 * 32;
-// mbarriers, each completing once per patch:
-//   tcgen05.commit   conv1 tiles in groups of three, conv2 tiles, conv3, conv4, conv5
-//   front -> MMA     im2col tile written (every front thread arrives)
-//   epilogue -> MMA  conv1 accumulators read; conv1 tiles 0..5 written (all
-//                    that conv2's first tile reads); every conv2 input plane
-//                    written; conv3, conv4, conv5 input planes written
-//   epilogue -> front  pooling buffer written (every epilogue thread arrives)
-//   front -> epilogue  pooling buffer read (one head warp arrives)
+constexpr int kColL2 = 9 * 32, kColL345 = 12 * 32, kColA1 = 13 * 32;
+static_assert(kColA1 + 9 * 8 <= kTmemCols, "tensor memory plan");
+// mbarriers, each completing once per patch (the pooling ring: once per
+// kNGap patches):
+//   tcgen05.commit     conv1 tiles in groups of three, conv2 tiles, conv3,
+//                      conv4, conv5
+//   conv1 group ->     conv1 operand written (MMA); conv1 accumulators read
+//                      (MMA); conv1 tiles 0..5 written, i.e. every input row
+//                      conv2's first tile reads (MMA); every conv2 input plane
+//                      written (MMA); patch buffer read (front)
+//   conv2..5 group ->  conv2 accumulators read (MMA); pooling buffer
+//                      written (head)
+//   front ->           normalised patch written (conv1 group)
+//   head ->            pooling buffer read (conv2..5 group)
 enum {
     kBarC1 = 0, kBarC2 = 3, kBarC3 = 6, kBarC4 = 7, kBarC5 = 8,
-    kBarURdy = 9, kBarC1Free = 10, kBarP2a = 11, kBarP2 = 12, kBarP3 = 13, kBarP4 = 14, kBarP5 = 15,
-    kBarGap = 16, kBarGapFree = 17,
-    kNBar = 18
+    kBarARdy = 9, kBarC1Free = 10, kBarP2a = 11, kBarP2 = 12, kBarPbFree = 13,
+    kBarC2Free = 14,
+    kBarGapFull = 15, kBarGapFree = kBarGapFull + kNGap, kBarPbRdy = kBarGapFree + kNGap,
+    kNBar = kBarPbRdy + 1
 };
+// (arrivals: one per warp of the producing group, after a __syncwarp)
 __host__ __device__ constexpr uint32_t bar_count(int b) {
-    return b == kBarURdy ? kFrontThreads : b == kBarGapFree ? 32 : b >= kBarC1Free ? kEpiThreads : 1;
+    return b < kBarARdy ? 1u
+           : b <= kBarPbFree ? (uint32_t)kAWarps
+           : b < kBarGapFree ? (uint32_t)kBWarps
+           : b < kBarPbRdy ? 1u
+                           : (uint32_t)kFrontWarps;
 }
 
 __device__ __forceinline__ void group_sync(int id, int n) {
@@ -258,24 +284,35 @@ __device__ __forceinline__ bool group_any(int id, int n, bool v) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// non-suspending bounded wait (the MMA lane wakes as soon as the phase flips)
-__device__ __forceinline__ bool mbar_wait_spin(uint64_t *bar, uint32_t parity) {
-    const uint32_t addr = smem_u32(bar);
-    for (uint32_t i = 0; i < kWaitPolls; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
+// One arrival for the whole warp, after every lane's earlier writes and
+// fences (the warp barrier orders them before lane 0's release).
+__device__ __forceinline__ void warp_arrive(uint64_t *bar) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
 }
-// 16 consecutive FP32 accumulator columns of this thread's TMEM lane, for one
-// or three tiles, with one wait
+// Lane 0 waits (bounded) and the warp continues together: the warp barrier
+// orders lane 0's acquire before every lane's later reads (and, after a
+// tcgen05.fence::after_thread_sync, before its tensor-memory loads).
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity) ? 1 : 0;
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+// one non-blocking look: has the barrier completed the phase of this parity?
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// 16 or 32 consecutive FP32 accumulator columns of this thread's TMEM lane,
+// with one wait
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     uint32_t r[16];
     asm volatile(
@@ -288,59 +325,69 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-__device__ __forceinline__ void tmem_ld16x3(uint32_t t0, uint32_t t1, uint32_t t2, float (*v)[16]) {
-    uint32_t r[48];
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
 #define VS_R16(o) "=r"(r[o + 0]), "=r"(r[o + 1]), "=r"(r[o + 2]), "=r"(r[o + 3]), "=r"(r[o + 4]), \
     "=r"(r[o + 5]), "=r"(r[o + 6]), "=r"(r[o + 7]), "=r"(r[o + 8]), "=r"(r[o + 9]), "=r"(r[o + 10]), \
     "=r"(r[o + 11]), "=r"(r[o + 12]), "=r"(r[o + 13]), "=r"(r[o + 14]), "=r"(r[o + 15])
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%48];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%49];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%50];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
-        : VS_R16(0), VS_R16(16), VS_R16(32)
-        : "r"(t0), "r"(t1), "r"(t2)
+        : VS_R16(0), VS_R16(16)
+        : "r"(taddr)
         : "memory");
 #undef VS_R16
 #pragma unroll
-    for (int i = 0; i < 48; ++i) v[i / 16][i % 16] = __uint_as_float(r[i]);
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
-// tensor-core MMA with a compile-time accumulate flag
-template <int ACC>
-__device__ __forceinline__ void umma_c(uint32_t dt, uint64_t ad, uint64_t bd) {
+// 8 consecutive 32-bit columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *w) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                 "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// tensor-core MMA, A from shared memory; acc = 0 overwrites the accumulator
+__device__ __forceinline__ void umma_s(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
-        "l"(ad), "l"(bd), "r"(kIdesc), "n"(ACC));
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
-
-// The conv3..5 input planes overwrite the start of the conv2 input planes
-// (kP345Bytes / 16 = 2616 sixteen-byte cells).  Cells no epilogue writes --
-// borders, the extra row/column of odd parity planes, tails -- must read as
-// zero, so each layer switch clears exactly those: p345_unwritten(u) for the
-// conv3..5 planes, p2_unwritten(u) for the conv2 planes.  They are disjoint
-// from the cells the epilogues write, so clearing needs no ordering against
-// the epilogue stores.
-__device__ __forceinline__ bool planes_written(int cell, int pitch, int rows_even, int pb) {
-    const int r = cell / pitch, c = cell - r * pitch;
-    const int py = (pb >> 1) & 1, px = pb & 1;  // parity plane of plane block pb
-    return r >= 1 && r <= rows_even - py && c >= 1 && c <= rows_even - px;
-}
-__device__ __forceinline__ bool p345_unwritten(int u) {
-    if (u < 16 * kPln3) return !planes_written(u % kPln3, 10, 9, u / kPln3);
-    u -= kP3Bytes / 16;
-    if (u < 0) return true;
-    if (u < 16 * kPln4) return !planes_written(u % kPln4, 6, 5, u / kPln4);
-    u -= kP4Bytes / 16;
-    if (u < 0) return true;
-    if (u < 4 * kPln5) {
-        const int c = u % kPln5, r = c / 7, x = c % 7;
-        return !(r >= 1 && r <= 5 && x >= 1 && x <= 5);
+// A 32->32 stride-2 layer's tile: 9 taps x 2 K-steps reading parity planes
+// (descriptor bases dA, dB; an operand at byte offset o from a base adds o >> 4
+// to the address field -- shared addresses stay below 2^18 bytes)
+__device__ __forceinline__ void conv_tile(uint32_t dt, uint64_t dA, uint64_t dB, int pln, int pitch, int m0, int l,
+                                          uint32_t idesc) {
+#pragma unroll
+    for (int i = 0; i < 18; ++i) {
+        const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t - 3 * ky;
+        const int plane = ((ky != 1) << 1) | (kx != 1);
+        const int shift = (ky != 0 ? pitch : 0) + (kx != 0 ? 1 : 0);
+        const uint64_t ad = dA + (uint64_t)((2 * ks * 4 + plane) * pln + m0 + shift);
+        const uint64_t bd = dB + (uint64_t)((pk_bl(l) + (t * 2 + ks) * 1024) >> 4);
+        umma_s(dt, ad, bd, idesc, (uint32_t)i);
     }
-    return true;
 }
-__device__ __forceinline__ bool p2_unwritten(int u) { return !planes_written(u % kPln2, 18, 17, u / kPln2); }
-constexpr int kP345Cells = kP345Bytes / 16;
+// conv5 (stride 1): one plane with a full border, input pitch 7
+__device__ __forceinline__ void conv5_tile(uint32_t dt, uint64_t dA5, uint64_t dB, uint32_t idesc) {
+#pragma unroll
+    for (int i = 0; i < 18; ++i) {
+        const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t - 3 * ky;
+        const uint64_t ad = dA5 + (uint64_t)((2 * ks) * kPln5 + ky * 7 + kx);
+        const uint64_t bd = dB + (uint64_t)((pk_bl(4) + (t * 2 + ks) * 1024) >> 4);
+        umma_s(dt, ad, bd, idesc, (uint32_t)i);
+    }
+}
+// tensor-core MMA, A from tensor memory (lane m = row m, K in bf16 pairs),
+// overwriting the accumulator
+__device__ __forceinline__ void umma_t0(uint32_t dt, uint32_t at, uint64_t bd) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(dt),
+        "r"(at), "l"(bd), "r"(kIdesc), "n"(0));
+}
 
 __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_constant__ CUtensorMap tmap,
                                                              const FwdParams P) {
@@ -354,17 +401,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     unsigned char *Wp = sm + kSmW;
-    unsigned char *X = sm + kSmP2;  // conv2 input planes, then conv3..5 input planes
-    unsigned char *U = sm + kSmU;
+    unsigned char *X2 = sm + kSmP2;      // conv2 input planes
+    unsigned char *X345 = sm + kSmP345;  // conv3, conv4, conv5 input planes
     __nv_bfloat16 *pb = (__nv_bfloat16 *)(sm + kSmPatch);
     float *gap = (float *)(sm + kSmGap);
     int16_t *stage = (int16_t *)(sm + kSmStage);
 
-    // ---- one-time set-up: weights, zeroed planes, barriers, tensor memory
+    // ---- one-time set-up: weights; zeroed planes and patch buffer (their
+    // borders are never written); barriers; tensor memory
     for (int i = tid; i < kPackedBytes / 16; i += kThreads)
         ((uint4 *)Wp)[i] = ((const uint4 *)P.packed)[i];
-    for (int i = tid; i < kP2Bytes / 16; i += kThreads) ((uint4 *)X)[i] = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < kPatchBytes / 16; i += kThreads) ((uint4 *)pb)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < (kSmGap - kSmP2) / 16; i += kThreads) ((uint4 *)X2)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         for (int b = 0; b < kNBar; ++b) mbar_init(&bar[b], bar_count(b));
         mbar_init(&pbar, 1);
@@ -384,189 +431,249 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
     const long long nk = (P.n - blockIdx.x + gridDim.x - 1) / gridDim.x;  // patches of this CTA
     volatile int *abort_flag = &s_abort;
 
-    if (warp < kEpiWarps) {
-        // ================================================================ epilogue
-        const int row = 32 * (warp & 3) + lane;  // accumulator row (TMEM lane)
-        const int half = warp >> 2;              // channels 16*half .. +15 (blocks 2h, 2h+1)
-        const uint32_t tq = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * half);
-        unsigned char *P3 = X + kP3Off, *P4 = X + kP4Off, *P5 = X + kP5Off;
-        const float *bias = (const float *)(Wp + kPkBias);
-        // destinations (16-byte units) of this thread's rows for channel block
-        // 2*half; block 2*half+1 is one plane set further; -1: junk row
-        int d1[9], d2[3], d3, d4, d5;
+    if (warp < kBWarp0) {
+        // ================================================================ conv1 group
+        const int row = 32 * warp + lane;                          // TMEM lane
+        const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's lane quarter
+        float b1[32];  // conv1 bias, held for the whole launch
 #pragma unroll
-        for (int mt = 0; mt < 9; ++mt) {
-            const int m = mt * 128 + row, y = m / 34, x = m % 34;
-            d1[mt] = (y < 33 && x < 33)
-                         ? (2 * half * 4 + (((y & 1) << 1) | (x & 1))) * kPln2 + ((y >> 1) + 1) * 18 + (x >> 1) + 1
-                         : -1;
+        for (int c = 0; c < 32; c += 4) {
+            const float4 v = *(const float4 *)(Wp + kPkBias + 4 * c);
+            b1[c] = v.x;
+            b1[c + 1] = v.y;
+            b1[c + 2] = v.z;
+            b1[c + 3] = v.w;
         }
-#pragma unroll
-        for (int mt = 0; mt < 3; ++mt) {
-            const int m = mt * 128 + row, y = m / 18, x = m % 18;
-            d2[mt] = (y < 17 && x < 17)
-                         ? (2 * half * 4 + (((y & 1) << 1) | (x & 1))) * kPln3 + ((y >> 1) + 1) * 10 + (x >> 1) + 1
-                         : -1;
-        }
-        {
-            int y = row / 10, x = row % 10;
-            d3 = (y < 9 && x < 9)
-                     ? (2 * half * 4 + (((y & 1) << 1) | (x & 1))) * kPln4 + ((y >> 1) + 1) * 6 + (x >> 1) + 1
-                     : -1;
-            y = row / 6; x = row % 6;
-            d4 = (y < 5 && x < 5) ? 2 * half * kPln5 + (y + 1) * 7 + (x + 1) : -1;
-            y = row / 7; x = row % 7;
-            d5 = (y < 5 && x < 5) ? y * 5 + x : -1;
-        }
-        auto load_bias = [&](int l, float *b) {
-#pragma unroll
-            for (int c = 0; c < 16; ++c) b[c] = bias[32 * l + 16 * half + c];
-        };
-        auto put2 = [&](unsigned char *base, int d, int next, uint4 lo, uint4 hi) {
-            *(uint4 *)(base + (long long)d * 16) = lo;
-            *(uint4 *)(base + (long long)(d + next) * 16) = hi;
-        };
-        auto save2 = [&](unsigned char *sv, int off, int pix, uint4 lo, uint4 hi) {
-            unsigned char *o = sv + off + pix * 64 + half * 32;
-            *(uint4 *)o = lo;
-            *(uint4 *)(o + 16) = hi;
-        };
-        // this thread's cells u = tid + 256 i of the overlapped region that a
-        // layer switch clears (bit i)
-        constexpr int kCellIters = (kP345Cells + kEpiThreads - 1) / kEpiThreads;
-        uint32_t clr345 = 0u, clr2 = 0u;
-#pragma unroll
-        for (int i = 0; i < kCellIters; ++i) {
-            const int u = tid + i * kEpiThreads;
-            if (u < kP345Cells) {
-                clr345 |= (uint32_t)p345_unwritten(u) << i;
-                clr2 |= (uint32_t)p2_unwritten(u) << i;
-            }
-        }
-        auto clear_cells = [&](uint32_t mask) {
-#pragma unroll
-            for (int i = 0; i < kCellIters; ++i)
-                if ((mask >> i) & 1u) ((uint4 *)X)[tid + i * kEpiThreads] = make_uint4(0, 0, 0, 0);
-        };
+        const unsigned short *pbu = (const unsigned short *)pb;
         bool ok = true;
-        float bl[16], acc[16];
         for (long long k = 0; k < nk; ++k) {
-            // a timed-out wait anywhere stops every epilogue thread here, together
-            if (group_any(1, kEpiThreads, !ok || *abort_flag)) {
+            // a timed-out wait anywhere stops every thread of the group here, together
+            if (group_any(1, kAThreads, !ok || *abort_flag)) {
                 ok = false;
                 break;
             }
             const uint32_t ph = (uint32_t)(k & 1);
             const long long pi = blockIdx.x + k * gridDim.x;
             unsigned char *sv = P.save ? P.save + pi * (long long)kSaveBytesTotal : nullptr;
-            // ---- conv1 epilogue -> conv2 input planes, three tiles per wait
-            load_bias(0, bl);
+            // ---- conv1 operand: output pixel m = 34 y + x takes at K = 3 ky + kx
+            // the input x0[2y - 1 + ky][2x - 1 + kx] (the patch buffer has a
+            // zero border: x0[r][c] is pb[(r + 1) * 67 + c + 1]).  The conv1
+            // MMAs of patch k - 1, which read these columns, have completed:
+            // this group waited for them before its epilogue.
+            ok &= warp_wait(&bar[kBarPbRdy], ph);
+            tc_fence_after();
+#pragma unroll 1
+            for (int mt = 0; mt < 9; ++mt) {
+                const int m = mt * 128 + row, y = m / 34, x = m - 34 * y;
+                const bool live = y < 33 && x < 33;
+                const unsigned short *src = pbu + (2 * y) * 67 + 2 * x;
+                uint32_t t[9];
 #pragma unroll
+                for (int q = 0; q < 9; ++q) t[q] = live ? (uint32_t)src[(q / 3) * 67 + (q % 3)] : 0u;
+                uint32_t w[8];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) w[q] = t[2 * q] | (t[2 * q + 1] << 16);
+                w[4] = t[8];
+                w[5] = w[6] = w[7] = 0u;
+                tmem_st8(tl + (uint32_t)(kColA1 + 8 * mt), w);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            warp_arrive(&bar[kBarARdy]);
+            if (lane == 0) mbar_arrive(&bar[kBarPbFree]);
+            // ---- conv1 epilogue -> conv2 input planes, three tiles per
+            // commit.  Group g writes plane rows 1..6, 6..12, 12..17; conv2
+            // tile t of the previous patch reads (for its valid pixels) plane
+            // rows 0..8, 7..15, 14..17, so group g waits for tile g of patch
+            // k - 1 (commits complete in order).
+#pragma unroll 1
             for (int g = 0; g < 3; ++g) {
-                ok &= mbar_wait(&bar[kBarC1 + g], ph);
+                if (k > 0) ok &= warp_wait(&bar[kBarC2 + g], ph ^ 1u);
+                ok &= warp_wait(&bar[kBarC1 + g], ph);
                 tc_fence_after();
-                float a3[3][16];
-                tmem_ld16x3(tq + (uint32_t)(96 * g), tq + (uint32_t)(96 * g + 32), tq + (uint32_t)(96 * g + 64), a3);
+#pragma unroll 1
+                for (int mt = 3 * g; mt < 3 * g + 3; ++mt) {
+                    float a[32];
+                    tmem_ld32(tl + (uint32_t)(32 * mt), a);
+                    // conv2 input cell (16-byte unit, channel block 0; block cb
+                    // is 4 cb planes further) of this thread's row; none for a
+                    // junk column or padding row
+                    const int m = mt * 128 + row, y = m / 34, x = m - 34 * y;
+                    if (y < 33 && x < 33) {
+                        const int d = (((y & 1) << 1) | (x & 1)) * kPln2 + ((y >> 1) + 1) * 18 + (x >> 1) + 1;
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const int mt = 3 * g + i;
-                    if (d1[mt] >= 0) {
-                        const uint4 lo = relu_pack8(a3[i], bl), hi = relu_pack8(a3[i] + 8, bl + 8);
-                        put2(X, d1[mt], 4 * kPln2, lo, hi);
-                        if (sv) {
-                            const int m = mt * 128 + row;
-                            save2(sv, kSvA1, (m / 34) * 33 + m % 34, lo, hi);
+                        for (int cb = 0; cb < 4; ++cb) {
+                            const uint4 v = relu_pack8(a + 8 * cb, b1 + 8 * cb);
+                            *(uint4 *)(X2 + (long long)(d + cb * 4 * kPln2) * 16) = v;
+                            if (sv) *(uint4 *)(sv + kSvA1 + (y * 33 + x) * 64 + cb * 16) = v;
                         }
                     }
                 }
                 if (g == 1) {
                     // tiles 0..5 hold every input row that conv2's first tile reads
                     fence_proxy_async_smem();
-                    mbar_arrive(&bar[kBarP2a]);
-                }
-            }
-            tc_fence_before();
-            mbar_arrive(&bar[kBarC1Free]);
-            fence_proxy_async_smem();
-            mbar_arrive(&bar[kBarP2]);
-            // ---- conv2 epilogue: all three tiles read, then the region is
-            // refilled with the conv3 input planes
-            load_bias(1, bl);
-            uint4 o2[3][2];
-#pragma unroll
-            for (int mt = 0; mt < 3; ++mt) {
-                ok &= mbar_wait(&bar[kBarC2 + mt], ph);
-                tc_fence_after();
-                tmem_ld16(tq + (uint32_t)(kColL2 + 32 * mt), acc);
-                o2[mt][0] = relu_pack8(acc, bl);
-                o2[mt][1] = relu_pack8(acc + 8, bl + 8);
-            }
-            clear_cells(clr345);  // conv2 has completed: its input is dead
-#pragma unroll
-            for (int mt = 0; mt < 3; ++mt) {
-                if (d2[mt] >= 0) {
-                    put2(P3, d2[mt], 4 * kPln3, o2[mt][0], o2[mt][1]);
-                    if (sv) {
-                        const int m = mt * 128 + row;
-                        save2(sv, kSvA2, (m / 18) * 17 + m % 18, o2[mt][0], o2[mt][1]);
-                    }
+                    warp_arrive(&bar[kBarP2a]);
                 }
             }
             tc_fence_before();
             fence_proxy_async_smem();
-            mbar_arrive(&bar[kBarP3]);
-            // ---- conv3 epilogue -> conv4 input planes
-            load_bias(2, bl);
-            ok &= mbar_wait(&bar[kBarC3], ph);
-            tc_fence_after();
-            tmem_ld16(tq + (uint32_t)kColL3, acc);
-            if (d3 >= 0) {
-                const uint4 lo = relu_pack8(acc, bl), hi = relu_pack8(acc + 8, bl + 8);
-                put2(P4, d3, 4 * kPln4, lo, hi);
-                if (sv) save2(sv, kSvA3, (row / 10) * 9 + row % 10, lo, hi);
-            }
-            tc_fence_before();
-            fence_proxy_async_smem();
-            mbar_arrive(&bar[kBarP4]);
-            // ---- conv4 epilogue -> conv5 input plane (stride 1)
-            load_bias(3, bl);
-            ok &= mbar_wait(&bar[kBarC4], ph);
-            tc_fence_after();
-            tmem_ld16(tq + (uint32_t)kColL4, acc);
-            if (d4 >= 0) {
-                const uint4 lo = relu_pack8(acc, bl), hi = relu_pack8(acc + 8, bl + 8);
-                put2(P5, d4, kPln5, lo, hi);
-                if (sv) save2(sv, kSvA4, (row / 6) * 5 + row % 6, lo, hi);
-            }
-            tc_fence_before();
-            fence_proxy_async_smem();
-            mbar_arrive(&bar[kBarP5]);
-            // ---- conv5 epilogue -> pooling buffer (once the head has read
-            // the previous patch's)
-            load_bias(4, bl);
-            ok &= mbar_wait(&bar[kBarC5], ph);
-            tc_fence_after();
-            tmem_ld16(tq + (uint32_t)kColL5, acc);
-            tc_fence_before();
-            if (k > 0) ok &= mbar_wait(&bar[kBarGapFree], ph ^ 1u);
-            if (d5 >= 0) {
-                const uint4 lo = relu_pack8(acc, bl), hi = relu_pack8(acc + 8, bl + 8);
-                const __nv_bfloat16 *h0 = (const __nv_bfloat16 *)&lo, *h1 = (const __nv_bfloat16 *)&hi;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    gap[d5 * 32 + 16 * half + c] = __bfloat162float(h0[c]);
-                    gap[d5 * 32 + 16 * half + 8 + c] = __bfloat162float(h1[c]);
-                }
-                if (sv) save2(sv, kSvA5, d5, lo, hi);
-            }
-            mbar_arrive(&bar[kBarGap]);
-            clear_cells(clr2);  // conv5 has completed: the conv3..5 planes are dead
+            warp_arrive(&bar[kBarC1Free]);
+            if (lane == 0) mbar_arrive(&bar[kBarP2]);
         }
         if (!ok) *abort_flag = 1;
         if (!ok && P.status && tid == 0) atomicExch(P.status, VS_ERR_TIMEOUT);
+    } else if (warp < kFrontWarp0) {
+        // ================================================================ conv2..5 group
+        const int wb = warp - kBWarp0;           // lane quarter
+        const int row = 32 * wb + lane;          // accumulator row (TMEM lane)
+        const uint32_t tq = tmem + ((uint32_t)(32 * wb) << 16);
+        unsigned char *P3 = X345 + kP3Off, *P4 = X345 + kP4Off, *P5 = X345 + kP5Off;
+        const float *bias = (const float *)(Wp + kPkBias);
+        // destinations (16-byte units) of this thread's rows for channel
+        // block 0 (block cb is 4 * cb planes further for the parity-plane
+        // layouts, cb planes for conv5's); -1: junk row.  Rows of the M = 64
+        // tiles (conv2 tile 2, conv4, conv5) are 16 * quarter + lane, held by
+        // lanes 0..15.
+        const int row64 = lane < 16 ? 16 * wb + lane : 64;
+        int d3, d4, d5;
+        {
+            int y = row / 10, x = row % 10;
+            d3 = (y < 9 && x < 9) ? (((y & 1) << 1) | (x & 1)) * kPln4 + ((y >> 1) + 1) * 6 + (x >> 1) + 1 : -1;
+            y = row64 / 6; x = row64 % 6;
+            d4 = (y < 5 && x < 5) ? (y + 1) * 7 + (x + 1) : -1;
+            y = row64 / 7; x = row64 % 7;
+            d5 = (y < 5 && x < 5) ? y * 5 + x : -1;
+        }
+        auto load_bias = [&](int l, float *b) {
+#pragma unroll
+            for (int c = 0; c < 32; c += 4) {
+                const float4 v = *(const float4 *)(bias + 32 * l + c);
+                b[c] = v.x;
+                b[c + 1] = v.y;
+                b[c + 2] = v.z;
+                b[c + 3] = v.w;
+            }
+        };
+        // bias + ReLU + bf16 of one accumulator row (32 channels) into four
+        // 16-byte blocks at base + (d + cb * next) * 16, and the save record
+        auto put4 = [&](unsigned char *base, int d, int next, const float *a, const float *bl, unsigned char *sv,
+                        int off, int pix) {
+#pragma unroll
+            for (int cb = 0; cb < 4; ++cb) {
+                const uint4 v = relu_pack8(const_cast<float *>(a) + 8 * cb, bl + 8 * cb);
+                *(uint4 *)(base + (long long)(d + cb * next) * 16) = v;
+                if (sv) *(uint4 *)(sv + off + pix * 64 + cb * 16) = v;
+            }
+        };
+        // conv3, conv4 and conv5 are issued by one thread of this group once
+        // the whole group has written their input (named barrier 2): the
+        // chain conv3 -> epilogue -> conv4 -> ... stays inside the group
+        const bool issuer = wb == 0 && lane == 0;
+        const uint64_t dB = sdesc(smem_u32(Wp), 128, 256);
+        const uint64_t dA3 = sdesc(smem_u32(P3), 4 * kPln3 * 16, 128);
+        const uint64_t dA4 = sdesc(smem_u32(P4), 4 * kPln4 * 16, 128);
+        const uint64_t dA5 = sdesc(smem_u32(P5), kPln5 * 16, 128);
+        const uint32_t t345 = tmem + (uint32_t)kColL345;
+        int last = -1;  // the issuer's last commit and its parity, for the exit wait
+        uint32_t last_ph = 0u;
+        bool ok = true;
+        float bl[32], acc[32];
+        for (long long k = 0; k < nk; ++k) {
+            if (group_any(2, kBThreads, !ok || *abort_flag)) {
+                ok = false;
+                break;
+            }
+            const uint32_t ph = (uint32_t)(k & 1);
+            const long long pi = blockIdx.x + k * gridDim.x;
+            unsigned char *sv = P.save ? P.save + pi * (long long)kSaveBytesTotal : nullptr;
+            // ---- conv2 epilogue -> conv3 input planes (which conv3 of
+            // patch k - 1 has read: this group waited for it below), tile by
+            // tile; after the last read the accumulators are free for the
+            // next patch's conv2
+            load_bias(1, bl);
+#pragma unroll 1
+            for (int mt = 0; mt < 3; ++mt) {
+                ok &= warp_wait(&bar[kBarC2 + mt], ph);
+                tc_fence_after();
+                tmem_ld32(tq + (uint32_t)(kColL2 + 32 * mt), acc);
+                if (mt == 2) {
+                    tc_fence_before();
+                    warp_arrive(&bar[kBarC2Free]);
+                }
+                const int m = mt < 2 ? mt * 128 + row : 256 + row64, y = m / 18, x = m - 18 * y;
+                if (y < 17 && x < 17)
+                    put4(P3, (((y & 1) << 1) | (x & 1)) * kPln3 + ((y >> 1) + 1) * 10 + (x >> 1) + 1, 4 * kPln3, acc,
+                         bl, sv, kSvA2, y * 17 + x);
+            }
+            fence_proxy_async_smem();
+            group_sync(2, kBThreads);  // conv3's input is written; conv5 of patch k-1 was read
+            if (issuer) {
+                tc_fence_after();
+                conv_tile(t345, dA3, dB, kPln3, 10, 0, 2, kIdesc);
+                umma_commit(&bar[kBarC3]);
+                last = kBarC3;
+                last_ph = ph;
+            }
+            // ---- conv3 epilogue -> conv4 input planes (the shared conv3..5
+            // accumulator is free once read)
+            load_bias(2, bl);
+            ok &= warp_wait(&bar[kBarC3], ph);
+            tc_fence_after();
+            tmem_ld32(tq + (uint32_t)kColL345, acc);
+            tc_fence_before();
+            if (d3 >= 0) put4(P4, d3, 4 * kPln4, acc, bl, sv, kSvA3, (row / 10) * 9 + row % 10);
+            fence_proxy_async_smem();
+            group_sync(2, kBThreads);
+            if (issuer) {
+                tc_fence_after();
+                conv_tile(t345, dA4, dB, kPln4, 6, 0, 3, kIdesc64);
+                umma_commit(&bar[kBarC4]);
+                last = kBarC4;
+            }
+            // ---- conv4 epilogue -> conv5 input plane (stride 1)
+            load_bias(3, bl);
+            ok &= warp_wait(&bar[kBarC4], ph);
+            tc_fence_after();
+            tmem_ld32(tq + (uint32_t)kColL345, acc);
+            tc_fence_before();
+            if (d4 >= 0) put4(P5, d4, kPln5, acc, bl, sv, kSvA4, (row64 / 6) * 5 + row64 % 6);
+            fence_proxy_async_smem();
+            group_sync(2, kBThreads);
+            if (issuer) {
+                tc_fence_after();
+                conv5_tile(t345, dA5, dB, kIdesc64);
+                umma_commit(&bar[kBarC5]);
+                last = kBarC5;
+            }
+            // ---- conv5 epilogue -> pooling buffer k % kNGap, once the head
+            // has read patch k - kNGap's
+            load_bias(4, bl);
+            ok &= warp_wait(&bar[kBarC5], ph);
+            tc_fence_after();
+            tmem_ld32(tq + (uint32_t)kColL345, acc);
+            tc_fence_before();
+            const int gb = (int)(k % kNGap);
+            if (k >= kNGap) ok &= warp_wait(&bar[kBarGapFree + gb], (uint32_t)(((k - kNGap) / kNGap) & 1));
+            float *gp = gap + gb * (kGapBytes / 4);
+            if (d5 >= 0) {
+#pragma unroll
+                for (int cb = 0; cb < 4; ++cb) {
+                    const uint4 v = relu_pack8(acc + 8 * cb, bl + 8 * cb);
+                    const __nv_bfloat16 *h = (const __nv_bfloat16 *)&v;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) gp[(8 * cb + c) * 25 + d5] = __bfloat162float(h[c]);
+                    if (sv) *(uint4 *)(sv + kSvA5 + d5 * 64 + cb * 16) = v;
+                }
+            }
+            warp_arrive(&bar[kBarGapFull + gb]);
+        }
+        // leave no MMA in flight: the issuer's last commit completes after its earlier MMAs
+        if (issuer && last >= 0) mbar_wait(&bar[last], last_ph);
+        if (!ok) *abort_flag = 1;
+        if (!ok && P.status && issuer) atomicExch(P.status, VS_ERR_TIMEOUT);
     } else if (warp < kMmaWarp) {
         // ================================================================ front
-        const int ft = tid - kEpiThreads, fw = warp - kEpiWarps;
+        const int ft = tid - kFrontWarp0 * 32, fw = warp - kFrontWarp0;
         const float *fc = (const float *)(Wp + kPkFc);
         auto stage_patch = [&](int cy, int cx) {
             const int x0 = floordiv(cx - 32, 8) * 8;
@@ -577,14 +684,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
         bool ok = true;
         uint32_t pphase = 0u;
         bool pending = false;  // a TMA load of a patch is in flight
-        if (ft == 0 && nk > 0) {
+        if (nk > 0) {
             int y, x;
             patch_rc(P, blockIdx.x, y, x);
-            if (patch_inside(P, y, x)) stage_patch(y, x);
+            if (patch_inside(P, y, x)) {
+                pending = true;
+                if (ft == 0) stage_patch(y, x);
+            }
         }
-        // iteration k: front end of patch k (k < nk), head of patch k - 2
-        for (long long k = 0; k < nk + 2; ++k) {
-            if (group_any(2, kFrontThreads, !ok || *abort_flag)) {
+        // iteration k: front end of patch k (k < nk), head of patch k - kNGap
+        for (long long k = 0; k < nk + kNGap; ++k) {
+            if (group_any(3, kFrontThreads, !ok || *abort_flag)) {
                 ok = false;
                 break;
             }
@@ -592,33 +702,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
             if (k < nk) {
                 int cy, cx;
                 patch_rc(P, pi, cy, cx);
-                int16_t pv[kPerFront];
+                // thread (fw, lane) holds, in registers, rows fw + 7 i of the
+                // 65 x 65 window at columns lane, lane + 32 (and 64 for lane 0)
+                int16_t v[kRowsFront][3];
                 if (patch_inside(P, cy, cx)) {
-                    ok &= mbar_wait(&pbar, pphase);
+                    ok &= warp_wait(&pbar, pphase);
                     pphase ^= 1u;
+                    pending = false;
                     const int off = (cx - 32) - floordiv(cx - 32, 8) * 8;
 #pragma unroll
-                    for (int j = 0; j < kPerFront; ++j) {
-                        const int e = ft + j * kFrontThreads, r = e / kPatch, c = e - r * kPatch;
-                        pv[j] = (e < kPatch * kPatch) ? stage[r * kStageW + off + c] : (int16_t)0;
+                    for (int i = 0; i < kRowsFront; ++i) {
+                        const int16_t *row = stage + min(fw + kFrontWarps * i, kPatch - 1) * kStageW + off;
+                        v[i][0] = row[lane];
+                        v[i][1] = row[lane + 32];
+                        v[i][2] = row[lane == 0 ? 64 : 0];
                     }
                 } else {
+                    // a window across the grid edge (or a strided one):
+                    // clamped loads, all in flight together
+                    const int gx0 = min(max(cx + (lane - 32) * P.step, 0), P.W - 1);
+                    const int gx1 = min(max(cx + lane * P.step, 0), P.W - 1);
+                    const int gx2 = min(max(cx + 32 * P.step, 0), P.W - 1);
 #pragma unroll
-                    for (int j = 0; j < kPerFront; ++j) {
-                        const int e = ft + j * kFrontThreads, r = e / kPatch, c = e - r * kPatch;
+                    for (int i = 0; i < kRowsFront; ++i) {
+                        const int r = min(fw + kFrontWarps * i, kPatch - 1);
                         const int gy = min(max(cy + (r - 32) * P.step, 0), P.H - 1);
-                        const int gx = min(max(cx + (c - 32) * P.step, 0), P.W - 1);
-                        pv[j] = (e < kPatch * kPatch) ? P.z[(long long)gy * P.pitch + gx] : (int16_t)0;
+                        const int16_t *row = P.z + (long long)gy * P.pitch;
+                        v[i][0] = row[gx0];
+                        v[i][1] = row[gx1];
+                        v[i][2] = row[gx2];
                     }
                 }
                 int sum = 0;
 #pragma unroll
-                for (int j = 0; j < kPerFront; ++j) sum += pv[j];
+                for (int i = 0; i < kRowsFront; ++i)
+                    if (fw + kFrontWarps * i < kPatch) sum += v[i][0] + v[i][1] + (lane == 0 ? v[i][2] : 0);
                 for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
                 if (lane == 0) s_red[fw] = sum;
-                group_sync(2, kFrontThreads);
-                // the staging tile has been read: prefetch the next patch
-                pending = false;
+                // every front thread has read the staging tile: prefetch the next patch
+                group_sync(3, kFrontThreads);
                 if (k + 1 < nk) {
                     int y, x;
                     patch_rc(P, pi + gridDim.x, y, x);
@@ -631,34 +753,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
 #pragma unroll
                 for (int q = 0; q < kFrontWarps; ++q) tot += s_red[q];
                 const float mean = (float)tot / (float)(kPatch * kPatch);
+                // the conv1 group has read patch k - 1 from the patch buffer
+                if (k > 0) ok &= warp_wait(&bar[kBarPbFree], (uint32_t)((k - 1) & 1));
                 unsigned char *sv = P.save ? P.save + pi * (long long)kSaveBytesTotal : nullptr;
+                __nv_bfloat16 *x0s = sv ? (__nv_bfloat16 *)(sv + kSvInput) : nullptr;
 #pragma unroll
-                for (int j = 0; j < kPerFront; ++j) {
-                    const int e = ft + j * kFrontThreads, r = e / kPatch, c = e - r * kPatch;
-                    if (e < kPatch * kPatch) {
-                        const __nv_bfloat16 x = __float2bfloat16_rn(((float)pv[j] - mean) * 1.0e-3f);
-                        pb[(r + 1) * 67 + (c + 1)] = x;
-                        if (sv) ((__nv_bfloat16 *)(sv + kSvInput))[e] = x;
+                for (int i = 0; i < kRowsFront; ++i) {
+                    const int r = fw + kFrontWarps * i;
+                    if (r < kPatch) {
+                        __nv_bfloat16 *dst = pb + (r + 1) * 67 + 1;
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            const int c = lane + 32 * q;
+                            if (q < 2 || lane == 0) {
+                                const __nv_bfloat16 x = __float2bfloat16_rn(((float)v[i][q] - mean) * 1.0e-3f);
+                                dst[c] = x;
+                                if (x0s) x0s[r * kPatch + c] = x;
+                            }
+                        }
                     }
                 }
+                warp_arrive(&bar[kBarPbRdy]);
             }
-            // ---- head of patch k - 2: global average pool, fc, sigmoid
+            // ---- head of patch k - kNGap: global average pool, fc, sigmoid
             // (fixed summation order), by the first front warp
-            if (k >= 2 && fw == 0) {
-                const long long ph2 = k - 2;
-                bool w = mbar_wait(&bar[kBarGap], (uint32_t)(ph2 & 1));
+            if (k >= kNGap && fw == 0) {
+                const long long hk = k - kNGap;
+                const int gb = (int)(hk % kNGap);
+                bool w = warp_wait(&bar[kBarGapFull + gb], (uint32_t)((hk / kNGap) & 1));
+                const float *gp = gap + gb * (kGapBytes / 4);
                 float gv[25];
 #pragma unroll
-                for (int r = 0; r < 25; ++r) gv[r] = gap[r * 32 + lane];
-                __syncwarp();
-                mbar_arrive(&bar[kBarGapFree]);
+                for (int r = 0; r < 25; ++r) gv[r] = gp[lane * 25 + r];
+                warp_arrive(&bar[kBarGapFree + gb]);
                 float g = 0.f;
 #pragma unroll
                 for (int r = 0; r < 25; ++r) g += gv[r];
                 g *= (1.0f / 25.0f);
                 float t = g * fc[lane];
                 for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                const long long p2 = blockIdx.x + ph2 * gridDim.x;
+                const long long p2 = blockIdx.x + hk * gridDim.x;
                 unsigned char *sv = P.save ? P.save + p2 * (long long)kSaveBytesTotal : nullptr;
                 if (lane == 0) {
                     const float logit = t + fc[32];
@@ -673,38 +807,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
                 if (sv) ((float *)(sv + kSvHead))[lane] = g;
                 ok &= w;
             }
-            if (k < nk) {
-                group_sync(2, kFrontThreads);
-                // im2col of this patch once the previous patch's conv1 has read U
-                if (k > 0) ok &= mbar_wait(&bar[kBarC1 + 2], (uint32_t)((k - 1) & 1));
-#pragma unroll
-                for (int j0 = 0; j0 < kRowsFront; j0 += 3) {
-                    uint32_t w[3][5];
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        const int m = ft + (j0 + j) * kFrontThreads, y = m / 34, x = m % 34;
-                        const unsigned short *src = (const unsigned short *)pb + (2 * y) * 67 + 2 * x;
-                        const bool live = m < 1152 && y < 33 && x < 33;
-                        uint32_t t[9];
-#pragma unroll
-                        for (int q = 0; q < 9; ++q) t[q] = live ? (uint32_t)src[(q / 3) * 67 + (q % 3)] : 0u;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) w[j][q] = t[2 * q] | (t[2 * q + 1] << 16);
-                        w[j][4] = t[8];
-                    }
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        const int m = ft + (j0 + j) * kFrontThreads;
-                        if (m < 1152) {
-                            unsigned char *dst = U + (m / 8) * 256 + (m % 8) * 16;
-                            *(uint4 *)dst = make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
-                            *(uint4 *)(dst + 128) = make_uint4(w[j][4], 0u, 0u, 0u);
-                        }
-                    }
-                }
-                fence_proxy_async_smem();
-                mbar_arrive(&bar[kBarURdy]);
-            }
         }
         // leave no TMA load in flight
         if (pending && ft == 0) mbar_wait(&pbar, pphase);
@@ -712,103 +814,61 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
         if (!ok && P.status && ft == 0) atomicExch(P.status, VS_ERR_TIMEOUT);
     } else {
         // ================================================================ MMA issue
-        const uint32_t sW = smem_u32(Wp), sX = smem_u32(X), sU = smem_u32(U);
-        // descriptor bases; an operand at byte offset o from a base adds o >> 4
-        // to the address field (shared addresses stay below 2^18 bytes)
-        const uint64_t dB = sdesc(sW, 128, 256);
-        const uint64_t dA1 = sdesc(sU, 128, 256);
-        const uint64_t dA2 = sdesc(sX, 4 * kPln2 * 16, 128);
-        const uint64_t dA3 = sdesc(sX + kP3Off, 4 * kPln3 * 16, 128);
-        const uint64_t dA4 = sdesc(sX + kP4Off, 4 * kPln4 * 16, 128);
-        const uint64_t dA5 = sdesc(sX + kP5Off, kPln5 * 16, 128);
-        bool ok = true;
-        int last = -1;  // barrier of the last commit, for the exit wait
-        uint32_t last_ph = 0u;
-        auto wait_all = [&](int b, uint32_t ph) {
-            bool r = true;
-            if (lane == 0) r = mbar_wait_spin(&bar[b], ph);
-            r = __shfl_sync(0xffffffffu, (int)r, 0) != 0;
-            tc_fence_after();
-            return r;
-        };
-        // a 32->32 layer's tile: 9 taps x 2 K-steps reading stride-2 parity planes
-        auto conv_tile = [&](uint64_t dA, int pln, int pitch, int m0, int l, uint32_t col) {
-#pragma unroll
-            for (int i = 0; i < 18; ++i) {
-                const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
-                const int plane = ((ky != 1) << 1) | (kx != 1);
-                const int shift = (ky != 0 ? pitch : 0) + (kx != 0 ? 1 : 0);
-                const uint64_t ad = dA + (uint64_t)((2 * ks * 4 + plane) * pln + m0 + shift);
-                const uint64_t bd = dB + (uint64_t)((pk_bl(l) + (t * 2 + ks) * 1024) >> 4);
-                if (i == 0) umma_c<0>(tmem + col, ad, bd);
-                else umma_c<1>(tmem + col, ad, bd);
-            }
-        };
-        for (long long k = 0; k < nk; ++k) {
-            if (__any_sync(0xffffffffu, !ok || *abort_flag)) break;
-            const uint32_t ph = (uint32_t)(k & 1);
-            // ---- conv1: the im2col tile is written and the previous patch's
-            // conv1 accumulators have been read
-            ok &= wait_all(kBarURdy, ph);
-            if (k > 0) ok &= wait_all(kBarC1Free, ph ^ 1u);
-            if (lane == 0) {
+        // conv1 (9 tiles, A from tensor memory) and conv2 (tile 0 once conv1
+        // tiles 0..5 are written, tiles 1 and 2 once all are) of each patch
+        if (lane == 0) {
+            const uint64_t dB = sdesc(smem_u32(Wp), 128, 256);
+            const uint64_t dA2 = sdesc(smem_u32(X2), 4 * kPln2 * 16, 128);
+            bool ok = true;
+            int last = -1;  // barrier of the last commit and its parity, for the exit wait
+            uint32_t last_ph = 0u;
+            auto wait = [&](int b, uint32_t ph, bool stop_on_abort = true) {
+                uint32_t i = 0;
+                while (!mbar_test(&bar[b], ph)) {
+                    if (++i >= kWaitPolls || (stop_on_abort && (i & 1023u) == 0 && *abort_flag)) return false;
+                }
+                return true;
+            };
+            for (long long k = 0; k < nk && ok; ++k) {
+                const uint32_t ph = (uint32_t)(k & 1);
+                // conv1: its operand is written and the previous patch's
+                // conv1 accumulators have been read
+                ok = wait(kBarARdy, ph) && (k == 0 || wait(kBarC1Free, ph ^ 1u));
+                if (!ok) break;
+                tc_fence_after();
 #pragma unroll
                 for (int mt = 0; mt < 9; ++mt) {
-                    umma_c<0>(tmem + (uint32_t)(32 * mt), dA1 + (uint64_t)(mt * 256), dB + (uint64_t)(kPkB1 >> 4));
+                    umma_t0(tmem + (uint32_t)(32 * mt), tmem + (uint32_t)(kColA1 + 8 * mt), dB + (uint64_t)(kPkB1 >> 4));
                     if (mt % 3 == 2) umma_commit(&bar[kBarC1 + mt / 3]);
                 }
-            }
-            __syncwarp();
-            // ---- conv2: 3 tiles, input pitch 18; the first needs conv1 tiles 0..5
-            ok &= wait_all(kBarP2a, ph);
-            if (lane == 0) {
-                conv_tile(dA2, kPln2, 18, 0, 1, (uint32_t)kColL2);
+                last = kBarC1 + 2;
+                last_ph = ph;
+                // conv2 tile 0: conv1 tiles 0..5 are in the planes and the
+                // previous patch's conv2 accumulators have been read
+                ok = wait(kBarP2a, ph) && (k == 0 || wait(kBarC2Free, ph ^ 1u));
+                if (!ok) break;
+                tc_fence_after();
+                conv_tile(tmem + (uint32_t)kColL2, dA2, dB, kPln2, 18, 0, 1, kIdesc);
                 umma_commit(&bar[kBarC2]);
+                last = kBarC2;
+                // conv2 tiles 1 and 2 (tile 2 holds output pixels 256..305: M = 64)
+                ok = wait(kBarP2, ph);
+                if (!ok) break;
+                tc_fence_after();
+                conv_tile(tmem + (uint32_t)(kColL2 + 32), dA2, dB, kPln2, 18, 128, 1, kIdesc);
+                umma_commit(&bar[kBarC2 + 1]);
+                conv_tile(tmem + (uint32_t)(kColL2 + 64), dA2, dB, kPln2, 18, 256, 1, kIdesc64);
+                umma_commit(&bar[kBarC2 + 2]);
+                last = kBarC2 + 2;
             }
-            __syncwarp();
-            ok &= wait_all(kBarP2, ph);
-            if (lane == 0) {
-                for (int mt = 1; mt < 3; ++mt) {
-                    conv_tile(dA2, kPln2, 18, mt * 128, 1, (uint32_t)(kColL2 + 32 * mt));
-                    umma_commit(&bar[kBarC2 + mt]);
-                }
+            // leave no MMA in flight: the last commit completes after every earlier MMA
+            if (last >= 0) wait(last, last_ph, false);
+            if (!ok) {
+                *abort_flag = 1;
+                if (P.status) atomicExch(P.status, VS_ERR_TIMEOUT);
             }
-            __syncwarp();
-            // ---- conv3: 1 tile, input pitch 10
-            ok &= wait_all(kBarP3, ph);
-            if (lane == 0) {
-                conv_tile(dA3, kPln3, 10, 0, 2, (uint32_t)kColL3);
-                umma_commit(&bar[kBarC3]);
-            }
-            __syncwarp();
-            // ---- conv4: 1 tile, input pitch 6
-            ok &= wait_all(kBarP4, ph);
-            if (lane == 0) {
-                conv_tile(dA4, kPln4, 6, 0, 3, (uint32_t)kColL4);
-                umma_commit(&bar[kBarC4]);
-            }
-            __syncwarp();
-            // ---- conv5 (stride 1): 1 tile, input pitch 7, one plane with a full border
-            ok &= wait_all(kBarP5, ph);
-            if (lane == 0) {
-#pragma unroll
-                for (int i = 0; i < 18; ++i) {
-                    const int t = i >> 1, ks = i & 1, ky = t / 3, kx = t % 3;
-                    const uint64_t ad = dA5 + (uint64_t)((2 * ks) * kPln5 + ky * 7 + kx);
-                    const uint64_t bd = dB + (uint64_t)((pk_bl(4) + (t * 2 + ks) * 1024) >> 4);
-                    if (i == 0) umma_c<0>(tmem + (uint32_t)kColL5, ad, bd);
-                    else umma_c<1>(tmem + (uint32_t)kColL5, ad, bd);
-                }
-                umma_commit(&bar[kBarC5]);
-            }
-            __syncwarp();
-            last = kBarC5;
-            last_ph = ph;
         }
-        // leave no MMA in flight
-        if (last >= 0) wait_all(last, last_ph);
-        if (!ok) *abort_flag = 1;
-        if (!ok && P.status && lane == 0) atomicExch(P.status, VS_ERR_TIMEOUT);
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -818,11 +878,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
 }
 
 // ------------------------------------------------------------------ training
-// Backward pass, layer by layer over a batch (the forward kernel saved every
-// activation).  Each CTA keeps its partial weight gradient in shared memory
-// over the patches it owns and adds it to the global gradient once, so the
-// global atomics do not scale with the batch.  Products take bf16-valued
-// operands (saved activations, bf16-rounded weights, bf16-rounded
+// The backward kernels are in cnn_bwd.cu; the optimiser step is here.
 
 // Adam (Kingma & Ba 2015) on the fp32 master weights; clears the gradients.
 __global__ void k_cnn_adam(float *__restrict__ w, float *__restrict__ g, float *__restrict__ m,

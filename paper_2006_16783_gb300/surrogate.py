@@ -206,16 +206,22 @@ def score_lattice_streamed(g, host, stride, packed, out, patch_step=1, chunks=8,
 
 def _main():
     """python -m paper_2006_16783_gb300.surrogate score-lattice --size N --stride S
-    scores an N x N ridged terrain with randomly initialised weights (for
-    timing and profiling the forward kernel)."""
+    scores an N x N ridged terrain with randomly initialised weights
+    (--patch-step P: patches sampled every P posts);
+    python -m paper_2006_16783_gb300.surrogate train-steps --size N --batch B --reps K
+    runs K training steps (forward with saved activations, backward, Adam)
+    on B random posts of that terrain with labels from vs_exact_vix.  Both
+    are for timing and profiling the network's kernels."""
     import argparse
     import sys
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["score-lattice"])
+    ap.add_argument("cmd", choices=["score-lattice", "train-steps"])
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--stride", type=int, default=16)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--patch-step", type=int, default=1)
     a = ap.parse_args()
     root = __file__.rsplit("/", 2)[0]
     if root not in sys.path:
@@ -225,13 +231,27 @@ def _main():
     _build.build()
     z = T.ridged_multifractal(a.size, a.size, 5, 0, 4000, 0.05, octaves=10, base_wavelength=640, device="cuda")
     g = V.Grid(z.contiguous())
-    packed = V.cnn_pack(init_master(0))
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    if a.cmd == "train-steps":
+        margin = 32 * a.patch_step
+        posts = sample_posts(a.size, a.size, a.batch, margin, 1, "cuda")
+        labels = exact_vix(g, posts, 100, 10, 10)
+        tr = Trainer(init_master(0), batch=a.batch, patch_step=a.patch_step)
+        for i in range(a.reps):
+            if i == a.reps - 1:
+                ev[0].record()
+            tr.train_step(g, posts, labels)
+        ev[1].record()
+        torch.cuda.synchronize()
+        print("batch %d, last step %.3f ms, mean |y - label| %.4f" % (a.batch, ev[0].elapsed_time(ev[1]),
+                                                                     float(tr.loss.item()) / (a.batch * a.reps)))
+        return
+    packed = V.cnn_pack(init_master(0))
     sc = None
     for i in range(a.reps):
         if i == a.reps - 1:
             ev[0].record()
-        sc = V.cnn_score_lattice(g, a.stride, packed)
+        sc = V.cnn_score_lattice(g, a.stride, packed, patch_step=a.patch_step)
     ev[1].record()
     torch.cuda.synchronize()
     print("patches %d, last launch %.3f ms, mean score %.4f" % (sc.numel(), ev[0].elapsed_time(ev[1]),
