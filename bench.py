@@ -1214,6 +1214,7 @@ def main():
             "patch_step": sur.tr.patch_step,
             "patches_per_step": sur.score.numel(), "train_posts": args.train_posts, "epochs": args.epochs,
             "train_loss_last_epoch": sur.train_loss, "label_s": sur.label_s, "train_s": sur.train_s,
+            "train_patches_per_s": args.train_posts * args.epochs / max(sur.train_s, 1e-9),
             "mae_heldout": sur.mae, "mae_sampled_vix": sur.mae_vix, "mae_posts": sur.mae_posts,
             "gpu_launches_per_step": (n_launch if head is sur else o_launch) / args.steps}
     if e2e:

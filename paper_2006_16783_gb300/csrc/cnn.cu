@@ -77,8 +77,12 @@ constexpr int kP3Off = 0, kP3Bytes = (16 * kPln3 + 40) * 16;
 constexpr int kP4Off = kP3Off + kP3Bytes, kP4Bytes = (16 * kPln4 + 104) * 16;
 constexpr int kP5Off = kP4Off + kP4Bytes, kP5Bytes = (4 * kPln5 + 100) * 16;
 constexpr int kP345Bytes = kP5Off + kP5Bytes;
-constexpr int kSmPatch = ((kSmP345 + kP345Bytes) + 127) & ~127;  // 67x67 bf16, zero border
-constexpr int kPatchBytes = ((67 * 67 * 2) + 127) & ~127;
+// the normalised patch, bf16 with a zero border, rows of kPbPitch = 66 elements: row r + 1 holds x0[r][0..64]
+// at 1..65, and its right border is the next row's left border (both zero).  An even pitch of 33 words
+// keeps the conv1 operand's loads free of bank conflicts where a warp's pixels wrap to the next output row.
+constexpr int kPbPitch = 66;
+constexpr int kSmPatch = ((kSmP345 + kP345Bytes) + 127) & ~127;
+constexpr int kPatchBytes = (((67 * kPbPitch + 1) * 2) + 127) & ~127;
 constexpr int kNGap = 3;  // pooling buffers (ring), each [32 channels][25 pixels] fp32
 constexpr int kGapBytes = 25 * 32 * 4;
 constexpr int kSmGap = kSmPatch + kPatchBytes;
@@ -457,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
             unsigned char *sv = P.save ? P.save + pi * (long long)kSaveBytesTotal : nullptr;
             // ---- conv1 operand: output pixel m = 34 y + x takes at K = 3 ky + kx
             // the input x0[2y - 1 + ky][2x - 1 + kx] (the patch buffer has a
-            // zero border: x0[r][c] is pb[(r + 1) * 67 + c + 1]).  The conv1
+            // zero border: x0[r][c] is pb[(r + 1) * kPbPitch + c + 1]).  The conv1
             // MMAs of patch k - 1, which read these columns, have completed:
             // this group waited for them before its epilogue.
             ok &= warp_wait(&bar[kBarPbRdy], ph);
@@ -466,10 +470,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
             for (int mt = 0; mt < 9; ++mt) {
                 const int m = mt * 128 + row, y = m / 34, x = m - 34 * y;
                 const bool live = y < 33 && x < 33;
-                const unsigned short *src = pbu + (2 * y) * 67 + 2 * x;
+                const unsigned short *src = pbu + (2 * y) * kPbPitch + 2 * x;
                 uint32_t t[9];
 #pragma unroll
-                for (int q = 0; q < 9; ++q) t[q] = live ? (uint32_t)src[(q / 3) * 67 + (q % 3)] : 0u;
+                for (int q = 0; q < 9; ++q) t[q] = live ? (uint32_t)src[(q / 3) * kPbPitch + (q % 3)] : 0u;
                 uint32_t w[8];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) w[q] = t[2 * q] | (t[2 * q + 1] << 16);
@@ -761,7 +765,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cnn_forward(const __grid_consta
                 for (int i = 0; i < kRowsFront; ++i) {
                     const int r = fw + kFrontWarps * i;
                     if (r < kPatch) {
-                        __nv_bfloat16 *dst = pb + (r + 1) * 67 + 1;
+                        __nv_bfloat16 *dst = pb + (r + 1) * kPbPitch + 1;
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
                             const int c = lane + 32 * q;
