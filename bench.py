@@ -415,6 +415,18 @@ def time_steps(pipe, steps, dist, dev):
     return ms, [statistics.median(x[i] for x in stage) for i in range(4)]
 
 
+def cnn_flops_per_patch():
+    """Algorithmic FLOPs of one patch of the network: 2 * outputs * 9 * cin
+    per 3x3 convolution (65 -> 33 -> 17 -> 9 -> 5 -> 5 pixels, 1 then 32
+    input channels, 32 output channels; every output counts all 9 taps) and
+    2 * 32 for the fc layer."""
+    n, tot = 65, 0
+    for cin, stride in ((1, 2), (32, 2), (32, 2), (32, 2), (32, 1)):
+        n = (n - 1) // stride + 1
+        tot += 2 * n * n * 32 * cin * 9
+    return tot + 2 * 32
+
+
 def max_over_ranks(value, dist, dev):
     """The slowest replica's figure (every rank gets it); identity without a
     process group."""
@@ -1167,11 +1179,16 @@ def main():
                          "note": "sequential greedy (one CTA or a leader cluster): bound by the "
                                  "latency of its dependent memory rounds and barriers, not by bandwidth"}
     if sur:
-        from oracle import cnn_oracle as C
-        flops = sur.score.numel() * C.flops_per_patch()
+        flops = sur.score.numel() * cnn_flops_per_patch()
         roof["cnn_lattice"] = {"bound": "tensor", "achieved": flops / (s_st[0] * 1e-3) / 1e12,
                                "peak": peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]),
                                "unit": "TFLOP/s", "traffic": None}
+        c = cnt.get("cnn_forward")
+        # DRAM bytes per patch from a capture with the same lattice stride and
+        # patch step (the windows of neighbouring patches overlap in L2)
+        if c and c.get("stride") == sur.stride and c.get("patch_step") == sur.tr.patch_step:
+            roof["cnn_lattice"]["traffic"] = sur.score.numel() * c["dram_bytes_per_unit"]
+            roof["cnn_lattice"]["traffic_source"] = "ncu on %s, scaled by patches" % c["workload"]
     for r in roof.values():
         r["frac"] = r["achieved"] / r["peak"]
     stage_roof = {"vix": "vix", "findmax": "findmax", "viewshed": "viewshed", "site": "site_loop",

@@ -69,3 +69,10 @@ def test_committed_counters_record():
     for k, r in rec["kernels"].items():
         assert abs(r["thread_inst_per_unit"] - r["thread_inst"] / r["units"]) < 1e-9 * r["thread_inst_per_unit"]
         assert r["units"] > 0 and 0 < r["issue_active_pct"] <= 100
+
+
+def test_cnn_flops_match_the_oracle():
+    """The bench's FLOP count per patch (used for the tensor roofline) is the
+    oracle's: 2 * outputs * 9 * cin * 32 per convolution plus the fc layer."""
+    from oracle import cnn_oracle as C
+    assert bench.cnn_flops_per_patch() == C.flops_per_patch() == 8368768
