@@ -260,3 +260,34 @@ def test_cnn_adam_step(V):
         C.adam_step(pw, {"a": gr.astype(np.float64)}, st, lr=1e-2)
     assert np.allclose(tw.cpu().numpy(), pw["a"], atol=1e-5)
     assert float(tg.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 151, 152, 153, 304, 305, 459, 611])
+def test_cnn_forward_any_patch_count(V, n):
+    """The forward keeps two patches in flight per CTA, with a ring of three
+    pooling buffers and per-patch barrier phases, so launches of 1 .. 4
+    patches per CTA (and CTAs with one patch fewer than others) exercise its
+    start and drain.  Every score, and every saved activation, equals the
+    same patch's in one large launch bit for bit (a patch's result does not
+    depend on its neighbours)."""
+    H, W = 300, 280
+    z = T.spectral_fbm(H, W, 0.8, 57, 0, 1800).numpy()
+    g = V.Grid.from_tensor(torch.as_tensor(z), "cuda")
+    from oracle import cnn_oracle as C
+    packed = V.cnn_pack(torch.as_tensor(C.flatten_params(_params(3))).cuda())
+    rng = np.random.default_rng(1000 + n)
+    big = 900
+    cy = rng.integers(0, H, big)
+    cx = rng.integers(0, W, big)
+    cy[::3] = rng.integers(32, H - 33, len(cy[::3]))  # TMA-staged and gathered windows mixed
+    cen = torch.as_tensor(cy * W + cx).cuda()
+    sb = V.cnn_save_bytes()
+    save = torch.zeros(big * sb, dtype=torch.uint8, device="cuda")
+    y = V.cnn_forward(g, cen, packed, save=save)
+    pick = torch.as_tensor(rng.choice(big, n, replace=False)).cuda()
+    save_n = torch.zeros(n * sb, dtype=torch.uint8, device="cuda")
+    y_n = V.cnn_forward(g, cen[pick].contiguous(), packed, save=save_n)
+    assert torch.equal(y_n, y[pick])
+    assert torch.equal(save_n.view(n, sb), save.view(big, sb)[pick])
+    # and without a save record (the inference path)
+    assert torch.equal(V.cnn_forward(g, cen[pick].contiguous(), packed), y[pick])
