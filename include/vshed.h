@@ -84,9 +84,11 @@ uint64_t vs_launch_count(void);
  *     the terrain in global memory (the path every R takes whose halo window
  *     does not fit in shared memory, R above ~280)
  *   VS_TUNE_SITE_CLUSTER: the greedy site loop of vs_site when every gain
- *     fits in one CTA's shared memory: 0 = default (a leader cluster of 8
- *     CTAs when bitmap rows are whole 16-byte vectors, i.e. (2R/32 + 2) % 4 == 0,
- *     else one CTA), 1 = one CTA, 2 / 4 / 8 / 16 = a leader cluster of that
+ *     fits in one CTA's shared memory: 0 = default (when bitmap rows are
+ *     whole 16-byte vectors, i.e. (2R/32 + 2) % 4 == 0, the multi-winner
+ *     leader cluster of 16 CTAs, or of 8 where 16 cannot be scheduled, and
+ *     the single-winner one of 8 CTAs where neither fits; else one CTA),
+ *     1 = one CTA, 2 / 4 / 8 / 16 = a leader cluster of that
  *     many CTAs (the leader keeps the gains and picks each winner, the window
  *     and refresh loads are split over the cluster's SMs).  R is the call's R.
  *     vs_site_batch always uses one CTA per job.
