@@ -48,10 +48,12 @@ __device__ __forceinline__ uint64_t block_max_u64(uint64_t v, uint64_t *red) {
 }
 
 // block blk (row-major over blocks) of one map; the CTA's threads all take part
+constexpr int kFmCols = 2048, kFmRows = 2048;  // block-count tables of the output offset
+
 template <typename V>
 __device__ __forceinline__ void findmax_block(const V *val, int H, int W, int stride, int Ws, int b, int k,
                                               int nbx, int blk, int64_t *out, uint64_t *red,
-                                              long long *s_offp) {
+                                              long long *s_offp, int *s_nx, int *s_ny) {
     long long &s_off = *s_offp;
     const int by = blk / nbx, bx = blk - (blk / nbx) * nbx;
     const long long i0 = ((long long)by * b + stride - 1) / stride;
@@ -61,14 +63,34 @@ __device__ __forceinline__ void findmax_block(const V *val, int H, int W, int st
     const long long j1 = llmin(((long long)(bx + 1) * b + stride - 1) / stride, Ws);
     const long long m = (i1 - i0) * (j1 - j0);
 
-    // output offset: sum of min(k, size) over the blocks before this one
+    // output offset: sum of min(k, size) over the blocks before this one.
+    // Block (qy, qx) holds ny(qy) * nx(qx) lattice posts; with the row and
+    // column counts in shared memory each thread sums one block column over
+    // the rows before this one (plus this row's columns left of this block),
+    // one multiply and min per term.  Grids of more block rows or columns
+    // than the tables hold take a term per block instead.
     {
         long long acc = 0;
-        for (int q = threadIdx.x; q < blk; q += blockDim.x) {
-            const int qy = q / nbx, qx = q - (q / nbx) * nbx;
-            const long long ny = lattice_count((long long)qy * b, llmin(H, (long long)(qy + 1) * b), stride);
-            const long long nx = lattice_count((long long)qx * b, llmin(W, (long long)(qx + 1) * b), stride);
-            acc += llmin(k, ny * nx);
+        if (nbx <= kFmCols && by < kFmRows) {
+            for (int q = threadIdx.x; q < nbx; q += blockDim.x)
+                s_nx[q] = (int)lattice_count((long long)q * b, llmin(W, (long long)(q + 1) * b), stride);
+            for (int q = threadIdx.x; q <= by; q += blockDim.x)
+                s_ny[q] = (int)lattice_count((long long)q * b, llmin(H, (long long)(q + 1) * b), stride);
+            __syncthreads();
+            for (int qx = threadIdx.x; qx < nbx; qx += blockDim.x) {
+                const long long nx = s_nx[qx];
+                long long a = 0;
+                for (int qy = 0; qy < by; ++qy) a += llmin(k, (long long)s_ny[qy] * nx);
+                if (qx < bx) a += llmin(k, (long long)s_ny[by] * nx);
+                acc += a;
+            }
+        } else {
+            for (int q = threadIdx.x; q < blk; q += blockDim.x) {
+                const int qy = q / nbx, qx = q - (q / nbx) * nbx;
+                const long long ny = lattice_count((long long)qy * b, llmin(H, (long long)(qy + 1) * b), stride);
+                const long long nx = lattice_count((long long)qx * b, llmin(W, (long long)(qx + 1) * b), stride);
+                acc += llmin(k, ny * nx);
+            }
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (uint64_t)acc;
@@ -109,7 +131,8 @@ __global__ void __launch_bounds__(kFmThreads) k_findmax(const V *val, int H, int
                                                         int64_t *out) {
     __shared__ uint64_t red[32];
     __shared__ long long s_off;
-    findmax_block<V>(val, H, W, stride, Ws, b, k, nbx, (int)blockIdx.x, out, red, &s_off);
+    __shared__ int s_nx[kFmCols], s_ny[kFmRows];
+    findmax_block<V>(val, H, W, stride, Ws, b, k, nbx, (int)blockIdx.x, out, red, &s_off, s_nx, s_ny);
 }
 
 // Many uint8 maps in one launch: the blocks of every job are numbered job by
@@ -128,10 +151,12 @@ struct FmBatch {
 __global__ void __launch_bounds__(kFmThreads) k_findmax_batch(const __grid_constant__ FmBatch B) {
     __shared__ uint64_t red[32];
     __shared__ long long s_off;
+    __shared__ int s_nx[kFmCols], s_ny[kFmRows];
     int j = 0;
     while (j + 1 < B.njobs && B.job[j + 1].blk0 <= (long long)blockIdx.x) ++j;
     const FmJob &J = B.job[j];
-    findmax_block<uint8_t>(J.val, J.H, J.W, 1, J.W, J.b, J.k, J.nbx, (int)(blockIdx.x - J.blk0), J.out, red, &s_off);
+    findmax_block<uint8_t>(J.val, J.H, J.W, 1, J.W, J.b, J.k, J.nbx, (int)(blockIdx.x - J.blk0), J.out, red, &s_off,
+                           s_nx, s_ny);
 }
 
 // Single pass for uint8 maps and k <= KM: every thread keeps its own KM
