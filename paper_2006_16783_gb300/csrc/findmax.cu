@@ -204,6 +204,13 @@ __global__ void __launch_bounds__(kFmThreads) k_findmax_u8(const uint8_t *__rest
         const uint32_t *words = (const uint32_t *)val;
         for (uint32_t wi = w0 + lane; wi < w1; wi += 32) {
             const uint32_t v4 = __ldg(words + wi);
+            // A thread meets its posts in increasing index order, so once its
+            // list is full a post can enter only with a value above the
+            // list's smallest (an equal value has a higher index, a smaller
+            // key): a word whose largest byte is not above it is skipped.
+            const uint32_t vmax = __vmaxu4(v4, __vmaxu4(v4 >> 8, v4 >> 16)) & 0xFFu;
+            const uint32_t vmax4 = vmax > ((v4 >> 24) & 0xFFu) ? vmax : ((v4 >> 24) & 0xFFu);
+            if (lst[KM - 1] != 0 && vmax4 <= (uint32_t)(lst[KM - 1] >> 32)) continue;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const uint32_t p = wi * 4 + j;
