@@ -119,9 +119,6 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ float bf16_round(float v) {
-    return __bfloat162float(__float2bfloat16_rn(v));
-}
 
 // ------------------------------------------------------------------ packing
 // fp32 master parameters -> bf16 B operands in the K-major core-matrix
