@@ -64,7 +64,10 @@ def test_vix_flat_interior(V):
 
 # ------------------------------------------------------------------ findmax
 @pytest.mark.parametrize("H,W,b,k", [(100, 100, 25, 1), (130, 77, 16, 3), (64, 64, 7, 20),
-                                     (33, 100, 40, 2), (5, 5, 1, 1), (300, 257, 64, 4)])
+                                     (33, 100, 40, 2), (5, 5, 1, 1), (300, 257, 64, 4),
+                                     # rows and blocks on 16-byte boundaries: the 16-post kernel
+                                     (320, 480, 48, 4), (96, 256, 16, 8), (200, 496, 64, 5),
+                                     (70, 1600, 800, 3), (50, 1056, 544, 8)])
 def test_findmax_parity(V, O, H, W, b, k):
     rng = np.random.default_rng(H + W + b + k)
     v = rng.integers(0, 6, (H, W)).astype(np.uint8)   # heavy ties
