@@ -325,8 +325,8 @@ int vs_viewshed_batch(const vs_viewshed_job *jobs, int32_t n_jobs, void *ws, siz
  * popcount(cum) >= ceil(coverage_target * H * W) before a step.
  * *n_chosen (device int32) receives the number chosen, or a negative VS_ERR_*
  * code when the device reports a failure (VS_ERR_TIMEOUT: a bounded wait of
- * the lazy greedy's grid barrier gave up; chosen[] and cum are then
- * incomplete).  Calling again with the returned cum continues the same greedy
+ * the lazy greedy's grid barrier, or of the leader cluster's band compaction
+ * for the next winner, gave up; chosen[] and cum are then incomplete).  Calling again with the returned cum continues the same greedy
  * sequence (checkpoint / resume).
  *
  * bm, cand, n, R describe the candidates exactly as vs_viewshed wrote them.

@@ -1038,17 +1038,21 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_loopq(const Site1Param
 // two best keys of its run of slots and their posts, so warp 0 picks the
 // round's winners with no block barrier (the owner of a winner promotes its
 // second key; a run whose second key is used up is rescanned by the warp).
-// The leader then compacts the winners' bands (slots within 2R rows) into a
-// list of (candidate, winner) pairs whose windows meet.  The workers (ranks
-// 1..Q-1) own window rows r = rank-1 (mod Q-1): on a round's first list they
-// compute every winner's delta rows and OR the winners into C (atomically: two
-// disjoint windows can share a boundary word of C), then every list adds
-// popc(V_c AND delta) over its overlap rows into the leader's sums, which the
-// leader subtracts from the gains.  A list holds at most kMultiList pairs; a
-// round whose pairs do not fit takes several lists.
+// While warp 0 picks, groups of the leader's other warps take each winner as
+// soon as it is accepted and compact its band (slots within 2R rows) into a
+// list of (candidate, winner) pairs whose windows meet.  A list holds at most
+// kMultiList pairs; a round whose pairs do not fit compacts its bands again
+// after the picks, in band order, over as many lists as they need.  The
+// workers (ranks 1..Q-1) own window rows r = rank-1 (mod Q-1): on a round's
+// first list they compute every winner's delta rows and OR the winners into C
+// (atomically: two disjoint windows can share a boundary word of C), then
+// every list adds popc(V_c AND delta) over its overlap rows into the leader's
+// sums, which the leader subtracts from the gains.
 constexpr int kMultiList = 1024;   // (candidate, winner) pairs per list
 constexpr int kMultiMaxL = 64;     // winners per round
 constexpr int kMultiItems = 8;     // band slots per leader thread and pass
+constexpr int kCompactG = 4;       // warps that compact one winner's band during the picks
+constexpr long kMultiSpin = 1L << 22;  // polls of a compacting warp for the next winner (~0.2 s)
 
 struct SiteMParams {
     Site1Params b;
@@ -1097,6 +1101,10 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
     __shared__ int s_blo[kMultiMaxL], s_bpref[kMultiMaxL + 1];
     __shared__ int s_wa[32], s_wb[32];
     __shared__ int s_nL, s_cut;
+    // the round's winners as warp 0 accepts them (count, then a final flag),
+    // the pairs that warps 1..31 compact from their bands meanwhile, and
+    // whether those pairs overflowed a list or a wait gave up
+    __shared__ int s_nacc, s_seldone, s_ntot, s_ovf, s_err;
 
     const uint32_t *sp = P.sp;
     if (rank == 0) {
@@ -1104,6 +1112,7 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
             s_gain[i] = (sp[i] == 0xFFFFFFFFu) ? 0u : P.gain0[P.sorig[i]];
         s_dirty[tid] = 1;
     }
+    if (tid == 0) s_err = 0;
     __syncthreads();
     long long covered = (rank == 0 && P.need >= 0) ? (long long)*P.covered0 : 0;
     int t = 0, L = 0, cursor = 0, NI = 0;
@@ -1146,6 +1155,12 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
                     for (int o = 16; o > 0; o >>= 1) k = u64max(k, __shfl_xor_sync(0xffffffffu, k, o));
                     if (lane == 0) s_wkey[wid] = k;
                 }
+                if (tid == 0) {
+                    s_nacc = 0;
+                    s_seldone = 0;
+                    s_ntot = 0;
+                    s_ovf = 0;
+                }
                 __syncthreads();
                 // ---- warp 0 picks the round's winners.  Lane j holds warp j's best
                 // key as (gain, ~slot) and the coordinates of winners j and j + 32;
@@ -1186,6 +1201,8 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
                                 s_tpost[own] = s_tpost2[own];
                                 s_t2ok[own] = 0;
                             }
+                            __threadfence_block();  // the winner (and its zero gain) before its count
+                            *(volatile int *)&s_nacc = nl + 1;
                         }
                         ++nl;
                         covered += g;
@@ -1211,23 +1228,119 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
                         const uint32_t ll = __reduce_max_sync(0xffffffffu, (uint32_t)(kk >> 32) == hh ? (uint32_t)kk : 0u);
                         if (lane == ow) { khi = hh; klo = ll; }
                     }
-                    if (lane == 0) s_nL = nl;
+                    if (lane == 0) {
+                        s_nL = nl;
+                        __threadfence_block();
+                        *(volatile int *)&s_seldone = 1;
+                    }
+                } else {
+                    // ---- meanwhile groups of kCompactG warps (of warps 1..31) take
+                    // winner j = group (mod groups) as soon as it is accepted: its
+                    // metadata and geometry (into every worker), its band size,
+                    // and the band slots whose windows meet its window appended
+                    // to the list, the band split over the group's warps.  The list's
+                    // order is free: each pair's refresh is added into its own
+                    // sum.  A later winner of the round is more than 2R from
+                    // every earlier one, so it is never a pair of theirs, and an
+                    // accepted winner's gain is 0 before its count is published.
+                    constexpr int kGroups = 31 / kCompactG;
+                    const int grp = (wid - 1) / kCompactG, part = (wid - 1) % kCompactG;
+                    for (int j = grp; grp < kGroups && j < kMultiMaxL; j += kGroups) {
+                        int ready = 0;
+                        if (lane == 0) {  // lane 0 polls; the warp follows its answer
+                            for (long it = 0;; ++it) {
+                                if (*(volatile int *)&s_nacc > j) { ready = 1; break; }
+                                if (*(volatile int *)&s_seldone) {
+                                    ready = *(volatile int *)&s_nacc > j;
+                                    break;
+                                }
+                                if (it > kMultiSpin) {
+                                    s_err = 1;
+                                    break;
+                                }
+                                __nanosleep(32);
+                            }
+                            __threadfence_block();
+                        }
+                        __syncwarp();
+                        if (!__shfl_sync(0xffffffffu, ready, 0)) break;
+                        const int slot = s_wslot[j], wx = s_wx[j], wy = s_wy[j];
+                        const int lo = (int)P.slo[slot], hi = (int)P.shi[slot];
+                        const int wgw0 = floordiv(wx - R, 32);
+                        const int4 wv = make_int4(wx, wy, wgw0, (int)P.sorig[slot]);
+                        if (part == 0) {
+                            if (lane == 0) {
+                                s_win[j] = wv;
+                                s_blo[j] = lo;
+                                s_bpref[j] = hi - lo;
+                            }
+                            if (lane >= 1 && lane < Q) *cl.map_shared_rank(&s_win[j], lane) = wv;
+                        }
+                        for (int i0 = lo + 32 * part; i0 < hi; i0 += 32 * kCompactG * kMultiItems) {
+                            uint32_t ip[kMultiItems], io[kMultiItems];
+                            bool gz[kMultiItems];
+#pragma unroll
+                            for (int q = 0; q < kMultiItems; ++q) {
+                                const int i = i0 + 32 * kCompactG * q + lane;
+                                gz[q] = i >= hi || s_gain[i] == 0u;
+                                ip[q] = i < hi ? sp[i] : 0u;
+                                io[q] = i < hi ? P.sorig[i] : 0u;
+                            }
+#pragma unroll
+                            for (int q = 0; q < kMultiItems; ++q) {
+                                const int i = i0 + 32 * kCompactG * q + lane;
+                                int4 geo = make_int4(0, 0, 0, 0);
+                                bool aff = false;
+                                if (!gz[q]) {
+                                    const int cx = (int)(ip[q] % (uint32_t)W), cy = (int)(ip[q] / (uint32_t)W);
+                                    if (abs(cx - wx) <= 2 * R && abs(cy - wy) <= 2 * R) {
+                                        const int cgw0 = floordiv(cx - R, 32);
+                                        const int ya = max(max(cy, wy) - R, 0), yb = min(min(cy, wy) + R, H - 1);
+                                        const int ga = max(max(cgw0, wgw0), 0), gb = min(min(cgw0, wgw0) + PR - 1, WWc - 1);
+                                        if (ya <= yb && ga <= gb) {
+                                            aff = true;
+                                            const int ra = ya - (wy - R), rb = yb - (wy - R);
+                                            const uint32_t vrow0 = io[q] * (uint32_t)P.words + (uint32_t)((ya - cy + R) * PR);
+                                            geo = make_int4(ra | (rb << 16),
+                                                            (gb - ga + 1) | ((ga - cgw0) << 10) | ((ga - wgw0) << 20),
+                                                            (int)vrow0, j);
+                                        }
+                                    }
+                                }
+                                const unsigned am = __ballot_sync(0xffffffffu, aff);
+                                if (am) {
+                                    int base = 0;
+                                    if (lane == 0) base = atomicAdd(&s_ntot, __popc(am));
+                                    base = __shfl_sync(0xffffffffu, base, 0);
+                                    if (aff) {
+                                        const int li = base + __popc(am & ((1u << lane) - 1u));
+                                        if (li < kMultiList) {
+                                            s_list[li] = i;
+                                            s_sum[li] = 0u;
+                                            for (int r = 1; r < Q; ++r) *cl.map_shared_rank(&s_geo[li], r) = geo;
+                                        } else {
+                                            s_ovf = 1;
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                    }
                 }
                 __syncthreads();
                 L = s_nL;
-                if (L == 0) {
+                if (L == 0 || s_err) {
                     stop = true;
+                } else if (!s_ovf) {
+                    // every pair is in one list
+                    NI = 0;
+                    cursor = 0;
+                    in_round = true;
+                    first = true;
+                    ++n_rounds;
                 } else {
-                    // ---- winner metadata and band sizes
-                    if (tid < L) {
-                        const int slot = s_wslot[tid];
-                        const int lo = (int)P.slo[slot], hi = (int)P.shi[slot];
-                        const int wx = s_wx[tid];
-                        s_win[tid] = make_int4(wx, s_wy[tid], floordiv(wx - R, 32), (int)P.sorig[slot]);
-                        s_blo[tid] = lo;
-                        s_bpref[tid] = hi - lo;
-                    }
-                    __syncthreads();
+                    // too many pairs for one list: the bands are compacted again
+                    // below, in band order, over as many lists as they need
                     if (wid == 0) {  // exclusive prefix of the band sizes (L <= 64)
                         const int a = lane < L ? s_bpref[lane] : 0;
                         const int b = lane + 32 < L ? s_bpref[lane + 32] : 0;
@@ -1239,11 +1352,6 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
                         if (lane + 32 < L) s_bpref[lane + 32] = ib - b;
                         if (lane == 31) s_bpref[L] = ib;
                     }
-                    // the winners' geometry into every worker
-                    for (int e = tid; e < L * Qw; e += kSiteThreads) {
-                        const int j = e % L, q = 1 + e / L;
-                        *cl.map_shared_rank(&s_win[j], q) = s_win[j];
-                    }
                     __syncthreads();
                     NI = s_bpref[L];
                     cursor = 0;
@@ -1254,6 +1362,7 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
             }
             // ---- compaction of band slots [cursor, NI) into the list
             int tot = 0;
+            if (!stop && NI == 0) tot = min(s_ntot, kMultiList);  // the list compacted during the picks
             if (!stop) {
                 while (cursor < NI && tot < kMultiList) {
                     const int chunk = min(NI - cursor, kMultiItems * kSiteThreads);
@@ -1513,7 +1622,7 @@ __global__ void __launch_bounds__(kSiteThreads, 1) k_site_multi(const SiteMParam
         }
     }
     if (rank == 0 && tid == 0) {
-        *P.n_chosen = t;
+        *P.n_chosen = s_err ? VS_ERR_TIMEOUT : t;
         M.stats[0] = n_rounds;
         M.stats[1] = n_lists;
         M.stats[2] = n_rescans;
